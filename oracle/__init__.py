@@ -1,0 +1,7 @@
+"""CPU FP64 oracle for GSE-TDVP1 (Yang & White, arXiv:2005.06104).
+
+TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the CPU
+baseline leg of the benchmark may import this package; the product path (the
+CUDA library and its binding) never does, and shares no code with it.
+"""
+from .gse_tdvp1 import *  # noqa: F401,F403

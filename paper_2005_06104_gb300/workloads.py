@@ -1,0 +1,304 @@
+"""Seeded synthetic inputs for GSE-TDVP1: lattices, Hamiltonian MPOs and MPS.
+
+This module holds no step of the method itself.  It builds the *inputs* the
+method takes (Sec. I: an MPS |psi> and the MPO of H), for the spin-1/2
+Heisenberg lattices of the paper's benchmarks (Sec. II.A, Eq. 11; Fig. 1a) and
+the one-axis-twisting model (Sec. II.B, Eq. 12).  Both the CUDA path (through
+the C-ABI) and the CPU oracle consume these arrays, so neither side can bias
+the other through its inputs.
+
+Conventions shared by every consumer:
+
+* spin basis index 0 = |up> (S^z=+1/2), 1 = |down>;
+* an MPS is a list of complex128 arrays A_i[m_{i-1}, d, m_i] with m_0 = m_N = 1;
+* an MPO is a list of complex128 arrays W_i[w_{i-1}, d, d, w_i] acting as
+  <s|W|s'> (second index = output spin, third = input spin), w_0 = w_N = 1;
+* the MPO is in finite-state ("start/done") form: at every inner bond channel 0
+  means "no operator placed yet" and the last channel means "term complete".
+  The left boundary selects "start" and the right boundary "done".
+"""
+from __future__ import annotations
+
+import numpy as np
+
+D = 2
+SZ = np.array([[0.5, 0.0], [0.0, -0.5]], dtype=np.complex128)
+SP = np.array([[0.0, 1.0], [0.0, 0.0]], dtype=np.complex128)  # |up><down|
+SM = SP.T.copy()
+SX = 0.5 * (SP + SM)
+SY = -0.5j * (SP - SM)
+ID2 = np.eye(2, dtype=np.complex128)
+
+
+# ---------------------------------------------------------------- lattices
+class Lattice:
+    """A set of sites with coordinates, a 1D path order and weighted bonds."""
+
+    def __init__(self, coords, bonds, fields=None, name=""):
+        self.coords = list(coords)            # path index -> (x, y)
+        self.n = len(self.coords)
+        b = {}
+        for i, j, J in bonds:
+            if i == j:
+                raise ValueError("self bond")
+            key = (min(i, j), max(i, j))
+            b[key] = b.get(key, 0.0) + float(J)
+        self.bonds = [(i, j, J) for (i, j), J in sorted(b.items()) if J != 0.0]
+        self.fields = np.zeros(self.n) if fields is None else np.asarray(fields, float)
+        self.name = name
+
+    def index_of(self, x, y):
+        return self.coords.index((x, y))
+
+
+def chain(n, J=1.0, fields=None):
+    """Open chain of n sites, nearest-neighbour couplings J."""
+    return Lattice([(x, 0) for x in range(n)],
+                   [(x, x + 1, J) for x in range(n - 1)], fields, f"chain{n}")
+
+
+def zigzag_ladder(lx, j_leg=1.0, j_rung=1.0):
+    """2 x lx ladder on the zigzag path of Fig. 1a: path index = 2x + y.
+
+    Leg bonds join path sites at distance 2, rung bonds at distance 1.
+    """
+    coords = [(i // 2, i % 2) for i in range(2 * lx)]
+    bonds = []
+    for x in range(lx):
+        for y in range(2):
+            if x + 1 < lx:
+                bonds.append((2 * x + y, 2 * (x + 1) + y, j_leg))
+        bonds.append((2 * x, 2 * x + 1, j_rung))
+    return Lattice(coords, bonds, name=f"ladder2x{lx}")
+
+
+def cylinder_snake(lx, ly=4, J=1.0):
+    """ly x lx cylinder (periodic in y, open in x) on the snake path.
+
+    Column x is walked y = 0..ly-1 when x is even and ly-1..0 when x is odd.
+    """
+    coords = []
+    for x in range(lx):
+        ys = range(ly) if x % 2 == 0 else range(ly - 1, -1, -1)
+        coords += [(x, y) for y in ys]
+    idx = {c: i for i, c in enumerate(coords)}
+    bonds = []
+    for x in range(lx):
+        for y in range(ly):
+            if x + 1 < lx:
+                bonds.append((idx[(x, y)], idx[(x + 1, y)], J))
+            if ly > 2 or y == 0:
+                bonds.append((idx[(x, y)], idx[(x, (y + 1) % ly)], J))
+    return Lattice(coords, bonds, name=f"cyl{ly}x{lx}")
+
+
+# ---------------------------------------------------------------- MPOs
+def _open_sites(lat):
+    """open[c] = sorted sites j <= c-1 (0-based) with a bond partner >= c.
+
+    c runs over cuts 0..n; cut c sits between path sites c-1 and c.
+    """
+    n = lat.n
+    far = [-1] * n
+    for i, j, _ in lat.bonds:
+        far[i] = max(far[i], j)
+    return [[j for j in range(c) if far[j] >= c] for c in range(n + 1)]
+
+
+def heisenberg_mpo(lat):
+    """MPO of H = sum_b J_b S_i.S_j + sum_i h_i S^z_i in start/done form.
+
+    Channels at an inner cut: 0 = start, 1+3k+{0,1,2} = open site k carrying
+    (S^z, S^+, S^-), last = done.  w = 2 + 3 * (number of open sites).
+    """
+    n = lat.n
+    opn = _open_sites(lat)
+    coup = {}
+    for i, j, J in lat.bonds:
+        coup[(i, j)] = J
+
+    def width(c):
+        if c == 0 or c == n:
+            return 1
+        return 2 + 3 * len(opn[c])
+
+    W = []
+    for i in range(n):
+        wl, wr = width(i), width(i + 1)
+        w = np.zeros((wl, D, D, wr), dtype=np.complex128)
+        l_start = 0
+        l_done = wl - 1 if i > 0 else None
+        r_start = 0 if i < n - 1 else None
+        r_done = wr - 1
+        if r_start is not None:
+            w[l_start, :, :, r_start] = ID2
+        w[l_start, :, :, r_done] += lat.fields[i] * SZ
+        if l_done is not None:
+            w[l_done, :, :, r_done] = ID2
+        if i < n - 1 and i in opn[i + 1]:
+            k = opn[i + 1].index(i)
+            for a, op in enumerate((SZ, SP, SM)):
+                w[l_start, :, :, 1 + 3 * k + a] = op
+        if i > 0:
+            for kl, j in enumerate(opn[i]):
+                if i < n - 1 and j in opn[i + 1]:
+                    kr = opn[i + 1].index(j)
+                    for a in range(3):
+                        w[1 + 3 * kl + a, :, :, 1 + 3 * kr + a] = ID2
+                J = coup.get((j, i), 0.0)
+                if J != 0.0:
+                    w[1 + 3 * kl + 0, :, :, r_done] += J * SZ
+                    w[1 + 3 * kl + 1, :, :, r_done] += 0.5 * J * SM
+                    w[1 + 3 * kl + 2, :, :, r_done] += 0.5 * J * SP
+        W.append(w)
+    return W
+
+
+def oat_mpo(n, chi=1.0):
+    """MPO of the one-axis-twisting Hamiltonian chi (S^z_tot)^2 (Eq. 12), w=3.
+
+    (S^z)^2 = sum_i (S^z_i)^2 + 2 sum_{i<j} S^z_i S^z_j; channels start,
+    "one S^z placed", done.
+    """
+    W = []
+    for i in range(n):
+        wl = 1 if i == 0 else 3
+        wr = 1 if i == n - 1 else 3
+        w = np.zeros((wl, D, D, wr), dtype=np.complex128)
+        rd = wr - 1
+        if i < n - 1:
+            w[0, :, :, 0] = ID2
+            w[0, :, :, 1] = 2.0 * chi * SZ
+        w[0, :, :, rd] += chi * SZ @ SZ
+        if i > 0:
+            w[1, :, :, rd] += SZ
+            w[2, :, :, rd] = ID2
+            if i < n - 1:
+                w[1, :, :, 1] = ID2
+        W.append(w)
+    return W
+
+
+def mpo_bond_dims(W):
+    return [W[0].shape[0]] + [w.shape[3] for w in W]
+
+
+# ---------------------------------------------------------------- states
+def product_state(vectors):
+    """MPS of bond dimension 1 from per-site 2-vectors (normalised)."""
+    out = []
+    for v in vectors:
+        v = np.asarray(v, dtype=np.complex128)
+        out.append((v / np.linalg.norm(v)).reshape(1, D, 1))
+    return out
+
+
+def neel_state(lat, flip=None):
+    """Neel product state: site (x, y) up iff x + y even; `flip` = (x, y) to flip."""
+    vecs = []
+    for (x, y) in lat.coords:
+        up = (x + y) % 2 == 0
+        if flip is not None and (x, y) == tuple(flip):
+            up = not up
+        vecs.append([1.0, 0.0] if up else [0.0, 1.0])
+    return product_state(vecs)
+
+
+def random_product_state(n, seed):
+    """Each site cos(t/2)|up> + e^{i p} sin(t/2)|down>, (t, p) uniform on the sphere."""
+    rng = np.random.default_rng(seed)
+    vecs = []
+    for _ in range(n):
+        ct = rng.uniform(-1.0, 1.0)
+        p = rng.uniform(0.0, 2.0 * np.pi)
+        t = np.arccos(ct)
+        vecs.append([np.cos(t / 2), np.exp(1j * p) * np.sin(t / 2)])
+    return product_state(vecs)
+
+
+def x_polarized_state(n):
+    """All spins along +x (Sec. II.B initial state)."""
+    return product_state([[1.0, 1.0]] * n)
+
+
+def full_bond_dims(n, chi):
+    return [min(chi, D ** i, D ** (n - i)) for i in range(n + 1)]
+
+
+def random_mps(n, chi, seed, bond_dims=None):
+    """Dense random complex MPS, entries N(0,1)+iN(0,1), bond dims min(chi, 2^i, 2^(n-i)).
+
+    The tensors are not canonical; the consumer canonicalises.
+    """
+    rng = np.random.default_rng(seed)
+    m = full_bond_dims(n, chi) if bond_dims is None else list(bond_dims)
+    out = []
+    for i in range(n):
+        shape = (m[i], D, m[i + 1])
+        a = rng.standard_normal(shape) + 1j * rng.standard_normal(shape)
+        out.append((a / np.sqrt(np.prod(shape))).astype(np.complex128))
+    return out
+
+
+def mps_bond_dims(mps):
+    return [mps[0].shape[0]] + [a.shape[2] for a in mps]
+
+
+# ---------------------------------------------------------------- workloads
+def lambda_top(lat):
+    """Sum_b J_b / 4: the ferromagnetic energy, the top of the Heisenberg spectrum
+    for J_b >= 0 (used for i*tau = 1/lambda in imaginary time, Sec. I.B)."""
+    return sum(J for _, _, J in lat.bonds) / 4.0
+
+
+def workload(name, seed=None):
+    """Named synthetic workloads (lattice, MPO, initial state, run parameters).
+
+    heis_chain10   : Heisenberg chain L=10, Neel, real time dt=0.1, k=2, chi<=16
+    ladder2x20_rd  : rung-decoupled 2x20 ladder (zigzag), random product state
+                     (seed 1), imaginary time dtau=0.1, k=3, chi<=128
+    ladder2x50     : rung-coupled 2x50 ladder (zigzag), Neel + flip at (25,0),
+                     real time dt=0.1, k=3, chi<=512
+    cyl4x16        : 4x16 cylinder (snake), Neel + flip at (8,0), real time
+                     dt=0.1, k=3, chi<=1024
+    """
+    if name == "heis_chain10":
+        lat = chain(10)
+        return dict(name=name, lattice=lat, mpo=heisenberg_mpo(lat), psi=neel_state(lat),
+                    kind="real", dt=0.1, k=2, tau=0.1, chi_max=16, steps=10,
+                    eps_k=1e-8, eps_m=1e-8, eps=0.0, tol=1e-12)
+    if name == "ladder2x20_rd":
+        lat = zigzag_ladder(20, 1.0, 0.0)
+        lam = lambda_top(lat)
+        return dict(name=name, lattice=lat, mpo=heisenberg_mpo(lat),
+                    psi=random_product_state(lat.n, 1 if seed is None else seed),
+                    kind="imag", dt=0.1, k=3, tau=-1j / lam, chi_max=128, steps=50,
+                    eps_k=1e-12, eps_m=1e-8, eps=1e-10, tol=1e-12)
+    if name == "ladder2x50":
+        lat = zigzag_ladder(50, 1.0, 1.0)
+        return dict(name=name, lattice=lat, mpo=heisenberg_mpo(lat),
+                    psi=neel_state(lat, flip=(25, 0)),
+                    kind="real", dt=0.1, k=3, tau=0.1, chi_max=512, steps=40,
+                    eps_k=1e-8, eps_m=1e-8, eps=0.0, tol=1e-12)
+    if name == "cyl4x16":
+        lat = cylinder_snake(16, 4)
+        return dict(name=name, lattice=lat, mpo=heisenberg_mpo(lat),
+                    psi=neel_state(lat, flip=(8, 0)),
+                    kind="real", dt=0.1, k=3, tau=0.1, chi_max=1024, steps=20,
+                    eps_k=1e-8, eps_m=1e-8, eps=0.0, tol=1e-12)
+    raise KeyError(name)
+
+
+def random_field_chains(n_chains=64, seed=0):
+    """Batch of independent random-field Heisenberg chains (PCG64, seed 0):
+    lengths U{20..60}, fields U[-2,2], chi_max U{32..128}; Neel start."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for _ in range(n_chains):
+        n = int(rng.integers(20, 61))
+        h = rng.uniform(-2.0, 2.0, size=n)
+        chi = int(rng.integers(32, 129))
+        lat = chain(n, 1.0, fields=h)
+        out.append(dict(lattice=lat, mpo=heisenberg_mpo(lat), psi=neel_state(lat),
+                        chi_max=chi, kind="real", dt=0.05, k=2, tau=0.05))
+    return out
