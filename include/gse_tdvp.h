@@ -1,0 +1,207 @@
+/*
+ * gse_tdvp.h -- C ABI of libgsetdvp.so, a GB300 (sm_103a) implementation of the
+ * global-subspace-expanded one-site TDVP (GSE-TDVP1) of Yang & White,
+ * "Time Dependent Variational Principle with Ancillary Krylov Subspace"
+ * (arXiv:2005.06104).
+ *
+ * Conventions (every call):
+ *   - complex numbers are complex128 stored as interleaved (re, im) doubles;
+ *   - an MPS site tensor A_i[m_{i-1}][d][m_i] is row-major, m_0 = m_N = 1
+ *     (the form of Eq. 1);
+ *   - an MPO site tensor W_i[w_{i-1}][d][d][w_i] is row-major and acts as
+ *     <s|W|s'> (second index output spin, third input spin), w_0 = w_N = 1;
+ *   - the MPO is in finite-state ("start/done") form: at every inner bond channel
+ *     0 means "no operator placed yet" and channel w_i - 1 means "term complete";
+ *     the left boundary is "start", the right boundary is "done".  This is what
+ *     lets the library build the MPO of 1 - i tau H from the MPO of H (Sec. I.C
+ *     step 1) with the same bond dimension;
+ *   - sites are numbered 0..N-1; "bond b" joins sites b-1 and b (1 <= b <= N-1);
+ *   - every call returns a tdvp_status; on error the handle keeps the last state
+ *     that completed a call and tdvp_last_error() describes the failure.  No C++
+ *     exception crosses this boundary;
+ *   - "stream" is a cudaStream_t passed as void*; every call is synchronous with
+ *     respect to the host on return (results that land in host memory are valid,
+ *     device outputs are complete).
+ */
+#ifndef GSE_TDVP_H
+#define GSE_TDVP_H
+
+#if defined(__GNUC__)
+#define TDVP_API __attribute__((visibility("default")))
+#else
+#define TDVP_API
+#endif
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  TDVP_OK = 0,
+  TDVP_ERR_INVALID_ARG = 1,       /* null pointer, bad site index, bad option   */
+  TDVP_ERR_SHAPE = 2,             /* inconsistent bond / physical dimensions    */
+  TDVP_ERR_OUT_OF_MEMORY = 3,     /* device allocation failed                   */
+  TDVP_ERR_LANCZOS_NOT_CONVERGED = 4,
+  TDVP_ERR_NONFINITE = 5,         /* NaN or Inf met in a norm or a coefficient  */
+  TDVP_ERR_TIMEOUT = 6,           /* a bounded device wait ran out              */
+  TDVP_ERR_CUDA = 7,              /* a CUDA runtime call failed                 */
+  TDVP_ERR_SVD_NOT_CONVERGED = 8
+} tdvp_status;
+
+typedef enum { TDVP_REAL = 0, TDVP_IMAG = 1 } tdvp_time;
+
+/* Arithmetic of the H_eff / environment contractions. */
+typedef enum {
+  TDVP_PREC_FP64 = 0,   /* FP64 on CUDA cores                                     */
+  TDVP_PREC_TF32X3 = 1  /* tcgen05 kind::tf32, operands split hi+lo, 3 products,
+                           FP32 accumulation in tensor memory                     */
+} tdvp_precision;
+
+typedef struct tdvp_handle tdvp_handle;
+
+typedef struct {
+  int n_sites;                   /* N >= 1                                          */
+  int d;                         /* physical dimension (2 for spin 1/2)             */
+  const int* bond_dims;          /* N + 1 entries, first and last equal 1           */
+  const double* const* sites;    /* N host pointers, site i holds
+                                    2 * m_i * d * m_{i+1} doubles                   */
+} tdvp_mps_desc;
+
+typedef struct {
+  int n_sites;
+  int d;
+  const int* bond_dims;          /* N + 1 MPO bond dims w_i, first and last equal 1 */
+  const double* const* sites;    /* N host pointers, site i holds
+                                    2 * w_i * d * d * w_{i+1} doubles               */
+} tdvp_mpo_desc;
+
+typedef struct {
+  double tau_re, tau_im;   /* Krylov operator 1 - i tau H (Eq. 10).  Real time:
+                              tau = dt; imaginary time: i tau = 1/lambda (Sec. I.B) */
+  double eps_k;            /* cutoff applying 1 - i tau H (Sec. I.B, eps_K)         */
+  double eps_m;            /* cutoff of the mixed density matrix, Eq. 6 (eps_M)     */
+  double eps;              /* cutoff inside the TDVP1 sweep, imaginary time (eps)   */
+  int chi_max;             /* cap on every bond dimension (state and Krylov vectors)*/
+  double lanczos_tol;      /* local exponential error target                        */
+  int lanczos_max;         /* maximum Krylov dimension of the local exponential     */
+  int precision;           /* tdvp_precision used inside tdvp_sweep                 */
+} tdvp_options;
+
+/* Fills `opt` with: tau = 0.1, eps_k = eps_m = 1e-8, eps = 0, chi_max = 1024,
+ * lanczos_tol = 1e-12, lanczos_max = 40, precision = FP64. */
+TDVP_API tdvp_status tdvp_default_options(tdvp_options* opt);
+
+/* Creates a handle.  Copies the host MPS and MPO into device memory that the
+ * library owns (the caller keeps its buffers), brings the MPS to left-canonical
+ * form with its centre at site N-1 (Eq. 1) and uploads the MPO of H.
+ * Errors: INVALID_ARG (null), SHAPE (dims inconsistent), OUT_OF_MEMORY, CUDA. */
+TDVP_API tdvp_status tdvp_create(const tdvp_mps_desc* mps, const tdvp_mpo_desc* mpo,
+                        const tdvp_options* opt, void* stream, tdvp_handle** out);
+
+TDVP_API tdvp_status tdvp_destroy(tdvp_handle* h);
+TDVP_API tdvp_status tdvp_set_options(tdvp_handle* h, const tdvp_options* opt);
+TDVP_API const char* tdvp_last_error(const tdvp_handle* h);
+TDVP_API const char* tdvp_status_string(tdvp_status s);
+
+/* Moves the orthogonality centre to `site` by exact gauge moves (SVDs that keep
+ * every singular value above 1e-14 s_max) and builds the environments L_site and
+ * R_site.  The state is unchanged. */
+TDVP_API tdvp_status tdvp_canonicalize(tdvp_handle* h, int site);
+
+/* GSE steps 1 and 2 (Sec. I.C): builds |psi~_l> = (1 - i tau H)^l |psi>,
+ * l = 1..k-1 (Eq. 10, cutoff eps_k, cap chi_max, each normalised) and extends
+ * the bond bases of |psi> right to left with the state-averaged projected
+ * density matrix of Eqs. 5-7 (cutoff eps_m).  Ends with the centre at site 0.
+ * weights: k-1 host doubles (w_l in rho~ = sum_l w_l C~_l^+ C~_l) or NULL for
+ * all ones.  k = 1 only moves the centre to site 0.  The state is unchanged. */
+TDVP_API tdvp_status tdvp_expand_basis(tdvp_handle* h, int k, const double* weights);
+
+/* GSE step 3 (Sec. I.C): one symmetric one-site TDVP sweep, left to right then
+ * right to left, each with time step dt/2.  kind = TDVP_REAL applies
+ * exp(-i H dt); TDVP_IMAG applies exp(-H dt) and renormalises after every local
+ * exponential, truncating with eps and chi_max.  Starts by moving the centre to
+ * site 0 if needed; ends with the centre at site 0. */
+TDVP_API tdvp_status tdvp_sweep(tdvp_handle* h, double dt, tdvp_time kind);
+
+/* One-site effective Hamiltonian at `site` (the operator whose exponential the
+ * TDVP1 sweep applies, Sec. I.C step 3; cost O(m^3 w d)):
+ *   y[a,s,b] = sum L[a,w,a'] W[w,s,s',v] x[a',s',b'] R[b,v,b']
+ * with the current environments L_site, R_site (call tdvp_canonicalize(site)
+ * first).  x_dev, y_dev: caller-owned DEVICE buffers of m_site * d * m_{site+1}
+ * complex128; they may not overlap.  precision: tdvp_precision. */
+TDVP_API tdvp_status tdvp_heff_apply(tdvp_handle* h, int site, const void* x_dev, void* y_dev,
+                            int precision);
+
+/* Zero-site effective Hamiltonian on bond b (the backward step of TDVP1):
+ *   y[a,b'] = sum L[a,w,a'] x[a',c] R[b',w,c]
+ * with L = environment of sites < b and R = environment of sites >= b; needs
+ * the centre at site b (tdvp_canonicalize(b)).  x_dev, y_dev: DEVICE buffers of
+ * m_b * m_b complex128.  FP64 only. */
+TDVP_API tdvp_status tdvp_keff_apply(tdvp_handle* h, int bond, const void* x_dev, void* y_dev,
+                            int precision);
+
+/* Local exponential by Lanczos (FP64 vectors, full re-orthogonalisation
+ * twice): y = exp(-i delta H_eff) x (REAL) or exp(-delta H_eff) x (IMAG) at
+ * `site` with the current environments.  iters (host, may be NULL) receives the
+ * Krylov dimension used.  Error LANCZOS_NOT_CONVERGED when lanczos_max steps do
+ * not reach lanczos_tol. */
+TDVP_API tdvp_status tdvp_evolve_site(tdvp_handle* h, int site, const void* x_dev, void* y_dev,
+                             double delta, tdvp_time kind, int precision, int* iters);
+
+/* Observables (host outputs). */
+TDVP_API tdvp_status tdvp_energy(tdvp_handle* h, double* e);   /* <C|H_eff C>/<C|C> at the centre */
+TDVP_API tdvp_status tdvp_norm(tdvp_handle* h, double* n);     /* |C| at the centre               */
+/* <psi|op_site|psi>/<psi|psi>; op: host d*d complex128 row-major <s|op|s'>. */
+TDVP_API tdvp_status tdvp_expect_local(tdvp_handle* h, const double* op, int site, double* re_im);
+TDVP_API tdvp_status tdvp_bond_dims(tdvp_handle* h, int* out);  /* N + 1 ints                   */
+TDVP_API tdvp_status tdvp_center(tdvp_handle* h, int* site);
+/* out[0..3]: discarded weight sums of the last call for eps_k, eps_m, eps, and the
+ * number of basis states added by the last extension; out[4]: total Lanczos
+ * iterations of the last sweep; out[5]: Lanczos calls of the last sweep. */
+TDVP_API tdvp_status tdvp_trunc_stats(tdvp_handle* h, double* out6);
+
+/* Copies the state to host buffers the caller allocated from tdvp_bond_dims
+ * (site i: 2 * m_i * d * m_{i+1} doubles). */
+TDVP_API tdvp_status tdvp_get_mps(tdvp_handle* h, double* const* sites_out);
+
+/* ---------------------------------------------------------------------------
+ * Timing of the H_eff applies inside a handle (CUDA events on the handle's
+ * stream).  tdvp_profile(h, 1) starts recording, 0 stops.  tdvp_profile_read
+ * writes out3 = {applies, total milliseconds, total algorithmic flops} since
+ * the last read (8 real flops per complex multiply-add,
+ * 8 [m_l d m_r (m_l w_l + m_r w_r) + m_l m_r nnz(W)] per apply) and resets. */
+TDVP_API tdvp_status tdvp_profile(tdvp_handle* h, int enable);
+TDVP_API tdvp_status tdvp_profile_read(tdvp_handle* h, double* out3);
+
+/* ---------------------------------------------------------------------------
+ * Handle-free contractions of one site on caller buffers (kernel-level entry
+ * points; the same code the handle uses).  Device buffers are caller-owned
+ * complex128 arrays; the MPO site W is a HOST array W[w_l][d][d][w_r].
+ * Scratch comes from a library-wide pool.  Calls are serialised internally.
+ * On error tdvp_contract_last_error() describes the failure. */
+typedef struct { int ml, mr, wl, wr, d; } tdvp_site_dims;
+
+/* y = H_eff x:  y[a,s,b] = sum L[a,w,a'] W[w,s,s',v] x[a',s',b'] R[b,v,b']
+ * L: ml*wl*ml, R: mr*wr*mr, x, y: ml*d*mr (Sec. I.C step 3). */
+TDVP_API tdvp_status tdvp_heff_contract(const tdvp_site_dims* dims, const void* L_dev, const double* W_host,
+                                        const void* R_dev, const void* x_dev, void* y_dev, int precision,
+                                        void* stream);
+/* y[a,c] = sum L[a,w,a'] x[a',b'] R[c,w,b']; L: ml*w*ml, R: mr*w*mr, x, y: ml*mr. */
+TDVP_API tdvp_status tdvp_keff_contract(int ml, int mr, int w, const void* L_dev, const void* R_dev,
+                                        const void* x_dev, void* y_dev, void* stream);
+/* side 0: out[b,v,b'] = sum conj(A[a,s,b]) E[a,w,a'] W[w,s,s',v] A[a',s',b']   (E: ml*wl*ml, out: mr*wr*mr)
+ * side 1: out[a,w,a'] = sum conj(A[a,s,b]) W[w,s,s',v] E[b,v,b'] A[a',s',b']   (E: mr*wr*mr, out: ml*wl*ml) */
+TDVP_API tdvp_status tdvp_env_contract(const tdvp_site_dims* dims, int side, const void* E_dev,
+                                       const double* W_host, const void* A_dev, void* out_dev, void* stream);
+/* y = exp(-i delta H_eff) x (REAL) or exp(-delta H_eff) x (IMAG) by Lanczos with
+ * full re-orthogonalisation twice, error target tol, at most nmax (<= 63) steps. */
+TDVP_API tdvp_status tdvp_expm_contract(const tdvp_site_dims* dims, const void* L_dev, const double* W_host,
+                                        const void* R_dev, const void* x_dev, void* y_dev, double delta,
+                                        tdvp_time kind, int precision, double tol, int nmax, int* iters,
+                                        void* stream);
+TDVP_API const char* tdvp_contract_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* GSE_TDVP_H */

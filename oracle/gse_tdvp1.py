@@ -425,3 +425,17 @@ def gse_tdvp1_step(psi, W, p, stats=None):
                        p.get("weights"))
     return tdvp1_sweep(psi, W, p["dt"], p["kind"], p.get("eps", 0.0), p["chi_max"],
                        p.get("tol", 1e-12), p.get("nmax", 40), stats)
+
+
+# ------------------------------------------------------------ sampled outputs at large sizes
+def heff_apply_entries(L, W, R, A, entries):
+    """Selected entries y[a,s,b] of the H_eff definition, one at a time:
+    y[a,s,b] = sum_{w,s',v} W[w,s,s',v] (L[a,w,:] A[:,s',:] R[b,v,:]^T)."""
+    out = []
+    for a, s, b in entries:
+        acc = 0.0j
+        for t in range(A.shape[1]):
+            M = L[a] @ A[:, t, :] @ R[b].T                  # (w_l, w_r)
+            acc += np.sum(W[:, s, t, :] * M)
+        out.append(acc)
+    return np.array(out)

@@ -1,0 +1,142 @@
+// One-site contractions (FP64 on CUDA cores) and the Lanczos exponential.
+#include <algorithm>
+
+#include "contract.cuh"
+
+namespace {
+const cplx kOne = {1.0, 0.0};
+const cplx kZero = {0.0, 0.0};
+constexpr double kBreakdown = 1e-13;  // Lanczos invariant-subspace threshold
+}  // namespace
+
+double heff_flops(const SiteOp& op) {
+  const double ml = op.ml, mr = op.mr, d = op.d;
+  return 8.0 * (ml * d * mr * (ml * op.wl + mr * op.wr) + ml * mr * (double)op.W->nnz);
+}
+
+void heff_fp64(cudaStream_t st, Scratch& s, const SiteOp& op, const cplx* x, cplx* y) {
+  const int ml = op.ml, mr = op.mr, wl = op.wl, wr = op.wr, d = op.d;
+  s.t1.ensure(s.pool, (size_t)ml * wl * d * mr);
+  s.t2.ensure(s.pool, (size_t)ml * d * wr * mr);
+  // T1[(a,w),(s',b')] = L[(a,w),a'] x[a',(s',b')]
+  zgemm(st, OP_N, OP_N, ml * wl, d * mr, ml, kOne, op.L, ml, x, d * mr, kZero, s.t1.data(), d * mr);
+  // T2[(a,s),(v,b')] = sum W[w,s,s',v] T1[(a,w),(s',b')]
+  wstage_left(st, *op.W, s.t1.data(), s.t2.data(), ml, mr);
+  // y[(a,s),b] = sum_{(v,b')} T2[(a,s),(v,b')] R[b,(v,b')]
+  zgemm(st, OP_N, OP_T, ml * d, mr, wr * mr, kOne, s.t2.data(), (long long)wr * mr, op.R, (long long)wr * mr, kZero,
+        y, mr);
+}
+
+void heff_apply_prec(cudaStream_t st, Scratch& s, const SiteOp& op, const cplx* x, cplx* y, int precision) {
+  if (precision == TDVP_PREC_TF32X3)
+    heff_tf32x3(st, s, op, x, y);
+  else
+    heff_fp64(st, s, op, x, y);
+}
+
+void keff_fp64(cudaStream_t st, Scratch& s, const cplx* L, int ml, const cplx* R, int mr, int w, const cplx* x,
+               cplx* y) {
+  s.t3.ensure(s.pool, (size_t)ml * w * mr);
+  zgemm(st, OP_N, OP_N, ml * w, mr, ml, kOne, L, ml, x, mr, kZero, s.t3.data(), mr);
+  zgemm(st, OP_N, OP_T, ml, mr, w * mr, kOne, s.t3.data(), (long long)w * mr, R, (long long)w * mr, kZero, y, mr);
+}
+
+void env_left_fp64(cudaStream_t st, Scratch& s, const cplx* L, const WSparse& W, const cplx* A, int ml, int mr, int d,
+                   cplx* Lout) {
+  const int wl = W.wl, wr = W.wr;
+  s.t1.ensure(s.pool, (size_t)ml * wl * d * mr);
+  s.t2.ensure(s.pool, (size_t)ml * d * wr * mr);
+  zgemm(st, OP_N, OP_N, ml * wl, d * mr, ml, kOne, L, ml, A, d * mr, kZero, s.t1.data(), d * mr);
+  wstage_left(st, W, s.t1.data(), s.t2.data(), ml, mr);
+  // Lout[b,(v,b')] = sum_{(a,s)} conj(A[(a,s),b]) T2[(a,s),(v,b')]
+  zgemm(st, OP_C, OP_N, mr, wr * mr, ml * d, kOne, A, mr, s.t2.data(), (long long)wr * mr, kZero, Lout,
+        (long long)wr * mr);
+}
+
+void env_right_fp64(cudaStream_t st, Scratch& s, const cplx* R, const WSparse& W, const cplx* B, int ml, int mr, int d,
+                    cplx* Rout) {
+  const int wl = W.wl, wr = W.wr;
+  s.t3.ensure(s.pool, (size_t)d * ml * mr);
+  permute_asb_sab(st, B, s.t3.data(), ml, d, mr);  // Bp[s][a][b]
+  s.t1.ensure(s.pool, (size_t)mr * wr * d * ml);
+  // U1[(b,v),(s',a')] = sum_b' R[(b,v),b'] Bp[(s',a'),b']
+  zgemm(st, OP_N, OP_T, mr * wr, d * ml, mr, kOne, R, mr, s.t3.data(), mr, kZero, s.t1.data(), d * ml);
+  s.t2.ensure(s.pool, (size_t)d * mr * wl * ml);
+  // U2[s][b][w][a'] = sum W[w,s,s',v] U1[b][v][s'][a']
+  wstage_right(st, W, s.t1.data(), s.t2.data(), mr, ml);
+  // Rout[a,(w,a')] = sum_{(s,b)} conj(B[a,(s,b)]) U2[(s,b),(w,a')]
+  zgemm(st, OP_R, OP_N, ml, wl * ml, d * mr, kOne, B, d * mr, s.t2.data(), (long long)wl * ml, kZero, Rout,
+        (long long)wl * ml);
+}
+
+void LanczosWork::init(DevicePool* pool) {
+  c.reset(pool, 64);
+  y.reset(pool, 64);
+  if (!real) TDVP_CUDA(cudaMalloc(&real, sizeof(double) * 256));
+}
+
+void LanczosWork::release() {
+  if (real) cudaFree(real);
+  real = nullptr;
+  V.release();
+  w.release();
+  c.release();
+  y.release();
+}
+
+int lanczos_expm(cudaStream_t st, DevicePool* pool, Blas1& blas, LanczosWork& lw,
+                 const std::function<void(const cplx*, cplx*)>& op, const cplx* x, cplx* out, long long n,
+                 double delta, int kind, double tol, int nmax) {
+  nmax = std::min(std::max(1, nmax), 63);
+  double* alpha = lw.real;
+  double* beta = lw.real + 64;
+  double* nrm2 = lw.real + 130;
+  double* err = lw.real + 132;
+  lw.V.ensure(pool, (size_t)(nmax + 1) * n);
+  lw.w.ensure(pool, (size_t)n);
+  cplx* V = lw.V.data();
+  cplx* wv = lw.w.data();
+  blas.norm2(st, x, n, nrm2);
+  double h_n2 = 0.0;
+  TDVP_CUDA(cudaMemcpyAsync(&h_n2, nrm2, sizeof(double), cudaMemcpyDeviceToHost, st));
+  TDVP_CUDA(cudaStreamSynchronize(st));
+  tdvp_require(std::isfinite(h_n2), TDVP_ERR_NONFINITE, "Lanczos: non-finite start vector");
+  const double beta0 = std::sqrt(h_n2);
+  if (beta0 == 0.0) {
+    TDVP_CUDA(cudaMemcpyAsync(out, x, n * sizeof(cplx), cudaMemcpyDeviceToDevice, st));
+    return 0;
+  }
+  scale_by_inv_sqrt(st, V, x, nrm2, n);
+  int used = 0;
+  double last_err = 0.0;
+  for (int j = 0; j < nmax; ++j) {
+    op(V + (long long)j * n, wv);
+    // alpha_j = Re <v_j, w>; w -= V (V^H w), twice (full re-orthogonalisation)
+    blas.multi_dot(st, V, n, j + 1, wv, n, lw.c.data());
+    copy_real_part(st, lw.c.data(), j, alpha);
+    multi_axpy_sub(st, wv, V, n, j + 1, lw.c.data(), n);
+    blas.multi_dot(st, V, n, j + 1, wv, n, lw.c.data());
+    multi_axpy_sub(st, wv, V, n, j + 1, lw.c.data(), n);
+    blas.norm2(st, wv, n, nrm2);
+    store_beta(st, nrm2, beta + j + 1);
+    tridiag_expv(st, alpha, beta, j + 1, delta, kind, nrm2, lw.y.data(), err);
+    double h_err[2];
+    TDVP_CUDA(cudaMemcpyAsync(h_err, err, sizeof(h_err), cudaMemcpyDeviceToHost, st));
+    TDVP_CUDA(cudaStreamSynchronize(st));
+    tdvp_require(std::isfinite(h_err[0]) && std::isfinite(h_err[1]), TDVP_ERR_NONFINITE,
+                 "Lanczos: non-finite coefficient");
+    last_err = h_err[0];
+    if (h_err[0] <= tol || h_err[1] <= kBreakdown || j + 1 == n) {
+      used = j + 1;
+      break;
+    }
+    if (j + 1 == nmax) break;
+    scale_by_inv_sqrt(st, V + (long long)(j + 1) * n, wv, nrm2, n);
+  }
+  if (used == 0)
+    throw TdvpError(TDVP_ERR_LANCZOS_NOT_CONVERGED,
+                    "Lanczos error estimate " + std::to_string(last_err) + " above tolerance after " +
+                        std::to_string(nmax) + " steps");
+  multi_combine(st, out, V, n, used, lw.y.data(), beta0, n);
+  return used;
+}

@@ -1,0 +1,58 @@
+// Tensor-network contractions of one site (H_eff, K_eff, environment updates)
+// and the Lanczos local exponential, as free functions over device pointers.
+// The engine and the handle-free C-ABI entry points share them.
+#pragma once
+#include <functional>
+
+#include "linalg.cuh"
+#include "tc_gemm.cuh"
+
+// Everything one-site contractions read: environments, MPO site, dimensions.
+struct SiteOp {
+  const cplx* L = nullptr;     // ml x wl x ml
+  const cplx* R = nullptr;     // mr x wr x mr
+  const WSparse* W = nullptr;  // MPO site (sparse lists on device)
+  int ml = 0, mr = 0, wl = 0, wr = 0, d = 2;
+  long long env_key = -1;      // identifies the (L, R) content for operand caching; -1 = never cache
+};
+
+// Work buffers reused across calls (drawn from a pool).
+struct Scratch {
+  DevicePool* pool = nullptr;
+  DArr t1, t2, t3;
+  TcEnvCache tc;
+};
+
+// Algorithmic flop count of one H_eff apply (8 real flops per complex multiply-add):
+// 8 [ml d mr (ml wl + mr wr) + ml mr nnz(W)]
+double heff_flops(const SiteOp& op);
+
+// y[a,s,b] = sum L[a,w,a'] W[w,s,s',v] x[a',s',b'] R[b,v,b']
+void heff_fp64(cudaStream_t st, Scratch& s, const SiteOp& op, const cplx* x, cplx* y);
+void heff_tf32x3(cudaStream_t st, Scratch& s, const SiteOp& op, const cplx* x, cplx* y);
+void heff_apply_prec(cudaStream_t st, Scratch& s, const SiteOp& op, const cplx* x, cplx* y, int precision);
+
+// y[a,c] = sum L[a,w,a'] x[a',b'] R[c,w,b']   (x: ml x mr; L: ml x w x ml; R: mr x w x mr)
+void keff_fp64(cudaStream_t st, Scratch& s, const cplx* L, int ml, const cplx* R, int mr, int w, const cplx* x,
+               cplx* y);
+
+// Lout[b,v,b'] = sum conj(A[a,s,b]) L[a,w,a'] W[w,s,s',v] A[a',s',b']
+void env_left_fp64(cudaStream_t st, Scratch& s, const cplx* L, const WSparse& W, const cplx* A, int ml, int mr,
+                   int d, cplx* Lout);
+// Rout[a,w,a'] = sum conj(B[a,s,b]) W[w,s,s',v] R[b,v,b'] B[a',s',b']
+void env_right_fp64(cudaStream_t st, Scratch& s, const cplx* R, const WSparse& W, const cplx* B, int ml, int mr,
+                    int d, cplx* Rout);
+
+// Lanczos exponential with full re-orthogonalisation applied twice:
+// out = exp(-i delta Op) x (kind 0) or exp(-delta Op) x (kind 1), Op Hermitian.
+// Returns the Krylov dimension used; throws LANCZOS_NOT_CONVERGED when nmax
+// steps do not bring the error estimate below tol.
+struct LanczosWork {
+  DArr V, w, c, y;
+  double* real = nullptr;  // device: alpha[64], beta[65], nrm2, err[2]
+  void init(DevicePool* pool);
+  void release();
+};
+int lanczos_expm(cudaStream_t st, DevicePool* pool, Blas1& blas, LanczosWork& lw,
+                 const std::function<void(const cplx*, cplx*)>& op, const cplx* x, cplx* out, long long n,
+                 double delta, int kind, double tol, int nmax);

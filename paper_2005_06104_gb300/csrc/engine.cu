@@ -1,0 +1,716 @@
+// GSE-TDVP1 engine (Yang & White, arXiv:2005.06104, Sec. I): device-resident
+// MPS, MPO and environments; H_eff / K_eff contractions; Lanczos local
+// exponentials; the symmetric TDVP1 sweep (Sec. I.C step 3); Krylov vectors
+// (1 - i tau H)^l |psi> (Eq. 10, Sec. I.C step 1) and the state-averaged basis
+// extension (Eqs. 3, 5-7, Sec. I.C step 2).
+#include <algorithm>
+#include <cstring>
+
+#include "engine.cuh"
+
+namespace {
+constexpr double kRankRtol = 1e-14;     // "SVD without truncation": keep s > 1e-14 s_max
+constexpr double kClusterRtol = 1e-8;   // never split a cluster of near-equal weights
+constexpr double kEigFloorRtol = 1e-14; // mixed density-matrix eigenvalues <= 1e-14 tr never count
+constexpr double kBreakdown = 1e-13;    // Lanczos invariant-subspace threshold
+const cplx kOne = {1.0, 0.0};
+const cplx kZero = {0.0, 0.0};
+const cplx kMinusOne = {-1.0, 0.0};
+}  // namespace
+
+int keep_count(const std::vector<double>& w, double total, double eps, int cap, double floor_) {
+  int n_cand = 0;
+  while (n_cand < (int)w.size() && w[n_cand] > floor_) ++n_cand;
+  if (n_cand == 0 || cap <= 0) return 0;
+  // minimal n with sum(w[n:n_cand]) <= eps * total
+  std::vector<double> tail(n_cand + 1, 0.0);
+  for (int j = n_cand - 1; j >= 0; --j) tail[j] = tail[j + 1] + w[j];
+  const double limit = eps * total;
+  int n = n_cand;
+  for (int j = 0; j <= n_cand; ++j)
+    if (tail[j] <= limit) {
+      n = j;
+      break;
+    }
+  auto inside = [&](int j) { return j > 0 && j < n_cand && (w[j - 1] - w[j]) <= kClusterRtol * w[j - 1]; };
+  while (inside(n)) ++n;
+  if (n > cap) {
+    n = cap;
+    while (inside(n)) --n;
+  }
+  return n;
+}
+
+namespace {
+// Selection functor for SVDs: numerical rank, then optional cutoff/cap on s^2.
+struct SvdRule {
+  double eps = 0.0;
+  int cap = 1 << 30;
+  double* discarded = nullptr;
+  int operator()(const std::vector<double>& s) const {
+    if (s.empty() || !(s[0] > 0.0)) return 0;
+    std::vector<double> w(s.size());
+    double tot = 0.0;
+    for (size_t i = 0; i < s.size(); ++i) {
+      w[i] = s[i] * s[i];
+      tot += w[i];
+    }
+    const double fl = (kRankRtol * s[0]) * (kRankRtol * s[0]);
+    const int n = keep_count(w, tot, eps, cap, fl);
+    if (discarded) {
+      double d = 0.0;
+      for (size_t i = n; i < w.size(); ++i) d += w[i];
+      *discarded += d / tot;
+    }
+    return n;
+  }
+};
+
+__global__ void k_apply_mpo_site(const cplx* __restrict__ W, const cplx* __restrict__ A, int ml, int wl,
+                                 int d, int mr, int wr, cplx* __restrict__ out) {
+  // out[(a,w), s, (b,v)] = sum_t W[w,s,t,v] A[a,t,b]
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long total = (long long)ml * wl * d * mr * wr;
+  if (e >= total) return;
+  const int v = e % wr;
+  long long r = e / wr;
+  const int b = r % mr;
+  r /= mr;
+  const int s = r % d;
+  r /= d;
+  const int w = r % wl;
+  const int a = r / wl;
+  cplx acc = mkc(0.0, 0.0);
+  for (int t = 0; t < d; ++t)
+    cfma(acc, W[(((long long)w * d + s) * d + t) * wr + v], A[((long long)a * d + t) * mr + b]);
+  out[e] = acc;
+}
+
+__global__ void k_apply_op_site(const cplx* __restrict__ op, const cplx* __restrict__ A, int ml, int d,
+                                int mr, cplx* __restrict__ out) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)ml * d * mr) return;
+  const int b = e % mr;
+  const int s = (e / mr) % d;
+  const long long a = e / ((long long)mr * d);
+  cplx acc = mkc(0.0, 0.0);
+  for (int t = 0; t < d; ++t) cfma(acc, op[s * d + t], A[(a * d + t) * mr + b]);
+  out[e] = acc;
+}
+
+__global__ void k_one(cplx* p) { p[0] = mkc(1.0, 0.0); }
+}  // namespace
+
+// ============================================================================
+// set-up
+// ============================================================================
+void Engine::init(const tdvp_mps_desc* mps, const tdvp_mpo_desc* mpo, const tdvp_options* o,
+                  cudaStream_t s) {
+  tdvp_require(mps && mpo, TDVP_ERR_INVALID_ARG, "null descriptor");
+  tdvp_require(mps->n_sites >= 1 && mps->n_sites == mpo->n_sites, TDVP_ERR_SHAPE,
+               "MPS and MPO lengths differ or are < 1");
+  tdvp_require(mps->d >= 1 && mps->d == mpo->d, TDVP_ERR_SHAPE, "physical dimensions differ");
+  tdvp_require(mps->bond_dims && mps->sites && mpo->bond_dims && mpo->sites, TDVP_ERR_INVALID_ARG,
+               "null arrays in descriptor");
+  N = mps->n_sites;
+  d = mps->d;
+  st = static_cast<cudaStream_t>(s);
+  if (o) opt = *o; else tdvp_default_options(&opt);
+  int dev = 0;
+  TDVP_CUDA(cudaGetDevice(&dev));
+  TDVP_CUDA(cudaDeviceGetAttribute(&sm_count, cudaDevAttrMultiProcessorCount, dev));
+  blas.init(&pool, sm_count);
+  psi.N = N;
+  psi.d = d;
+  psi.m.assign(mps->bond_dims, mps->bond_dims + N + 1);
+  w.assign(mpo->bond_dims, mpo->bond_dims + N + 1);
+  tdvp_require(psi.m[0] == 1 && psi.m[N] == 1, TDVP_ERR_SHAPE, "MPS boundary bond dims must be 1");
+  tdvp_require(w[0] == 1 && w[N] == 1, TDVP_ERR_SHAPE, "MPO boundary bond dims must be 1");
+  for (int i = 0; i <= N; ++i)
+    tdvp_require(psi.m[i] >= 1 && w[i] >= 1, TDVP_ERR_SHAPE, "bond dims must be >= 1");
+  psi.A.resize(N);
+  for (int i = 0; i < N; ++i) {
+    tdvp_require(mps->sites[i] != nullptr, TDVP_ERR_INVALID_ARG, "null MPS site pointer");
+    const size_t n = (size_t)psi.m[i] * d * psi.m[i + 1];
+    psi.A[i].reset(&pool, n);
+    TDVP_CUDA(cudaMemcpyAsync(psi.A[i].data(), mps->sites[i], n * sizeof(cplx), cudaMemcpyHostToDevice, st));
+  }
+  W_host.resize(N);
+  Wsp.resize(N);
+  for (int i = 0; i < N; ++i) {
+    tdvp_require(mpo->sites[i] != nullptr, TDVP_ERR_INVALID_ARG, "null MPO site pointer");
+    const size_t n = (size_t)w[i] * d * d * w[i + 1];
+    W_host[i].resize(n);
+    std::memcpy(W_host[i].data(), mpo->sites[i], n * sizeof(cplx));
+    for (const cplx& x : W_host[i])
+      tdvp_require(std::isfinite(x.x) && std::isfinite(x.y), TDVP_ERR_NONFINITE, "non-finite MPO entry");
+    Wsp[i].build(W_host[i].data(), w[i], w[i + 1], d);
+    Wsp[i].upload();
+  }
+  L.resize(N);
+  R.resize(N);
+  Lok.assign(N, 0);
+  Rok.assign(N, 0);
+  scr.pool = &pool;
+  lw.init(&pool);
+  // left-canonical form with the centre at N-1 (Eq. 1)
+  center = 0;
+  for (int i = 0; i + 1 < N; ++i) move_right(i, 0.0, 1 << 30, false);
+  center = N - 1;
+  sync();
+}
+
+void Engine::release() {
+  for (auto& ws : Wsp) ws.free_device();
+  lw.release();
+  for (auto& p : ev_pairs) {
+    cudaEventDestroy(p.first);
+    cudaEventDestroy(p.second);
+  }
+  for (auto& ev : ev_pool) cudaEventDestroy(ev);
+  ev_pairs.clear();
+  ev_pool.clear();
+}
+
+// ============================================================================
+// environments
+// ============================================================================
+void Engine::invalidate_from_site(int i) {
+  for (int j = i + 1; j < N; ++j) Lok[j] = 0;  // L[j] uses sites < j
+  for (int j = 0; j < i && j < N; ++j) Rok[j] = 0;  // R[j] uses sites > j
+  ++env_epoch;
+}
+
+void Engine::ensure_L(int i) {
+  if (!Lok[0]) {
+    L[0].reset(&pool, 1);
+    k_one<<<1, 1, 0, st>>>(L[0].data());
+    TDVP_CHECK_LAUNCH();
+    Lok[0] = 1;
+  }
+  int j = i;
+  while (!Lok[j]) --j;
+  for (; j < i; ++j) env_left(j);
+}
+
+void Engine::ensure_R(int i) {
+  if (!Rok[N - 1]) {
+    R[N - 1].reset(&pool, 1);
+    k_one<<<1, 1, 0, st>>>(R[N - 1].data());
+    TDVP_CHECK_LAUNCH();
+    Rok[N - 1] = 1;
+  }
+  int j = i;
+  while (!Rok[j]) ++j;
+  for (; j > i; --j) env_right(j);
+}
+
+// L[i+1] from L[i] and A[i]; R[i-1] from R[i] and A[i]
+void Engine::env_left(int i) {
+  const int ml = psi.m[i], mr = psi.m[i + 1];
+  L[i + 1].ensure(&pool, (size_t)mr * w[i + 1] * mr);
+  env_left_fp64(st, scr, L[i].data(), Wsp[i], psi.A[i].data(), ml, mr, d, L[i + 1].data());
+  Lok[i + 1] = 1;
+  ++env_epoch;
+}
+
+void Engine::env_right(int i) {
+  const int ml = psi.m[i], mr = psi.m[i + 1];
+  R[i - 1].ensure(&pool, (size_t)ml * w[i] * ml);
+  env_right_fp64(st, scr, R[i].data(), Wsp[i], psi.A[i].data(), ml, mr, d, R[i - 1].data());
+  Rok[i - 1] = 1;
+  ++env_epoch;
+}
+
+SiteOp Engine::site_op(int i) {
+  SiteOp op;
+  op.L = L[i].data();
+  op.R = R[i].data();
+  op.W = &Wsp[i];
+  op.ml = psi.m[i];
+  op.mr = psi.m[i + 1];
+  op.wl = w[i];
+  op.wr = w[i + 1];
+  op.d = d;
+  op.env_key = ((long long)i << 40) ^ env_epoch;
+  return op;
+}
+
+void Engine::heff(int site, const cplx* x, cplx* y, int precision) {
+  const SiteOp op = site_op(site);
+  if (!profile) {
+    heff_apply_prec(st, scr, op, x, y, precision);
+    return;
+  }
+  cudaEvent_t a, b;
+  if (ev_pool.size() >= 2) {
+    a = ev_pool.back();
+    ev_pool.pop_back();
+    b = ev_pool.back();
+    ev_pool.pop_back();
+  } else {
+    TDVP_CUDA(cudaEventCreate(&a));
+    TDVP_CUDA(cudaEventCreate(&b));
+  }
+  TDVP_CUDA(cudaEventRecord(a, st));
+  heff_apply_prec(st, scr, op, x, y, precision);
+  TDVP_CUDA(cudaEventRecord(b, st));
+  ev_pairs.emplace_back(a, b);
+  prof_flops += heff_flops(op);
+  prof_count += 1;
+}
+
+// ============================================================================
+// gauge moves (SVD; real time keeps s > 1e-14 s_max, imaginary time also cuts)
+// ============================================================================
+void Engine::move_right(int i, double eps, int cap, bool trunc) {
+  const int ml = psi.m[i], mr = psi.m[i + 1], mr2 = psi.m[i + 2];
+  SvdRule rule;
+  if (trunc) {
+    rule.eps = eps;
+    rule.cap = cap;
+    rule.discarded = &disc_eps;
+  }
+  SvdOut sv;
+  svd_jacobi(st, &pool, psi.A[i].data(), ml * d, mr, rule, sv, true, true);
+  const int r = sv.rank;
+  tdvp_require(r >= 1, TDVP_ERR_NONFINITE, "move_right: zero tensor");
+  // C = S Vh (r x mr); A[i+1] <- C A[i+1]
+  DArr C(&pool, (size_t)r * mr);
+  double* d_s = nullptr;
+  TDVP_CUDA(cudaMallocAsync(&d_s, sizeof(double) * r, st));
+  TDVP_CUDA(cudaMemcpyAsync(d_s, sv.s.data(), sizeof(double) * r, cudaMemcpyHostToDevice, st));
+  scale_rows(st, C.data(), sv.Vh.data(), d_s, r, mr);
+  DArr nxt(&pool, (size_t)r * d * mr2);
+  zgemm(st, OP_N, OP_N, r, d * mr2, mr, kOne, C.data(), mr, psi.A[i + 1].data(), d * mr2, kZero, nxt.data(),
+        d * mr2);
+  psi.A[i] = std::move(sv.U);
+  psi.A[i + 1] = std::move(nxt);
+  psi.m[i + 1] = r;
+  TDVP_CUDA(cudaFreeAsync(d_s, st));
+  invalidate_from_site(i);
+  invalidate_from_site(i + 1);
+}
+
+void Engine::move_left(int i, double eps, int cap, bool trunc) {
+  const int ml = psi.m[i], mr = psi.m[i + 1], ml0 = psi.m[i - 1];
+  SvdRule rule;
+  if (trunc) {
+    rule.eps = eps;
+    rule.cap = cap;
+    rule.discarded = &disc_eps;
+  }
+  SvdOut sv;
+  svd_jacobi(st, &pool, psi.A[i].data(), ml, d * mr, rule, sv, true, true);
+  const int r = sv.rank;
+  tdvp_require(r >= 1, TDVP_ERR_NONFINITE, "move_left: zero tensor");
+  DArr C(&pool, (size_t)ml * r);
+  double* d_s = nullptr;
+  TDVP_CUDA(cudaMallocAsync(&d_s, sizeof(double) * r, st));
+  TDVP_CUDA(cudaMemcpyAsync(d_s, sv.s.data(), sizeof(double) * r, cudaMemcpyHostToDevice, st));
+  scale_cols(st, C.data(), sv.U.data(), d_s, ml, r);
+  DArr prv(&pool, (size_t)ml0 * d * r);
+  zgemm(st, OP_N, OP_N, ml0 * d, r, ml, kOne, psi.A[i - 1].data(), ml, C.data(), r, kZero, prv.data(), r);
+  psi.A[i] = std::move(sv.Vh);
+  psi.A[i - 1] = std::move(prv);
+  psi.m[i] = r;
+  TDVP_CUDA(cudaFreeAsync(d_s, st));
+  invalidate_from_site(i);
+  invalidate_from_site(i - 1);
+}
+
+void Engine::canonicalize(int c) {
+  tdvp_require(c >= 0 && c < N, TDVP_ERR_INVALID_ARG, "site out of range");
+  while (center < c) {
+    move_right(center, 0.0, 1 << 30, false);
+    ++center;
+  }
+  while (center > c) {
+    move_left(center, 0.0, 1 << 30, false);
+    --center;
+  }
+  ensure_L(c);
+  ensure_R(c);
+}
+
+// ============================================================================
+// Lanczos exponential (full re-orthogonalisation, applied twice)
+// ============================================================================
+int Engine::lanczos(const std::function<void(const cplx*, cplx*)>& op, const cplx* x, cplx* out,
+                    long long n, double delta, int kind) {
+  const int used = lanczos_expm(st, &pool, blas, lw, op, x, out, n, delta, kind, opt.lanczos_tol, opt.lanczos_max);
+  lanczos_iters += used;
+  lanczos_calls += 1;
+  return used;
+}
+
+// ============================================================================
+// TDVP1 sweep (Sec. I.C step 3): L->R then R->L, each with dt/2
+// ============================================================================
+void Engine::sweep(double dt, int kind) {
+  canonicalize(0);
+  for (int i = 0; i < N; ++i) ensure_R(i);
+  ensure_L(0);
+  const double delta = 0.5 * dt;
+  const bool imag = kind == TDVP_IMAG;
+  const int prec = opt.precision;
+  lanczos_iters = lanczos_calls = 0;
+  disc_eps = 0.0;
+  DArr y;
+  auto normalize = [&](cplx* v, long long n) {
+    blas.norm2(st, v, n, lw.real + 140);
+    scale_by_inv_sqrt(st, v, v, lw.real + 140, n);
+  };
+  auto evolve_site = [&](int i) {
+    const long long n = (long long)psi.m[i] * d * psi.m[i + 1];
+    y.ensure(&pool, n);
+    lanczos([&](const cplx* a, cplx* b) { heff(i, a, b, prec); }, psi.A[i].data(), y.data(), n, delta,
+            kind);
+    if (imag) normalize(y.data(), n);
+    TDVP_CUDA(cudaMemcpyAsync(psi.A[i].data(), y.data(), n * sizeof(cplx), cudaMemcpyDeviceToDevice, st));
+  };
+  for (int i = 0; i < N; ++i) {
+    evolve_site(i);
+    if (i == N - 1) break;
+    const int ml = psi.m[i], mold = psi.m[i + 1], mr2 = psi.m[i + 2];
+    SvdRule rule;
+    if (imag) {
+      rule.eps = opt.eps;
+      rule.cap = opt.chi_max;
+      rule.discarded = &disc_eps;
+    }
+    SvdOut sv;
+    svd_jacobi(st, &pool, psi.A[i].data(), ml * d, mold, rule, sv, true, true);
+    const int r = sv.rank;
+    tdvp_require(r >= 1, TDVP_ERR_NONFINITE, "sweep: zero site tensor");
+    DArr C(&pool, (size_t)r * mold);
+    double* d_s = nullptr;
+    TDVP_CUDA(cudaMallocAsync(&d_s, sizeof(double) * r, st));
+    TDVP_CUDA(cudaMemcpyAsync(d_s, sv.s.data(), sizeof(double) * r, cudaMemcpyHostToDevice, st));
+    scale_rows(st, C.data(), sv.Vh.data(), d_s, r, mold);
+    TDVP_CUDA(cudaFreeAsync(d_s, st));
+    psi.A[i] = std::move(sv.U);
+    psi.m[i + 1] = r;  // L[i+1] is r x w x r, R[i] still mold x w x mold
+    env_left(i);
+    DArr C2(&pool, (size_t)r * mold);
+    const cplx* Lb = L[i + 1].data();
+    const cplx* Rb = R[i].data();
+    const int wb = w[i + 1];
+    lanczos([&](const cplx* a, cplx* b) { keff_fp64(st, scr, Lb, r, Rb, mold, wb, a, b); }, C.data(), C2.data(),
+            (long long)r * mold, -delta, kind);
+    if (imag) normalize(C2.data(), (long long)r * mold);
+    DArr nxt(&pool, (size_t)r * d * mr2);
+    zgemm(st, OP_N, OP_N, r, d * mr2, mold, kOne, C2.data(), mold, psi.A[i + 1].data(), d * mr2, kZero,
+          nxt.data(), d * mr2);
+    psi.A[i + 1] = std::move(nxt);
+    center = i + 1;
+    for (int j = i + 2; j < N; ++j) Lok[j] = 0;
+  }
+  for (int i = N - 1; i >= 0; --i) {
+    evolve_site(i);
+    if (i == 0) break;
+    const int mold = psi.m[i], mr = psi.m[i + 1], ml0 = psi.m[i - 1];
+    SvdRule rule;
+    if (imag) {
+      rule.eps = opt.eps;
+      rule.cap = opt.chi_max;
+      rule.discarded = &disc_eps;
+    }
+    SvdOut sv;
+    svd_jacobi(st, &pool, psi.A[i].data(), mold, d * mr, rule, sv, true, true);
+    const int r = sv.rank;
+    tdvp_require(r >= 1, TDVP_ERR_NONFINITE, "sweep: zero site tensor");
+    DArr C(&pool, (size_t)mold * r);
+    double* d_s = nullptr;
+    TDVP_CUDA(cudaMallocAsync(&d_s, sizeof(double) * r, st));
+    TDVP_CUDA(cudaMemcpyAsync(d_s, sv.s.data(), sizeof(double) * r, cudaMemcpyHostToDevice, st));
+    scale_cols(st, C.data(), sv.U.data(), d_s, mold, r);
+    TDVP_CUDA(cudaFreeAsync(d_s, st));
+    psi.A[i] = std::move(sv.Vh);
+    psi.m[i] = r;
+    env_right(i);  // R[i-1]: r x w x r
+    DArr C2(&pool, (size_t)mold * r);
+    const cplx* Lb = L[i].data();
+    const cplx* Rb = R[i - 1].data();
+    const int wb = w[i];
+    lanczos([&](const cplx* a, cplx* b) { keff_fp64(st, scr, Lb, mold, Rb, r, wb, a, b); }, C.data(), C2.data(),
+            (long long)mold * r, -delta, kind);
+    if (imag) normalize(C2.data(), (long long)mold * r);
+    DArr prv(&pool, (size_t)ml0 * d * r);
+    zgemm(st, OP_N, OP_N, ml0 * d, r, mold, kOne, psi.A[i - 1].data(), mold, C2.data(), r, kZero, prv.data(),
+          r);
+    psi.A[i - 1] = std::move(prv);
+    center = i - 1;
+    for (int j = 0; j < i - 1; ++j) Rok[j] = 0;
+    for (int j = i; j < N; ++j) Lok[j] = 0;
+  }
+  center = 0;
+  for (int j = 1; j < N; ++j) Lok[j] = 0;
+  sync();
+}
+
+// ============================================================================
+// Krylov vectors and basis extension (Sec. I.A-I.C, steps 1-2)
+// ============================================================================
+namespace {
+// MPO of 1 - i tau H with the bond dimension of H's MPO.  In start/done form
+// every term enters the "done" channel exactly once, so scaling the entries
+// W[x, done] (x != done) by -i tau scales each term once; the identity enters
+// as (1/N) 1 on each site's start -> done entry.
+std::vector<cplx> one_minus_itau_h_site(const std::vector<cplx>& W, int i, int N, int wl, int wr, int d,
+                                        double tau_re, double tau_im) {
+  std::vector<cplx> out = W;
+  const cplx c = mkc(tau_im, -tau_re);  // -i tau
+  const int done_r = wr - 1;
+  const int done_l = i > 0 ? wl - 1 : -1;
+  for (int x = 0; x < wl; ++x) {
+    if (x == done_l) continue;
+    for (int s = 0; s < d; ++s)
+      for (int t = 0; t < d; ++t) {
+        cplx& e = out[((x * d + s) * d + t) * wr + done_r];
+        e = cmul(c, e);
+      }
+  }
+  for (int s = 0; s < d; ++s) out[((0 * d + s) * d + s) * wr + done_r].x += 1.0 / N;
+  return out;
+}
+}  // namespace
+
+void Engine::expand_basis(int k, const double* weights) {
+  tdvp_require(k >= 1 && k <= 16, TDVP_ERR_INVALID_ARG, "krylov order k must be in 1..16");
+  disc_k = disc_m = 0.0;
+  added_states = 0;
+  canonicalize(N - 1);  // left-canonical, centre at N-1 (Eq. 1)
+  if (k == 1) {
+    canonicalize(0);
+    return;
+  }
+  std::vector<double> wts(k - 1, 1.0);
+  if (weights)
+    for (int l = 0; l < k - 1; ++l) {
+      tdvp_require(std::isfinite(weights[l]) && weights[l] >= 0.0, TDVP_ERR_INVALID_ARG,
+                   "weights must be finite and >= 0");
+      wts[l] = weights[l];
+    }
+  // ---- step 1: |psi~_l> = (1 - i tau H)^l |psi>, compressed (eps_k, chi_max), normalised
+  std::vector<DArr> Wk(N);
+  for (int i = 0; i < N; ++i) {
+    auto h = one_minus_itau_h_site(W_host[i], i, N, w[i], w[i + 1], d, opt.tau_re, opt.tau_im);
+    Wk[i].reset(&pool, h.size());
+    TDVP_CUDA(cudaMemcpyAsync(Wk[i].data(), h.data(), h.size() * sizeof(cplx), cudaMemcpyHostToDevice, st));
+    TDVP_CUDA(cudaStreamSynchronize(st));
+  }
+  std::vector<MpsDev> phis(k - 1);
+  const MpsDev* prev = &psi;
+  for (int l = 0; l < k - 1; ++l) {
+    MpsDev& ph = phis[l];
+    ph.N = N;
+    ph.d = d;
+    ph.m.resize(N + 1);
+    ph.A.resize(N);
+    for (int i = 0; i <= N; ++i) ph.m[i] = prev->m[i] * w[i];
+    for (int i = 0; i < N; ++i) {
+      const int ml = prev->m[i], mr = prev->m[i + 1];
+      const long long tot = (long long)ml * w[i] * d * mr * w[i + 1];
+      ph.A[i].reset(&pool, tot);
+      k_apply_mpo_site<<<ceil_div(tot, 256), 256, 0, st>>>(Wk[i].data(), prev->A[i].data(), ml, w[i], d, mr,
+                                                           w[i + 1], ph.A[i].data());
+      TDVP_CHECK_LAUNCH();
+    }
+    // right-canonicalise (numerical rank only), then cut left to right
+    for (int i = N - 1; i >= 1; --i) {
+      const int ml = ph.m[i], mr = ph.m[i + 1], ml0 = ph.m[i - 1];
+      SvdOut sv;
+      svd_jacobi(st, &pool, ph.A[i].data(), ml, d * mr, SvdRule{}, sv, true, true);
+      const int r = std::max(1, sv.rank);
+      DArr C(&pool, (size_t)ml * r);
+      double* d_s = nullptr;
+      TDVP_CUDA(cudaMallocAsync(&d_s, sizeof(double) * r, st));
+      TDVP_CUDA(cudaMemcpyAsync(d_s, sv.s.data(), sizeof(double) * r, cudaMemcpyHostToDevice, st));
+      scale_cols(st, C.data(), sv.U.data(), d_s, ml, r);
+      TDVP_CUDA(cudaFreeAsync(d_s, st));
+      DArr prv(&pool, (size_t)ml0 * d * r);
+      zgemm(st, OP_N, OP_N, ml0 * d, r, ml, kOne, ph.A[i - 1].data(), ml, C.data(), r, kZero, prv.data(), r);
+      ph.A[i] = std::move(sv.Vh);
+      ph.A[i - 1] = std::move(prv);
+      ph.m[i] = r;
+    }
+    for (int i = 0; i + 1 < N; ++i) {
+      const int ml = ph.m[i], mr = ph.m[i + 1], mr2 = ph.m[i + 2];
+      SvdRule rule;
+      rule.eps = opt.eps_k;
+      rule.cap = opt.chi_max;
+      rule.discarded = &disc_k;
+      SvdOut sv;
+      svd_jacobi(st, &pool, ph.A[i].data(), ml * d, mr, rule, sv, true, true);
+      const int r = std::max(1, sv.rank);
+      DArr C(&pool, (size_t)r * mr);
+      double* d_s = nullptr;
+      TDVP_CUDA(cudaMallocAsync(&d_s, sizeof(double) * r, st));
+      TDVP_CUDA(cudaMemcpyAsync(d_s, sv.s.data(), sizeof(double) * r, cudaMemcpyHostToDevice, st));
+      scale_rows(st, C.data(), sv.Vh.data(), d_s, r, mr);
+      TDVP_CUDA(cudaFreeAsync(d_s, st));
+      DArr nxt(&pool, (size_t)r * d * mr2);
+      zgemm(st, OP_N, OP_N, r, d * mr2, mr, kOne, C.data(), mr, ph.A[i + 1].data(), d * mr2, kZero, nxt.data(),
+            d * mr2);
+      ph.A[i] = std::move(sv.U);
+      ph.A[i + 1] = std::move(nxt);
+      ph.m[i + 1] = r;
+    }
+    {
+      const long long n = (long long)ph.m[N - 1] * d;
+      blas.norm2(st, ph.A[N - 1].data(), n, lw.real + 150);
+      scale_by_inv_sqrt(st, ph.A[N - 1].data(), ph.A[N - 1].data(), lw.real + 150, n);
+    }
+    prev = &ph;
+  }
+  // ---- step 2: basis extension, right to left (Eqs. 3, 5-7)
+  const int nk = k - 1;
+  for (int i = N - 1; i >= 1; --i) {
+    const int ml = psi.m[i], mp = psi.m[i + 1], cols = d * mp, ml0 = psi.m[i - 1];
+    const cplx* X = psi.A[i].data();
+    SvdOut sv;
+    svd_jacobi(st, &pool, X, ml, cols, SvdRule{}, sv, false, true);  // C = U S B, rank-revealing
+    const int r = sv.rank;
+    tdvp_require(r >= 1, TDVP_ERR_NONFINITE, "extension: zero centre tensor");
+    int nb = 0;
+    DArr Bbar;
+    if (r < cols) {
+      // Y = [sqrt(w_1) C~_1; ...]  (sum m~ x cols); tr rho~ = |Y|_F^2
+      int rows = 0;
+      for (int l = 0; l < nk; ++l) rows += phis[l].m[i];
+      DArr Y(&pool, (size_t)rows * cols);
+      int off = 0;
+      for (int l = 0; l < nk; ++l) {
+        const int ml_l = phis[l].m[i];
+        scale_host(st, Y.data() + (long long)off * cols, phis[l].A[i].data(), mkc(std::sqrt(wts[l]), 0.0),
+                   (long long)ml_l * cols);
+        off += ml_l;
+      }
+      blas.norm2(st, Y.data(), (long long)rows * cols, lw.real + 151);
+      double tr = 0.0;
+      TDVP_CUDA(cudaMemcpyAsync(&tr, lw.real + 151, sizeof(double), cudaMemcpyDeviceToHost, st));
+      TDVP_CUDA(cudaStreamSynchronize(st));
+      // Y P = Y - (Y B^H) B : rho_bar = (Y P)^H (Y P) = P rho~ P  (Eq. 6)
+      DArr G(&pool, (size_t)rows * r);
+      for (int pass = 0; pass < 2; ++pass) {
+        zgemm(st, OP_N, OP_C, rows, r, cols, kOne, Y.data(), cols, sv.Vh.data(), cols, kZero, G.data(), r);
+        zgemm(st, OP_N, OP_N, rows, cols, r, kMinusOne, G.data(), r, sv.Vh.data(), cols, kOne, Y.data(), cols);
+      }
+      int cap = cols - r;
+      cap = std::min(cap, opt.chi_max - r);
+      if (cap > 0 && tr > 0.0) {
+        const double eps_m = opt.eps_m;
+        double* disc = &disc_m;
+        auto rule = [tr, eps_m, cap, disc](const std::vector<double>& s) -> int {
+          std::vector<double> ev(s.size());
+          for (size_t q = 0; q < s.size(); ++q) ev[q] = s[q] * s[q];
+          const int n = keep_count(ev, tr, eps_m, cap, kEigFloorRtol * tr);
+          double dsum = 0.0;
+          for (size_t q = n; q < ev.size(); ++q) dsum += ev[q];
+          *disc += dsum / tr;
+          return n;
+        };
+        SvdOut sy;
+        svd_jacobi(st, &pool, Y.data(), rows, cols, rule, sy, false, true);
+        nb = sy.rank;
+        if (nb > 0) {
+          // enforce B_bar B^H = 0 to rounding: project off range(B) twice, re-orthonormalise
+          DArr Gb(&pool, (size_t)nb * r);
+          for (int pass = 0; pass < 2; ++pass) {
+            zgemm(st, OP_N, OP_C, nb, r, cols, kOne, sy.Vh.data(), cols, sv.Vh.data(), cols, kZero, Gb.data(), r);
+            zgemm(st, OP_N, OP_N, nb, cols, r, kMinusOne, Gb.data(), r, sv.Vh.data(), cols, kOne, sy.Vh.data(),
+                  cols);
+          }
+          SvdOut so;
+          struct KeepAll {
+            int operator()(const std::vector<double>& s) const { return (int)s.size(); }
+          };
+          svd_jacobi(st, &pool, sy.Vh.data(), nb, cols, KeepAll{}, so, false, true);
+          Bbar = std::move(so.Vh);
+          nb = so.rank;
+        }
+      }
+    }
+    added_states += nb;
+    const int mnew = r + nb;
+    DArr Bp(&pool, (size_t)mnew * cols);
+    TDVP_CUDA(cudaMemcpyAsync(Bp.data(), sv.Vh.data(), (size_t)r * cols * sizeof(cplx), cudaMemcpyDeviceToDevice,
+                              st));
+    if (nb > 0)
+      TDVP_CUDA(cudaMemcpyAsync(Bp.data() + (long long)r * cols, Bbar.data(), (size_t)nb * cols * sizeof(cplx),
+                                cudaMemcpyDeviceToDevice, st));
+    // centres move by Eq. 3: C_{i-1} = A_{i-1} (C_i B'^H), likewise for every psi~_l
+    DArr G(&pool, (size_t)ml * mnew);
+    zgemm(st, OP_N, OP_C, ml, mnew, cols, kOne, X, cols, Bp.data(), cols, kZero, G.data(), mnew);
+    DArr prv(&pool, (size_t)ml0 * d * mnew);
+    zgemm(st, OP_N, OP_N, ml0 * d, mnew, ml, kOne, psi.A[i - 1].data(), ml, G.data(), mnew, kZero, prv.data(),
+          mnew);
+    for (int l = 0; l < nk; ++l) {
+      MpsDev& ph = phis[l];
+      const int mlp = ph.m[i], mlp0 = ph.m[i - 1];
+      DArr Gl(&pool, (size_t)mlp * mnew);
+      zgemm(st, OP_N, OP_C, mlp, mnew, cols, kOne, ph.A[i].data(), cols, Bp.data(), cols, kZero, Gl.data(), mnew);
+      DArr pp(&pool, (size_t)mlp0 * d * mnew);
+      zgemm(st, OP_N, OP_N, mlp0 * d, mnew, mlp, kOne, ph.A[i - 1].data(), mlp, Gl.data(), mnew, kZero, pp.data(),
+            mnew);
+      ph.A[i - 1] = std::move(pp);
+      ph.A[i].release();
+      ph.m[i] = mnew;
+    }
+    psi.A[i] = std::move(Bp);
+    psi.A[i - 1] = std::move(prv);
+    psi.m[i] = mnew;
+  }
+  center = 0;
+  for (int j = 0; j < N; ++j) Lok[j] = Rok[j] = 0;
+  sync();
+}
+
+// ============================================================================
+// observables
+// ============================================================================
+double Engine::energy() {
+  const int c = center;
+  ensure_L(c);
+  ensure_R(c);
+  const long long n = (long long)psi.m[c] * d * psi.m[c + 1];
+  DArr y(&pool, n);
+  heff(c, psi.A[c].data(), y.data(), TDVP_PREC_FP64);
+  blas.multi_dot(st, psi.A[c].data(), n, 1, y.data(), n, lw.c.data());
+  blas.norm2(st, psi.A[c].data(), n, lw.real + 152);
+  cplx e;
+  double nn;
+  TDVP_CUDA(cudaMemcpyAsync(&e, lw.c.data(), sizeof(cplx), cudaMemcpyDeviceToHost, st));
+  TDVP_CUDA(cudaMemcpyAsync(&nn, lw.real + 152, sizeof(double), cudaMemcpyDeviceToHost, st));
+  sync();
+  return e.x / nn;
+}
+
+double Engine::norm() {
+  const int c = center;
+  const long long n = (long long)psi.m[c] * d * psi.m[c + 1];
+  blas.norm2(st, psi.A[c].data(), n, lw.real + 153);
+  double nn;
+  TDVP_CUDA(cudaMemcpyAsync(&nn, lw.real + 153, sizeof(double), cudaMemcpyDeviceToHost, st));
+  sync();
+  return std::sqrt(nn);
+}
+
+cplx Engine::expect_local(const double* op, int site) {
+  canonicalize(site);
+  const long long n = (long long)psi.m[site] * d * psi.m[site + 1];
+  DArr o(&pool, (size_t)d * d), y(&pool, n);
+  TDVP_CUDA(cudaMemcpyAsync(o.data(), op, sizeof(cplx) * d * d, cudaMemcpyHostToDevice, st));
+  k_apply_op_site<<<ceil_div(n, 256), 256, 0, st>>>(o.data(), psi.A[site].data(), psi.m[site], d,
+                                                      psi.m[site + 1], y.data());
+  TDVP_CHECK_LAUNCH();
+  blas.multi_dot(st, psi.A[site].data(), n, 1, y.data(), n, lw.c.data());
+  blas.norm2(st, psi.A[site].data(), n, lw.real + 154);
+  cplx e;
+  double nn;
+  TDVP_CUDA(cudaMemcpyAsync(&e, lw.c.data(), sizeof(cplx), cudaMemcpyDeviceToHost, st));
+  TDVP_CUDA(cudaMemcpyAsync(&nn, lw.real + 154, sizeof(double), cudaMemcpyDeviceToHost, st));
+  sync();
+  return mkc(e.x / nn, e.y / nn);
+}

@@ -1,0 +1,78 @@
+// Device-resident GSE-TDVP1 engine: state, environments and the algorithm
+// steps of Sec. I (basis extension, Krylov vectors, TDVP1 sweep).
+#pragma once
+#include <functional>
+
+#include "contract.cuh"
+
+// Number of leading (descending) weights kept under the truncation rule:
+// relative discarded weight <= eps * total, values <= floor never kept, a cut
+// never splits a cluster of values within relative 1e-8 (grow to the cluster's
+// end; if that breaks the cap, shrink to its start).
+int keep_count(const std::vector<double>& w_desc, double total, double eps, int cap, double floor_);
+
+struct MpsDev {
+  int N = 0, d = 2;
+  std::vector<int> m;        // N + 1 bond dims
+  std::vector<DArr> A;       // A[i]: m[i] x d x m[i+1]
+};
+
+struct Engine {
+  // problem
+  int N = 0, d = 2;
+  std::vector<int> w;                    // MPO bond dims
+  std::vector<std::vector<cplx>> W_host; // MPO of H (host copy)
+  std::vector<WSparse> Wsp;              // MPO of H (device sparse)
+  MpsDev psi;
+  int center = 0;
+  tdvp_options opt{};
+  cudaStream_t st = nullptr;
+  DevicePool pool;
+  Blas1 blas;
+  int sm_count = 148;
+  // environments: L[i] = sites < i (m_i x w_i x m_i); R[i] = sites > i (m_{i+1} x w_{i+1} x m_{i+1})
+  std::vector<DArr> L, R;
+  std::vector<char> Lok, Rok;
+  // contraction scratch and Lanczos work space
+  Scratch scr;
+  LanczosWork lw;
+  long long env_epoch = 0;  // bumped whenever an environment is rebuilt or dropped
+  // optional timing of the H_eff applies (CUDA events on the engine stream)
+  bool profile = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pairs;
+  double prof_flops = 0.0;
+  long long prof_count = 0;
+  // statistics of the last calls
+  double disc_k = 0, disc_m = 0, disc_eps = 0;
+  int added_states = 0;
+  long long lanczos_iters = 0, lanczos_calls = 0;
+
+  void init(const tdvp_mps_desc* mps, const tdvp_mpo_desc* mpo, const tdvp_options* o, cudaStream_t s);
+  void release();
+
+  // environments
+  void ensure_L(int i);
+  void ensure_R(int i);
+  void invalidate_from_site(int i);  // A[i] changed
+  // contractions (FP64 unless precision says otherwise)
+  void heff(int site, const cplx* x, cplx* y, int precision);
+  SiteOp site_op(int site);
+  void env_left(int i);   // L[i+1] from L[i], A[i]
+  void env_right(int i);  // R[i-1] from R[i], A[i]
+  // gauge moves
+  void move_right(int i, double eps, int cap, bool imag_trunc);
+  void move_left(int i, double eps, int cap, bool imag_trunc);
+  void canonicalize(int c);
+  // Lanczos exponential: out = exp(-i delta Op) x (kind 0) or exp(-delta Op) x (kind 1)
+  int lanczos(const std::function<void(const cplx*, cplx*)>& op, const cplx* x, cplx* out,
+              long long n, double delta, int kind);
+  // algorithm steps
+  void sweep(double dt, int kind);
+  void expand_basis(int k, const double* weights);
+  // observables
+  double energy();
+  double norm();
+  cplx expect_local(const double* op, int site);
+  void sync() { TDVP_CUDA(cudaStreamSynchronize(st)); }
+};

@@ -1,0 +1,1045 @@
+// FP64 complex kernels of the GSE-TDVP1 path: GEMM, MPO-tensor contraction
+// stages, Krylov-vector BLAS-1, the small tridiagonal exponential of the
+// Lanczos exponentiator and a one-sided Jacobi SVD.
+#include <algorithm>
+#include <numeric>
+
+#include "linalg.cuh"
+
+// ============================================================================
+// ZGEMM (CUDA cores).  64x64 output tile, 8-deep K slices, 256 threads, each
+// thread accumulates a 4x4 block (rows ty+16i, cols tx+16j).
+// ============================================================================
+namespace {
+constexpr int GB_M = 64, GB_N = 64, GB_K = 8;
+
+template <int OPA, int OPB>
+__global__ void __launch_bounds__(256)
+    k_zgemm(int M, int N, int K, cplx alpha, const cplx* __restrict__ A, long long lda,
+            long long sA, const cplx* __restrict__ B, long long ldb, long long sB, cplx beta,
+            cplx* __restrict__ C, long long ldc, long long sC) {
+  __shared__ cplx As[GB_K][GB_M + 1];
+  __shared__ cplx Bs[GB_K][GB_N + 1];
+  const long long bz = blockIdx.z;
+  A += bz * sA;
+  B += bz * sB;
+  C += bz * sC;
+  const int m0 = blockIdx.y * GB_M, n0 = blockIdx.x * GB_N;
+  const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
+  cplx acc[4][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j) acc[i][j] = mkc(0.0, 0.0);
+
+  for (int k0 = 0; k0 < K; k0 += GB_K) {
+#pragma unroll
+    for (int e = tid; e < GB_M * GB_K; e += 256) {
+      int m, k;
+      if (OPA == OP_N || OPA == OP_R) {
+        m = e / GB_K;
+        k = e % GB_K;
+      } else {
+        k = e / GB_M;
+        m = e % GB_M;
+      }
+      const int gm = m0 + m, gk = k0 + k;
+      cplx v = mkc(0.0, 0.0);
+      if (gm < M && gk < K) {
+        v = (OPA == OP_N || OPA == OP_R) ? A[(long long)gm * lda + gk] : A[(long long)gk * lda + gm];
+        if (OPA == OP_C || OPA == OP_R) v.y = -v.y;
+      }
+      As[k][m] = v;
+    }
+#pragma unroll
+    for (int e = tid; e < GB_K * GB_N; e += 256) {
+      int k, n;
+      if (OPB == OP_N || OPB == OP_R) {
+        k = e / GB_N;
+        n = e % GB_N;
+      } else {
+        n = e / GB_K;
+        k = e % GB_K;
+      }
+      const int gn = n0 + n, gk = k0 + k;
+      cplx v = mkc(0.0, 0.0);
+      if (gn < N && gk < K) {
+        v = (OPB == OP_N || OPB == OP_R) ? B[(long long)gk * ldb + gn] : B[(long long)gn * ldb + gk];
+        if (OPB == OP_C || OPB == OP_R) v.y = -v.y;
+      }
+      Bs[k][n] = v;
+    }
+    __syncthreads();
+#pragma unroll
+    for (int kk = 0; kk < GB_K; ++kk) {
+      cplx a[4], b[4];
+#pragma unroll
+      for (int i = 0; i < 4; ++i) a[i] = As[kk][ty + 16 * i];
+#pragma unroll
+      for (int j = 0; j < 4; ++j) b[j] = Bs[kk][tx + 16 * j];
+#pragma unroll
+      for (int i = 0; i < 4; ++i)
+#pragma unroll
+        for (int j = 0; j < 4; ++j) cfma(acc[i][j], a[i], b[j]);
+    }
+    __syncthreads();
+  }
+  const bool use_beta = (beta.x != 0.0 || beta.y != 0.0);
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    const int gm = m0 + ty + 16 * i;
+    if (gm >= M) continue;
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int gn = n0 + tx + 16 * j;
+      if (gn >= N) continue;
+      cplx r = cmul(alpha, acc[i][j]);
+      cplx* c = C + (long long)gm * ldc + gn;
+      if (use_beta) r = cadd(r, cmul(beta, *c));
+      *c = r;
+    }
+  }
+}
+
+template <int OPA>
+void zgemm_b(int opB, dim3 g, cudaStream_t st, int M, int N, int K, cplx alpha, const cplx* A,
+             long long lda, long long sA, const cplx* B, long long ldb, long long sB, cplx beta,
+             cplx* C, long long ldc, long long sC) {
+  switch (opB) {
+    case OP_N: k_zgemm<OPA, OP_N><<<g, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC); break;
+    case OP_T: k_zgemm<OPA, OP_T><<<g, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC); break;
+    case OP_C: k_zgemm<OPA, OP_C><<<g, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC); break;
+    default:   k_zgemm<OPA, OP_R><<<g, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC); break;
+  }
+}
+}  // namespace
+
+void zgemm(cudaStream_t st, int opA, int opB, int M, int N, int K, cplx alpha, const cplx* A,
+           long long lda, const cplx* B, long long ldb, cplx beta, cplx* C, long long ldc,
+           int batch, long long sA, long long sB, long long sC) {
+  if (M <= 0 || N <= 0 || batch <= 0) return;
+  tdvp_require(batch <= 65535, TDVP_ERR_INVALID_ARG, "zgemm: batch too large");
+  tdvp_require(ceil_div(M, GB_M) <= 65535, TDVP_ERR_INVALID_ARG, "zgemm: M too large");
+  if (K <= 0) {  // C = beta C
+    tdvp_require(beta.x == 0.0 && beta.y == 0.0, TDVP_ERR_INVALID_ARG, "zgemm: K=0 with beta");
+    for (int b = 0; b < batch; ++b)
+      for (int r = 0; r < M; ++r)
+        TDVP_CUDA(cudaMemsetAsync(C + b * sC + (long long)r * ldc, 0, sizeof(cplx) * N, st));
+    return;
+  }
+  dim3 g(ceil_div(N, GB_N), ceil_div(M, GB_M), batch);
+  switch (opA) {
+    case OP_N: zgemm_b<OP_N>(opB, g, st, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC); break;
+    case OP_T: zgemm_b<OP_T>(opB, g, st, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC); break;
+    case OP_C: zgemm_b<OP_C>(opB, g, st, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC); break;
+    default:   zgemm_b<OP_R>(opB, g, st, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC); break;
+  }
+  TDVP_CHECK_LAUNCH();
+}
+
+// ============================================================================
+// MPO-tensor stages
+// ============================================================================
+void WSparse::build(const cplx* W, int wl_, int wr_, int d_) {
+  wl = wl_;
+  wr = wr_;
+  d = d_;
+  l_off.assign(d * wr + 1, 0);
+  r_off.assign(d * wl + 1, 0);
+  l_idx.clear();
+  l_val.clear();
+  r_idx.clear();
+  r_val.clear();
+  auto at = [&](int w, int s, int t, int v) { return W[((w * d + s) * d + t) * wr + v]; };
+  nnz = 0;
+  for (int s = 0; s < d; ++s)
+    for (int v = 0; v < wr; ++v) {
+      for (int w = 0; w < wl; ++w)
+        for (int t = 0; t < d; ++t) {
+          cplx x = at(w, s, t, v);
+          if (x.x != 0.0 || x.y != 0.0) {
+            l_idx.push_back(w);
+            l_idx.push_back(t);
+            l_val.push_back(x);
+          }
+        }
+      l_off[s * wr + v + 1] = (int)l_val.size();
+    }
+  for (int s = 0; s < d; ++s)
+    for (int w = 0; w < wl; ++w) {
+      for (int v = 0; v < wr; ++v)
+        for (int t = 0; t < d; ++t) {
+          cplx x = at(w, s, t, v);
+          if (x.x != 0.0 || x.y != 0.0) {
+            r_idx.push_back(v);
+            r_idx.push_back(t);
+            r_val.push_back(x);
+          }
+        }
+      r_off[s * wl + w + 1] = (int)r_val.size();
+    }
+  nnz = (int)l_val.size();
+}
+
+void WSparse::upload() {
+  free_device();
+  auto up = [](auto& vec, auto** dst) {
+    using T = typename std::remove_reference<decltype(vec)>::type::value_type;
+    size_t bytes = std::max<size_t>(1, vec.size()) * sizeof(T);
+    TDVP_CUDA(cudaMalloc((void**)dst, bytes));
+    if (!vec.empty()) TDVP_CUDA(cudaMemcpy(*dst, vec.data(), vec.size() * sizeof(T), cudaMemcpyHostToDevice));
+  };
+  up(l_off, &d_l_off);
+  up(l_idx, &d_l_idx);
+  up(l_val, &d_l_val);
+  up(r_off, &d_r_off);
+  up(r_idx, &d_r_idx);
+  up(r_val, &d_r_val);
+}
+
+void WSparse::free_device() {
+  cudaFree(d_l_off);
+  cudaFree(d_l_idx);
+  cudaFree(d_l_val);
+  cudaFree(d_r_off);
+  cudaFree(d_r_idx);
+  cudaFree(d_r_val);
+  d_l_off = d_l_idx = d_r_off = d_r_idx = nullptr;
+  d_l_val = d_r_val = nullptr;
+}
+
+namespace {
+__global__ void k_wstage_left(const cplx* __restrict__ in, cplx* __restrict__ out, int WL, int WR,
+                              int D, int C, const int* __restrict__ off, const int* __restrict__ idx,
+                              const cplx* __restrict__ val) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int sv = blockIdx.y;
+  const long long a = blockIdx.z;
+  if (c >= C) return;
+  const int s = sv / WR, v = sv % WR;
+  cplx acc = mkc(0.0, 0.0);
+  for (int e = off[sv]; e < off[sv + 1]; ++e) {
+    const int w = idx[2 * e], t = idx[2 * e + 1];
+    cfma(acc, val[e], in[((a * WL + w) * D + t) * C + c]);
+  }
+  out[((a * D + s) * WR + v) * C + c] = acc;
+}
+
+__global__ void k_wstage_right(const cplx* __restrict__ in, cplx* __restrict__ out, int B, int WL,
+                               int WR, int D, int C, const int* __restrict__ off,
+                               const int* __restrict__ idx, const cplx* __restrict__ val) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int sw = blockIdx.y;
+  const long long b = blockIdx.z;
+  if (c >= C) return;
+  const int s = sw / WL, w = sw % WL;
+  cplx acc = mkc(0.0, 0.0);
+  for (int e = off[sw]; e < off[sw + 1]; ++e) {
+    const int v = idx[2 * e], t = idx[2 * e + 1];
+    cfma(acc, val[e], in[((b * WR + v) * D + t) * C + c]);
+  }
+  out[(((long long)s * B + b) * WL + w) * C + c] = acc;
+}
+
+__global__ void k_permute_asb(const cplx* __restrict__ in, cplx* __restrict__ out, int A, int S, int B) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long n = (long long)A * S * B;
+  if (i >= n) return;
+  const int b = i % B;
+  const long long as = i / B;
+  const int s = as % S;
+  const long long a = as / S;
+  out[((long long)s * A + a) * B + b] = in[i];
+}
+}  // namespace
+
+void wstage_left(cudaStream_t st, const WSparse& w, const cplx* in, cplx* out, int A, int C) {
+  tdvp_require(A <= 65535, TDVP_ERR_INVALID_ARG, "wstage_left: too many rows");
+  dim3 g(ceil_div(C, 128), w.d * w.wr, A);
+  k_wstage_left<<<g, 128, 0, st>>>(in, out, w.wl, w.wr, w.d, C, w.d_l_off, w.d_l_idx, w.d_l_val);
+  TDVP_CHECK_LAUNCH();
+}
+
+void wstage_right(cudaStream_t st, const WSparse& w, const cplx* in, cplx* out, int B, int C) {
+  tdvp_require(B <= 65535, TDVP_ERR_INVALID_ARG, "wstage_right: too many rows");
+  dim3 g(ceil_div(C, 128), w.d * w.wl, B);
+  k_wstage_right<<<g, 128, 0, st>>>(in, out, B, w.wl, w.wr, w.d, C, w.d_r_off, w.d_r_idx, w.d_r_val);
+  TDVP_CHECK_LAUNCH();
+}
+
+void permute_asb_sab(cudaStream_t st, const cplx* in, cplx* out, int A, int S, int B) {
+  const long long n = (long long)A * S * B;
+  if (n == 0) return;
+  k_permute_asb<<<ceil_div(n, 256), 256, 0, st>>>(in, out, A, S, B);
+  TDVP_CHECK_LAUNCH();
+}
+
+// ============================================================================
+// BLAS-1 (deterministic two-pass reductions)
+// ============================================================================
+namespace {
+constexpr int RED_THREADS = 256;
+constexpr int MD_CH = 8;
+
+__device__ __forceinline__ cplx warp_sum(cplx v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+    k_multidot_partial(const cplx* __restrict__ V, long long ldv, int nvec, const cplx* __restrict__ w,
+                       long long n, cplx* __restrict__ partial) {
+  __shared__ cplx red[MD_CH][RED_THREADS / 32];
+  const int G = gridDim.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int k0 = 0; k0 < nvec; k0 += MD_CH) {
+    cplx acc[MD_CH];
+#pragma unroll
+    for (int q = 0; q < MD_CH; ++q) acc[q] = mkc(0.0, 0.0);
+    for (long long i = (long long)blockIdx.x * RED_THREADS + threadIdx.x; i < n;
+         i += (long long)G * RED_THREADS) {
+      const cplx wi = w[i];
+#pragma unroll
+      for (int q = 0; q < MD_CH; ++q)
+        if (k0 + q < nvec) cfma_conj(acc[q], V[(long long)(k0 + q) * ldv + i], wi);
+    }
+#pragma unroll
+    for (int q = 0; q < MD_CH; ++q) {
+      cplx s = warp_sum(acc[q]);
+      if (lane == 0) red[q][warp] = s;
+    }
+    __syncthreads();
+    if (threadIdx.x < MD_CH && k0 + (int)threadIdx.x < nvec) {
+      cplx s = mkc(0.0, 0.0);
+      for (int u = 0; u < RED_THREADS / 32; ++u) s = cadd(s, red[threadIdx.x][u]);
+      partial[(long long)(k0 + threadIdx.x) * G + blockIdx.x] = s;
+    }
+    __syncthreads();
+  }
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+    k_reduce_partial_c(const cplx* __restrict__ partial, int G, cplx* __restrict__ out) {
+  __shared__ cplx red[RED_THREADS / 32];
+  const int k = blockIdx.x;
+  cplx s = mkc(0.0, 0.0);
+  for (int g = threadIdx.x; g < G; g += RED_THREADS) s = cadd(s, partial[(long long)k * G + g]);
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    cplx t = mkc(0.0, 0.0);
+    for (int u = 0; u < RED_THREADS / 32; ++u) t = cadd(t, red[u]);
+    out[k] = t;
+  }
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+    k_norm2_partial(const cplx* __restrict__ x, long long n, double* __restrict__ partial) {
+  __shared__ double red[RED_THREADS / 32];
+  double acc = 0.0;
+  for (long long i = (long long)blockIdx.x * RED_THREADS + threadIdx.x; i < n;
+       i += (long long)gridDim.x * RED_THREADS)
+    acc += cabs2(x[i]);
+  acc = warp_sum(acc);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = acc;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int u = 0; u < RED_THREADS / 32; ++u) t += red[u];
+    partial[blockIdx.x] = t;
+  }
+}
+
+__global__ void __launch_bounds__(RED_THREADS)
+    k_reduce_partial_d(const double* __restrict__ partial, int G, double* __restrict__ out) {
+  __shared__ double red[RED_THREADS / 32];
+  double s = 0.0;
+  for (int g = threadIdx.x; g < G; g += RED_THREADS) s += partial[g];
+  s = warp_sum(s);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int u = 0; u < RED_THREADS / 32; ++u) t += red[u];
+    *out = t;
+  }
+}
+
+__global__ void k_multi_axpy_sub(cplx* __restrict__ w, const cplx* __restrict__ V, long long ldv,
+                                 int nvec, const cplx* __restrict__ c, long long n) {
+  __shared__ cplx cs[64];
+  for (int k = threadIdx.x; k < nvec && k < 64; k += blockDim.x) cs[k] = c[k];
+  __syncthreads();
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  cplx acc = mkc(0.0, 0.0);
+  for (int k = 0; k < nvec; ++k) cfma(acc, V[(long long)k * ldv + i], cs[k]);
+  w[i] = csub(w[i], acc);
+}
+
+__global__ void k_multi_combine(cplx* __restrict__ y, const cplx* __restrict__ V, long long ldv,
+                                int nvec, const cplx* __restrict__ c, double scale, long long n) {
+  __shared__ cplx cs[64];
+  for (int k = threadIdx.x; k < nvec && k < 64; k += blockDim.x) cs[k] = c[k];
+  __syncthreads();
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  cplx acc = mkc(0.0, 0.0);
+  for (int k = 0; k < nvec; ++k) cfma(acc, V[(long long)k * ldv + i], cs[k]);
+  y[i] = cscale(acc, scale);
+}
+
+__global__ void k_scale_inv_sqrt(cplx* __restrict__ dst, const cplx* __restrict__ src,
+                                 const double* __restrict__ nrm2, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double s = 1.0 / sqrt(*nrm2);
+  dst[i] = cscale(src[i], s);
+}
+
+__global__ void k_scale_host(cplx* __restrict__ dst, const cplx* __restrict__ src, cplx s, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  dst[i] = cmul(src[i], s);
+}
+
+__global__ void k_copy_real(const cplx* c, int j, double* alpha) { alpha[j] = c[j].x; }
+__global__ void k_store_beta(const double* nrm2, double* slot) { *slot = sqrt(*nrm2); }
+}  // namespace
+
+void Blas1::init(DevicePool* p, int sm_count) {
+  pool = p;
+  max_blocks = 2 * sm_count;
+  partial.reset(pool, (size_t)max_blocks * 64);
+}
+
+static int red_blocks(long long n, int max_blocks) {
+  return std::max(1, std::min<int>(max_blocks, ceil_div(n, RED_THREADS * 4)));
+}
+
+void Blas1::multi_dot(cudaStream_t st, const cplx* V, long long ldv, int nvec, const cplx* w,
+                      long long n, cplx* out) {
+  tdvp_require(nvec <= 64, TDVP_ERR_INVALID_ARG, "multi_dot: nvec > 64");
+  const int G = red_blocks(n, max_blocks);
+  k_multidot_partial<<<G, RED_THREADS, 0, st>>>(V, ldv, nvec, w, n, partial.data());
+  TDVP_CHECK_LAUNCH();
+  k_reduce_partial_c<<<nvec, RED_THREADS, 0, st>>>(partial.data(), G, out);
+  TDVP_CHECK_LAUNCH();
+}
+
+void Blas1::norm2(cudaStream_t st, const cplx* x, long long n, double* out) {
+  const int G = red_blocks(n, max_blocks);
+  double* part = reinterpret_cast<double*>(partial.data());
+  k_norm2_partial<<<G, RED_THREADS, 0, st>>>(x, n, part);
+  TDVP_CHECK_LAUNCH();
+  k_reduce_partial_d<<<1, RED_THREADS, 0, st>>>(part, G, out);
+  TDVP_CHECK_LAUNCH();
+}
+
+void multi_axpy_sub(cudaStream_t st, cplx* w, const cplx* V, long long ldv, int nvec, const cplx* c,
+                    long long n) {
+  tdvp_require(nvec <= 64, TDVP_ERR_INVALID_ARG, "multi_axpy: nvec > 64");
+  if (n == 0 || nvec == 0) return;
+  k_multi_axpy_sub<<<ceil_div(n, 256), 256, 0, st>>>(w, V, ldv, nvec, c, n);
+  TDVP_CHECK_LAUNCH();
+}
+
+void multi_combine(cudaStream_t st, cplx* y, const cplx* V, long long ldv, int nvec, const cplx* c,
+                   double scale, long long n) {
+  tdvp_require(nvec <= 64, TDVP_ERR_INVALID_ARG, "multi_combine: nvec > 64");
+  if (n == 0) return;
+  k_multi_combine<<<ceil_div(n, 256), 256, 0, st>>>(y, V, ldv, nvec, c, scale, n);
+  TDVP_CHECK_LAUNCH();
+}
+
+void scale_by_inv_sqrt(cudaStream_t st, cplx* dst, const cplx* src, const double* nrm2, long long n) {
+  if (n == 0) return;
+  k_scale_inv_sqrt<<<ceil_div(n, 256), 256, 0, st>>>(dst, src, nrm2, n);
+  TDVP_CHECK_LAUNCH();
+}
+
+void scale_host(cudaStream_t st, cplx* dst, const cplx* src, cplx s, long long n) {
+  if (n == 0) return;
+  k_scale_host<<<ceil_div(n, 256), 256, 0, st>>>(dst, src, s, n);
+  TDVP_CHECK_LAUNCH();
+}
+
+void fill_zero(cudaStream_t st, cplx* p, long long n) {
+  if (n) TDVP_CUDA(cudaMemsetAsync(p, 0, n * sizeof(cplx), st));
+}
+
+void copy_real_part(cudaStream_t st, const cplx* c, int j, double* alpha) {
+  k_copy_real<<<1, 1, 0, st>>>(c, j, alpha);
+  TDVP_CHECK_LAUNCH();
+}
+
+void store_beta(cudaStream_t st, const double* nrm2, double* slot) {
+  k_store_beta<<<1, 1, 0, st>>>(nrm2, slot);
+  TDVP_CHECK_LAUNCH();
+}
+
+// ============================================================================
+// exp(coef T) e_0 for a small symmetric tridiagonal T (Lanczos matrix).
+//
+// Chebyshev expansion on the Gershgorin interval [lo, hi] of T, T = c + h X
+// with spec(X) in [-1, 1]:
+//   real time  exp(-i delta T) = e^{-i delta c} sum_k eps_k (-i sgn delta)^k J_k(|delta| h) T_k(X)
+//   imag time  exp(-delta T)   = e^{-delta lo} sum_k eps_k (-1)^k e^{-x} I_k(x) T_k(X),  delta > 0
+//                              = e^{|delta| hi} sum_k eps_k e^{-x} I_k(x) T_k(X),        delta < 0
+// with x = |delta| h, eps_0 = 1, eps_k = 2.  J_k and e^{-x} I_k come from Miller's
+// backward recurrence normalised by J_0 + 2 sum J_2k = 1 and I_0 + 2 sum I_k = e^x.
+// One block; thread i owns component i (n <= 64).
+// ============================================================================
+namespace {
+constexpr int TRI_MAX = 64;
+constexpr int CHEB_MAX = 1024;
+
+__global__ void __launch_bounds__(TRI_MAX)
+    k_tridiag_expv(const double* __restrict__ alpha, const double* __restrict__ beta, int n,
+                   double delta, int kind, const double* __restrict__ nrm2_next,
+                   cplx* __restrict__ y, double* __restrict__ err) {
+  __shared__ double d[TRI_MAX], o[TRI_MAX + 1];
+  __shared__ double tk[TRI_MAX], tkm[TRI_MAX];
+  __shared__ double coef[CHEB_MAX + 1];
+  __shared__ double sh_c, sh_h, sh_lo, sh_hi;
+  __shared__ int sh_K, sh_bad;
+  const int i = threadIdx.x;
+  if (i < n) d[i] = alpha[i];
+  if (i <= n) o[i] = (i >= 1 && i < n) ? beta[i] : 0.0;
+  __syncthreads();
+  if (i == 0) {
+    double lo = 1e300, hi = -1e300;
+    for (int r = 0; r < n; ++r) {
+      const double rad = fabs(o[r]) + fabs(o[r + 1]);
+      lo = fmin(lo, d[r] - rad);
+      hi = fmax(hi, d[r] + rad);
+    }
+    const double c = 0.5 * (hi + lo), h = 0.5 * (hi - lo);
+    sh_c = c;
+    sh_h = h;
+    sh_lo = lo;
+    sh_hi = hi;
+    const double x = fabs(delta) * h;
+    int K = (int)(x + 10.0 * cbrt(x + 1.0) + 40.0);
+    sh_bad = 0;
+    if (K > CHEB_MAX) {
+      K = CHEB_MAX;
+      sh_bad = 1;
+    }
+    sh_K = K;
+    // Miller backward recurrence, start well above K
+    const int M = 2 * ((K + 40 + (int)x) / 2 + 1);
+    for (int k = 0; k <= K; ++k) coef[k] = 0.0;
+    if (x < 1e-300) {
+      coef[0] = 1.0;
+    } else {
+      double jp1 = 0.0, jk = 1e-280, norm = 0.0;
+      for (int k = M; k >= 1; --k) {
+        // value at index k is jk, at k+1 is jp1; produce index k-1
+        const double jm1 = (kind == 0) ? (2.0 * k / x) * jk - jp1 : (2.0 * k / x) * jk + jp1;
+        if (k <= K) coef[k] = jk;
+        if (kind == 0) {
+          if ((k & 1) == 0) norm += 2.0 * jk;
+        } else {
+          norm += 2.0 * jk;
+        }
+        jp1 = jk;
+        jk = jm1;
+        if (fabs(jk) > 1e250) {  // rescale
+          const double f = 1e-250;
+          jk *= f;
+          jp1 *= f;
+          norm *= f;
+          for (int q = k; q <= K; ++q) coef[q] *= f;
+        }
+      }
+      coef[0] = jk;
+      norm += jk;
+      for (int k = 0; k <= K; ++k) coef[k] /= norm;
+    }
+  }
+  __syncthreads();
+  const int K = sh_K;
+  const double c = sh_c, h = sh_h;
+  const double inv_h = h > 0.0 ? 1.0 / h : 0.0;
+  // scaled matrix X = (T - c) / h
+  const double xd = (i < n) ? (d[i] - c) * inv_h : 0.0;
+  const double xl = (i < n && i >= 1) ? o[i] * inv_h : 0.0;
+  const double xr = (i + 1 < n) ? o[i + 1] * inv_h : 0.0;
+  double acc_re = 0.0, acc_im = 0.0;
+  // T_0 e0 = e0
+  double cur = (i == 0) ? 1.0 : 0.0, prev = 0.0;
+  for (int k = 0; k <= K; ++k) {
+    // coefficient eps_k * phase_k * coef[k]
+    const double ck = (k == 0 ? 1.0 : 2.0) * coef[k];
+    double pre, pim;
+    if (kind == 0) {
+      // (-i sgn)^k
+      const int m = k & 3;
+      const double sgn = delta >= 0 ? 1.0 : -1.0;
+      pre = (m == 0) ? 1.0 : (m == 2 ? -1.0 : 0.0);
+      pim = (m == 1) ? -sgn : (m == 3 ? sgn : 0.0);
+    } else {
+      pre = (delta >= 0 && (k & 1)) ? -1.0 : 1.0;
+      pim = 0.0;
+    }
+    acc_re += ck * pre * cur;
+    acc_im += ck * pim * cur;
+    if (k == K) break;
+    if (i < n) tk[i] = cur;
+    __syncthreads();
+    double xv = 0.0;
+    if (i < n) {
+      xv = xd * cur;
+      if (i >= 1) xv += xl * tk[i - 1];
+      if (i + 1 < n) xv += xr * tk[i + 1];
+    }
+    const double nxt = (k == 0) ? xv : 2.0 * xv - prev;
+    __syncthreads();
+    prev = cur;
+    cur = nxt;
+  }
+  (void)tkm;
+  if (i < n) {
+    double fre, fim;
+    if (kind == 0) {
+      const double ph = -delta * c;
+      fre = cos(ph);
+      fim = sin(ph);
+    } else {
+      const double e = (delta >= 0) ? exp(-delta * sh_lo) : exp(-delta * sh_hi);
+      fre = e;
+      fim = 0.0;
+    }
+    y[i] = mkc(fre * acc_re - fim * acc_im, fre * acc_im + fim * acc_re);
+    if (i == n - 1) {
+      const double b = sqrt(*nrm2_next);
+      const double ylast = sqrt(cabs2(y[i]));
+      err[0] = sh_bad ? 1e300 : b * ylast;
+      err[1] = b;
+    }
+  }
+}
+}  // namespace
+
+void tridiag_expv(cudaStream_t st, const double* alpha, const double* beta, int n, double delta,
+                  int kind, const double* nrm2_next, cplx* y, double* err) {
+  tdvp_require(n >= 1 && n < TRI_MAX, TDVP_ERR_INVALID_ARG, "tridiag_expv: n out of range");
+  k_tridiag_expv<<<1, TRI_MAX, 0, st>>>(alpha, beta, n, delta, kind, nrm2_next, y, err);
+  TDVP_CHECK_LAUNCH();
+}
+
+// ============================================================================
+// One-sided Jacobi SVD (Hestenes) in FP64.  The working matrix X (p x q,
+// column-major) has its q columns orthogonalised by unitary plane rotations
+// applied from the right, accumulated in Vx (q x q): X0 Vx = U S.
+// Rows >= cols: X0 = M.  Rows < cols: X0 = M^H (so p >= q always).
+// Columns are paired by the round-robin (circle) schedule; one sweep = qpad-1
+// rounds of qpad/2 disjoint pairs.
+// ============================================================================
+namespace {
+__device__ __forceinline__ void rr_pair(int round, int k, int qpad, int& P, int& Q) {
+  const int m = qpad - 1;
+  if (k == 0) {
+    P = round;
+    Q = m;
+  } else {
+    P = (round + k) % m;
+    Q = (round - k + m) % m;
+  }
+  if (P > Q) {
+    int t = P;
+    P = Q;
+    Q = t;
+  }
+}
+
+// Rotation from a = |x_p|^2, b = |x_q|^2, c = x_p^H x_q:
+//   x_p' = cs x_p - sn e^{-i phi} x_q,  x_q' = sn e^{i phi} x_p + cs x_q,  c = |c| e^{i phi}
+__device__ __forceinline__ bool jacobi_params(double a, double b, cplx c, double tol, double& cs,
+                                              cplx& sne) {
+  const double ac = sqrt(cabs2(c));
+  if (!(ac > tol * sqrt(a * b)) || ac == 0.0) return false;
+  const double zeta = (b - a) / (2.0 * ac);
+  const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
+  cs = 1.0 / sqrt(1.0 + t * t);
+  const double sn = cs * t;
+  sne = mkc(sn * c.x / ac, sn * c.y / ac);  // sn e^{i phi}
+  return true;
+}
+
+__device__ __forceinline__ void rotate_pair(cplx& xp, cplx& xq, double cs, cplx sne) {
+  // xp' = cs xp - conj(sne) xq ; xq' = sne xp + cs xq
+  const cplx np = csub(cscale(xp, cs), cmul(cconj(sne), xq));
+  const cplx nq = cadd(cmul(sne, xp), cscale(xq, cs));
+  xp = np;
+  xq = nq;
+}
+
+__global__ void k_svd_prepare(const cplx* __restrict__ M, int rows, int cols, int orient,
+                              cplx* __restrict__ X, cplx* __restrict__ V, int p, int q, int want_v) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long nx = (long long)p * q;
+  if (i < nx) {
+    const int r = i % p;
+    const int c = i / p;
+    X[i] = (orient == 0) ? M[(long long)r * cols + c] : cconj(M[(long long)c * cols + r]);
+  }
+  if (want_v && i < (long long)q * q) {
+    const int r = i % q, c = i / q;
+    V[i] = mkc(r == c ? 1.0 : 0.0, 0.0);
+  }
+}
+
+// Large path: one block per pair.
+__global__ void __launch_bounds__(256)
+    k_jacobi_round(cplx* __restrict__ X, cplx* __restrict__ V, int p, int q, int qpad, int round,
+                   double tol, int want_v, int* __restrict__ rotated) {
+  __shared__ double ra[8], rb[8];
+  __shared__ cplx rc[8];
+  __shared__ double s_cs;
+  __shared__ cplx s_sne;
+  __shared__ int s_do;
+  int P, Q;
+  rr_pair(round, blockIdx.x, qpad, P, Q);
+  if (Q >= q) return;
+  cplx* xp = X + (long long)P * p;
+  cplx* xq = X + (long long)Q * p;
+  double a = 0.0, b = 0.0;
+  cplx c = mkc(0.0, 0.0);
+  for (int r = threadIdx.x; r < p; r += blockDim.x) {
+    const cplx u = xp[r], v = xq[r];
+    a += cabs2(u);
+    b += cabs2(v);
+    cfma_conj(c, u, v);
+  }
+  a = warp_sum(a);
+  b = warp_sum(b);
+  c = warp_sum(c);
+  const int warp = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    ra[warp] = a;
+    rb[warp] = b;
+    rc[warp] = c;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double A = 0, B = 0;
+    cplx Cc = mkc(0, 0);
+    for (int u = 0; u < (int)(blockDim.x >> 5); ++u) {
+      A += ra[u];
+      B += rb[u];
+      Cc = cadd(Cc, rc[u]);
+    }
+    double cs;
+    cplx sne;
+    s_do = jacobi_params(A, B, Cc, tol, cs, sne) ? 1 : 0;
+    s_cs = cs;
+    s_sne = sne;
+    if (s_do) *rotated = 1;
+  }
+  __syncthreads();
+  if (!s_do) return;
+  const double cs = s_cs;
+  const cplx sne = s_sne;
+  for (int r = threadIdx.x; r < p; r += blockDim.x) {
+    cplx u = xp[r], v = xq[r];
+    rotate_pair(u, v, cs, sne);
+    xp[r] = u;
+    xq[r] = v;
+  }
+  if (want_v) {
+    cplx* vp = V + (long long)P * q;
+    cplx* vq = V + (long long)Q * q;
+    for (int r = threadIdx.x; r < q; r += blockDim.x) {
+      cplx u = vp[r], v = vq[r];
+      rotate_pair(u, v, cs, sne);
+      vp[r] = u;
+      vq[r] = v;
+    }
+  }
+}
+
+// Small path: the whole problem in shared memory, one block, warps own pairs.
+__global__ void __launch_bounds__(256)
+    k_jacobi_small(cplx* __restrict__ Xg, cplx* __restrict__ Vg, int p, int q, int qpad,
+                   double tol, int want_v, int max_sweeps, int* __restrict__ sweeps_out) {
+  extern __shared__ cplx sm[];
+  cplx* X = sm;
+  cplx* V = sm + (long long)p * q;
+  __shared__ int s_rot;
+  const int nx = p * q, nv = want_v ? q * q : 0;
+  for (int e = threadIdx.x; e < nx; e += blockDim.x) X[e] = Xg[e];
+  for (int e = threadIdx.x; e < nv; e += blockDim.x) V[e] = Vg[e];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    if (threadIdx.x == 0) s_rot = 0;
+    __syncthreads();
+    for (int round = 0; round < qpad - 1; ++round) {
+      for (int k = warp; k < qpad / 2; k += nw) {
+        int P, Q;
+        rr_pair(round, k, qpad, P, Q);
+        if (Q >= q) continue;
+        cplx* xp = X + P * p;
+        cplx* xq = X + Q * p;
+        double a = 0.0, b = 0.0;
+        cplx c = mkc(0.0, 0.0);
+        for (int r = lane; r < p; r += 32) {
+          const cplx u = xp[r], v = xq[r];
+          a += cabs2(u);
+          b += cabs2(v);
+          cfma_conj(c, u, v);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          a += __shfl_xor_sync(0xffffffffu, a, o);
+          b += __shfl_xor_sync(0xffffffffu, b, o);
+          c.x += __shfl_xor_sync(0xffffffffu, c.x, o);
+          c.y += __shfl_xor_sync(0xffffffffu, c.y, o);
+        }
+        double cs;
+        cplx sne;
+        if (!jacobi_params(a, b, c, tol, cs, sne)) continue;
+        if (lane == 0) s_rot = 1;
+        for (int r = lane; r < p; r += 32) {
+          cplx u = xp[r], v = xq[r];
+          rotate_pair(u, v, cs, sne);
+          xp[r] = u;
+          xq[r] = v;
+        }
+        if (want_v) {
+          cplx* vp = V + P * q;
+          cplx* vq = V + Q * q;
+          for (int r = lane; r < q; r += 32) {
+            cplx u = vp[r], v = vq[r];
+            rotate_pair(u, v, cs, sne);
+            vp[r] = u;
+            vq[r] = v;
+          }
+        }
+      }
+      __syncthreads();
+    }
+    const int rot = s_rot;
+    __syncthreads();
+    if (!rot) break;
+  }
+  for (int e = threadIdx.x; e < nx; e += blockDim.x) Xg[e] = X[e];
+  for (int e = threadIdx.x; e < nv; e += blockDim.x) Vg[e] = V[e];
+  if (threadIdx.x == 0) *sweeps_out = sweep + 1;
+}
+
+__global__ void k_colnorms(const cplx* __restrict__ X, int p, int q, double* __restrict__ s) {
+  const int j = blockIdx.x;
+  double a = 0.0;
+  for (int r = threadIdx.x; r < p; r += blockDim.x) a += cabs2(X[(long long)j * p + r]);
+  __shared__ double red[8];
+  a = warp_sum(a);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int u = 0; u < (int)(blockDim.x >> 5); ++u) t += red[u];
+    s[j] = sqrt(t);
+  }
+}
+
+// U[i*keep + r] from column perm[r] of a column-major (ld x *) matrix,
+// divided by s_sorted[r] when `normalise`.
+__global__ void k_gather_cols(const cplx* __restrict__ src, long long ld, int nrows,
+                              const int* __restrict__ perm, const double* __restrict__ s_sorted,
+                              int keep, int normalise, int conj_out, int transpose_out,
+                              cplx* __restrict__ dst) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)nrows * keep) return;
+  const int r = e % keep;
+  const int i = e / keep;
+  cplx v = src[(long long)perm[r] * ld + i];
+  if (normalise) v = cscale(v, 1.0 / s_sorted[r]);
+  if (conj_out) v = cconj(v);
+  if (transpose_out)
+    dst[(long long)r * nrows + i] = v;  // keep x nrows
+  else
+    dst[(long long)i * keep + r] = v;   // nrows x keep
+}
+}  // namespace
+
+void svd_jacobi_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows, int cols,
+                     int (*select)(const std::vector<double>& s, void* ctx), void* ctx,
+                     SvdOut& out, bool want_u, bool want_v) {
+  out.rows = rows;
+  out.cols = cols;
+  out.s.clear();
+  out.rank = 0;
+  out.U.release();
+  out.Vh.release();
+  if (rows == 0 || cols == 0) return;
+  const int orient = rows >= cols ? 0 : 1;
+  const int p = orient == 0 ? rows : cols;
+  const int q = orient == 0 ? cols : rows;
+  const int qpad = q + (q & 1);
+  // accumulated rotations are needed for V (orient 0) or U (orient 1)
+  const bool need_acc = orient == 0 ? want_v : want_u;
+  DArr X(pool, (size_t)p * q), Vx(pool, need_acc ? (size_t)q * q : 1);
+  {
+    const long long n = std::max<long long>((long long)p * q, need_acc ? (long long)q * q : 0);
+    k_svd_prepare<<<ceil_div(n, 256), 256, 0, st>>>(M, rows, cols, orient, X.data(), Vx.data(), p, q,
+                                                    need_acc ? 1 : 0);
+    TDVP_CHECK_LAUNCH();
+  }
+  const double tol = std::max(1e-15, std::sqrt((double)p) * 2.2e-16);
+  const int max_sweeps = 60;
+  const size_t small_bytes = ((size_t)p * q + (need_acc ? (size_t)q * q : 0)) * sizeof(cplx);
+  int* d_flag = nullptr;
+  TDVP_CUDA(cudaMallocAsync(&d_flag, sizeof(int), st));
+  int sweeps = 0;
+  if (q > 1) {
+    if (small_bytes <= 96 * 1024) {
+      static bool attr_set = false;
+      if (!attr_set) {
+        TDVP_CUDA(cudaFuncSetAttribute(k_jacobi_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       96 * 1024));
+        attr_set = true;
+      }
+      k_jacobi_small<<<1, 256, small_bytes, st>>>(X.data(), Vx.data(), p, q, qpad, tol,
+                                                   need_acc ? 1 : 0, max_sweeps, d_flag);
+      TDVP_CHECK_LAUNCH();
+      TDVP_CUDA(cudaMemcpyAsync(&sweeps, d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+      TDVP_CUDA(cudaStreamSynchronize(st));
+      if (sweeps > max_sweeps) {
+        cudaFreeAsync(d_flag, st);
+        throw TdvpError(TDVP_ERR_SVD_NOT_CONVERGED, "Jacobi SVD did not converge");
+      }
+    } else {
+      bool converged = false;
+      for (sweeps = 1; sweeps <= max_sweeps; ++sweeps) {
+        TDVP_CUDA(cudaMemsetAsync(d_flag, 0, sizeof(int), st));
+        for (int round = 0; round < qpad - 1; ++round) {
+          k_jacobi_round<<<qpad / 2, 256, 0, st>>>(X.data(), Vx.data(), p, q, qpad, round, tol,
+                                                    need_acc ? 1 : 0, d_flag);
+        }
+        TDVP_CHECK_LAUNCH();
+        int rot = 0;
+        TDVP_CUDA(cudaMemcpyAsync(&rot, d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+        TDVP_CUDA(cudaStreamSynchronize(st));
+        if (!rot) {
+          converged = true;
+          break;
+        }
+      }
+      if (!converged) {
+        cudaFreeAsync(d_flag, st);
+        throw TdvpError(TDVP_ERR_SVD_NOT_CONVERGED, "Jacobi SVD did not converge");
+      }
+    }
+  }
+  TDVP_CUDA(cudaFreeAsync(d_flag, st));
+  out.sweeps = sweeps;
+  // singular values = column norms
+  double* d_s = nullptr;
+  TDVP_CUDA(cudaMallocAsync(&d_s, sizeof(double) * q, st));
+  k_colnorms<<<q, 256, 0, st>>>(X.data(), p, q, d_s);
+  TDVP_CHECK_LAUNCH();
+  std::vector<double> s(q);
+  TDVP_CUDA(cudaMemcpyAsync(s.data(), d_s, sizeof(double) * q, cudaMemcpyDeviceToHost, st));
+  TDVP_CUDA(cudaStreamSynchronize(st));
+  for (double v : s)
+    tdvp_require(std::isfinite(v), TDVP_ERR_NONFINITE, "SVD: non-finite singular value");
+  std::vector<int> perm(q);
+  std::iota(perm.begin(), perm.end(), 0);
+  std::stable_sort(perm.begin(), perm.end(), [&](int a, int b) { return s[a] > s[b]; });
+  out.s.resize(q);
+  for (int r = 0; r < q; ++r) out.s[r] = s[perm[r]];
+  const int keep = std::max(0, std::min(q, select(out.s, ctx)));
+  out.rank = keep;
+  if (keep == 0) {
+    cudaFreeAsync(d_s, st);
+    return;
+  }
+  int* d_perm = nullptr;
+  double* d_ss = nullptr;
+  TDVP_CUDA(cudaMallocAsync(&d_perm, sizeof(int) * keep, st));
+  TDVP_CUDA(cudaMallocAsync(&d_ss, sizeof(double) * keep, st));
+  TDVP_CUDA(cudaMemcpyAsync(d_perm, perm.data(), sizeof(int) * keep, cudaMemcpyHostToDevice, st));
+  TDVP_CUDA(cudaMemcpyAsync(d_ss, out.s.data(), sizeof(double) * keep, cudaMemcpyHostToDevice, st));
+  if (want_u) {
+    out.U.reset(pool, (size_t)rows * keep);
+    const long long n = (long long)rows * keep;
+    if (orient == 0)  // U = X[:, perm] / s
+      k_gather_cols<<<ceil_div(n, 256), 256, 0, st>>>(X.data(), p, rows, d_perm, d_ss, keep, 1, 0, 0,
+                                                      out.U.data());
+    else  // U = Vx[:, perm]
+      k_gather_cols<<<ceil_div(n, 256), 256, 0, st>>>(Vx.data(), q, rows, d_perm, d_ss, keep, 0, 0, 0,
+                                                      out.U.data());
+    TDVP_CHECK_LAUNCH();
+  }
+  if (want_v) {
+    out.Vh.reset(pool, (size_t)keep * cols);
+    const long long n = (long long)cols * keep;
+    if (orient == 0)  // Vh[r][j] = conj(Vx[j, perm r])
+      k_gather_cols<<<ceil_div(n, 256), 256, 0, st>>>(Vx.data(), q, cols, d_perm, d_ss, keep, 0, 1, 1,
+                                                      out.Vh.data());
+    else  // Vh[r][j] = conj(X[j, perm r]) / s
+      k_gather_cols<<<ceil_div(n, 256), 256, 0, st>>>(X.data(), p, cols, d_perm, d_ss, keep, 1, 1, 1,
+                                                      out.Vh.data());
+    TDVP_CHECK_LAUNCH();
+  }
+  TDVP_CUDA(cudaFreeAsync(d_perm, st));
+  TDVP_CUDA(cudaFreeAsync(d_ss, st));
+  TDVP_CUDA(cudaFreeAsync(d_s, st));
+}
+
+// ============================================================================
+// small helpers
+// ============================================================================
+namespace {
+__global__ void k_scale_rows(cplx* __restrict__ out, const cplx* __restrict__ in,
+                             const double* __restrict__ s, int r, int c) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)r * c) return;
+  out[e] = cscale(in[e], s[e / c]);
+}
+__global__ void k_scale_cols(cplx* __restrict__ out, const cplx* __restrict__ in,
+                             const double* __restrict__ s, int rows, int r) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)rows * r) return;
+  out[e] = cscale(in[e], s[e % r]);
+}
+__global__ void k_copy_block(cplx* __restrict__ dst, long long ldd, const cplx* __restrict__ src,
+                             long long lds, int rows, int cols) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)rows * cols) return;
+  const int r = e / cols, c = e % cols;
+  dst[r * ldd + c] = src[r * lds + c];
+}
+}  // namespace
+
+void scale_rows(cudaStream_t st, cplx* out, const cplx* in, const double* s_dev, int r, int c) {
+  const long long n = (long long)r * c;
+  if (!n) return;
+  k_scale_rows<<<ceil_div(n, 256), 256, 0, st>>>(out, in, s_dev, r, c);
+  TDVP_CHECK_LAUNCH();
+}
+void scale_cols(cudaStream_t st, cplx* out, const cplx* in, const double* s_dev, int rows, int r) {
+  const long long n = (long long)rows * r;
+  if (!n) return;
+  k_scale_cols<<<ceil_div(n, 256), 256, 0, st>>>(out, in, s_dev, rows, r);
+  TDVP_CHECK_LAUNCH();
+}
+void copy_block(cudaStream_t st, cplx* dst, long long ldd, const cplx* src, long long lds, int rows,
+                int cols) {
+  const long long n = (long long)rows * cols;
+  if (!n) return;
+  k_copy_block<<<ceil_div(n, 256), 256, 0, st>>>(dst, ldd, src, lds, rows, cols);
+  TDVP_CHECK_LAUNCH();
+}

@@ -1,0 +1,111 @@
+// FP64 complex building blocks of the GSE-TDVP1 path (CUDA cores).
+#pragma once
+#include "common.cuh"
+
+enum GemmOp { OP_N = 0, OP_T = 1, OP_C = 2, OP_R = 3 };  // R = conjugate, not transposed
+
+// C[m,n] = alpha * sum_k opA(A)[m,k] opB(B)[k,n] + beta * C[m,n], all row-major.
+// opA(A)[m,k] = A[m*lda+k] (N), A[k*lda+m] (T), conj(A[k*lda+m]) (C), conj(A[m*lda+k]) (R).
+// batch > 1 uses strides sA, sB, sC (elements).
+void zgemm(cudaStream_t st, int opA, int opB, int M, int N, int K, cplx alpha, const cplx* A,
+           long long lda, const cplx* B, long long ldb, cplx beta, cplx* C, long long ldc,
+           int batch = 1, long long sA = 0, long long sB = 0, long long sC = 0);
+
+// Sparse description of one MPO site tensor W[w][s][t][v] for the contraction
+// stages: entries grouped by output (s, v) for left moves and by (s, w) for
+// right moves.
+struct WSparse {
+  int wl = 0, wr = 0, d = 0;
+  int nnz = 0;
+  // left grouping: for out row (s, v): entries (w, t) with value
+  std::vector<int> l_off;           // d*wr + 1
+  std::vector<int> l_idx;           // 2*nnz: (w, t)
+  std::vector<cplx> l_val;
+  // right grouping: for out row (s, w): entries (v, t)
+  std::vector<int> r_off;           // d*wl + 1
+  std::vector<int> r_idx;
+  std::vector<cplx> r_val;
+  // device copies
+  int* d_l_off = nullptr;
+  int* d_l_idx = nullptr;
+  cplx* d_l_val = nullptr;
+  int* d_r_off = nullptr;
+  int* d_r_idx = nullptr;
+  cplx* d_r_val = nullptr;
+  void build(const cplx* W, int wl, int wr, int d);  // host W
+  void upload();
+  void free_device();
+};
+
+// out[a][s][v][c] = sum_{(w,t)} W[w,s,t,v] in[a][w][t][c]      (A = rows a, C = cols c)
+void wstage_left(cudaStream_t st, const WSparse& w, const cplx* in, cplx* out, int A, int C);
+// out[s][b][w][c] = sum_{(v,t)} W[w,s,t,v] in[b][v][t][c]
+void wstage_right(cudaStream_t st, const WSparse& w, const cplx* in, cplx* out, int B, int C);
+
+// out[s][a][b] = in[a][s][b] (and back with the inverse flag)
+void permute_asb_sab(cudaStream_t st, const cplx* in, cplx* out, int A, int S, int B);
+
+// Reductions (deterministic, two-pass).  Results land in device memory.
+struct Blas1 {
+  DevicePool* pool = nullptr;
+  DArr partial;          // scratch for block partials
+  int max_blocks = 0;
+  void init(DevicePool* p, int sm_count);
+  // out[k] = sum_i conj(V[k*ldv + i]) w[i], k < nvec
+  void multi_dot(cudaStream_t st, const cplx* V, long long ldv, int nvec, const cplx* w,
+                 long long n, cplx* out);
+  // *out = sum_i |x_i|^2 (double in device memory)
+  void norm2(cudaStream_t st, const cplx* x, long long n, double* out);
+};
+// w[i] -= sum_k V[k*ldv+i] c[k]
+void multi_axpy_sub(cudaStream_t st, cplx* w, const cplx* V, long long ldv, int nvec,
+                    const cplx* c, long long n);
+// y[i] = scale * sum_k V[k*ldv+i] c[k]  (scale read from host value)
+void multi_combine(cudaStream_t st, cplx* y, const cplx* V, long long ldv, int nvec,
+                   const cplx* c, double scale, long long n);
+// dst = src * (1 / sqrt(*nrm2))   (nrm2 in device memory)
+void scale_by_inv_sqrt(cudaStream_t st, cplx* dst, const cplx* src, const double* nrm2,
+                       long long n);
+void scale_host(cudaStream_t st, cplx* dst, const cplx* src, cplx s, long long n);
+void fill_zero(cudaStream_t st, cplx* p, long long n);
+// Lanczos bookkeeping: alpha[j] = Re c[j]
+void copy_real_part(cudaStream_t st, const cplx* c, int j, double* alpha);
+// y[0..n) = exp(coef * T) e_0 for T tridiagonal (diag alpha, off beta[1..n-1]);
+// kind 0: coef = -i delta, kind 1: coef = -delta.  err[0] = sqrt(nrm2_next) |y[n-1]|,
+// err[1] = sqrt(nrm2_next) (beta_n), both written to device memory.
+void tridiag_expv(cudaStream_t st, const double* alpha, const double* beta, int n,
+                  double delta, int kind, const double* nrm2_next, cplx* y, double* err);
+void store_beta(cudaStream_t st, const double* nrm2, double* beta_slot);
+
+// One-sided Jacobi SVD of a complex FP64 matrix (row-major rows x cols).
+struct SvdOut {
+  int rows = 0, cols = 0, rank = 0;  // rank = number of computed singular values kept
+  std::vector<double> s;             // sorted descending, all min(rows, cols)
+  DArr U;                            // rows x keep   (row-major)
+  DArr Vh;                           // keep x cols   (row-major)
+  int sweeps = 0;
+};
+// Computes the SVD and sorts it; `select` picks how many to keep from the sorted s.
+// want_u/want_v: which factors to materialise.
+template <class Select>
+void svd_jacobi(cudaStream_t st, DevicePool* pool, const cplx* M, int rows, int cols,
+                Select select, SvdOut& out, bool want_u = true, bool want_v = true);
+// implemented for this signature:
+void svd_jacobi_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows, int cols,
+                     int (*select)(const std::vector<double>& s, void* ctx), void* ctx,
+                     SvdOut& out, bool want_u, bool want_v);
+template <class Select>
+inline void svd_jacobi(cudaStream_t st, DevicePool* pool, const cplx* M, int rows, int cols,
+                       Select select, SvdOut& out, bool want_u, bool want_v) {
+  auto thunk = [](const std::vector<double>& s, void* ctx) -> int {
+    return (*static_cast<Select*>(ctx))(s);
+  };
+  svd_jacobi_keep(st, pool, M, rows, cols, thunk, &select, out, want_u, want_v);
+}
+
+// rows-of-Vh scaling helpers: out[r][c] = s[r] * Vh[r][c]; out[i][r] = U[i][r] * s[r]
+void scale_rows(cudaStream_t st, cplx* out, const cplx* in, const double* s_dev, int r, int c);
+void scale_cols(cudaStream_t st, cplx* out, const cplx* in, const double* s_dev, int rows, int r);
+// copy a (rows x cols) block into a (rows x ldo) destination at column offset
+void copy_block(cudaStream_t st, cplx* dst, long long ldd, const cplx* src, long long lds,
+                int rows, int cols);

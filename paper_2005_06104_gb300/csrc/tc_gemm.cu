@@ -1,0 +1,449 @@
+// Tensor-core H_eff for sm_103a: complex contractions mapped to real
+// tcgen05 GEMMs with TF32 operands split hi + lo (three products, FP32
+// accumulation in tensor memory).
+//
+// Real embedding of a complex product C = A B (4M form): A stays interleaved
+// (re, im) along K; B is expanded to the real (2N x 2K) operand
+//   [ Re B  -Im B ]
+//   [ Im B   Re B ]  (rows (n, re/im), K index (k, re/im))
+// so that one real GEMM writes C interleaved.
+//
+// GEMM kernel: one CTA per 128 x 128 output tile, 6 warps:
+//   warp 0      TMA producer (cp.async.bulk.tensor, 128B swizzle, 3 stages)
+//   warp 1      TMEM allocator and single-thread tcgen05.mma issuer
+//   warps 2..5  epilogue: tcgen05.ld from TMEM lanes 32*(warp%4) .. +31
+// Every mbarrier wait is bounded by a wall-clock limit; on expiry the CTA
+// records an error word, drains its own copies and MMAs (bounded) and frees
+// its tensor memory before returning.
+#include <cuda.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
+
+#include "contract.cuh"
+
+namespace tc {
+constexpr int BM = 128, BN = 128, BK = 32, STAGES = 3;
+constexpr int A_TILE = BM * BK * 4;                        // 16 KiB
+constexpr int B_TILE = BN * BK * 4;                        // 16 KiB
+constexpr int STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;       // 64 KiB
+constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+constexpr int TMEM_COLS = 128;
+constexpr unsigned long long kWaitNs = 2000000000ull;      // 2 s per wait
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ unsigned long long globaltimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}\n"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait: false when the time limit ran out
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_try(bar, parity)) return true;
+  const unsigned long long t0 = globaltimer();
+  while (true) {
+    for (int i = 0; i < 256; ++i)
+      if (mbar_try(bar, parity)) return true;
+    if (globaltimer() - t0 > kWaitNs) return false;
+  }
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map, uint32_t bar, int x, int y) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1, {%2, %3}], [%4];" ::"r"(
+          dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
+      : "memory");
+}
+// Shared-memory matrix descriptor: K-major, 128B swizzle, 8-row groups 1024 B apart.
+__device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
+  uint64_t d = 0;
+  d |= (uint64_t)((addr >> 4) & 0x3FFF);          // start address
+  d |= (uint64_t)1 << 16;                          // leading byte offset (unused for swizzled K-major)
+  d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset
+  d |= (uint64_t)1 << 46;                          // descriptor version (sm_100 family)
+  d |= (uint64_t)2 << 61;                          // layout: 128B swizzle
+  return d;
+}
+// Instruction descriptor, kind::tf32: D = F32, A = B = TF32, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_tf32(int M, int N) {
+  return (1u << 4)                       // D format F32
+         | (2u << 7)                     // A format TF32
+         | (2u << 10)                    // B format TF32
+         | ((uint32_t)(N >> 3) << 17)    // N / 8
+         | ((uint32_t)(M >> 4) << 24);   // M / 16
+}
+__device__ __forceinline__ void mma_tf32(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(da), "l"(db), "r"(idesc), "r"(acc)
+      : "memory");
+}
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar) : "memory");
+}
+__device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
+__device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
+
+__global__ void __launch_bounds__(192, 1)
+    k_gemm_tf32x3(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
+                  const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo, int M,
+                  int N, int nkb, void* __restrict__ out, long long ldo, int out_f64, int* __restrict__ err) {
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + STAGES;
+  uint64_t* accf = bars + 2 * STAGES;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    mbar_init(smem_u32(accf), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer
+    int issued = 0;
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % STAGES, it = kb / STAGES;
+      if (it > 0 && !mbar_wait(smem_u32(&empty[s]), (it - 1) & 1)) {
+        *abort_flag = 1;
+        break;
+      }
+      if (*abort_flag) break;
+      uint8_t* st = smem + s * STAGE_BYTES;
+      const uint32_t fb = smem_u32(&full[s]);
+      mbar_expect_tx(fb, STAGE_BYTES);
+      tma_load_2d(smem_u32(st), &tmAhi, fb, kb * BK, m0);
+      tma_load_2d(smem_u32(st + A_TILE), &tmAlo, fb, kb * BK, m0);
+      tma_load_2d(smem_u32(st + 2 * A_TILE), &tmBhi, fb, kb * BK, n0);
+      tma_load_2d(smem_u32(st + 2 * A_TILE + B_TILE), &tmBlo, fb, kb * BK, n0);
+      issued = kb + 1;
+    }
+    if (*abort_flag) {
+      // drain our own copies still in flight (bounded)
+      for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
+        (void)mbar_wait(smem_u32(&full[kb % STAGES]), (kb / STAGES) & 1);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    const uint32_t idesc = idesc_tf32(BM, BN);
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % STAGES, it = kb / STAGES;
+      if (!mbar_wait(smem_u32(&full[s]), it & 1)) {
+        *abort_flag = 1;
+        break;
+      }
+      if (*abort_flag) break;
+      fence_after();
+      const uint32_t a_hi = smem_u32(smem + s * STAGE_BYTES);
+      const uint32_t a_lo = a_hi + A_TILE;
+      const uint32_t b_hi = a_hi + 2 * A_TILE;
+      const uint32_t b_lo = b_hi + B_TILE;
+#pragma unroll
+      for (int k = 0; k < BK / 8; ++k) {
+        const uint32_t off = k * 32;  // 8 tf32 = 32 bytes along K inside the swizzle atom
+        mma_tf32(tmem, sdesc(a_hi + off), sdesc(b_hi + off), idesc, (kb | k) != 0 ? 1u : 0u);
+        mma_tf32(tmem, sdesc(a_hi + off), sdesc(b_lo + off), idesc, 1u);
+        mma_tf32(tmem, sdesc(a_lo + off), sdesc(b_hi + off), idesc, 1u);
+      }
+      mma_commit(smem_u32(&empty[s]));
+    }
+    mma_commit(smem_u32(accf));  // fires when every issued MMA has completed
+  } else if (warp >= 2) {
+    // ---------------- epilogue
+    bool ok = mbar_wait(smem_u32(accf), 0);
+    if (!ok) *abort_flag = 1;
+    ok = __all_sync(0xffffffffu, ok && !*abort_flag);  // keep the .aligned loads warp-uniform
+    fence_after();
+    if (ok) {
+      const int q = warp & 3;
+      const int row = q * 32 + lane;
+      const int gm = m0 + row;
+#pragma unroll 1
+      for (int c0 = 0; c0 < BN; c0 += 16) {
+        uint32_t v[16];
+        asm volatile(
+            "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
+            : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
+              "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
+            : "r"(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+        if (gm < M) {
+#pragma unroll
+          for (int j = 0; j < 16; ++j) {
+            const int gn = n0 + c0 + j;
+            if (gn < N) {
+              const float f = __uint_as_float(v[j]);
+              if (out_f64)
+                static_cast<double*>(out)[(long long)gm * ldo + gn] = (double)f;
+              else
+                static_cast<float*>(out)[(long long)gm * ldo + gn] = f;
+            }
+          }
+        }
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+  if (threadIdx.x == 0 && *abort_flag) atomicExch(err, 1);
+}
+
+// ---------------------------------------------------------------- operand preparation
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+__device__ __forceinline__ void split2(double x, float& hi, float& lo) {
+  hi = to_tf32((float)x);
+  lo = to_tf32((float)(x - (double)hi));
+}
+
+// dst[r][k2] (ld) from complex src[r][c] interleaved; zero for k2 >= 2 cols and
+// for the padding rows r >= rows (up to rows_pad)
+__global__ void k_split_interleaved(const cplx* __restrict__ src, int rows, int rows_pad, int cols, int ld,
+                                    float* __restrict__ hi, float* __restrict__ lo) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)rows_pad * ld) return;
+  const int k2 = e % ld;
+  const long long r = e / ld;
+  float h = 0.f, l = 0.f;
+  if (k2 < 2 * cols && r < rows) {
+    const cplx v = src[r * cols + (k2 >> 1)];
+    split2((k2 & 1) ? v.y : v.x, h, l);
+  }
+  hi[e] = h;
+  lo[e] = l;
+}
+
+// Real expansion of a complex B operand.  Logical complex B[k][n] (k < K, n < Nc);
+// src_kn: stored as src[k*Nc + n], else as src[n*K + k].  dst rows (n, c'), K index (k, c):
+//   (re,re) = Re, (re,im) = -Im, (im,re) = Im, (im,im) = Re.  ld >= 2K, zero padded.
+__global__ void k_expand_b(const cplx* __restrict__ src, int K, int Nc, int src_kn, int ld, int rows_pad,
+                           float* __restrict__ hi, float* __restrict__ lo) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)rows_pad * ld) return;
+  const int k2 = e % ld;
+  const long long n2 = e / ld;
+  float h = 0.f, l = 0.f;
+  if (k2 < 2 * K && n2 < 2LL * Nc) {
+    const int k = k2 >> 1, c = k2 & 1;
+    const long long n = n2 >> 1;
+    const int cp = (int)(n2 & 1);
+    const cplx v = src_kn ? src[(long long)k * Nc + n] : src[n * K + k];
+    double x;
+    if (cp == 0)
+      x = (c == 0) ? v.x : -v.y;
+    else
+      x = (c == 0) ? v.y : v.x;
+    split2(x, h, l);
+  }
+  hi[e] = h;
+  lo[e] = l;
+}
+
+// MPO stage on FP32 T1[a][w][t][b'] (complex) into the split stage-3 A operand
+// T2[(a,s)][(v,b',c)] = sum_{(w,t)} W[w,s,t,v] T1[a,w,t,b'].
+__global__ void k_stage2(const float2* __restrict__ T1, int WL, int WR, int D, int MR, const int* __restrict__ off,
+                         const int* __restrict__ idx, const cplx* __restrict__ val, int ld, float* __restrict__ hi,
+                         float* __restrict__ lo) {
+  const int b = blockIdx.x * blockDim.x + threadIdx.x;
+  const int sv = blockIdx.y;
+  const long long a = blockIdx.z;
+  if (b >= MR) return;
+  const int s = sv / WR, v = sv % WR;
+  double re = 0.0, im = 0.0;
+  for (int e = off[sv]; e < off[sv + 1]; ++e) {
+    const int w = idx[2 * e], t = idx[2 * e + 1];
+    const float2 x = T1[((a * WL + w) * D + t) * MR + b];
+    const cplx c = val[e];
+    re += c.x * (double)x.x - c.y * (double)x.y;
+    im += c.x * (double)x.y + c.y * (double)x.x;
+  }
+  const long long o = (a * D + s) * (long long)ld + 2LL * ((long long)v * MR + b);
+  float h, l;
+  split2(re, h, l);
+  hi[o] = h;
+  lo[o] = l;
+  split2(im, h, l);
+  hi[o + 1] = h;
+  lo[o + 1] = l;
+}
+
+__global__ void k_zero_pad_cols(float* __restrict__ hi, float* __restrict__ lo, int rows, int ld, int from) {
+  const int w = ld - from;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)rows * w) return;
+  const long long r = e / w;
+  const int c = from + (int)(e % w);
+  hi[r * ld + c] = 0.f;
+  lo[r * ld + c] = 0.f;
+}
+
+// ---------------------------------------------------------------- host side
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    cudaDriverEntryPointQueryResult q;
+    void* p = nullptr;
+    TDVP_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
+    tdvp_require(q == cudaDriverEntryPointSuccess && p, TDVP_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
+    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+CUtensorMap make_map(const float* base, int rows, int ld, int box_rows) {
+  tdvp_require((reinterpret_cast<uintptr_t>(base) & 15) == 0, TDVP_ERR_INVALID_ARG, "TMA base not 16B aligned");
+  tdvp_require(ld % 32 == 0, TDVP_ERR_INVALID_ARG, "TMA row length must be a multiple of 32");
+  tdvp_require(rows % box_rows == 0, TDVP_ERR_INVALID_ARG, "TMA operand rows must be padded to the box");
+  CUtensorMap m;
+  std::memset(&m, 0, sizeof(m));
+  cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
+  cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
+  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t estr[2] = {1, 1};
+  CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  tdvp_require(r == CUDA_SUCCESS, TDVP_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
+  return m;
+}
+
+void gemm_tf32x3(cudaStream_t st, const float* Ahi, const float* Alo, const float* Bhi, const float* Blo, int M, int N,
+                 int ldk, void* out, long long ldo, bool out_f64, int* d_err) {
+  static bool attr = false;
+  if (!attr) {
+    TDVP_CUDA(cudaFuncSetAttribute(k_gemm_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    attr = true;
+  }
+  if (M <= 0 || N <= 0) return;
+  tdvp_require(ldk % BK == 0 && ldk > 0, TDVP_ERR_INVALID_ARG, "gemm_tf32x3: K must be padded to 32");
+  // operands hold ceil(M/128)*128 and ceil(N/128)*128 rows (zero padded): no TMA box leaves the buffer
+  const int Mp = ceil_div(M, BM) * BM, Np = ceil_div(N, BN) * BN;
+  const CUtensorMap ma = make_map(Ahi, Mp, ldk, BM), mal = make_map(Alo, Mp, ldk, BM);
+  const CUtensorMap mb = make_map(Bhi, Np, ldk, BN), mbl = make_map(Blo, Np, ldk, BN);
+  dim3 grid(ceil_div(N, BN), ceil_div(M, BM));
+  tdvp_require(grid.y <= 65535, TDVP_ERR_INVALID_ARG, "gemm_tf32x3: M too large");
+  k_gemm_tf32x3<<<grid, 192, SMEM_BYTES, st>>>(ma, mal, mb, mbl, M, N, ldk / BK, out, ldo, out_f64 ? 1 : 0, d_err);
+  TDVP_CHECK_LAUNCH();
+}
+
+inline int pad32(int k) { return (k + 31) / 32 * 32; }
+inline int pad128(int k) { return (k + 127) / 128 * 128; }
+}  // namespace tc
+
+using namespace tc;
+
+void heff_tf32x3(cudaStream_t st, Scratch& s, const SiteOp& op, const cplx* x, cplx* y) {
+  const int ml = op.ml, mr = op.mr, wl = op.wl, wr = op.wr, d = op.d;
+  TcEnvCache& c = s.tc;
+  DevicePool* pool = s.pool;
+  const int M1 = ml * wl, K1p = pad32(2 * ml), N1 = 2 * d * mr;
+  const int M3 = ml * d, K3 = 2 * wr * mr, K3p = pad32(K3), N3 = 2 * mr;
+  if (c.err.bytes() == 0) {
+    c.err.ensure(pool, sizeof(int));
+    TDVP_CUDA(cudaMemsetAsync(c.err.as<int>(), 0, sizeof(int), st));
+  }
+  const int M1p = pad128(M1), N1p = pad128(N1), M3p = pad128(M3), N3p = pad128(N3);
+  if (op.env_key < 0 || c.key != op.env_key) {
+    c.Lhi.ensure(pool, sizeof(float) * (size_t)M1p * K1p);
+    c.Llo.ensure(pool, sizeof(float) * (size_t)M1p * K1p);
+    long long n = (long long)M1p * K1p;
+    k_split_interleaved<<<ceil_div(n, 256), 256, 0, st>>>(op.L, M1, M1p, ml, K1p, c.Lhi.as<float>(),
+                                                          c.Llo.as<float>());
+    TDVP_CHECK_LAUNCH();
+    c.Rhi.ensure(pool, sizeof(float) * (size_t)N3p * K3p);
+    c.Rlo.ensure(pool, sizeof(float) * (size_t)N3p * K3p);
+    n = (long long)N3p * K3p;
+    // R[b][(v,b')] is B[k=(v,b')][n=b] stored n-major
+    k_expand_b<<<ceil_div(n, 256), 256, 0, st>>>(op.R, wr * mr, mr, 0, K3p, N3p, c.Rhi.as<float>(),
+                                                 c.Rlo.as<float>());
+    TDVP_CHECK_LAUNCH();
+    c.key = op.env_key;
+  }
+  // stage 1: T1[(a,w)][(s',b',c)] = L x
+  c.Bhi.ensure(pool, sizeof(float) * (size_t)N1p * K1p);
+  c.Blo.ensure(pool, sizeof(float) * (size_t)N1p * K1p);
+  {
+    const long long n = (long long)N1p * K1p;
+    k_expand_b<<<ceil_div(n, 256), 256, 0, st>>>(x, ml, d * mr, 1, K1p, N1p, c.Bhi.as<float>(), c.Blo.as<float>());
+    TDVP_CHECK_LAUNCH();
+  }
+  c.T1.ensure(pool, sizeof(float) * (size_t)M1 * N1);
+  gemm_tf32x3(st, c.Lhi.as<float>(), c.Llo.as<float>(), c.Bhi.as<float>(), c.Blo.as<float>(), M1, N1, K1p,
+              c.T1.as<float>(), N1, false, c.err.as<int>());
+  // stage 2: MPO tensor
+  c.T2hi.ensure(pool, sizeof(float) * (size_t)M3p * K3p);
+  c.T2lo.ensure(pool, sizeof(float) * (size_t)M3p * K3p);
+  {
+    const WSparse& ws = *op.W;
+    tdvp_require(ml <= 65535, TDVP_ERR_INVALID_ARG, "heff_tc: bond too large");
+    dim3 g(ceil_div(mr, 128), d * wr, ml);
+    k_stage2<<<g, 128, 0, st>>>(c.T1.as<float2>(), wl, wr, d, mr, ws.d_l_off, ws.d_l_idx, ws.d_l_val, K3p,
+                                c.T2hi.as<float>(), c.T2lo.as<float>());
+    TDVP_CHECK_LAUNCH();
+    if (K3p > K3) {
+      const long long n = (long long)M3 * (K3p - K3);
+      k_zero_pad_cols<<<ceil_div(n, 256), 256, 0, st>>>(c.T2hi.as<float>(), c.T2lo.as<float>(), M3, K3p, K3);
+      TDVP_CHECK_LAUNCH();
+    }
+    if (M3p > M3) {
+      const size_t off = (size_t)M3 * K3p, bytes = sizeof(float) * (size_t)(M3p - M3) * K3p;
+      TDVP_CUDA(cudaMemsetAsync(c.T2hi.as<float>() + off, 0, bytes, st));
+      TDVP_CUDA(cudaMemsetAsync(c.T2lo.as<float>() + off, 0, bytes, st));
+    }
+  }
+  // stage 3: y[(a,s)][(b,c)] = T2 R^T  (FP64 output, interleaved complex)
+  gemm_tf32x3(st, c.T2hi.as<float>(), c.T2lo.as<float>(), c.Rhi.as<float>(), c.Rlo.as<float>(), M3, N3, K3p,
+              reinterpret_cast<double*>(y), N3, true, c.err.as<int>());
+  int h_err = 0;
+  TDVP_CUDA(cudaMemcpyAsync(&h_err, c.err.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, st));
+  TDVP_CUDA(cudaStreamSynchronize(st));
+  tdvp_require(h_err == 0, TDVP_ERR_TIMEOUT, "tensor-core GEMM: a bounded pipeline wait ran out");
+}

@@ -1,0 +1,307 @@
+"""Python binding of libgsetdvp.so (C ABI in include/gse_tdvp.h).
+
+Argument marshalling only: every step of GSE-TDVP1 runs in the CUDA library.
+Device buffers are torch CUDA tensors (complex128), host tensors numpy arrays.
+Importing this module loads the library and raises ImportError when it has
+not been built (`python -m paper_2005_06104_gb300.build` or
+`__graft_entry__.build()`); there is no other implementation to fall back to.
+"""
+from __future__ import annotations
+
+import ctypes as C
+import os
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "libgsetdvp.so")
+HEADER = os.path.join(os.path.dirname(HERE), "include", "gse_tdvp.h")
+
+if not os.path.exists(LIB_PATH):
+    raise ImportError(f"{LIB_PATH} is missing: build the CUDA library first")
+_lib = C.CDLL(LIB_PATH)
+
+REAL, IMAG = 0, 1
+PREC_FP64, PREC_TF32X3 = 0, 1
+STATUS = {0: "ok", 1: "invalid argument", 2: "shape mismatch", 3: "out of memory",
+          4: "Lanczos not converged", 5: "non-finite value", 6: "device wait timed out",
+          7: "CUDA error", 8: "SVD not converged"}
+
+
+class TDVPError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Options(C.Structure):
+    _fields_ = [("tau_re", C.c_double), ("tau_im", C.c_double), ("eps_k", C.c_double),
+                ("eps_m", C.c_double), ("eps", C.c_double), ("chi_max", C.c_int),
+                ("lanczos_tol", C.c_double), ("lanczos_max", C.c_int), ("precision", C.c_int)]
+
+
+class _Desc(C.Structure):
+    _fields_ = [("n_sites", C.c_int), ("d", C.c_int), ("bond_dims", C.POINTER(C.c_int)),
+                ("sites", C.POINTER(C.c_void_p))]
+
+
+_h = C.c_void_p
+_sig = {
+    "tdvp_default_options": [C.POINTER(Options)],
+    "tdvp_create": [C.POINTER(_Desc), C.POINTER(_Desc), C.POINTER(Options), C.c_void_p, C.POINTER(_h)],
+    "tdvp_destroy": [_h],
+    "tdvp_set_options": [_h, C.POINTER(Options)],
+    "tdvp_canonicalize": [_h, C.c_int],
+    "tdvp_expand_basis": [_h, C.c_int, C.c_void_p],
+    "tdvp_sweep": [_h, C.c_double, C.c_int],
+    "tdvp_heff_apply": [_h, C.c_int, C.c_void_p, C.c_void_p, C.c_int],
+    "tdvp_keff_apply": [_h, C.c_int, C.c_void_p, C.c_void_p, C.c_int],
+    "tdvp_evolve_site": [_h, C.c_int, C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.c_int,
+                         C.POINTER(C.c_int)],
+    "tdvp_energy": [_h, C.POINTER(C.c_double)],
+    "tdvp_norm": [_h, C.POINTER(C.c_double)],
+    "tdvp_expect_local": [_h, C.c_void_p, C.c_int, C.POINTER(C.c_double)],
+    "tdvp_bond_dims": [_h, C.POINTER(C.c_int)],
+    "tdvp_center": [_h, C.POINTER(C.c_int)],
+    "tdvp_trunc_stats": [_h, C.POINTER(C.c_double)],
+    "tdvp_get_mps": [_h, C.POINTER(C.c_void_p)],
+    "tdvp_profile": [_h, C.c_int],
+    "tdvp_profile_read": [_h, C.POINTER(C.c_double)],
+}
+for _name, _args in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = C.c_int
+_lib.tdvp_last_error.argtypes = [_h]
+_lib.tdvp_last_error.restype = C.c_char_p
+_lib.tdvp_status_string.argtypes = [C.c_int]
+_lib.tdvp_status_string.restype = C.c_char_p
+_lib.tdvp_contract_last_error.argtypes = []
+_lib.tdvp_contract_last_error.restype = C.c_char_p
+
+
+class SiteDims(C.Structure):
+    _fields_ = [("ml", C.c_int), ("mr", C.c_int), ("wl", C.c_int), ("wr", C.c_int), ("d", C.c_int)]
+
+
+_raw = {
+    "tdvp_heff_contract": [C.POINTER(SiteDims), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                           C.c_int, C.c_void_p],
+    "tdvp_keff_contract": [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
+    "tdvp_env_contract": [C.POINTER(SiteDims), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                          C.c_void_p],
+    "tdvp_expm_contract": [C.POINTER(SiteDims), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                           C.c_double, C.c_int, C.c_int, C.c_double, C.c_int, C.POINTER(C.c_int), C.c_void_p],
+}
+for _name, _args in _raw.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = C.c_int
+
+
+def _raw_chk(s):
+    if s != 0:
+        raise TDVPError(s, _lib.tdvp_contract_last_error().decode())
+
+
+def _ptr(t):
+    return C.c_void_p(t.data_ptr())
+
+
+def _host(w):
+    w = np.ascontiguousarray(w, dtype=np.complex128)
+    return w, C.c_void_p(w.ctypes.data)
+
+
+def _stream(stream):
+    return C.c_void_p(stream or 0)
+
+
+def heff_contract(L, W, R, x, y, precision=PREC_FP64, stream=None):
+    """y = H_eff x on caller tensors: L, R, x, y torch CUDA complex128; W numpy [wl, d, d, wr]."""
+    ml, wl, _ = L.shape
+    mr, wr, _ = R.shape
+    d = W.shape[1]
+    Wc, wp = _host(W)
+    _raw_chk(_lib.tdvp_heff_contract(C.byref(SiteDims(ml, mr, wl, wr, d)), _ptr(L), wp, _ptr(R), _ptr(x), _ptr(y),
+                                     precision, _stream(stream)))
+
+
+def keff_contract(L, R, x, y, stream=None):
+    ml, w, _ = L.shape
+    mr = R.shape[0]
+    _raw_chk(_lib.tdvp_keff_contract(ml, mr, w, _ptr(L), _ptr(R), _ptr(x), _ptr(y), _stream(stream)))
+
+
+def env_contract(side, E, W, A, out, stream=None):
+    """side 0: left environment update through site A; side 1: right environment update."""
+    ml, d, mr = A.shape
+    wl, wr = W.shape[0], W.shape[3]
+    Wc, wp = _host(W)
+    _raw_chk(_lib.tdvp_env_contract(C.byref(SiteDims(ml, mr, wl, wr, d)), side, _ptr(E), wp, _ptr(A), _ptr(out),
+                                    _stream(stream)))
+
+
+def expm_contract(L, W, R, x, y, delta, kind=REAL, precision=PREC_FP64, tol=1e-12, nmax=40, stream=None):
+    ml, wl, _ = L.shape
+    mr, wr, _ = R.shape
+    d = W.shape[1]
+    Wc, wp = _host(W)
+    it = C.c_int(0)
+    _raw_chk(_lib.tdvp_expm_contract(C.byref(SiteDims(ml, mr, wl, wr, d)), _ptr(L), wp, _ptr(R), _ptr(x), _ptr(y),
+                                     delta, kind, precision, tol, nmax, C.byref(it), _stream(stream)))
+    return it.value
+
+
+def declared_symbols(header=HEADER):
+    """Names of the entry points include/gse_tdvp.h declares."""
+    import re
+    txt = open(header).read()
+    return sorted(set(re.findall(r"TDVP_API\s+[\w\s\*]+?\b(tdvp_\w+)\s*\(", txt)))
+
+
+def default_options(**kw):
+    o = Options()
+    _lib.tdvp_default_options(C.byref(o))
+    for k, v in kw.items():
+        if k == "tau":
+            v = complex(v)
+            o.tau_re, o.tau_im = v.real, v.imag
+        else:
+            setattr(o, k, v)
+    return o
+
+
+class _Pinned:
+    """Keeps ctypes views of a list of host arrays alive for one call."""
+
+    def __init__(self, arrays, dims):
+        self.arrays = [np.ascontiguousarray(a, dtype=np.complex128) for a in arrays]
+        self.dims = (C.c_int * len(dims))(*dims)
+        self.ptrs = (C.c_void_p * len(self.arrays))(*[a.ctypes.data for a in self.arrays])
+
+    def desc(self, d):
+        return _Desc(len(self.arrays), d, self.dims, self.ptrs)
+
+
+class GseTdvp:
+    """One GSE-TDVP1 state on the GPU (wraps a tdvp_handle)."""
+
+    def __init__(self, mps, mpo, stream=None, **opts):
+        mps_dims = [mps[0].shape[0]] + [a.shape[2] for a in mps]
+        mpo_dims = [mpo[0].shape[0]] + [w.shape[3] for w in mpo]
+        d = mps[0].shape[1]
+        self._m = _Pinned(mps, mps_dims)
+        self._w = _Pinned(mpo, mpo_dims)
+        self.n = len(mps)
+        self.d = d
+        self.opts = default_options(**opts)
+        h = _h()
+        s = _lib.tdvp_create(C.byref(self._m.desc(d)), C.byref(self._w.desc(d)), C.byref(self.opts),
+                             C.c_void_p(stream or 0), C.byref(h))
+        if s != 0:
+            raise TDVPError(s, "tdvp_create failed")
+        self.h = h
+        del self._m, self._w
+
+    def _chk(self, s):
+        if s != 0:
+            raise TDVPError(s, _lib.tdvp_last_error(self.h).decode())
+
+    def close(self):
+        if getattr(self, "h", None):
+            _lib.tdvp_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_options(self, **kw):
+        for k, v in kw.items():
+            if k == "tau":
+                v = complex(v)
+                self.opts.tau_re, self.opts.tau_im = v.real, v.imag
+            else:
+                setattr(self.opts, k, v)
+        self._chk(_lib.tdvp_set_options(self.h, C.byref(self.opts)))
+
+    def canonicalize(self, site):
+        self._chk(_lib.tdvp_canonicalize(self.h, site))
+
+    def expand_basis(self, k, weights=None):
+        w = None
+        if weights is not None:
+            w = (C.c_double * len(weights))(*weights)
+        self._chk(_lib.tdvp_expand_basis(self.h, k, C.cast(w, C.c_void_p) if w is not None else None))
+
+    def sweep(self, dt, kind=REAL):
+        self._chk(_lib.tdvp_sweep(self.h, dt, kind))
+
+    def step(self, dt, kind, k, weights=None):
+        """One GSE-TDVP1 time step: expand (steps 1-2) then sweep (step 3)."""
+        self.expand_basis(k, weights)
+        self.sweep(dt, kind)
+
+    def heff_apply(self, site, x, y, precision=PREC_FP64):
+        self._chk(_lib.tdvp_heff_apply(self.h, site, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                       precision))
+
+    def keff_apply(self, bond, x, y, precision=PREC_FP64):
+        self._chk(_lib.tdvp_keff_apply(self.h, bond, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                       precision))
+
+    def evolve_site(self, site, x, y, delta, kind=REAL, precision=PREC_FP64):
+        it = C.c_int(0)
+        self._chk(_lib.tdvp_evolve_site(self.h, site, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
+                                        delta, kind, precision, C.byref(it)))
+        return it.value
+
+    def energy(self):
+        v = C.c_double()
+        self._chk(_lib.tdvp_energy(self.h, C.byref(v)))
+        return v.value
+
+    def norm(self):
+        v = C.c_double()
+        self._chk(_lib.tdvp_norm(self.h, C.byref(v)))
+        return v.value
+
+    def expect_local(self, op, site):
+        op = np.ascontiguousarray(op, dtype=np.complex128)
+        out = (C.c_double * 2)()
+        self._chk(_lib.tdvp_expect_local(self.h, C.c_void_p(op.ctypes.data), site, out))
+        return complex(out[0], out[1])
+
+    def bond_dims(self):
+        out = (C.c_int * (self.n + 1))()
+        self._chk(_lib.tdvp_bond_dims(self.h, out))
+        return list(out)
+
+    def center(self):
+        v = C.c_int()
+        self._chk(_lib.tdvp_center(self.h, C.byref(v)))
+        return v.value
+
+    def trunc_stats(self):
+        out = (C.c_double * 6)()
+        self._chk(_lib.tdvp_trunc_stats(self.h, out))
+        return dict(disc_k=out[0], disc_m=out[1], disc_eps=out[2], added=int(out[3]),
+                    lanczos_iters=int(out[4]), lanczos_calls=int(out[5]))
+
+    def profile(self, enable=True):
+        self._chk(_lib.tdvp_profile(self.h, 1 if enable else 0))
+
+    def profile_read(self):
+        out = (C.c_double * 3)()
+        self._chk(_lib.tdvp_profile_read(self.h, out))
+        return dict(applies=int(out[0]), ms=out[1], flops=out[2])
+
+    def get_mps(self):
+        m = self.bond_dims()
+        arrs = [np.empty((m[i], self.d, m[i + 1]), dtype=np.complex128) for i in range(self.n)]
+        ptrs = (C.c_void_p * self.n)(*[a.ctypes.data for a in arrs])
+        self._chk(_lib.tdvp_get_mps(self.h, ptrs))
+        return arrs

@@ -1,0 +1,53 @@
+"""The C-ABI library builds, loads and exports every entry point the header declares (no GPU)."""
+import ctypes as C
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+LIB = os.path.join(ROOT, "paper_2005_06104_gb300", "libgsetdvp.so")
+HEADER = os.path.join(ROOT, "include", "gse_tdvp.h")
+
+
+@pytest.fixture(scope="module")
+def lib():
+    if not os.path.exists(LIB):
+        from paper_2005_06104_gb300 import build
+        build.build()
+    return C.CDLL(LIB)
+
+
+def declared():
+    txt = open(HEADER).read()
+    return sorted(set(re.findall(r"TDVP_API\s+[\w\s\*]+?\b(tdvp_\w+)\s*\(", txt)))
+
+
+def test_header_declares_the_boundary():
+    names = declared()
+    for must in ("tdvp_create", "tdvp_destroy", "tdvp_expand_basis", "tdvp_sweep", "tdvp_heff_apply",
+                 "tdvp_energy", "tdvp_norm", "tdvp_expect_local", "tdvp_get_mps", "tdvp_heff_contract"):
+        assert must in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in declared() if not hasattr(lib, n)]
+    assert not missing, missing
+
+
+def test_host_side_argument_checks(lib):
+    lib.tdvp_status_string.restype = C.c_char_p
+    assert lib.tdvp_status_string(0) == b"ok"
+    assert lib.tdvp_status_string(4) == b"Lanczos not converged"
+    # null arguments are rejected before any device work
+    assert lib.tdvp_create(None, None, None, None, None) == 1
+    assert lib.tdvp_default_options(None) == 1
+    assert lib.tdvp_destroy(None) == 1
+
+
+def test_default_options_struct(lib):
+    from paper_2005_06104_gb300 import gse_tdvp as g
+    o = g.default_options(tau=-0.25j, chi_max=77)
+    assert o.chi_max == 77 and o.tau_im == -0.25 and o.tau_re == 0.0
+    assert o.lanczos_tol == 1e-12 and o.lanczos_max == 40 and o.precision == g.PREC_FP64
+    assert g.declared_symbols() == declared()

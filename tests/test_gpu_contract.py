@@ -1,0 +1,164 @@
+"""Kernel-level parity: one-site contractions on the GPU (through the C ABI)
+against the oracle on identical seeded operands.
+
+FP64 results agree to rounding (relative 1e-12, norm-wise).  The split-TF32
+tensor-core form is held to relative 1e-5: each product keeps about 22
+significant bits (hi + lo, the lo*lo term dropped, |x - hi - lo| <= 2^-22 |x|),
+FP32 accumulation adds about 2^-24 sqrt(K) per output, and two GEMMs are
+chained, which bounds the norm-wise error near 3e-6 for these shapes.
+"""
+import numpy as np
+import pytest
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+import oracle as O
+from paper_2005_06104_gb300 import workloads as wl
+
+TOL64 = 1e-12
+TOL_TC = 1e-5
+
+
+@pytest.fixture(scope="module")
+def g():
+    assert torch.cuda.is_available()
+    from paper_2005_06104_gb300 import gse_tdvp
+    return gse_tdvp
+
+
+def _rand(rng, *shape):
+    return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) / np.sqrt(shape[-1])
+
+
+def _dev(*arrs):
+    return [torch.from_numpy(np.ascontiguousarray(a)).cuda() for a in arrs]
+
+
+def _rel(a, b):
+    return np.linalg.norm(a - b) / max(np.linalg.norm(b), 1e-300)
+
+
+W_LADDER = wl.heisenberg_mpo(wl.zigzag_ladder(6, 1.0, 1.0))
+W_CYL = wl.heisenberg_mpo(wl.cylinder_snake(6, 4))
+SHAPES = [  # (ml, mr, W site) -- several tiles with ragged tails, the boundary sites, w = 1
+    (1, 2, W_LADDER[0]), (2, 4, W_LADDER[1]), (37, 45, W_LADDER[5]), (100, 90, W_LADDER[6]),
+    (129, 127, W_LADDER[7]), (96, 160, W_CYL[10]), (64, 1, W_LADDER[-1]),
+]
+
+
+@pytest.mark.parametrize("ml,mr,W", SHAPES, ids=lambda v: str(v) if np.isscalar(v) else "W")
+@pytest.mark.parametrize("prec", ["fp64", "tf32x3"])
+def test_heff_contract_matches_oracle(g, ml, mr, W, prec):
+    rng = np.random.default_rng(ml * 1000 + mr)
+    L = _rand(rng, ml, W.shape[0], ml)
+    R = _rand(rng, mr, W.shape[3], mr)
+    x = _rand(rng, ml, W.shape[1], mr)
+    Ld, Rd, xd = _dev(L, R, x)
+    yd = torch.empty_like(xd)
+    g.heff_contract(Ld, W, Rd, xd, yd, precision=g.PREC_FP64 if prec == "fp64" else g.PREC_TF32X3)
+    ref = O.heff_apply(L, W, R, x)
+    err = _rel(yd.cpu().numpy(), ref)
+    assert err < (TOL64 if prec == "fp64" else TOL_TC), err
+
+
+@pytest.mark.parametrize("ml,mr,w", [(1, 1, 1), (3, 5, 5), (70, 66, 8), (130, 129, 14)])
+def test_keff_contract_matches_oracle(g, ml, mr, w):
+    rng = np.random.default_rng(ml + 7 * mr)
+    L = _rand(rng, ml, w, ml)
+    R = _rand(rng, mr, w, mr)
+    x = _rand(rng, ml, mr)
+    Ld, Rd, xd = _dev(L, R, x)
+    yd = torch.empty_like(xd)
+    g.keff_contract(Ld, Rd, xd, yd)
+    assert _rel(yd.cpu().numpy(), O.keff_apply(L, R, x)) < TOL64
+
+
+@pytest.mark.parametrize("ml,mr,W", SHAPES, ids=lambda v: str(v) if np.isscalar(v) else "W")
+def test_env_updates_match_oracle(g, ml, mr, W):
+    rng = np.random.default_rng(3 * ml + mr)
+    A = _rand(rng, ml, W.shape[1], mr)
+    L = _rand(rng, ml, W.shape[0], ml)
+    R = _rand(rng, mr, W.shape[3], mr)
+    Ad, Ld, Rd = _dev(A, L, R)
+    Lo = torch.empty((mr, W.shape[3], mr), dtype=torch.complex128, device="cuda")
+    Ro = torch.empty((ml, W.shape[0], ml), dtype=torch.complex128, device="cuda")
+    g.env_contract(0, Ld, W, Ad, Lo)
+    g.env_contract(1, Rd, W, Ad, Ro)
+    assert _rel(Lo.cpu().numpy(), O.env_left_step(L, A, W)) < TOL64
+    assert _rel(Ro.cpu().numpy(), O.env_right_step(R, A, W)) < TOL64
+
+
+
+
+@pytest.mark.parametrize("kind", ["real", "imag"])
+@pytest.mark.parametrize("prec", ["fp64", "tf32x3"])
+def test_lanczos_exponential_matches_oracle(g, kind, prec):
+    # environments of a random canonical MPS make H_eff Hermitian, as in the sweep
+    lat = wl.zigzag_ladder(5, 1.0, 1.0)
+    W = wl.heisenberg_mpo(lat)
+    psi = O.right_canonicalize(wl.random_mps(lat.n, 24, 4))
+    c = 4
+    for i in range(c):
+        ml, d, mr = psi[i].shape
+        U, S, Vh, _ = O.svd_truncate(psi[i].reshape(ml * d, mr))
+        psi[i] = U.reshape(ml, d, -1)
+        psi[i + 1] = np.tensordot(S[:, None] * Vh, psi[i + 1], axes=([1], [0]))
+    Ls, Rs = O.build_envs(psi, W, c)
+    x = psi[c]
+    delta = 0.05 if kind == "real" else 0.1
+    ref, it_ref = O.lanczos_expm(lambda v: O.heff_apply(Ls[c], W[c], Rs[c], v), x, delta, kind)
+    Ld, Rd, xd = _dev(Ls[c], Rs[c], x)
+    yd = torch.empty_like(xd)
+    it = g.expm_contract(Ld, W[c], Rd, xd, yd, delta, kind=g.REAL if kind == "real" else g.IMAG,
+                         precision=g.PREC_FP64 if prec == "fp64" else g.PREC_TF32X3)
+    err = _rel(yd.cpu().numpy(), ref)
+    if prec == "fp64":
+        assert err < 1e-11 and it == it_ref
+    else:
+        assert err < TOL_TC and abs(it - it_ref) <= 2
+
+
+def test_lanczos_nonconvergence_is_reported(g):
+    rng = np.random.default_rng(9)
+    W = W_LADDER[5]
+    L = _rand(rng, 30, W.shape[0], 30)
+    L = L + L.conj().transpose(2, 1, 0)
+    R = _rand(rng, 30, W.shape[3], 30)
+    R = R + R.conj().transpose(2, 1, 0)
+    x = _rand(rng, 30, 2, 30)
+    Ld, Rd, xd = _dev(L, R, x)
+    yd = torch.empty_like(xd)
+    with pytest.raises(g.TDVPError) as e:
+        g.expm_contract(Ld, W, Rd, xd, yd, 5.0, nmax=2)
+    assert e.value.status == 4
+
+
+def test_heff_full_size_sampled(g):
+    """chi = 1024, w = 14 (the 4-wide cylinder's widest MPO site): sampled outputs of
+    the tensor-core and FP64 applies against the oracle's entry-by-entry definition."""
+    W = max(W_CYL, key=lambda w: w.shape[0] * w.shape[3])
+    assert W.shape[0] == 14 and W.shape[3] == 14
+    m = 1024
+    gen = torch.Generator(device="cuda").manual_seed(5)
+
+    def rnd(*shape):
+        return torch.complex(torch.randn(*shape, generator=gen, device="cuda", dtype=torch.float64),
+                             torch.randn(*shape, generator=gen, device="cuda", dtype=torch.float64)) / np.sqrt(shape[-1])
+    Ld, Rd, xd = rnd(m, 14, m), rnd(m, 14, m), rnd(m, 2, m)
+    y64 = torch.empty_like(xd)
+    ytc = torch.empty_like(xd)
+    g.heff_contract(Ld, W, Rd, xd, y64, precision=g.PREC_FP64)
+    g.heff_contract(Ld, W, Rd, xd, ytc, precision=g.PREC_TF32X3)
+    L, R, x = Ld.cpu().numpy(), Rd.cpu().numpy(), xd.cpu().numpy()
+    rng = np.random.default_rng(1)
+    entries = [(int(rng.integers(m)), int(rng.integers(2)), int(rng.integers(m))) for _ in range(12)]
+    entries += [(0, 0, 0), (m - 1, 1, m - 1), (127, 1, 128), (128, 0, 1023)]
+    ref = O.heff_apply_entries(L, W, R, x, entries)
+    got64 = np.array([y64[a, s, b].item() for a, s, b in entries])
+    gottc = np.array([ytc[a, s, b].item() for a, s, b in entries])
+    scale = np.linalg.norm(ref) / np.sqrt(len(ref))
+    assert np.max(np.abs(got64 - ref)) < 1e-11 * scale
+    assert np.max(np.abs(gottc - ref)) < 3e-5 * scale
+    # the whole output: the two GPU forms agree norm-wise
+    assert (torch.linalg.norm(ytc - y64) / torch.linalg.norm(y64)).item() < TOL_TC
