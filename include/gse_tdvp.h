@@ -104,7 +104,7 @@ TDVP_API const char* tdvp_last_error(const tdvp_handle* h);
 TDVP_API const char* tdvp_status_string(tdvp_status s);
 
 /* Moves the orthogonality centre to `site` by exact gauge moves (SVDs that keep
- * every singular value above 1e-14 s_max) and builds the environments L_site and
+ * every singular value above 1e-12 s_max) and builds the environments L_site and
  * R_site.  The state is unchanged. */
 TDVP_API tdvp_status tdvp_canonicalize(tdvp_handle* h, int site);
 
@@ -115,6 +115,12 @@ TDVP_API tdvp_status tdvp_canonicalize(tdvp_handle* h, int site);
  * weights: k-1 host doubles (w_l in rho~ = sum_l w_l C~_l^+ C~_l) or NULL for
  * all ones.  k = 1 only moves the centre to site 0.  The state is unchanged. */
 TDVP_API tdvp_status tdvp_expand_basis(tdvp_handle* h, int k, const double* weights);
+
+/* One Krylov vector in place (Eq. 10 with l = 1, Sec. I.B): the state becomes
+ * (1 - i tau H)|psi>, applied by the density-matrix approach with cutoff eps_k
+ * and cap chi_max, normalised, left-canonical with the centre at site N-1.
+ * (tdvp_expand_basis builds its Krylov vectors with the same routine.) */
+TDVP_API tdvp_status tdvp_apply_krylov(tdvp_handle* h);
 
 /* GSE step 3 (Sec. I.C): one symmetric one-site TDVP sweep, left to right then
  * right to left, each with time step dt/2.  kind = TDVP_REAL applies

@@ -126,6 +126,10 @@ tdvp_status tdvp_expand_basis(tdvp_handle* h, int k, const double* weights) {
   return guarded(h, [&] { h->eng.expand_basis(k, weights); });
 }
 
+tdvp_status tdvp_apply_krylov(tdvp_handle* h) {
+  return guarded(h, [&] { h->eng.apply_krylov(); });
+}
+
 tdvp_status tdvp_sweep(tdvp_handle* h, double dt, tdvp_time kind) {
   return guarded(h, [&] {
     tdvp_require(std::isfinite(dt), TDVP_ERR_INVALID_ARG, "dt not finite");
@@ -145,6 +149,7 @@ tdvp_status tdvp_heff_apply(tdvp_handle* h, int site, const void* x, void* y, in
     e.ensure_R(site);
     e.heff(site, static_cast<const cplx*>(x), static_cast<cplx*>(y), precision);
     e.sync();
+    tc_check(e.st, e.scr);
   });
 }
 
@@ -356,6 +361,7 @@ tdvp_status tdvp_heff_contract(const tdvp_site_dims* dims, const void* L, const 
     heff_apply_prec(st, c.scr, op, static_cast<const cplx*>(x), static_cast<cplx*>(y), precision);
     TDVP_CUDA(cudaStreamSynchronize(st));
     w.free_device();
+    tc_check(st, c.scr);
   });
 }
 
@@ -421,10 +427,12 @@ tdvp_status tdvp_expm_contract(const tdvp_site_dims* dims, const void* L, const 
           static_cast<const cplx*>(x), static_cast<cplx*>(y), n, delta, kind, tol, nmax);
     } catch (...) {
       w.free_device();
+      tc_check(st, c.scr);
       throw;
     }
     TDVP_CUDA(cudaStreamSynchronize(st));
     w.free_device();
+    tc_check(st, c.scr);
     if (iters) *iters = it;
   });
 }

@@ -31,6 +31,9 @@ double heff_flops(const SiteOp& op);
 void heff_fp64(cudaStream_t st, Scratch& s, const SiteOp& op, const cplx* x, cplx* y);
 void heff_tf32x3(cudaStream_t st, Scratch& s, const SiteOp& op, const cplx* x, cplx* y);
 void heff_apply_prec(cudaStream_t st, Scratch& s, const SiteOp& op, const cplx* x, cplx* y, int precision);
+// Reads the tensor-core error word of the launches since the last check (synchronises);
+// throws TDVP_ERR_TIMEOUT when a bounded device wait ran out.
+void tc_check(cudaStream_t st, Scratch& s);
 
 // y[a,c] = sum L[a,w,a'] x[a',b'] R[c,w,b']   (x: ml x mr; L: ml x w x ml; R: mr x w x mr)
 void keff_fp64(cudaStream_t st, Scratch& s, const cplx* L, int ml, const cplx* R, int mr, int w, const cplx* x,

@@ -9,9 +9,9 @@
 #include "engine.cuh"
 
 namespace {
-constexpr double kRankRtol = 1e-14;     // "SVD without truncation": keep s > 1e-14 s_max
+constexpr double kRankRtol = 1e-12;     // "SVD without truncation": keep s > 1e-12 s_max
 constexpr double kClusterRtol = 1e-8;   // never split a cluster of near-equal weights
-constexpr double kEigFloorRtol = 1e-14; // mixed density-matrix eigenvalues <= 1e-14 tr never count
+constexpr double kEigFloorRtol = 1e-12; // mixed density-matrix eigenvalues <= 1e-12 tr never count
 constexpr double kBreakdown = 1e-13;    // Lanczos invariant-subspace threshold
 const cplx kOne = {1.0, 0.0};
 const cplx kZero = {0.0, 0.0};
@@ -99,6 +99,26 @@ __global__ void k_apply_op_site(const cplx* __restrict__ op, const cplx* __restr
 }
 
 __global__ void k_one(cplx* p) { p[0] = mkc(1.0, 0.0); }
+
+// Right density environment, last stage:
+// F[w][a][wb][ab] = sum_{(t,v,tb,vb)} Om[(w,wb),(t,v,tb,vb)] T2[v][a][t][vb][ab][tb],
+// Om[(w,wb),(t,v,tb,vb)] = sum_s W[w,s,t,v] conj(W[wb,s,tb,vb]).
+__global__ void k_omega_stage(const cplx* __restrict__ T2, cplx* __restrict__ F, int ml, int d, int wl, int wr,
+                              const int* __restrict__ off, const int* __restrict__ idx,
+                              const cplx* __restrict__ val) {
+  const int ab = blockIdx.x * blockDim.x + threadIdx.x;
+  const int pr = blockIdx.y;  // w * wl + wb
+  const long long a = blockIdx.z;
+  if (ab >= ml) return;
+  cplx acc = mkc(0.0, 0.0);
+  for (int e = off[pr]; e < off[pr + 1]; ++e) {
+    const int t = idx[4 * e], v = idx[4 * e + 1], tb = idx[4 * e + 2], vb = idx[4 * e + 3];
+    const long long o = (((((long long)v * ml + a) * d + t) * wr + vb) * ml + ab) * d + tb;
+    cfma(acc, val[e], T2[o]);
+  }
+  const int w = pr / wl, wb = pr % wl;
+  F[(((long long)w * ml + a) * wl + wb) * ml + ab] = acc;
+}
 }  // namespace
 
 // ============================================================================
@@ -338,7 +358,14 @@ void Engine::canonicalize(int c) {
 // ============================================================================
 int Engine::lanczos(const std::function<void(const cplx*, cplx*)>& op, const cplx* x, cplx* out,
                     long long n, double delta, int kind) {
-  const int used = lanczos_expm(st, &pool, blas, lw, op, x, out, n, delta, kind, opt.lanczos_tol, opt.lanczos_max);
+  int used = 0;
+  try {
+    used = lanczos_expm(st, &pool, blas, lw, op, x, out, n, delta, kind, opt.lanczos_tol, opt.lanczos_max);
+  } catch (...) {
+    tc_check(st, scr);  // a device timeout explains a failure better than what followed it
+    throw;
+  }
+  tc_check(st, scr);
   lanczos_iters += used;
   lanczos_calls += 1;
   return used;
@@ -476,6 +503,152 @@ std::vector<cplx> one_minus_itau_h_site(const std::vector<cplx>& W, int i, int N
 }
 }  // namespace
 
+void Engine::build_krylov_op(KrylovOp& kop) {
+  kop.Wsp.resize(N);
+  kop.om_off.resize(N);
+  kop.om_idx.resize(N);
+  kop.om_val.resize(N);
+  for (int i = 0; i < N; ++i) {
+    const int wl = w[i], wr = w[i + 1];
+    auto h = one_minus_itau_h_site(W_host[i], i, N, wl, wr, d, opt.tau_re, opt.tau_im);
+    kop.Wsp[i].build(h.data(), wl, wr, d);
+    kop.Wsp[i].upload();
+    // Om[(w,wb),(t,v,tb,vb)] = sum_s W[w,s,t,v] conj(W[wb,s,tb,vb]), kept where nonzero
+    std::vector<int> off(wl * wl + 1, 0), idx;
+    std::vector<cplx> val;
+    auto at = [&](int ww, int s_, int t, int v) { return h[((ww * d + s_) * d + t) * wr + v]; };
+    for (int ww = 0; ww < wl; ++ww)
+      for (int wb = 0; wb < wl; ++wb) {
+        for (int t = 0; t < d; ++t)
+          for (int v = 0; v < wr; ++v)
+            for (int tb = 0; tb < d; ++tb)
+              for (int vb = 0; vb < wr; ++vb) {
+                cplx acc = mkc(0.0, 0.0);
+                for (int s_ = 0; s_ < d; ++s_) cfma_conj(acc, at(wb, s_, tb, vb), at(ww, s_, t, v));
+                if (acc.x != 0.0 || acc.y != 0.0) {
+                  idx.insert(idx.end(), {t, v, tb, vb});
+                  val.push_back(acc);
+                }
+              }
+        off[ww * wl + wb + 1] = (int)val.size();
+      }
+    auto up = [&](auto& vec, auto** dst) {
+      using T = typename std::remove_reference<decltype(vec)>::type::value_type;
+      TDVP_CUDA(cudaMalloc((void**)dst, std::max<size_t>(1, vec.size()) * sizeof(T)));
+      if (!vec.empty())
+        TDVP_CUDA(cudaMemcpy(*dst, vec.data(), vec.size() * sizeof(T), cudaMemcpyHostToDevice));
+    };
+    up(off, &kop.om_off[i]);
+    up(idx, &kop.om_idx[i]);
+    up(val, &kop.om_val[i]);
+  }
+}
+
+void KrylovOp::release() {
+  for (auto& ws : Wsp) ws.free_device();
+  for (auto* p : om_off) cudaFree(p);
+  for (auto* p : om_idx) cudaFree(p);
+  for (auto* p : om_val) cudaFree(p);
+  om_off.clear();
+  om_idx.clear();
+  om_val.clear();
+  Wsp.clear();
+}
+
+// One Krylov vector by the density-matrix approach (Sec. I.B): out = (1 - i tau H) src
+// compressed left to right with cutoff eps_k and cap chi_max, then normalised.
+// R->L: right density environments F_i[v][b][vb][bb] of (W src)(W src)^+ over sites > i.
+// L->R: X[at][w][a] = <compressed left | exact left>; at site i
+//   G[(at,s),(v,b)] = sum W[w,s,t,v] X[at,w,a] A[a,t,b],  rho = G F_i G^+ (size d m~),
+//   its leading eigenvectors are the new left-orthonormal tensor, X <- U^+ G.
+// This reaches, up to ties, the state of exact application followed by a
+// right-canonical sweep and left-to-right SVD truncation.
+void Engine::krylov_apply(const KrylovOp& kop, const MpsDev& src, MpsDev& out) {
+  const cplx one = mkc(1.0, 0.0), zero = mkc(0.0, 0.0);
+  std::vector<DArr> F(N);
+  F[N - 1].reset(&pool, 1);
+  k_one<<<1, 1, 0, st>>>(F[N - 1].data());
+  TDVP_CHECK_LAUNCH();
+  DArr T1, T2;
+  for (int i = N - 1; i >= 1; --i) {
+    const int ml = src.m[i], m = src.m[i + 1], wl = w[i], wr = w[i + 1];
+    const cplx* A = src.A[i].data();
+    T1.ensure(&pool, (size_t)wr * ml * d * wr * m);
+    // T1[v][(a,t)][(vb,bb)] = sum_b A[(a,t),b] F[v][b][(vb,bb)]
+    zgemm(st, OP_N, OP_N, ml * d, wr * m, m, one, A, m, F[i].data(), (long long)wr * m, zero, T1.data(),
+          (long long)wr * m, wr, 0, (long long)m * wr * m, (long long)ml * d * wr * m);
+    // T2[(v,a,t,vb),(ab,tb)] = sum_bb T1[(v,a,t,vb),bb] conj(A[(ab,tb),bb])
+    T2.ensure(&pool, (size_t)wr * ml * d * wr * ml * d);
+    zgemm(st, OP_N, OP_C, wr * ml * d * wr, ml * d, m, one, T1.data(), m, A, m, zero, T2.data(), ml * d);
+    F[i - 1].reset(&pool, (size_t)wl * ml * wl * ml);
+    tdvp_require(ml <= 65535, TDVP_ERR_INVALID_ARG, "krylov: bond too large");
+    dim3 g(ceil_div(ml, 128), wl * wl, ml);
+    k_omega_stage<<<g, 128, 0, st>>>(T2.data(), F[i - 1].data(), ml, d, wl, wr, kop.om_off[i], kop.om_idx[i],
+                                      kop.om_val[i]);
+    TDVP_CHECK_LAUNCH();
+  }
+  T1.release();
+  T2.release();
+  out.N = N;
+  out.d = d;
+  out.m.assign(N + 1, 1);
+  out.A.clear();
+  out.A.resize(N);
+  DArr X(&pool, 1), Y1, G, H1, rho;
+  k_one<<<1, 1, 0, st>>>(X.data());
+  TDVP_CHECK_LAUNCH();
+  int mt = 1;
+  for (int i = 0; i < N; ++i) {
+    const int ml = src.m[i], mr = src.m[i + 1], wl = w[i], wr = w[i + 1];
+    Y1.ensure(&pool, (size_t)mt * wl * d * mr);
+    zgemm(st, OP_N, OP_N, mt * wl, d * mr, ml, one, X.data(), ml, src.A[i].data(), d * mr, zero, Y1.data(), d * mr);
+    G.ensure(&pool, (size_t)mt * d * wr * mr);
+    wstage_left(st, kop.Wsp[i], Y1.data(), G.data(), mt, mr);  // G[at][s][v][b]
+    if (i == N - 1) {
+      out.A[i].reset(&pool, (size_t)mt * d);
+      TDVP_CUDA(cudaMemcpyAsync(out.A[i].data(), G.data(), sizeof(cplx) * mt * d, cudaMemcpyDeviceToDevice, st));
+      out.m[i] = mt;
+      break;
+    }
+    const int n = mt * d, K = wr * mr;
+    H1.ensure(&pool, (size_t)n * K);
+    zgemm(st, OP_N, OP_N, n, K, K, one, G.data(), K, F[i].data(), K, zero, H1.data(), K);
+    rho.ensure(&pool, (size_t)n * n);
+    zgemm(st, OP_N, OP_C, n, n, K, one, H1.data(), K, G.data(), K, zero, rho.data(), n);
+    F[i].release();
+    // eigen-decomposition of the Hermitian PSD rho through its SVD (singular values = eigenvalues)
+    const double eps_k = opt.eps_k;
+    const int cap = opt.chi_max;
+    double* disc = &disc_k;
+    auto rule = [eps_k, cap, disc](const std::vector<double>& ev) -> int {
+      double tot = 0.0;
+      for (double v : ev) tot += v;
+      if (!(tot > 0.0)) return 0;
+      const int nk = keep_count(ev, tot, eps_k, cap, 1e-14 * ev[0]);
+      double ds = 0.0;
+      for (size_t q = nk; q < ev.size(); ++q) ds += ev[q];
+      *disc += ds / tot;
+      return nk;
+    };
+    SvdOut sv;
+    svd_jacobi(st, &pool, rho.data(), n, n, rule, sv, true, false);
+    const int keep = std::max(1, sv.rank);
+    tdvp_require(sv.rank >= 1, TDVP_ERR_NONFINITE, "krylov: zero density matrix");
+    // X <- U^+ G  : [keep][v][b]
+    DArr Xn(&pool, (size_t)keep * K);
+    zgemm(st, OP_C, OP_N, keep, K, n, one, sv.U.data(), keep, G.data(), K, zero, Xn.data(), K);
+    out.A[i] = std::move(sv.U);  // (mt d) x keep  = [at][s][new]
+    out.m[i] = mt;
+    out.m[i + 1] = keep;
+    X = std::move(Xn);
+    mt = keep;
+  }
+  out.m[N] = 1;
+  const long long n = (long long)out.m[N - 1] * d;
+  blas.norm2(st, out.A[N - 1].data(), n, lw.real + 150);
+  scale_by_inv_sqrt(st, out.A[N - 1].data(), out.A[N - 1].data(), lw.real + 150, n);
+}
+
 void Engine::expand_basis(int k, const double* weights) {
   tdvp_require(k >= 1 && k <= 16, TDVP_ERR_INVALID_ARG, "krylov order k must be in 1..16");
   disc_k = disc_m = 0.0;
@@ -493,77 +666,10 @@ void Engine::expand_basis(int k, const double* weights) {
       wts[l] = weights[l];
     }
   // ---- step 1: |psi~_l> = (1 - i tau H)^l |psi>, compressed (eps_k, chi_max), normalised
-  std::vector<DArr> Wk(N);
-  for (int i = 0; i < N; ++i) {
-    auto h = one_minus_itau_h_site(W_host[i], i, N, w[i], w[i + 1], d, opt.tau_re, opt.tau_im);
-    Wk[i].reset(&pool, h.size());
-    TDVP_CUDA(cudaMemcpyAsync(Wk[i].data(), h.data(), h.size() * sizeof(cplx), cudaMemcpyHostToDevice, st));
-    TDVP_CUDA(cudaStreamSynchronize(st));
-  }
+  KrylovOp kop;
+  build_krylov_op(kop);
   std::vector<MpsDev> phis(k - 1);
-  const MpsDev* prev = &psi;
-  for (int l = 0; l < k - 1; ++l) {
-    MpsDev& ph = phis[l];
-    ph.N = N;
-    ph.d = d;
-    ph.m.resize(N + 1);
-    ph.A.resize(N);
-    for (int i = 0; i <= N; ++i) ph.m[i] = prev->m[i] * w[i];
-    for (int i = 0; i < N; ++i) {
-      const int ml = prev->m[i], mr = prev->m[i + 1];
-      const long long tot = (long long)ml * w[i] * d * mr * w[i + 1];
-      ph.A[i].reset(&pool, tot);
-      k_apply_mpo_site<<<ceil_div(tot, 256), 256, 0, st>>>(Wk[i].data(), prev->A[i].data(), ml, w[i], d, mr,
-                                                           w[i + 1], ph.A[i].data());
-      TDVP_CHECK_LAUNCH();
-    }
-    // right-canonicalise (numerical rank only), then cut left to right
-    for (int i = N - 1; i >= 1; --i) {
-      const int ml = ph.m[i], mr = ph.m[i + 1], ml0 = ph.m[i - 1];
-      SvdOut sv;
-      svd_jacobi(st, &pool, ph.A[i].data(), ml, d * mr, SvdRule{}, sv, true, true);
-      const int r = std::max(1, sv.rank);
-      DArr C(&pool, (size_t)ml * r);
-      double* d_s = nullptr;
-      TDVP_CUDA(cudaMallocAsync(&d_s, sizeof(double) * r, st));
-      TDVP_CUDA(cudaMemcpyAsync(d_s, sv.s.data(), sizeof(double) * r, cudaMemcpyHostToDevice, st));
-      scale_cols(st, C.data(), sv.U.data(), d_s, ml, r);
-      TDVP_CUDA(cudaFreeAsync(d_s, st));
-      DArr prv(&pool, (size_t)ml0 * d * r);
-      zgemm(st, OP_N, OP_N, ml0 * d, r, ml, kOne, ph.A[i - 1].data(), ml, C.data(), r, kZero, prv.data(), r);
-      ph.A[i] = std::move(sv.Vh);
-      ph.A[i - 1] = std::move(prv);
-      ph.m[i] = r;
-    }
-    for (int i = 0; i + 1 < N; ++i) {
-      const int ml = ph.m[i], mr = ph.m[i + 1], mr2 = ph.m[i + 2];
-      SvdRule rule;
-      rule.eps = opt.eps_k;
-      rule.cap = opt.chi_max;
-      rule.discarded = &disc_k;
-      SvdOut sv;
-      svd_jacobi(st, &pool, ph.A[i].data(), ml * d, mr, rule, sv, true, true);
-      const int r = std::max(1, sv.rank);
-      DArr C(&pool, (size_t)r * mr);
-      double* d_s = nullptr;
-      TDVP_CUDA(cudaMallocAsync(&d_s, sizeof(double) * r, st));
-      TDVP_CUDA(cudaMemcpyAsync(d_s, sv.s.data(), sizeof(double) * r, cudaMemcpyHostToDevice, st));
-      scale_rows(st, C.data(), sv.Vh.data(), d_s, r, mr);
-      TDVP_CUDA(cudaFreeAsync(d_s, st));
-      DArr nxt(&pool, (size_t)r * d * mr2);
-      zgemm(st, OP_N, OP_N, r, d * mr2, mr, kOne, C.data(), mr, ph.A[i + 1].data(), d * mr2, kZero, nxt.data(),
-            d * mr2);
-      ph.A[i] = std::move(sv.U);
-      ph.A[i + 1] = std::move(nxt);
-      ph.m[i + 1] = r;
-    }
-    {
-      const long long n = (long long)ph.m[N - 1] * d;
-      blas.norm2(st, ph.A[N - 1].data(), n, lw.real + 150);
-      scale_by_inv_sqrt(st, ph.A[N - 1].data(), ph.A[N - 1].data(), lw.real + 150, n);
-    }
-    prev = &ph;
-  }
+  for (int l = 0; l < k - 1; ++l) krylov_apply(kop, l == 0 ? psi : phis[l - 1], phis[l]);
   // ---- step 2: basis extension, right to left (Eqs. 3, 5-7)
   const int nk = k - 1;
   for (int i = N - 1; i >= 1; --i) {
@@ -662,7 +768,23 @@ void Engine::expand_basis(int k, const double* weights) {
     psi.A[i - 1] = std::move(prv);
     psi.m[i] = mnew;
   }
+  kop.release();
   center = 0;
+  for (int j = 0; j < N; ++j) Lok[j] = Rok[j] = 0;
+  sync();
+}
+
+void Engine::apply_krylov() {
+  canonicalize(N - 1);
+  KrylovOp kop;
+  build_krylov_op(kop);
+  MpsDev out;
+  disc_k = 0.0;
+  krylov_apply(kop, psi, out);
+  kop.release();
+  psi.m = out.m;
+  for (int i = 0; i < N; ++i) psi.A[i] = std::move(out.A[i]);
+  center = N - 1;
   for (int j = 0; j < N; ++j) Lok[j] = Rok[j] = 0;
   sync();
 }

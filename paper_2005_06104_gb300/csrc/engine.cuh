@@ -17,7 +17,18 @@ struct MpsDev {
   std::vector<DArr> A;       // A[i]: m[i] x d x m[i+1]
 };
 
+// MPO of 1 - i tau H on the device (sparse lists for the site stage and the
+// products Om = W conj(W) for the density environments).
+struct KrylovOp {
+  std::vector<WSparse> Wsp;
+  std::vector<int*> om_off, om_idx;
+  std::vector<cplx*> om_val;
+  void release();
+};
+
 struct Engine {
+  // declared first so it is destroyed last: every DArr below returns its block here
+  DevicePool pool;
   // problem
   int N = 0, d = 2;
   std::vector<int> w;                    // MPO bond dims
@@ -27,7 +38,6 @@ struct Engine {
   int center = 0;
   tdvp_options opt{};
   cudaStream_t st = nullptr;
-  DevicePool pool;
   Blas1 blas;
   int sm_count = 148;
   // environments: L[i] = sites < i (m_i x w_i x m_i); R[i] = sites > i (m_{i+1} x w_{i+1} x m_{i+1})
@@ -70,6 +80,9 @@ struct Engine {
   // algorithm steps
   void sweep(double dt, int kind);
   void expand_basis(int k, const double* weights);
+  void build_krylov_op(KrylovOp& kop);
+  void krylov_apply(const KrylovOp& kop, const MpsDev& src, MpsDev& out);
+  void apply_krylov();  // state <- normalised, compressed (1 - i tau H) state
   // observables
   double energy();
   double norm();

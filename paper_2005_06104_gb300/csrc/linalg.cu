@@ -665,8 +665,13 @@ __device__ __forceinline__ void rr_pair(int round, int k, int qpad, int& P, int&
 
 // Rotation from a = |x_p|^2, b = |x_q|^2, c = x_p^H x_q:
 //   x_p' = cs x_p - sn e^{-i phi} x_q,  x_q' = sn e^{i phi} x_p + cs x_q,  c = |c| e^{i phi}
-__device__ __forceinline__ bool jacobi_params(double a, double b, cplx c, double tol, double& cs,
-                                              cplx& sne) {
+// Pairs whose larger column is below floor2 (1e-32 |M|_F^2, i.e. numerically zero next
+// to the matrix) or whose smaller column is negligible next to the larger one
+// are left alone: rotating rounding noise never converges.
+__device__ __forceinline__ bool jacobi_params(double a, double b, cplx c, double tol, double floor2,
+                                              double& cs, cplx& sne) {
+  const double big = fmax(a, b), small = fmin(a, b);
+  if (big <= floor2 || small <= 1e-32 * big) return false;
   const double ac = sqrt(cabs2(c));
   if (!(ac > tol * sqrt(a * b)) || ac == 0.0) return false;
   const double zeta = (b - a) / (2.0 * ac);
@@ -700,18 +705,14 @@ __global__ void k_svd_prepare(const cplx* __restrict__ M, int rows, int cols, in
   }
 }
 
-// Large path: one block per pair.
-__global__ void __launch_bounds__(256)
-    k_jacobi_round(cplx* __restrict__ X, cplx* __restrict__ V, int p, int q, int qpad, int round,
-                   double tol, int want_v, int* __restrict__ rotated) {
+// One pair (P, Q) rotated by a whole block; returns true when a rotation was applied.
+__device__ bool jacobi_pair_block(cplx* __restrict__ X, cplx* __restrict__ V, int p, int q, int P, int Q,
+                                  double tol, double floor2, int want_v) {
   __shared__ double ra[8], rb[8];
   __shared__ cplx rc[8];
   __shared__ double s_cs;
   __shared__ cplx s_sne;
   __shared__ int s_do;
-  int P, Q;
-  rr_pair(round, blockIdx.x, qpad, P, Q);
-  if (Q >= q) return;
   cplx* xp = X + (long long)P * p;
   cplx* xq = X + (long long)Q * p;
   double a = 0.0, b = 0.0;
@@ -742,15 +743,16 @@ __global__ void __launch_bounds__(256)
     }
     double cs;
     cplx sne;
-    s_do = jacobi_params(A, B, Cc, tol, cs, sne) ? 1 : 0;
+    s_do = jacobi_params(A, B, Cc, tol, floor2, cs, sne) ? 1 : 0;
     s_cs = cs;
     s_sne = sne;
-    if (s_do) *rotated = 1;
   }
   __syncthreads();
-  if (!s_do) return;
+  const int doit = s_do;
   const double cs = s_cs;
   const cplx sne = s_sne;
+  __syncthreads();  // the shared slots are reused by the next pair
+  if (!doit) return false;
   for (int r = threadIdx.x; r < p; r += blockDim.x) {
     cplx u = xp[r], v = xq[r];
     rotate_pair(u, v, cs, sne);
@@ -767,12 +769,102 @@ __global__ void __launch_bounds__(256)
       vq[r] = v;
     }
   }
+  return true;
+}
+
+// Large path, one launch per round: one block per pair.
+__global__ void __launch_bounds__(256)
+    k_jacobi_round(cplx* __restrict__ X, cplx* __restrict__ V, int p, int q, int qpad, int round,
+                   double tol, const double* __restrict__ fro2, int want_v, int* __restrict__ rotated) {
+  int P, Q;
+  rr_pair(round, blockIdx.x, qpad, P, Q);
+  if (Q >= q) return;
+  if (jacobi_pair_block(X, V, p, q, P, Q, tol, 1e-32 * (*fro2), want_v) && threadIdx.x == 0) *rotated = 1;
+}
+
+// Grid-wide barrier for the cooperative path (all blocks co-resident by cooperative
+// launch).  Every wait is bounded: after 2 s the barrier records an error and
+// returns false, and the kernel unwinds.
+struct GridBar {
+  unsigned count;
+  unsigned gen;
+  int err;
+  int rot[3];
+};
+
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+
+__device__ bool grid_sync(GridBar* b, unsigned nblocks) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    volatile unsigned* vgen = &b->gen;
+    volatile int* verr = &b->err;
+    const unsigned g = *vgen;
+    __threadfence();
+    const unsigned arrived = atomicAdd(&b->count, 1u);
+    if (arrived == nblocks - 1) {
+      atomicExch(&b->count, 0u);
+      __threadfence();
+      atomicAdd(&b->gen, 1u);
+    } else {
+      const unsigned long long t0 = gtimer();
+      while (*vgen == g) {
+        if (*verr) {
+          ok = 0;
+          break;
+        }
+        if (gtimer() - t0 > 2000000000ull) {
+          atomicExch(&b->err, 1);
+          ok = 0;
+          break;
+        }
+      }
+    }
+    __threadfence();
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// Medium path: one cooperative launch runs every sweep; blocks stride over the
+// pairs of a round and meet at a grid barrier between rounds.
+__global__ void __launch_bounds__(256)
+    k_jacobi_coop(cplx* __restrict__ X, cplx* __restrict__ V, int p, int q, int qpad, double tol,
+                  const double* __restrict__ fro2, int want_v, int max_sweeps, GridBar* bar,
+                  int* __restrict__ sweeps_out) {
+  const double floor2 = 1e-32 * (*fro2);
+  for (int sweep = 0; sweep < max_sweeps; ++sweep) {
+    if (blockIdx.x == 0 && threadIdx.x == 0) bar->rot[(sweep + 1) % 3] = 0;
+    for (int round = 0; round < qpad - 1; ++round) {
+      for (int k = blockIdx.x; k < qpad / 2; k += gridDim.x) {
+        int P, Q;
+        rr_pair(round, k, qpad, P, Q);
+        if (Q >= q) continue;
+        if (jacobi_pair_block(X, V, p, q, P, Q, tol, floor2, want_v) && threadIdx.x == 0) bar->rot[sweep % 3] = 1;
+      }
+      if (!grid_sync(bar, gridDim.x)) return;
+    }
+    const int rot = ((volatile int*)bar->rot)[sweep % 3];
+    if (!rot) {
+      if (blockIdx.x == 0 && threadIdx.x == 0) *sweeps_out = sweep + 1;
+      return;
+    }
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) *sweeps_out = max_sweeps + 1;
 }
 
 // Small path: the whole problem in shared memory, one block, warps own pairs.
 __global__ void __launch_bounds__(256)
     k_jacobi_small(cplx* __restrict__ Xg, cplx* __restrict__ Vg, int p, int q, int qpad,
-                   double tol, int want_v, int max_sweeps, int* __restrict__ sweeps_out) {
+                   double tol, const double* __restrict__ fro2, int want_v, int max_sweeps,
+                   int* __restrict__ sweeps_out) {
+  const double floor2 = 1e-32 * (*fro2);
   extern __shared__ cplx sm[];
   cplx* X = sm;
   cplx* V = sm + (long long)p * q;
@@ -809,7 +901,7 @@ __global__ void __launch_bounds__(256)
         }
         double cs;
         cplx sne;
-        if (!jacobi_params(a, b, c, tol, cs, sne)) continue;
+        if (!jacobi_params(a, b, c, tol, floor2, cs, sne)) continue;
         if (lane == 0) s_rot = 1;
         for (int r = lane; r < p; r += 32) {
           cplx u = xp[r], v = xq[r];
@@ -837,6 +929,20 @@ __global__ void __launch_bounds__(256)
   for (int e = threadIdx.x; e < nx; e += blockDim.x) Xg[e] = X[e];
   for (int e = threadIdx.x; e < nv; e += blockDim.x) Vg[e] = V[e];
   if (threadIdx.x == 0) *sweeps_out = sweep + 1;
+}
+
+__global__ void k_fro2(const cplx* __restrict__ X, long long n, double* __restrict__ out) {
+  __shared__ double red[8];
+  double a = 0.0;
+  for (long long i = threadIdx.x; i < n; i += blockDim.x) a += cabs2(X[i]);
+  a = warp_sum(a);
+  if ((threadIdx.x & 31) == 0) red[threadIdx.x >> 5] = a;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double t = 0.0;
+    for (int u = 0; u < (int)(blockDim.x >> 5); ++u) t += red[u];
+    *out = t;
+  }
 }
 
 __global__ void k_colnorms(const cplx* __restrict__ X, int p, int q, double* __restrict__ s) {
@@ -901,7 +1007,10 @@ void svd_jacobi_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows,
   const int max_sweeps = 60;
   const size_t small_bytes = ((size_t)p * q + (need_acc ? (size_t)q * q : 0)) * sizeof(cplx);
   int* d_flag = nullptr;
-  TDVP_CUDA(cudaMallocAsync(&d_flag, sizeof(int), st));
+  TDVP_CUDA(cudaMallocAsync(&d_flag, sizeof(int) + sizeof(double) * 2, st));
+  double* d_fro2 = reinterpret_cast<double*>(d_flag + 2);
+  k_fro2<<<1, 256, 0, st>>>(X.data(), (long long)p * q, d_fro2);
+  TDVP_CHECK_LAUNCH();
   int sweeps = 0;
   if (q > 1) {
     if (small_bytes <= 96 * 1024) {
@@ -911,7 +1020,7 @@ void svd_jacobi_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows,
                                        96 * 1024));
         attr_set = true;
       }
-      k_jacobi_small<<<1, 256, small_bytes, st>>>(X.data(), Vx.data(), p, q, qpad, tol,
+      k_jacobi_small<<<1, 256, small_bytes, st>>>(X.data(), Vx.data(), p, q, qpad, tol, d_fro2,
                                                    need_acc ? 1 : 0, max_sweeps, d_flag);
       TDVP_CHECK_LAUNCH();
       TDVP_CUDA(cudaMemcpyAsync(&sweeps, d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -921,23 +1030,35 @@ void svd_jacobi_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows,
         throw TdvpError(TDVP_ERR_SVD_NOT_CONVERGED, "Jacobi SVD did not converge");
       }
     } else {
-      bool converged = false;
-      for (sweeps = 1; sweeps <= max_sweeps; ++sweeps) {
-        TDVP_CUDA(cudaMemsetAsync(d_flag, 0, sizeof(int), st));
-        for (int round = 0; round < qpad - 1; ++round) {
-          k_jacobi_round<<<qpad / 2, 256, 0, st>>>(X.data(), Vx.data(), p, q, qpad, round, tol,
-                                                    need_acc ? 1 : 0, d_flag);
-        }
-        TDVP_CHECK_LAUNCH();
-        int rot = 0;
-        TDVP_CUDA(cudaMemcpyAsync(&rot, d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
-        TDVP_CUDA(cudaStreamSynchronize(st));
-        if (!rot) {
-          converged = true;
-          break;
-        }
+      static int coop_blocks = 0;
+      if (coop_blocks == 0) {
+        int dev = 0, sms = 0, per_sm = 0;
+        TDVP_CUDA(cudaGetDevice(&dev));
+        TDVP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+        TDVP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_coop, 256, 0));
+        coop_blocks = std::max(1, sms * std::max(1, per_sm));
       }
-      if (!converged) {
+      const int nblk = std::max(1, std::min(qpad / 2, coop_blocks));
+      GridBar* bar = nullptr;
+      TDVP_CUDA(cudaMallocAsync(&bar, sizeof(GridBar), st));
+      TDVP_CUDA(cudaMemsetAsync(bar, 0, sizeof(GridBar), st));
+      cplx* xp = X.data();
+      cplx* vp = Vx.data();
+      int pp = p, qq = q, qp = qpad, wv = need_acc ? 1 : 0, ms = max_sweeps;
+      double tl = tol;
+      const double* fr = d_fro2;
+      void* args[] = {&xp, &vp, &pp, &qq, &qp, &tl, &fr, &wv, &ms, &bar, &d_flag};
+      TDVP_CUDA(cudaLaunchCooperativeKernel((void*)k_jacobi_coop, dim3(nblk), dim3(256), args, 0, st));
+      GridBar hb;
+      TDVP_CUDA(cudaMemcpyAsync(&sweeps, d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
+      TDVP_CUDA(cudaMemcpyAsync(&hb, bar, sizeof(GridBar), cudaMemcpyDeviceToHost, st));
+      TDVP_CUDA(cudaStreamSynchronize(st));
+      TDVP_CUDA(cudaFreeAsync(bar, st));
+      if (hb.err) {
+        cudaFreeAsync(d_flag, st);
+        throw TdvpError(TDVP_ERR_TIMEOUT, "Jacobi SVD: a grid barrier wait ran out");
+      }
+      if (sweeps > max_sweeps) {
         cudaFreeAsync(d_flag, st);
         throw TdvpError(TDVP_ERR_SVD_NOT_CONVERGED, "Jacobi SVD did not converge");
       }

@@ -12,6 +12,10 @@
 //   warp 0      TMA producer (cp.async.bulk.tensor, 128B swizzle, 3 stages)
 //   warp 1      TMEM allocator and single-thread tcgen05.mma issuer
 //   warps 2..5  epilogue: tcgen05.ld from TMEM lanes 32*(warp%4) .. +31
+// The tensor core's FP32 accumulation error grows linearly with the number of
+// products summed in one accumulator (measured); K is therefore split into
+// chunks of 128 that alternate between two TMEM accumulators, and the epilogue
+// warps add each finished chunk into FP32 registers.
 // Every mbarrier wait is bounded by a wall-clock limit; on expiry the CTA
 // records an error word, drains its own copies and MMAs (bounded) and frees
 // its tensor memory before returning.
@@ -28,7 +32,8 @@ constexpr int A_TILE = BM * BK * 4;                        // 16 KiB
 constexpr int B_TILE = BN * BK * 4;                        // 16 KiB
 constexpr int STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;       // 64 KiB
 constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
-constexpr int TMEM_COLS = 128;
+constexpr int TMEM_COLS = 256;     // two 128-column accumulators (ping-pong)
+constexpr int CHUNK_KB = 4;        // k-blocks per accumulation chunk (K = 128)
 constexpr unsigned long long kWaitNs = 2000000000ull;      // 2 s per wait
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
@@ -105,6 +110,14 @@ __device__ __forceinline__ void mma_commit(uint32_t bar) {
 __device__ __forceinline__ void fence_before() { asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory"); }
 __device__ __forceinline__ void fence_after() { asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory"); }
 
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+// K is consumed in chunks of CHUNK_KB k-blocks.  Each chunk accumulates in one of
+// two TMEM buffers (ping-pong) and the epilogue warps add it into FP32 registers
+// with round-to-nearest adds, so the tensor core's own accumulator only ever
+// sums CHUNK_KB * BK products.
 __global__ void __launch_bounds__(192, 1)
     k_gemm_tf32x3(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
                   const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo, int M,
@@ -114,18 +127,25 @@ __global__ void __launch_bounds__(192, 1)
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
   uint64_t* full = bars;
   uint64_t* empty = bars + STAGES;
-  uint64_t* accf = bars + 2 * STAGES;
-  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 1);
+  uint64_t* tfull = bars + 2 * STAGES;
+  uint64_t* tempty = bars + 2 * STAGES + 2;
+  uint64_t* done = bars + 2 * STAGES + 4;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int nchunks = (nkb + CHUNK_KB - 1) / CHUNK_KB;
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(smem_u32(&full[s]), 1);
       mbar_init(smem_u32(&empty[s]), 1);
     }
-    mbar_init(smem_u32(accf), 1);
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&tfull[b]), 1);
+      mbar_init(smem_u32(&tempty[b]), 4);
+    }
+    mbar_init(smem_u32(done), 1);
     *abort_flag = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
@@ -167,59 +187,94 @@ __global__ void __launch_bounds__(192, 1)
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
     const uint32_t idesc = idesc_tf32(BM, BN);
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % STAGES, it = kb / STAGES;
-      if (!mbar_wait(smem_u32(&full[s]), it & 1)) {
+    for (int c = 0; c < nchunks && !*abort_flag; ++c) {
+      const int b = c & 1, u = c >> 1;
+      if (u > 0 && !mbar_wait(smem_u32(&tempty[b]), (u - 1) & 1)) {
         *abort_flag = 1;
         break;
       }
-      if (*abort_flag) break;
       fence_after();
-      const uint32_t a_hi = smem_u32(smem + s * STAGE_BYTES);
-      const uint32_t a_lo = a_hi + A_TILE;
-      const uint32_t b_hi = a_hi + 2 * A_TILE;
-      const uint32_t b_lo = b_hi + B_TILE;
+      const uint32_t acc_tmem = tmem + (uint32_t)(b * BN);
+      const int kb_end = min(nkb, (c + 1) * CHUNK_KB);
+      for (int kb = c * CHUNK_KB; kb < kb_end; ++kb) {
+        const int s = kb % STAGES, it = kb / STAGES;
+        if (!mbar_wait(smem_u32(&full[s]), it & 1)) {
+          *abort_flag = 1;
+          break;
+        }
+        fence_after();
+        const uint32_t a_hi = smem_u32(smem + s * STAGE_BYTES);
+        const uint32_t a_lo = a_hi + A_TILE;
+        const uint32_t b_hi = a_hi + 2 * A_TILE;
+        const uint32_t b_lo = b_hi + B_TILE;
 #pragma unroll
-      for (int k = 0; k < BK / 8; ++k) {
-        const uint32_t off = k * 32;  // 8 tf32 = 32 bytes along K inside the swizzle atom
-        mma_tf32(tmem, sdesc(a_hi + off), sdesc(b_hi + off), idesc, (kb | k) != 0 ? 1u : 0u);
-        mma_tf32(tmem, sdesc(a_hi + off), sdesc(b_lo + off), idesc, 1u);
-        mma_tf32(tmem, sdesc(a_lo + off), sdesc(b_hi + off), idesc, 1u);
+        for (int k = 0; k < BK / 8; ++k) {
+          const uint32_t off = k * 32;  // 8 tf32 = 32 bytes along K inside the swizzle atom
+          const uint32_t first = (kb == c * CHUNK_KB && k == 0) ? 0u : 1u;
+          mma_tf32(acc_tmem, sdesc(a_hi + off), sdesc(b_hi + off), idesc, first);
+          mma_tf32(acc_tmem, sdesc(a_hi + off), sdesc(b_lo + off), idesc, 1u);
+          mma_tf32(acc_tmem, sdesc(a_lo + off), sdesc(b_hi + off), idesc, 1u);
+        }
+        mma_commit(smem_u32(&empty[s]));
       }
-      mma_commit(smem_u32(&empty[s]));
+      if (*abort_flag) break;
+      mma_commit(smem_u32(&tfull[b]));
     }
-    mma_commit(smem_u32(accf));  // fires when every issued MMA has completed
+    mma_commit(smem_u32(done));  // fires when every issued MMA has completed
   } else if (warp >= 2) {
-    // ---------------- epilogue
-    bool ok = mbar_wait(smem_u32(accf), 0);
-    if (!ok) *abort_flag = 1;
-    ok = __all_sync(0xffffffffu, ok && !*abort_flag);  // keep the .aligned loads warp-uniform
-    fence_after();
-    if (ok) {
-      const int q = warp & 3;
-      const int row = q * 32 + lane;
-      const int gm = m0 + row;
-#pragma unroll 1
+    // ---------------- epilogue: promote chunk partials into FP32 registers
+    const int q = warp & 3;
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    float acc[BN];
+#pragma unroll
+    for (int j = 0; j < BN; ++j) acc[j] = 0.f;
+    bool ok = true;
+    for (int c = 0; c < nchunks; ++c) {
+      const int b = c & 1, u = c >> 1;
+      bool got = mbar_wait(smem_u32(&tfull[b]), u & 1);
+      if (!got) *abort_flag = 1;
+      ok = __all_sync(0xffffffffu, got && !*abort_flag);  // keep the .aligned loads warp-uniform
+      if (!ok) break;
+      fence_after();
+#pragma unroll
       for (int c0 = 0; c0 < BN; c0 += 16) {
         uint32_t v[16];
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
               "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-            : "r"(tmem + ((uint32_t)(q * 32) << 16) + (uint32_t)c0));
+            : "r"(tmem + lane_base + (uint32_t)(b * BN + c0)));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
-        if (gm < M) {
 #pragma unroll
-          for (int j = 0; j < 16; ++j) {
-            const int gn = n0 + c0 + j;
-            if (gn < N) {
-              const float f = __uint_as_float(v[j]);
-              if (out_f64)
-                static_cast<double*>(out)[(long long)gm * ldo + gn] = (double)f;
-              else
-                static_cast<float*>(out)[(long long)gm * ldo + gn] = f;
-            }
-          }
+        for (int j = 0; j < 16; ++j) acc[c0 + j] += __uint_as_float(v[j]);
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&tempty[b]));
+    }
+    const int gm = m0 + q * 32 + lane;
+    if (ok && gm < M) {
+      if (out_f64) {
+        double* o = static_cast<double*>(out) + (long long)gm * ldo + n0;
+        if (n0 + BN <= N && (ldo & 1) == 0) {
+#pragma unroll
+          for (int j = 0; j < BN; j += 2)
+            *reinterpret_cast<double2*>(o + j) = make_double2((double)acc[j], (double)acc[j + 1]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < BN; ++j)
+            if (n0 + j < N) o[j] = (double)acc[j];
+        }
+      } else {
+        float* o = static_cast<float*>(out) + (long long)gm * ldo + n0;
+        if (n0 + BN <= N && (ldo & 3) == 0) {
+#pragma unroll
+          for (int j = 0; j < BN; j += 4)
+            *reinterpret_cast<float4*>(o + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
+        } else {
+#pragma unroll
+          for (int j = 0; j < BN; ++j)
+            if (n0 + j < N) o[j] = acc[j];
         }
       }
     }
@@ -227,6 +282,8 @@ __global__ void __launch_bounds__(192, 1)
   fence_before();
   __syncthreads();
   if (warp == 1) {
+    // every MMA issued by this CTA has completed before its tensor memory is freed
+    (void)mbar_wait(smem_u32(done), 0);
     fence_after();
     asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
   }
@@ -442,8 +499,18 @@ void heff_tf32x3(cudaStream_t st, Scratch& s, const SiteOp& op, const cplx* x, c
   // stage 3: y[(a,s)][(b,c)] = T2 R^T  (FP64 output, interleaved complex)
   gemm_tf32x3(st, c.T2hi.as<float>(), c.T2lo.as<float>(), c.Rhi.as<float>(), c.Rlo.as<float>(), M3, N3, K3p,
               reinterpret_cast<double*>(y), N3, true, c.err.as<int>());
+  c.pending = true;
+}
+
+void tc_check(cudaStream_t st, Scratch& s) {
+  TcEnvCache& c = s.tc;
+  if (!c.pending || c.err.bytes() == 0) return;
   int h_err = 0;
   TDVP_CUDA(cudaMemcpyAsync(&h_err, c.err.as<int>(), sizeof(int), cudaMemcpyDeviceToHost, st));
   TDVP_CUDA(cudaStreamSynchronize(st));
-  tdvp_require(h_err == 0, TDVP_ERR_TIMEOUT, "tensor-core GEMM: a bounded pipeline wait ran out");
+  c.pending = false;
+  if (h_err != 0) {
+    TDVP_CUDA(cudaMemsetAsync(c.err.as<int>(), 0, sizeof(int), st));
+    throw TdvpError(TDVP_ERR_TIMEOUT, "tensor-core GEMM: a bounded pipeline wait ran out");
+  }
 }

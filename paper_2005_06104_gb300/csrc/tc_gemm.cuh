@@ -11,6 +11,7 @@ struct TcEnvCache {
   RawBuf Rhi, Rlo;   // R expanded to a real (2 m_r) x (2 w_r m_r) operand, hi / lo
   RawBuf Bhi, Blo;   // per-apply operand of the vector (stage 1 B operand)
   RawBuf T1, T2hi, T2lo;  // stage outputs
-  RawBuf err;        // device status word
+  RawBuf err;        // device status word (non-zero: a bounded wait ran out)
+  bool pending = false;  // launches since the last check of `err`
 };
 

@@ -53,6 +53,7 @@ _sig = {
     "tdvp_set_options": [_h, C.POINTER(Options)],
     "tdvp_canonicalize": [_h, C.c_int],
     "tdvp_expand_basis": [_h, C.c_int, C.c_void_p],
+    "tdvp_apply_krylov": [_h],
     "tdvp_sweep": [_h, C.c_double, C.c_int],
     "tdvp_heff_apply": [_h, C.c_int, C.c_void_p, C.c_void_p, C.c_int],
     "tdvp_keff_apply": [_h, C.c_int, C.c_void_p, C.c_void_p, C.c_int],
@@ -236,6 +237,10 @@ class GseTdvp:
         if weights is not None:
             w = (C.c_double * len(weights))(*weights)
         self._chk(_lib.tdvp_expand_basis(self.h, k, C.cast(w, C.c_void_p) if w is not None else None))
+
+    def apply_krylov(self):
+        """State <- normalised, compressed (1 - i tau H)|psi> (one Krylov vector, Eq. 10)."""
+        self._chk(_lib.tdvp_apply_krylov(self.h))
 
     def sweep(self, dt, kind=REAL):
         self._chk(_lib.tdvp_sweep(self.h, dt, kind))

@@ -71,6 +71,23 @@ def test_tdvp1_sweep_matches_oracle(g, kind):
     st.close()
 
 
+@pytest.mark.parametrize("tau,eps_k,cap", [(0.1, 1e-10, 64), (-0.25j, 1e-12, 64), (0.1, 1e-6, 12)])
+def test_krylov_vector_matches_oracle(g, tau, eps_k, cap):
+    """Density-matrix application of 1 - i tau H (GPU) == exact application + SVD compression (oracle)."""
+    lat = wl.zigzag_ladder(6, 1.0, 0.6)
+    W = wl.heisenberg_mpo(lat)
+    psi = O.left_canonicalize(wl.random_mps(lat.n, 6, 21))
+    psi[-1] /= np.linalg.norm(psi[-1])
+    st = g.GseTdvp(psi, W, tau=tau, eps_k=eps_k, chi_max=cap)
+    st.apply_krylov()
+    ref = O.krylov_vectors(psi, W, tau, 2, eps_k, cap)[0]
+    mine = st.get_mps()
+    assert st.bond_dims() == wl.mps_bond_dims(ref)
+    assert abs(abs(O.mps_overlap(mine, ref)) - 1) < 1e-10
+    assert abs(st.norm() - 1) < 1e-12
+    st.close()
+
+
 def test_expand_basis_matches_oracle(g):
     lat = wl.zigzag_ladder(6, 1.0, 1.0)
     W = wl.heisenberg_mpo(lat)
@@ -134,20 +151,20 @@ def test_gse_imaginary_time_decoupled_ladder(g):
 
 def test_precision_form_energy_and_norm(g):
     """Split-TF32 sweeps hold relative energy error <= 1e-7 and norm drift <= 1e-10 per step
-    against the FP64 GPU form (real time)."""
+    against the FP64 GPU form (real time, rung-coupled ladder, Neel with one flipped spin)."""
     lat = wl.zigzag_ladder(8, 1.0, 1.0)
     W = wl.heisenberg_mpo(lat)
-    psi = O.right_canonicalize(wl.random_mps(lat.n, 48, 2))
-    psi[0] /= np.linalg.norm(psi[0])
-    a = g.GseTdvp(psi, W, precision=g.PREC_FP64)
-    b = g.GseTdvp(psi, W, precision=g.PREC_TF32X3)
+    psi = wl.neel_state(lat, flip=(4, 0))
+    kw = dict(tau=0.1, eps_k=1e-8, eps_m=1e-8, chi_max=48)
+    a = g.GseTdvp(psi, W, precision=g.PREC_FP64, **kw)
+    b = g.GseTdvp(psi, W, precision=g.PREC_TF32X3, **kw)
     e0 = a.energy()
-    for _ in range(3):
-        a.sweep(0.05, g.REAL)
-        b.sweep(0.05, g.REAL)
+    for _ in range(4):
+        a.step(0.1, g.REAL, 3)
+        b.step(0.1, g.REAL, 3)
         assert abs(b.norm() - 1) < 1e-10
         assert abs(b.energy() - a.energy()) <= 1e-7 * abs(a.energy())
-    assert abs(a.energy() - e0) < 1e-10
+    assert abs(a.energy() - e0) < 1e-10 * abs(e0)
     a.close()
     b.close()
 
