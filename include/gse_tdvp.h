@@ -179,6 +179,16 @@ TDVP_API tdvp_status tdvp_get_mps(tdvp_handle* h, double* const* sites_out);
 TDVP_API tdvp_status tdvp_profile(tdvp_handle* h, int enable);
 TDVP_API tdvp_status tdvp_profile_read(tdvp_handle* h, double* out3);
 
+/* Per-phase timing (CUDA events on the handle's stream).  tdvp_trace(h, 1)
+ * starts recording; tdvp_trace_read writes the milliseconds spent since the
+ * last read into out[0..n) and resets.  Phases: 0 local exponentials of the
+ * sweep (H_eff Lanczos), 1 backward bond exponentials (K_eff Lanczos), 2 SVDs
+ * of the sweep's gauge moves, 3 environment updates, 4 Krylov vectors (step 1),
+ * 5 basis extension (step 2), 6 gauge moves of tdvp_canonicalize.  Intervals
+ * nest (phase 3 also runs inside 0..2), so the entries do not add up. */
+TDVP_API tdvp_status tdvp_trace(tdvp_handle* h, int enable);
+TDVP_API tdvp_status tdvp_trace_read(tdvp_handle* h, double* out, int n);
+
 /* ---------------------------------------------------------------------------
  * Handle-free contractions of one site on caller buffers (kernel-level entry
  * points; the same code the handle uses).  Device buffers are caller-owned
@@ -206,6 +216,25 @@ TDVP_API tdvp_status tdvp_expm_contract(const tdvp_site_dims* dims, const void* 
                                         tdvp_time kind, int precision, double tol, int nmax, int* iters,
                                         void* stream);
 TDVP_API const char* tdvp_contract_last_error(void);
+
+/* y = H_eff x exactly as tdvp_heff_contract(..., TDVP_PREC_FP64, ...), but
+ * without allocating device memory.  The paper has no counterpart: this entry
+ * exists for callers that cannot call cudaMalloc (a host framework that owns
+ * every device allocation, or a loop that must never block on the allocator).
+ * Its intermediates live in a fixed 32 MiB file-scope device array that every
+ * GPU loading the library keeps until the process exits; the limits are
+ * (m_l w_l d m_r + m_l d w_r m_r) * 16 bytes <= 31 MiB and w_l d d w_r <= 16384,
+ * and larger sizes return TDVP_ERR_INVALID_ARG.  The first call on a device
+ * looks up that array's device address (cudaGetSymbolAddress) with the device
+ * current, so make the first call on each device outside any stream capture.
+ * All calls share the one array and keep its last contents (nothing in it
+ * needs to start at zero); calls serialise on the host, but calls that overlap
+ * on the GPU (different streams, or a caller that does not wait) race.  The
+ * call synchronises `stream` before returning.  err (may be NULL) receives up
+ * to err_len bytes of message on failure. */
+TDVP_API tdvp_status tdvp_heff_contract_noalloc(const tdvp_site_dims* dims, const void* L_dev,
+                                                const double* W_host, const void* R_dev, const void* x_dev,
+                                                void* y_dev, void* stream, char* err, int err_len);
 
 #ifdef __cplusplus
 }

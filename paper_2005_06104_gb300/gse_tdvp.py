@@ -68,6 +68,8 @@ _sig = {
     "tdvp_get_mps": [_h, C.POINTER(C.c_void_p)],
     "tdvp_profile": [_h, C.c_int],
     "tdvp_profile_read": [_h, C.POINTER(C.c_double)],
+    "tdvp_trace": [_h, C.c_int],
+    "tdvp_trace_read": [_h, C.POINTER(C.c_double), C.c_int],
 }
 for _name, _args in _sig.items():
     _f = getattr(_lib, _name)
@@ -152,6 +154,24 @@ def expm_contract(L, W, R, x, y, delta, kind=REAL, precision=PREC_FP64, tol=1e-1
     _raw_chk(_lib.tdvp_expm_contract(C.byref(SiteDims(ml, mr, wl, wr, d)), _ptr(L), wp, _ptr(R), _ptr(x), _ptr(y),
                                      delta, kind, precision, tol, nmax, C.byref(it), _stream(stream)))
     return it.value
+
+
+_lib.tdvp_heff_contract_noalloc.argtypes = [C.POINTER(SiteDims), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                             C.c_void_p, C.c_void_p, C.c_char_p, C.c_int]
+_lib.tdvp_heff_contract_noalloc.restype = C.c_int
+
+
+def heff_contract_noalloc(L, W, R, x, y, stream=None):
+    """y = H_eff x (FP64) with no device allocation (scratch in a fixed device array)."""
+    ml, wl, _ = L.shape
+    mr, wr, _ = R.shape
+    d = W.shape[1]
+    Wc, wp = _host(W)
+    buf = C.create_string_buffer(512)
+    s = _lib.tdvp_heff_contract_noalloc(C.byref(SiteDims(ml, mr, wl, wr, d)), _ptr(L), wp, _ptr(R), _ptr(x),
+                                        _ptr(y), _stream(stream), buf, 512)
+    if s != 0:
+        raise TDVPError(s, buf.value.decode())
 
 
 def declared_symbols(header=HEADER):
@@ -303,6 +323,16 @@ class GseTdvp:
         out = (C.c_double * 3)()
         self._chk(_lib.tdvp_profile_read(self.h, out))
         return dict(applies=int(out[0]), ms=out[1], flops=out[2])
+
+    PHASES = ("lanczos_site", "lanczos_bond", "svd_sweep", "env", "krylov", "extend", "canonicalize")
+
+    def trace(self, enable=True):
+        self._chk(_lib.tdvp_trace(self.h, 1 if enable else 0))
+
+    def trace_read(self):
+        out = (C.c_double * len(self.PHASES))()
+        self._chk(_lib.tdvp_trace_read(self.h, out, len(self.PHASES)))
+        return dict(zip(self.PHASES, list(out)))
 
     def get_mps(self):
         m = self.bond_dims()
