@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--dt", type=float, default=0.1)
     ap.add_argument("--heff-chi", type=int, default=1024, help="bond dimension of the H_eff roofline probe")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--heff-probe", action="store_true",
+                    help="only time the tensor-core H_eff apply at --heff-chi (the profiling target)")
     return ap.parse_args()
 
 
@@ -247,8 +249,10 @@ def run_gpu(args):
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
+    phases = {}
     for _ in range(args.steps):
         st.profile(True)
+        st.trace(True)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
         step()
@@ -256,6 +260,8 @@ def run_gpu(args):
         b.synchronize()
         ts.append(a.elapsed_time(b))
         pr = st.profile_read()
+        for kk, vv in st.trace_read().items():
+            phases[kk] = phases.get(kk, 0.0) + vv / args.steps
         heff_ms += pr["ms"]
         heff_flops += pr["flops"]
         heff_n += pr["applies"]
@@ -331,6 +337,7 @@ def run_gpu(args):
                               "rel_energy_err": abs(e_tc - e_64) / abs(e_64) if e_64 else None,
                               "norm_drift": abs(n_tc - 1.0)},
         "step_stats": nfo,
+        "phases_ms_per_step": phases,
         "cpu_baseline": cpu,
         "e2e": {"value": len(e2e_ts) / sum(e2e_ts), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
@@ -344,9 +351,21 @@ def run_gpu(args):
         dist.destroy_process_group()
 
 
+def run_heff_probe(args):
+    import torch
+    from paper_2005_06104_gb300 import gse_tdvp as g
+    from paper_2005_06104_gb300 import workloads as wl
+    W = max(wl.heisenberg_mpo(wl.cylinder_snake(16, 4)), key=lambda w: w.shape[0] * w.shape[3])
+    flops, ms = heff_roofline(g, torch, args.heff_chi, W)
+    print(json.dumps({"heff_chi": args.heff_chi, "w": int(W.shape[0]), "ms_per_apply": ms,
+                      "algorithmic_tflops": flops / ms / 1e9}), flush=True)
+
+
 def main():
     args = parse()
-    if args.impl == "reference":
+    if args.heff_probe:
+        run_heff_probe(args)
+    elif args.impl == "reference":
         run_reference(args)
     else:
         run_gpu(args)

@@ -275,6 +275,18 @@ tdvp_status tdvp_profile_read(tdvp_handle* h, double* out) {
   });
 }
 
+tdvp_status tdvp_trace(tdvp_handle* h, int enable) {
+  return guarded(h, [&] { h->eng.tracer.on = enable != 0; });
+}
+
+tdvp_status tdvp_trace_read(tdvp_handle* h, double* out, int n) {
+  return guarded(h, [&] {
+    tdvp_require(out != nullptr && n >= 0, TDVP_ERR_INVALID_ARG, "null output");
+    h->eng.sync();
+    h->eng.tracer.read(out, n);
+  });
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------

@@ -135,6 +135,7 @@ void Engine::init(const tdvp_mps_desc* mps, const tdvp_mpo_desc* mpo, const tdvp
   N = mps->n_sites;
   d = mps->d;
   st = static_cast<cudaStream_t>(s);
+  tracer.st = st;
   if (o) opt = *o; else tdvp_default_options(&opt);
   int dev = 0;
   TDVP_CUDA(cudaGetDevice(&dev));
@@ -190,6 +191,7 @@ void Engine::release() {
   for (auto& ev : ev_pool) cudaEventDestroy(ev);
   ev_pairs.clear();
   ev_pool.clear();
+  tracer.release();
 }
 
 // ============================================================================
@@ -227,6 +229,7 @@ void Engine::ensure_R(int i) {
 
 // L[i+1] from L[i] and A[i]; R[i-1] from R[i] and A[i]
 void Engine::env_left(int i) {
+  PhaseScope ps(tracer, PH_ENV);
   const int ml = psi.m[i], mr = psi.m[i + 1];
   L[i + 1].ensure(&pool, (size_t)mr * w[i + 1] * mr);
   env_left_fp64(st, scr, L[i].data(), Wsp[i], psi.A[i].data(), ml, mr, d, L[i + 1].data());
@@ -235,6 +238,7 @@ void Engine::env_left(int i) {
 }
 
 void Engine::env_right(int i) {
+  PhaseScope ps(tracer, PH_ENV);
   const int ml = psi.m[i], mr = psi.m[i + 1];
   R[i - 1].ensure(&pool, (size_t)ml * w[i] * ml);
   env_right_fp64(st, scr, R[i].data(), Wsp[i], psi.A[i].data(), ml, mr, d, R[i - 1].data());
@@ -341,6 +345,7 @@ void Engine::move_left(int i, double eps, int cap, bool trunc) {
 
 void Engine::canonicalize(int c) {
   tdvp_require(c >= 0 && c < N, TDVP_ERR_INVALID_ARG, "site out of range");
+  PhaseScope ps(tracer, PH_CANON);
   while (center < c) {
     move_right(center, 0.0, 1 << 30, false);
     ++center;
@@ -391,6 +396,7 @@ void Engine::sweep(double dt, int kind) {
   auto evolve_site = [&](int i) {
     const long long n = (long long)psi.m[i] * d * psi.m[i + 1];
     y.ensure(&pool, n);
+    PhaseScope ps(tracer, PH_LANCZOS_SITE);
     lanczos([&](const cplx* a, cplx* b) { heff(i, a, b, prec); }, psi.A[i].data(), y.data(), n, delta,
             kind);
     if (imag) normalize(y.data(), n);
@@ -407,7 +413,10 @@ void Engine::sweep(double dt, int kind) {
       rule.discarded = &disc_eps;
     }
     SvdOut sv;
-    svd_jacobi(st, &pool, psi.A[i].data(), ml * d, mold, rule, sv, true, true);
+    {
+      PhaseScope ps(tracer, PH_SVD);
+      svd_jacobi(st, &pool, psi.A[i].data(), ml * d, mold, rule, sv, true, true);
+    }
     const int r = sv.rank;
     tdvp_require(r >= 1, TDVP_ERR_NONFINITE, "sweep: zero site tensor");
     DArr C(&pool, (size_t)r * mold);
@@ -423,8 +432,11 @@ void Engine::sweep(double dt, int kind) {
     const cplx* Lb = L[i + 1].data();
     const cplx* Rb = R[i].data();
     const int wb = w[i + 1];
-    lanczos([&](const cplx* a, cplx* b) { keff_fp64(st, scr, Lb, r, Rb, mold, wb, a, b); }, C.data(), C2.data(),
-            (long long)r * mold, -delta, kind);
+    {
+      PhaseScope ps(tracer, PH_LANCZOS_BOND);
+      lanczos([&](const cplx* a, cplx* b) { keff_fp64(st, scr, Lb, r, Rb, mold, wb, a, b); }, C.data(),
+              C2.data(), (long long)r * mold, -delta, kind);
+    }
     if (imag) normalize(C2.data(), (long long)r * mold);
     DArr nxt(&pool, (size_t)r * d * mr2);
     zgemm(st, OP_N, OP_N, r, d * mr2, mold, kOne, C2.data(), mold, psi.A[i + 1].data(), d * mr2, kZero,
@@ -444,7 +456,10 @@ void Engine::sweep(double dt, int kind) {
       rule.discarded = &disc_eps;
     }
     SvdOut sv;
-    svd_jacobi(st, &pool, psi.A[i].data(), mold, d * mr, rule, sv, true, true);
+    {
+      PhaseScope ps(tracer, PH_SVD);
+      svd_jacobi(st, &pool, psi.A[i].data(), mold, d * mr, rule, sv, true, true);
+    }
     const int r = sv.rank;
     tdvp_require(r >= 1, TDVP_ERR_NONFINITE, "sweep: zero site tensor");
     DArr C(&pool, (size_t)mold * r);
@@ -460,8 +475,11 @@ void Engine::sweep(double dt, int kind) {
     const cplx* Lb = L[i].data();
     const cplx* Rb = R[i - 1].data();
     const int wb = w[i];
-    lanczos([&](const cplx* a, cplx* b) { keff_fp64(st, scr, Lb, mold, Rb, r, wb, a, b); }, C.data(), C2.data(),
-            (long long)mold * r, -delta, kind);
+    {
+      PhaseScope ps(tracer, PH_LANCZOS_BOND);
+      lanczos([&](const cplx* a, cplx* b) { keff_fp64(st, scr, Lb, mold, Rb, r, wb, a, b); }, C.data(),
+              C2.data(), (long long)mold * r, -delta, kind);
+    }
     if (imag) normalize(C2.data(), (long long)mold * r);
     DArr prv(&pool, (size_t)ml0 * d * r);
     zgemm(st, OP_N, OP_N, ml0 * d, r, mold, kOne, psi.A[i - 1].data(), mold, C2.data(), r, kZero, prv.data(),
@@ -669,7 +687,11 @@ void Engine::expand_basis(int k, const double* weights) {
   KrylovOp kop;
   build_krylov_op(kop);
   std::vector<MpsDev> phis(k - 1);
-  for (int l = 0; l < k - 1; ++l) krylov_apply(kop, l == 0 ? psi : phis[l - 1], phis[l]);
+  {
+    PhaseScope ps(tracer, PH_KRYLOV);
+    for (int l = 0; l < k - 1; ++l) krylov_apply(kop, l == 0 ? psi : phis[l - 1], phis[l]);
+  }
+  PhaseScope ps_ext(tracer, PH_EXTEND);
   // ---- step 2: basis extension, right to left (Eqs. 3, 5-7)
   const int nk = k - 1;
   for (int i = N - 1; i >= 1; --i) {

@@ -26,6 +26,71 @@ struct KrylovOp {
   void release();
 };
 
+// Phases timed by the tracer (CUDA events on the engine stream).
+enum TracePhase { PH_LANCZOS_SITE = 0, PH_LANCZOS_BOND, PH_SVD, PH_ENV, PH_KRYLOV, PH_EXTEND, PH_CANON, PH_COUNT };
+
+struct Tracer {
+  bool on = false;
+  cudaStream_t st = nullptr;
+  std::vector<cudaEvent_t> pool;
+  struct Mark {
+    int phase;
+    cudaEvent_t a, b;
+  };
+  std::vector<Mark> marks;
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    TDVP_CUDA(cudaEventCreate(&e));
+    return e;
+  }
+  // sums per phase (ms) and recycles the events; the stream must be idle
+  void read(double* out, int n) {
+    for (int p = 0; p < n; ++p) out[p] = 0.0;
+    for (auto& m : marks) {
+      float t = 0.f;
+      TDVP_CUDA(cudaEventElapsedTime(&t, m.a, m.b));
+      if (m.phase < n) out[m.phase] += t;
+      pool.push_back(m.a);
+      pool.push_back(m.b);
+    }
+    marks.clear();
+  }
+  void release() {
+    for (auto& m : marks) {
+      cudaEventDestroy(m.a);
+      cudaEventDestroy(m.b);
+    }
+    for (auto e : pool) cudaEventDestroy(e);
+    marks.clear();
+    pool.clear();
+  }
+};
+
+// Records one interval of `phase` on the stream while it is in scope.
+struct PhaseScope {
+  Tracer& tr;
+  int phase;
+  cudaEvent_t a = nullptr;
+  PhaseScope(Tracer& t, int p) : tr(t), phase(p) {
+    if (tr.on) {
+      a = tr.get();
+      cudaEventRecord(a, tr.st);
+    }
+  }
+  ~PhaseScope() {
+    if (tr.on && a) {
+      cudaEvent_t b = tr.get();
+      cudaEventRecord(b, tr.st);
+      tr.marks.push_back({phase, a, b});
+    }
+  }
+};
+
 struct Engine {
   // declared first so it is destroyed last: every DArr below returns its block here
   DevicePool pool;
@@ -53,6 +118,7 @@ struct Engine {
   std::vector<std::pair<cudaEvent_t, cudaEvent_t>> ev_pairs;
   double prof_flops = 0.0;
   long long prof_count = 0;
+  Tracer tracer;
   // statistics of the last calls
   double disc_k = 0, disc_m = 0, disc_eps = 0;
   int added_states = 0;
