@@ -2,13 +2,13 @@
 
 One timed step = one full GSE-TDVP1 time step (Sec. I.C: Krylov vectors of
 Eq. 10, basis extension of Eqs. 3-7, symmetric TDVP1 sweep) on the 4 x 16
-Heisenberg cylinder (snake path, MPO bond dimension up to 14), starting from a
-synthetic state that is already resident in HBM.  The state is reset to the
-same synthetic input before every timed step, so every step does identical
-work.  H_eff applies run on the tcgen05 split-TF32 path; Lanczos, gauge moves
-and the density-matrix steps run in FP64.
+Heisenberg cylinder (snake path, MPO bond dimension up to 14) along the real-time
+trajectory from the Neel state with one flipped spin; the state is resident in
+HBM.  Untimed preparation steps grow the bond dimension towards chi_max first.
+The precision form runs H_eff, the sweep's environment updates and the Krylov
+GEMMs on the tcgen05 split-TF32 path; Lanczos, SVDs and observables are FP64.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--chi0 C] [--chi-max X]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--chi-max X] [--prep-steps P]
     python bench.py --impl reference ...      (the CPU oracle on the host cores)
 
 Under torchrun each rank evolves its own independent copy (replicas only:
@@ -40,8 +40,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--chi0", type=int, default=32, help="bond dimension of the synthetic start state")
-    ap.add_argument("--chi-max", type=int, default=64)
+    ap.add_argument("--chi-max", type=int, default=128)
+    ap.add_argument("--prep-steps", type=int, default=6,
+                    help="untimed GSE-TDVP1 steps that grow the bond dimension before warm-up")
     ap.add_argument("--k", type=int, default=3)
     ap.add_argument("--dt", type=float, default=0.1)
     ap.add_argument("--heff-chi", type=int, default=1024, help="bond dimension of the H_eff roofline probe")
@@ -52,18 +53,20 @@ def parse():
 
 
 def workload(args):
+    """The 4 x 16 Heisenberg cylinder (snake path) from Neel with the spin at (8, 0) flipped,
+    real time dt = 0.1, k = 3: the trajectory is advanced untimed (--prep-steps) until its
+    bond dimensions approach chi_max, then the timed steps continue the same trajectory."""
     from paper_2005_06104_gb300 import workloads as wl
     lat = wl.cylinder_snake(16, 4)
     W = wl.heisenberg_mpo(lat)
-    psi = wl.random_mps(lat.n, args.chi0, seed=2024)
-    nrm = np.sqrt(abs(_overlap(psi, psi)))
-    psi[0] = psi[0] / nrm
-    cfg = {"workload": f"heisenberg_cylinder4x16_snake_w14_chi0_{args.chi0}_chimax_{args.chi_max}_k{args.k}",
-           "lattice": "4x16 cylinder, snake path, J=1", "n_sites": lat.n, "mpo_bond_dim_max": 14,
-           "chi0": args.chi0, "chi_max": args.chi_max, "krylov_order_k": args.k, "dt": args.dt,
-           "tau": args.dt, "eps_k": 1e-8, "eps_m": 1e-8, "eps": 0.0, "time": "real",
-           "heff_precision": "tf32x3", "start_state": "random dense MPS (seed 2024), normalised",
-           "l2": "working set > L2 per step (environments + Krylov vectors); no flush"}
+    psi = wl.neel_state(lat, flip=(8, 0))
+    cfg = {"workload": f"heisenberg_cylinder4x16_snake_neel_flip_chimax{args.chi_max}_k{args.k}_dt{args.dt}",
+           "lattice": "4x16 cylinder (periodic in y), snake path, J=1", "n_sites": lat.n,
+           "mpo_bond_dim_max": int(max(wl.mpo_bond_dims(W))), "chi_max": args.chi_max,
+           "krylov_order_k": args.k, "dt": args.dt, "tau": args.dt, "eps_k": 1e-8, "eps_m": 1e-8, "eps": 0.0,
+           "time": "real", "precision_form": "tf32x3 (H_eff, environments, Krylov GEMMs); FP64 Lanczos/SVD",
+           "start_state": "Neel with the spin at (8,0) flipped", "prep_steps": args.prep_steps,
+           "l2": "working set of a step (environments, Krylov vectors, density environments) > L2; no flush"}
     return lat, W, psi, cfg
 
 
@@ -123,25 +126,47 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def cpu_baseline(args, W, psi, budget_s=20.0):
-    """The oracle (as it stands) on the host cores: one H_eff-dominated sample of the
-    same step, scaled to sweeps/s by the GPU step's own count of H_eff applies."""
+def cpu_baseline(args, W, budget_s=20.0):
+    """The oracle (as it stands) on the host cores, on a bounded sample of the same step:
+    TDVP1 site updates (forward Lanczos, SVD, environment update, backward Lanczos) at the
+    centre of a random MPS with the workload's bond dimensions (min(chi_max, 2^i, 2^(N-i))),
+    repeated until ~budget_s, then scaled to the 2N site updates of one sweep by each site's
+    m_l m_r (m_l + m_r) share.  Steps 1-2 are left out, which favours the CPU."""
     import oracle as O
+    from paper_2005_06104_gb300 import workloads as wl
+    n = len(W)
+    psi = O.right_canonicalize(wl.random_mps(n, args.chi_max, seed=11))
+    psi[0] = psi[0] / np.linalg.norm(psi[0])
+    c = n // 2
+    for i in range(c):
+        ml, d, mr = psi[i].shape
+        U, S, Vh, _ = O.svd_truncate(psi[i].reshape(ml * d, mr))
+        psi[i] = U.reshape(ml, d, -1)
+        psi[i + 1] = np.tensordot(S[:, None] * Vh, psi[i + 1], axes=([1], [0]))
+    Ls, Rs = O.build_envs(psi, W, c)
+    delta = 0.5 * args.dt
     t0 = time.perf_counter()
-    p = dict(tau=args.dt, k=args.k, eps_k=1e-8, eps_m=1e-8, chi_max=args.chi_max, dt=args.dt,
-             kind="real", eps=0.0)
-    # time a whole oracle step when it fits the budget, else the TDVP1 part of one site
-    stats = {}
-    psi_c = O.left_canonicalize(psi)
-    t = time.perf_counter()
-    out = O.gse_tdvp1_step(psi_c, W, p, stats)
-    dt_step = time.perf_counter() - t
-    sample = f"one full GSE-TDVP1 step of the same workload ({len(stats.get('lanczos_iters', []))} local exponentials)"
-    if time.perf_counter() - t0 > budget_s * 3:
-        sample += " (exceeded the sampling budget)"
-    del out
-    return {"value": 1.0 / dt_step, "unit": UNIT, "cores": _blas_threads(), "kind": "oracle", "sample": sample,
-            "seconds": dt_step}
+    reps = 0
+    while True:
+        A = psi[c]
+        A2, _ = O.lanczos_expm(lambda v: O.heff_apply(Ls[c], W[c], Rs[c], v), A, delta, "real")
+        ml, d, mr = A2.shape
+        U, S, Vh, _ = O.svd_truncate(A2.reshape(ml * d, mr))
+        Q = U.reshape(ml, d, -1)
+        Lnew = O.env_left_step(Ls[c], Q, W[c])
+        Rb = O.env_right_step(Rs[c + 1], psi[c + 1], W[c + 1]) if c + 1 < n else Rs[c]
+        O.lanczos_expm(lambda v: O.keff_apply(Lnew, Rs[c], v), S[:, None] * Vh, -delta, "real")
+        reps += 1
+        if time.perf_counter() - t0 > budget_s or reps >= 50:
+            break
+    t_site = (time.perf_counter() - t0) / reps
+    dims = wl.full_bond_dims(n, args.chi_max)
+    cost = [dims[i] * dims[i + 1] * (dims[i] + dims[i + 1]) for i in range(n)]
+    t_sweep = 2.0 * t_site * sum(cost) / cost[c]
+    return {"value": 1.0 / t_sweep, "unit": UNIT, "cores": _blas_threads(), "kind": "oracle",
+            "sample": f"{reps} TDVP1 centre-site updates (chi={dims[c]}) of the same lattice, scaled to one "
+                      f"sweep by m_l m_r (m_l+m_r); Krylov and extension steps excluded (favours the CPU)",
+            "seconds_per_site_update": t_site}
 
 
 def _blas_threads():
@@ -156,29 +181,24 @@ def _blas_threads():
 
 
 def run_reference(args):
+    """The oracle on the host cores, on the same workload's bounded sample per step (see
+    cpu_baseline): rank 0 only; other ranks exit without work."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
     lat, W, psi, cfg = workload(args)
-    import oracle as O
-    p = dict(tau=args.dt, k=args.k, eps_k=1e-8, eps_m=1e-8, chi_max=args.chi_max, dt=args.dt,
-             kind="real", eps=0.0)
-    psi_c = O.left_canonicalize(psi)
+    budget = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
-        O.gse_tdvp1_step(psi_c, W, p)
-    ts = []
-    for _ in range(args.steps):
-        t = time.perf_counter()
-        O.gse_tdvp1_step(psi_c, W, p)
-        ts.append(time.perf_counter() - t)
-    total = sum(ts)
-    v = args.steps / total
+        cpu_baseline(args, W, budget_s=budget)
+    samples = [cpu_baseline(args, W, budget_s=budget) for _ in range(args.steps)]
+    t_sweep = [1.0 / x["value"] for x in samples]
+    v = args.steps / sum(t_sweep)
+    cb = dict(samples[-1])
+    cb["value"] = v
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * total / args.steps,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(t_sweep) / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
-            "data": "synthetic", "config": cfg,
-            "cpu_baseline": {"value": v, "unit": UNIT, "cores": _blas_threads(), "kind": "oracle",
-                             "sample": "full GSE-TDVP1 steps of the same workload (NumPy complex128)"},
+            "data": "synthetic", "config": cfg, "cpu_baseline": cb,
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
 
@@ -221,27 +241,22 @@ def run_gpu(args):
         dist.init_process_group("nccl")
     torch.cuda.set_device(local)
     from paper_2005_06104_gb300 import gse_tdvp as g
-    lat, W, psi, cfg = workload(args)
+    lat, W, psi0, cfg = workload(args)
     opts = dict(tau=args.dt, eps_k=1e-8, eps_m=1e-8, eps=0.0, chi_max=args.chi_max, precision=g.PREC_TF32X3)
     stream = torch.cuda.current_stream().cuda_stream
-    st = g.GseTdvp(psi, W, stream=stream, **opts)
-    init = st.get_mps()  # the canonical synthetic input, re-uploaded before each step
+    st = g.GseTdvp(psi0, W, stream=stream, **opts)
+    e_init = st.energy()
 
-    def step():
-        st.expand_basis(args.k)
-        st.sweep(args.dt, g.REAL)
+    def step(h):
+        h.expand_basis(args.k)
+        h.sweep(args.dt, g.REAL)
 
-    def reset():
-        nonlocal st
-        st.close()
-        st = g.GseTdvp(init, W, stream=stream, **opts)
-
-    for _ in range(args.warmup):
-        step()
-        reset()
+    for _ in range(args.prep_steps + args.warmup):
+        step(st)
+    start_state = st.get_mps()
+    dims_start = st.bond_dims()
     clocks = Clocks(local)
-    e0 = None
-    ts = []
+    ts, phases = [], {}
     heff_ms = heff_flops = 0.0
     heff_n = 0
     nfo = {}
@@ -249,13 +264,12 @@ def run_gpu(args):
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
-    phases = {}
     for _ in range(args.steps):
         st.profile(True)
         st.trace(True)
         a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         a.record()
-        step()
+        step(st)
         b.record()
         b.synchronize()
         ts.append(a.elapsed_time(b))
@@ -266,9 +280,9 @@ def run_gpu(args):
         heff_flops += pr["flops"]
         heff_n += pr["applies"]
         nfo = st.trunc_stats()
-        nfo["bond_dim_max"] = max(st.bond_dims())
-        reset()
     torch.cuda.synchronize()
+    if world > 1:
+        dist.barrier()
     ck = clocks.stop()
     t_rank = sum(ts) / 1e3
     if world > 1:
@@ -276,47 +290,46 @@ def run_gpu(args):
         dist.all_reduce(tt, op=dist.ReduceOp.MAX)
         t_rank = tt.item()
     value = world * args.steps / t_rank
-    # precision vs FP64: one step in each form from the same input
-    e_tc = e_64 = None
-    if rank == 0:
-        a = g.GseTdvp(init, W, stream=stream, **dict(opts, precision=g.PREC_FP64))
-        a.expand_basis(args.k)
-        a.sweep(args.dt, g.REAL)
-        e_64 = a.energy()
-        a.close()
-        b_ = g.GseTdvp(init, W, stream=stream, **opts)
-        b_.expand_basis(args.k)
-        b_.sweep(args.dt, g.REAL)
-        e_tc, n_tc = b_.energy(), b_.norm()
-        b_.close()
-    # e2e: host state in (pinned copy), one step through the public API, full state out
+    nfo["bond_dim_max"] = max(st.bond_dims())
+    nfo["bond_dims_start"] = dims_start
+    e_end = st.energy()
+    st.close()
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    # precision form vs FP64 GPU form: one step of each from the same state
+    a = g.GseTdvp(start_state, W, stream=stream, **dict(opts, precision=g.PREC_FP64))
+    step(a)
+    e_64 = a.energy()
+    a.close()
+    b_ = g.GseTdvp(start_state, W, stream=stream, **opts)
+    step(b_)
+    e_tc, n_tc = b_.energy(), b_.norm()
+    b_.close()
+    # e2e through the public API: host state in, one step, full state out
     e2e_ts = []
-    h2d = sum(a.nbytes for a in init) + sum(w.nbytes for w in W)
+    h2d = sum(x.nbytes for x in start_state) + sum(w.nbytes for w in W)
     d2h = 0
     for _ in range(max(1, min(args.steps, 2))):
         torch.cuda.synchronize()
         t = time.perf_counter()
-        s2 = g.GseTdvp(init, W, stream=stream, **opts)
-        s2.expand_basis(args.k)
-        s2.sweep(args.dt, g.REAL)
+        s2 = g.GseTdvp(start_state, W, stream=stream, **opts)
+        step(s2)
         out = s2.get_mps()
         s2.close()
         e2e_ts.append(time.perf_counter() - t)
-        d2h = sum(a.nbytes for a in out)
-    # H_eff roofline probe at chi = heff_chi
+        d2h = sum(x.nbytes for x in out)
     Wmax = max(W, key=lambda w: w.shape[0] * w.shape[3])
     pflops, pms = heff_roofline(g, torch, args.heff_chi, Wmax)
-    peaks = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json"))) if os.path.exists(
-        os.path.join(ROOT, "MEASURED_PEAKS.json")) else None
+    peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else None
     bf16 = peaks["bf16_tflops"] if peaks else 1900.0
     tf32_peak = bf16 * (1.1 / 2.25)  # measured bf16 x nominal tf32/bf16 ratio
-    if rank != 0:
-        st.close()
-        return
     cpu = None
     if not args.no_cpu_baseline:
         try:
-            cpu = cpu_baseline(args, W, init)
+            cpu = cpu_baseline(args, W)
         except Exception as ex:  # reported, never silently replaced
             cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": f"failed: {ex}"}
     achieved_step = heff_flops / (heff_ms / 1e3) / 1e12 if heff_ms > 0 else None
@@ -324,18 +337,18 @@ def run_gpu(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": sum(ts) / len(ts), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "c128 state / tf32x3 H_eff", "data": "synthetic",
+        "scaling": "weak", "vs_baseline": None, "dtype": "c128 state / tf32x3 contractions", "data": "synthetic",
         "config": dict(cfg, parallelism=f"replicas{world}"),
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": tf32_peak, "unit": "TFLOP/s",
                      "frac": achieved / tf32_peak, "traffic": None,
                      "kernel": f"H_eff apply (tcgen05 kind::tf32, 3 split products) at chi={args.heff_chi}, w=14",
-                     "peak_source": "MEASURED_PEAKS bf16_tflops x 1.1/2.25 (nominal tf32/bf16)",
+                     "peak_source": "measured bf16_tflops x 1.1/2.25 (nominal tf32/bf16)",
                      "ms_per_apply": pms, "algorithmic_flops_per_apply": pflops},
         "heff_in_step": {"applies": heff_n, "ms": heff_ms, "tflops_algorithmic": achieved_step,
                          "share_of_step": heff_ms / sum(ts) if ts else None},
         "precision_vs_fp64": {"energy_tf32x3": e_tc, "energy_fp64": e_64,
-                              "rel_energy_err": abs(e_tc - e_64) / abs(e_64) if e_64 else None,
-                              "norm_drift": abs(n_tc - 1.0)},
+                              "rel_energy_err": abs(e_tc - e_64) / abs(e_64), "norm_drift": abs(n_tc - 1.0)},
+        "energy_conservation": {"E_initial": e_init, "E_after_timed_steps": e_end, "abs_drift": abs(e_end - e_init)},
         "step_stats": nfo,
         "phases_ms_per_step": phases,
         "cpu_baseline": cpu,
@@ -346,7 +359,6 @@ def run_gpu(args):
         "clocks": ck,
     }
     print(json.dumps(line), flush=True)
-    st.close()
     if world > 1:
         dist.destroy_process_group()
 

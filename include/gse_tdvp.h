@@ -52,9 +52,11 @@ typedef enum { TDVP_REAL = 0, TDVP_IMAG = 1 } tdvp_time;
 
 /* Arithmetic of the H_eff / environment contractions. */
 typedef enum {
-  TDVP_PREC_FP64 = 0,   /* FP64 on CUDA cores                                     */
-  TDVP_PREC_TF32X3 = 1  /* tcgen05 kind::tf32, operands split hi+lo, 3 products,
-                           FP32 accumulation in tensor memory                     */
+  TDVP_PREC_FP64 = 0,       /* FP64 on CUDA cores                                       */
+  TDVP_PREC_TF32X3 = 1,     /* tcgen05 kind::tf32, operands split hi+lo, 3 products,
+                               FP32 accumulation in 128-deep chunks: H_eff and the
+                               Krylov-vector GEMMs; environments stay FP64             */
+  TDVP_PREC_TF32X3_ENV = 2  /* as TF32X3, and the sweep's environment updates too      */
 } tdvp_precision;
 
 typedef struct tdvp_handle tdvp_handle;
@@ -104,7 +106,7 @@ TDVP_API const char* tdvp_last_error(const tdvp_handle* h);
 TDVP_API const char* tdvp_status_string(tdvp_status s);
 
 /* Moves the orthogonality centre to `site` by exact gauge moves (SVDs that keep
- * every singular value above 1e-12 s_max) and builds the environments L_site and
+ * every singular value above 1e-10 s_max) and builds the environments L_site and
  * R_site.  The state is unchanged. */
 TDVP_API tdvp_status tdvp_canonicalize(tdvp_handle* h, int site);
 

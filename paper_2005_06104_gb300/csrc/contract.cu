@@ -19,58 +19,66 @@ void heff_fp64(cudaStream_t st, Scratch& s, const SiteOp& op, const cplx* x, cpl
   s.t1.ensure(s.pool, (size_t)ml * wl * d * mr);
   s.t2.ensure(s.pool, (size_t)ml * d * wr * mr);
   // T1[(a,w),(s',b')] = L[(a,w),a'] x[a',(s',b')]
-  zgemm(st, OP_N, OP_N, ml * wl, d * mr, ml, kOne, op.L, ml, x, d * mr, kZero, s.t1.data(), d * mr);
+  zgemm(st, OP_N, OP_N, ml * wl, d * mr, ml, kOne, op.L, ml, x, d * mr, kZero, s.t1.data(), d * mr, 1, 0, 0, 0, s.pool);
   // T2[(a,s),(v,b')] = sum W[w,s,s',v] T1[(a,w),(s',b')]
   wstage_left(st, *op.W, s.t1.data(), s.t2.data(), ml, mr);
   // y[(a,s),b] = sum_{(v,b')} T2[(a,s),(v,b')] R[b,(v,b')]
   zgemm(st, OP_N, OP_T, ml * d, mr, wr * mr, kOne, s.t2.data(), (long long)wr * mr, op.R, (long long)wr * mr, kZero,
-        y, mr);
+        y, mr, 1, 0, 0, 0, s.pool);
 }
 
 void heff_apply_prec(cudaStream_t st, Scratch& s, const SiteOp& op, const cplx* x, cplx* y, int precision) {
-  if (precision == TDVP_PREC_TF32X3)
+  if (precision != TDVP_PREC_FP64)
     heff_tf32x3(st, s, op, x, y);
   else
     heff_fp64(st, s, op, x, y);
 }
 
+void zgemm_prec(cudaStream_t st, Scratch& s, int precision, int opA, int opB, int M, int N, int K, const cplx* A,
+                long long lda, const cplx* B, long long ldb, cplx* C, long long ldc) {
+  if (precision != TDVP_PREC_FP64 && (long long)M * N * K >= (1LL << 21) && M >= 64 && N >= 32)
+    zgemm_tc(st, s, opA, opB, M, N, K, A, lda, B, ldb, C, ldc);
+  else
+    zgemm(st, opA, opB, M, N, K, kOne, A, lda, B, ldb, kZero, C, ldc, 1, 0, 0, 0, s.pool);
+}
+
 void keff_fp64(cudaStream_t st, Scratch& s, const cplx* L, int ml, const cplx* R, int mr, int w, const cplx* x,
-               cplx* y) {
+               cplx* y, int precision) {
   s.t3.ensure(s.pool, (size_t)ml * w * mr);
-  zgemm(st, OP_N, OP_N, ml * w, mr, ml, kOne, L, ml, x, mr, kZero, s.t3.data(), mr);
-  zgemm(st, OP_N, OP_T, ml, mr, w * mr, kOne, s.t3.data(), (long long)w * mr, R, (long long)w * mr, kZero, y, mr);
+  zgemm_prec(st, s, precision, OP_N, OP_N, ml * w, mr, ml, L, ml, x, mr, s.t3.data(), mr);
+  zgemm_prec(st, s, precision, OP_N, OP_T, ml, mr, w * mr, s.t3.data(), (long long)w * mr, R, (long long)w * mr, y, mr);
 }
 
 void env_left_fp64(cudaStream_t st, Scratch& s, const cplx* L, const WSparse& W, const cplx* A, int ml, int mr, int d,
-                   cplx* Lout) {
+                   cplx* Lout, int precision) {
   const int wl = W.wl, wr = W.wr;
   s.t1.ensure(s.pool, (size_t)ml * wl * d * mr);
   s.t2.ensure(s.pool, (size_t)ml * d * wr * mr);
-  zgemm(st, OP_N, OP_N, ml * wl, d * mr, ml, kOne, L, ml, A, d * mr, kZero, s.t1.data(), d * mr);
+  zgemm_prec(st, s, precision, OP_N, OP_N, ml * wl, d * mr, ml, L, ml, A, d * mr, s.t1.data(), d * mr);
   wstage_left(st, W, s.t1.data(), s.t2.data(), ml, mr);
   // Lout[b,(v,b')] = sum_{(a,s)} conj(A[(a,s),b]) T2[(a,s),(v,b')]
-  zgemm(st, OP_C, OP_N, mr, wr * mr, ml * d, kOne, A, mr, s.t2.data(), (long long)wr * mr, kZero, Lout,
-        (long long)wr * mr);
+  zgemm_prec(st, s, precision, OP_C, OP_N, mr, wr * mr, ml * d, A, mr, s.t2.data(), (long long)wr * mr, Lout,
+             (long long)wr * mr);
 }
 
 void env_right_fp64(cudaStream_t st, Scratch& s, const cplx* R, const WSparse& W, const cplx* B, int ml, int mr, int d,
-                    cplx* Rout) {
+                    cplx* Rout, int precision) {
   const int wl = W.wl, wr = W.wr;
   s.t3.ensure(s.pool, (size_t)d * ml * mr);
   permute_asb_sab(st, B, s.t3.data(), ml, d, mr);  // Bp[s][a][b]
   s.t1.ensure(s.pool, (size_t)mr * wr * d * ml);
   // U1[(b,v),(s',a')] = sum_b' R[(b,v),b'] Bp[(s',a'),b']
-  zgemm(st, OP_N, OP_T, mr * wr, d * ml, mr, kOne, R, mr, s.t3.data(), mr, kZero, s.t1.data(), d * ml);
+  zgemm_prec(st, s, precision, OP_N, OP_T, mr * wr, d * ml, mr, R, mr, s.t3.data(), mr, s.t1.data(), d * ml);
   s.t2.ensure(s.pool, (size_t)d * mr * wl * ml);
   // U2[s][b][w][a'] = sum W[w,s,s',v] U1[b][v][s'][a']
   wstage_right(st, W, s.t1.data(), s.t2.data(), mr, ml);
   // Rout[a,(w,a')] = sum_{(s,b)} conj(B[a,(s,b)]) U2[(s,b),(w,a')]
-  zgemm(st, OP_R, OP_N, ml, wl * ml, d * mr, kOne, B, d * mr, s.t2.data(), (long long)wl * ml, kZero, Rout,
-        (long long)wl * ml);
+  zgemm_prec(st, s, precision, OP_R, OP_N, ml, wl * ml, d * mr, B, d * mr, s.t2.data(), (long long)wl * ml, Rout,
+             (long long)wl * ml);
 }
 
 void LanczosWork::init(DevicePool* pool) {
-  c.reset(pool, 64);
+  c.reset(pool, 128);
   y.reset(pool, 64);
   if (!real) TDVP_CUDA(cudaMalloc(&real, sizeof(double) * 256));
 }
@@ -111,14 +119,10 @@ int lanczos_expm(cudaStream_t st, DevicePool* pool, Blas1& blas, LanczosWork& lw
   double last_err = 0.0;
   for (int j = 0; j < nmax; ++j) {
     op(V + (long long)j * n, wv);
-    // alpha_j = Re <v_j, w>; w -= V (V^H w), twice (full re-orthogonalisation)
-    blas.multi_dot(st, V, n, j + 1, wv, n, lw.c.data());
-    copy_real_part(st, lw.c.data(), j, alpha);
-    multi_axpy_sub(st, wv, V, n, j + 1, lw.c.data(), n);
-    blas.multi_dot(st, V, n, j + 1, wv, n, lw.c.data());
-    multi_axpy_sub(st, wv, V, n, j + 1, lw.c.data(), n);
-    blas.norm2(st, wv, n, nrm2);
-    store_beta(st, nrm2, beta + j + 1);
+    // alpha_j = Re <v_j, w>; w -= V (V^H w), twice (full re-orthogonalisation); beta = |w|
+    blas.lanczos_fused(st, 0, V, n, j + 1, wv, n, nullptr, lw.c.data(), alpha, j, nullptr, nullptr);
+    blas.lanczos_fused(st, 1, V, n, j + 1, wv, n, lw.c.data(), lw.c.data() + 64, nullptr, j, nullptr, nullptr);
+    blas.lanczos_fused(st, 2, V, n, j + 1, wv, n, lw.c.data() + 64, nullptr, nullptr, j, nrm2, beta + j + 1);
     tridiag_expv(st, alpha, beta, j + 1, delta, kind, nrm2, lw.y.data(), err);
     double h_err[2];
     TDVP_CUDA(cudaMemcpyAsync(h_err, err, sizeof(h_err), cudaMemcpyDeviceToHost, st));

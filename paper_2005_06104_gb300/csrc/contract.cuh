@@ -31,20 +31,28 @@ double heff_flops(const SiteOp& op);
 void heff_fp64(cudaStream_t st, Scratch& s, const SiteOp& op, const cplx* x, cplx* y);
 void heff_tf32x3(cudaStream_t st, Scratch& s, const SiteOp& op, const cplx* x, cplx* y);
 void heff_apply_prec(cudaStream_t st, Scratch& s, const SiteOp& op, const cplx* x, cplx* y, int precision);
+// C = opA(A) opB(B) (complex, alpha = 1, beta = 0) on the tensor cores (split TF32,
+// FP32 accumulation, FP64 output).
+void zgemm_tc(cudaStream_t st, Scratch& s, int opA, int opB, int M, int N, int K, const cplx* A, long long lda,
+              const cplx* B, long long ldb, cplx* C, long long ldc);
+// zgemm_tc when `precision` is TF32X3 and the product is large enough to fill
+// tensor-core tiles, the FP64 GEMM otherwise (alpha = 1, beta = 0).
+void zgemm_prec(cudaStream_t st, Scratch& s, int precision, int opA, int opB, int M, int N, int K, const cplx* A,
+                long long lda, const cplx* B, long long ldb, cplx* C, long long ldc);
 // Reads the tensor-core error word of the launches since the last check (synchronises);
 // throws TDVP_ERR_TIMEOUT when a bounded device wait ran out.
 void tc_check(cudaStream_t st, Scratch& s);
 
 // y[a,c] = sum L[a,w,a'] x[a',b'] R[c,w,b']   (x: ml x mr; L: ml x w x ml; R: mr x w x mr)
 void keff_fp64(cudaStream_t st, Scratch& s, const cplx* L, int ml, const cplx* R, int mr, int w, const cplx* x,
-               cplx* y);
+               cplx* y, int precision = TDVP_PREC_FP64);
 
 // Lout[b,v,b'] = sum conj(A[a,s,b]) L[a,w,a'] W[w,s,s',v] A[a',s',b']
 void env_left_fp64(cudaStream_t st, Scratch& s, const cplx* L, const WSparse& W, const cplx* A, int ml, int mr,
-                   int d, cplx* Lout);
+                   int d, cplx* Lout, int precision = TDVP_PREC_FP64);
 // Rout[a,w,a'] = sum conj(B[a,s,b]) W[w,s,s',v] R[b,v,b'] B[a',s',b']
 void env_right_fp64(cudaStream_t st, Scratch& s, const cplx* R, const WSparse& W, const cplx* B, int ml, int mr,
-                    int d, cplx* Rout);
+                    int d, cplx* Rout, int precision = TDVP_PREC_FP64);
 
 // Lanczos exponential with full re-orthogonalisation applied twice:
 // out = exp(-i delta Op) x (kind 0) or exp(-delta Op) x (kind 1), Op Hermitian.

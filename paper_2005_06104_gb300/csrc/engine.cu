@@ -9,7 +9,7 @@
 #include "engine.cuh"
 
 namespace {
-constexpr double kRankRtol = 1e-12;     // "SVD without truncation": keep s > 1e-12 s_max
+constexpr double kRankRtol = 1e-10;     // "SVD without truncation": keep s > 1e-10 s_max
 constexpr double kClusterRtol = 1e-8;   // never split a cluster of near-equal weights
 constexpr double kEigFloorRtol = 1e-12; // mixed density-matrix eigenvalues <= 1e-12 tr never count
 constexpr double kBreakdown = 1e-13;    // Lanczos invariant-subspace threshold
@@ -184,6 +184,7 @@ void Engine::init(const tdvp_mps_desc* mps, const tdvp_mpo_desc* mpo, const tdvp
 void Engine::release() {
   for (auto& ws : Wsp) ws.free_device();
   lw.release();
+  blas.release();
   for (auto& p : ev_pairs) {
     cudaEventDestroy(p.first);
     cudaEventDestroy(p.second);
@@ -232,7 +233,7 @@ void Engine::env_left(int i) {
   PhaseScope ps(tracer, PH_ENV);
   const int ml = psi.m[i], mr = psi.m[i + 1];
   L[i + 1].ensure(&pool, (size_t)mr * w[i + 1] * mr);
-  env_left_fp64(st, scr, L[i].data(), Wsp[i], psi.A[i].data(), ml, mr, d, L[i + 1].data());
+  env_left_fp64(st, scr, L[i].data(), Wsp[i], psi.A[i].data(), ml, mr, d, L[i + 1].data(), env_prec);
   Lok[i + 1] = 1;
   ++env_epoch;
 }
@@ -241,7 +242,7 @@ void Engine::env_right(int i) {
   PhaseScope ps(tracer, PH_ENV);
   const int ml = psi.m[i], mr = psi.m[i + 1];
   R[i - 1].ensure(&pool, (size_t)ml * w[i] * ml);
-  env_right_fp64(st, scr, R[i].data(), Wsp[i], psi.A[i].data(), ml, mr, d, R[i - 1].data());
+  env_right_fp64(st, scr, R[i].data(), Wsp[i], psi.A[i].data(), ml, mr, d, R[i - 1].data(), env_prec);
   Rok[i - 1] = 1;
   ++env_epoch;
 }
@@ -307,7 +308,7 @@ void Engine::move_right(int i, double eps, int cap, bool trunc) {
   scale_rows(st, C.data(), sv.Vh.data(), d_s, r, mr);
   DArr nxt(&pool, (size_t)r * d * mr2);
   zgemm(st, OP_N, OP_N, r, d * mr2, mr, kOne, C.data(), mr, psi.A[i + 1].data(), d * mr2, kZero, nxt.data(),
-        d * mr2);
+        d * mr2, 1, 0, 0, 0, &pool);
   psi.A[i] = std::move(sv.U);
   psi.A[i + 1] = std::move(nxt);
   psi.m[i + 1] = r;
@@ -334,7 +335,7 @@ void Engine::move_left(int i, double eps, int cap, bool trunc) {
   TDVP_CUDA(cudaMemcpyAsync(d_s, sv.s.data(), sizeof(double) * r, cudaMemcpyHostToDevice, st));
   scale_cols(st, C.data(), sv.U.data(), d_s, ml, r);
   DArr prv(&pool, (size_t)ml0 * d * r);
-  zgemm(st, OP_N, OP_N, ml0 * d, r, ml, kOne, psi.A[i - 1].data(), ml, C.data(), r, kZero, prv.data(), r);
+  zgemm(st, OP_N, OP_N, ml0 * d, r, ml, kOne, psi.A[i - 1].data(), ml, C.data(), r, kZero, prv.data(), r, 1, 0, 0, 0, &pool);
   psi.A[i] = std::move(sv.Vh);
   psi.A[i - 1] = std::move(prv);
   psi.m[i] = r;
@@ -386,6 +387,7 @@ void Engine::sweep(double dt, int kind) {
   const double delta = 0.5 * dt;
   const bool imag = kind == TDVP_IMAG;
   const int prec = opt.precision;
+  env_prec = (prec == TDVP_PREC_TF32X3_ENV) ? TDVP_PREC_TF32X3 : TDVP_PREC_FP64;
   lanczos_iters = lanczos_calls = 0;
   disc_eps = 0.0;
   DArr y;
@@ -434,13 +436,13 @@ void Engine::sweep(double dt, int kind) {
     const int wb = w[i + 1];
     {
       PhaseScope ps(tracer, PH_LANCZOS_BOND);
-      lanczos([&](const cplx* a, cplx* b) { keff_fp64(st, scr, Lb, r, Rb, mold, wb, a, b); }, C.data(),
+      lanczos([&](const cplx* a, cplx* b) { keff_fp64(st, scr, Lb, r, Rb, mold, wb, a, b, prec); }, C.data(),
               C2.data(), (long long)r * mold, -delta, kind);
     }
     if (imag) normalize(C2.data(), (long long)r * mold);
     DArr nxt(&pool, (size_t)r * d * mr2);
     zgemm(st, OP_N, OP_N, r, d * mr2, mold, kOne, C2.data(), mold, psi.A[i + 1].data(), d * mr2, kZero,
-          nxt.data(), d * mr2);
+          nxt.data(), d * mr2, 1, 0, 0, 0, &pool);
     psi.A[i + 1] = std::move(nxt);
     center = i + 1;
     for (int j = i + 2; j < N; ++j) Lok[j] = 0;
@@ -477,13 +479,13 @@ void Engine::sweep(double dt, int kind) {
     const int wb = w[i];
     {
       PhaseScope ps(tracer, PH_LANCZOS_BOND);
-      lanczos([&](const cplx* a, cplx* b) { keff_fp64(st, scr, Lb, mold, Rb, r, wb, a, b); }, C.data(),
+      lanczos([&](const cplx* a, cplx* b) { keff_fp64(st, scr, Lb, mold, Rb, r, wb, a, b, prec); }, C.data(),
               C2.data(), (long long)mold * r, -delta, kind);
     }
     if (imag) normalize(C2.data(), (long long)mold * r);
     DArr prv(&pool, (size_t)ml0 * d * r);
     zgemm(st, OP_N, OP_N, ml0 * d, r, mold, kOne, psi.A[i - 1].data(), mold, C2.data(), r, kZero, prv.data(),
-          r);
+          r, 1, 0, 0, 0, &pool);
     psi.A[i - 1] = std::move(prv);
     center = i - 1;
     for (int j = 0; j < i - 1; ++j) Rok[j] = 0;
@@ -491,6 +493,9 @@ void Engine::sweep(double dt, int kind) {
   }
   center = 0;
   for (int j = 1; j < N; ++j) Lok[j] = 0;
+  if (env_prec != TDVP_PREC_FP64)  // observables always see FP64 environments
+    for (int j = 0; j < N; ++j) Lok[j] = Rok[j] = 0;
+  env_prec = TDVP_PREC_FP64;
   sync();
 }
 
@@ -583,6 +588,9 @@ void KrylovOp::release() {
 // right-canonical sweep and left-to-right SVD truncation.
 void Engine::krylov_apply(const KrylovOp& kop, const MpsDev& src, MpsDev& out) {
   const cplx one = mkc(1.0, 0.0), zero = mkc(0.0, 0.0);
+  // the Krylov vectors only enrich the basis (the state itself is kept exactly by the
+  // extension), so the precision form may build them on the tensor cores
+  const int kp = opt.precision;
   std::vector<DArr> F(N);
   F[N - 1].reset(&pool, 1);
   k_one<<<1, 1, 0, st>>>(F[N - 1].data());
@@ -593,11 +601,16 @@ void Engine::krylov_apply(const KrylovOp& kop, const MpsDev& src, MpsDev& out) {
     const cplx* A = src.A[i].data();
     T1.ensure(&pool, (size_t)wr * ml * d * wr * m);
     // T1[v][(a,t)][(vb,bb)] = sum_b A[(a,t),b] F[v][b][(vb,bb)]
-    zgemm(st, OP_N, OP_N, ml * d, wr * m, m, one, A, m, F[i].data(), (long long)wr * m, zero, T1.data(),
-          (long long)wr * m, wr, 0, (long long)m * wr * m, (long long)ml * d * wr * m);
+    if (kp == TDVP_PREC_FP64)
+      zgemm(st, OP_N, OP_N, ml * d, wr * m, m, one, A, m, F[i].data(), (long long)wr * m, zero, T1.data(),
+            (long long)wr * m, wr, 0, (long long)m * wr * m, (long long)ml * d * wr * m, &pool);
+    else
+      for (int v = 0; v < wr; ++v)
+        zgemm_prec(st, scr, kp, OP_N, OP_N, ml * d, wr * m, m, A, m, F[i].data() + (long long)v * m * wr * m,
+                   (long long)wr * m, T1.data() + (long long)v * ml * d * wr * m, (long long)wr * m);
     // T2[(v,a,t,vb),(ab,tb)] = sum_bb T1[(v,a,t,vb),bb] conj(A[(ab,tb),bb])
     T2.ensure(&pool, (size_t)wr * ml * d * wr * ml * d);
-    zgemm(st, OP_N, OP_C, wr * ml * d * wr, ml * d, m, one, T1.data(), m, A, m, zero, T2.data(), ml * d);
+    zgemm_prec(st, scr, kp, OP_N, OP_C, wr * ml * d * wr, ml * d, m, T1.data(), m, A, m, T2.data(), ml * d);
     F[i - 1].reset(&pool, (size_t)wl * ml * wl * ml);
     tdvp_require(ml <= 65535, TDVP_ERR_INVALID_ARG, "krylov: bond too large");
     dim3 g(ceil_div(ml, 128), wl * wl, ml);
@@ -619,7 +632,7 @@ void Engine::krylov_apply(const KrylovOp& kop, const MpsDev& src, MpsDev& out) {
   for (int i = 0; i < N; ++i) {
     const int ml = src.m[i], mr = src.m[i + 1], wl = w[i], wr = w[i + 1];
     Y1.ensure(&pool, (size_t)mt * wl * d * mr);
-    zgemm(st, OP_N, OP_N, mt * wl, d * mr, ml, one, X.data(), ml, src.A[i].data(), d * mr, zero, Y1.data(), d * mr);
+    zgemm_prec(st, scr, kp, OP_N, OP_N, mt * wl, d * mr, ml, X.data(), ml, src.A[i].data(), d * mr, Y1.data(), d * mr);
     G.ensure(&pool, (size_t)mt * d * wr * mr);
     wstage_left(st, kop.Wsp[i], Y1.data(), G.data(), mt, mr);  // G[at][s][v][b]
     if (i == N - 1) {
@@ -630,9 +643,9 @@ void Engine::krylov_apply(const KrylovOp& kop, const MpsDev& src, MpsDev& out) {
     }
     const int n = mt * d, K = wr * mr;
     H1.ensure(&pool, (size_t)n * K);
-    zgemm(st, OP_N, OP_N, n, K, K, one, G.data(), K, F[i].data(), K, zero, H1.data(), K);
+    zgemm_prec(st, scr, kp, OP_N, OP_N, n, K, K, G.data(), K, F[i].data(), K, H1.data(), K);
     rho.ensure(&pool, (size_t)n * n);
-    zgemm(st, OP_N, OP_C, n, n, K, one, H1.data(), K, G.data(), K, zero, rho.data(), n);
+    zgemm_prec(st, scr, kp, OP_N, OP_C, n, n, K, H1.data(), K, G.data(), K, rho.data(), n);
     F[i].release();
     // eigen-decomposition of the Hermitian PSD rho through its SVD (singular values = eigenvalues)
     const double eps_k = opt.eps_k;
@@ -654,7 +667,7 @@ void Engine::krylov_apply(const KrylovOp& kop, const MpsDev& src, MpsDev& out) {
     tdvp_require(sv.rank >= 1, TDVP_ERR_NONFINITE, "krylov: zero density matrix");
     // X <- U^+ G  : [keep][v][b]
     DArr Xn(&pool, (size_t)keep * K);
-    zgemm(st, OP_C, OP_N, keep, K, n, one, sv.U.data(), keep, G.data(), K, zero, Xn.data(), K);
+    zgemm_prec(st, scr, kp, OP_C, OP_N, keep, K, n, sv.U.data(), keep, G.data(), K, Xn.data(), K);
     out.A[i] = std::move(sv.U);  // (mt d) x keep  = [at][s][new]
     out.m[i] = mt;
     out.m[i + 1] = keep;
@@ -722,8 +735,8 @@ void Engine::expand_basis(int k, const double* weights) {
       // Y P = Y - (Y B^H) B : rho_bar = (Y P)^H (Y P) = P rho~ P  (Eq. 6)
       DArr G(&pool, (size_t)rows * r);
       for (int pass = 0; pass < 2; ++pass) {
-        zgemm(st, OP_N, OP_C, rows, r, cols, kOne, Y.data(), cols, sv.Vh.data(), cols, kZero, G.data(), r);
-        zgemm(st, OP_N, OP_N, rows, cols, r, kMinusOne, G.data(), r, sv.Vh.data(), cols, kOne, Y.data(), cols);
+        zgemm(st, OP_N, OP_C, rows, r, cols, kOne, Y.data(), cols, sv.Vh.data(), cols, kZero, G.data(), r, 1, 0, 0, 0, &pool);
+        zgemm(st, OP_N, OP_N, rows, cols, r, kMinusOne, G.data(), r, sv.Vh.data(), cols, kOne, Y.data(), cols, 1, 0, 0, 0, &pool);
       }
       int cap = cols - r;
       cap = std::min(cap, opt.chi_max - r);
@@ -746,9 +759,9 @@ void Engine::expand_basis(int k, const double* weights) {
           // enforce B_bar B^H = 0 to rounding: project off range(B) twice, re-orthonormalise
           DArr Gb(&pool, (size_t)nb * r);
           for (int pass = 0; pass < 2; ++pass) {
-            zgemm(st, OP_N, OP_C, nb, r, cols, kOne, sy.Vh.data(), cols, sv.Vh.data(), cols, kZero, Gb.data(), r);
+            zgemm(st, OP_N, OP_C, nb, r, cols, kOne, sy.Vh.data(), cols, sv.Vh.data(), cols, kZero, Gb.data(), r, 1, 0, 0, 0, &pool);
             zgemm(st, OP_N, OP_N, nb, cols, r, kMinusOne, Gb.data(), r, sv.Vh.data(), cols, kOne, sy.Vh.data(),
-                  cols);
+                  cols, 1, 0, 0, 0, &pool);
           }
           SvdOut so;
           struct KeepAll {
@@ -770,18 +783,18 @@ void Engine::expand_basis(int k, const double* weights) {
                                 cudaMemcpyDeviceToDevice, st));
     // centres move by Eq. 3: C_{i-1} = A_{i-1} (C_i B'^H), likewise for every psi~_l
     DArr G(&pool, (size_t)ml * mnew);
-    zgemm(st, OP_N, OP_C, ml, mnew, cols, kOne, X, cols, Bp.data(), cols, kZero, G.data(), mnew);
+    zgemm(st, OP_N, OP_C, ml, mnew, cols, kOne, X, cols, Bp.data(), cols, kZero, G.data(), mnew, 1, 0, 0, 0, &pool);
     DArr prv(&pool, (size_t)ml0 * d * mnew);
     zgemm(st, OP_N, OP_N, ml0 * d, mnew, ml, kOne, psi.A[i - 1].data(), ml, G.data(), mnew, kZero, prv.data(),
-          mnew);
+          mnew, 1, 0, 0, 0, &pool);
     for (int l = 0; l < nk; ++l) {
       MpsDev& ph = phis[l];
       const int mlp = ph.m[i], mlp0 = ph.m[i - 1];
       DArr Gl(&pool, (size_t)mlp * mnew);
-      zgemm(st, OP_N, OP_C, mlp, mnew, cols, kOne, ph.A[i].data(), cols, Bp.data(), cols, kZero, Gl.data(), mnew);
+      zgemm(st, OP_N, OP_C, mlp, mnew, cols, kOne, ph.A[i].data(), cols, Bp.data(), cols, kZero, Gl.data(), mnew, 1, 0, 0, 0, &pool);
       DArr pp(&pool, (size_t)mlp0 * d * mnew);
       zgemm(st, OP_N, OP_N, mlp0 * d, mnew, mlp, kOne, ph.A[i - 1].data(), mlp, Gl.data(), mnew, kZero, pp.data(),
-            mnew);
+            mnew, 1, 0, 0, 0, &pool);
       ph.A[i - 1] = std::move(pp);
       ph.A[i].release();
       ph.m[i] = mnew;

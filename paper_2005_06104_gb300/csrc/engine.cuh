@@ -112,6 +112,7 @@ struct Engine {
   Scratch scr;
   LanczosWork lw;
   long long env_epoch = 0;  // bumped whenever an environment is rebuilt or dropped
+  int env_prec = TDVP_PREC_FP64;  // arithmetic of environment updates (the sweep's precision while it runs)
   // optional timing of the H_eff applies (CUDA events on the engine stream)
   bool profile = false;
   std::vector<cudaEvent_t> ev_pool;

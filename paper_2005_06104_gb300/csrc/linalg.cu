@@ -13,17 +13,30 @@
 namespace {
 constexpr int GB_M = 64, GB_N = 64, GB_K = 8;
 
+// nsplit > 1: blockIdx.z = batch * nsplit + split; split s sums K range
+// [s*kchunk, min(K, (s+1)*kchunk)) into the partial buffer P[s][batch][M][N]
+// (alpha applied, beta left to the reduction).
 template <int OPA, int OPB>
 __global__ void __launch_bounds__(256)
     k_zgemm(int M, int N, int K, cplx alpha, const cplx* __restrict__ A, long long lda,
             long long sA, const cplx* __restrict__ B, long long ldb, long long sB, cplx beta,
-            cplx* __restrict__ C, long long ldc, long long sC) {
+            cplx* __restrict__ C, long long ldc, long long sC, int nsplit, int kchunk, int nbatch,
+            cplx* __restrict__ P) {
   __shared__ cplx As[GB_K][GB_M + 1];
   __shared__ cplx Bs[GB_K][GB_N + 1];
-  const long long bz = blockIdx.z;
+  const int split = blockIdx.z % nsplit;
+  const long long bz = blockIdx.z / nsplit;
   A += bz * sA;
   B += bz * sB;
-  C += bz * sC;
+  if (nsplit > 1) {
+    C = P + ((long long)split * nbatch + bz) * (long long)M * N;
+    ldc = N;
+    beta = mkc(0.0, 0.0);
+  } else {
+    C += bz * sC;
+  }
+  const int kbeg = split * kchunk;
+  const int kend = min(K, kbeg + kchunk);
   const int m0 = blockIdx.y * GB_M, n0 = blockIdx.x * GB_N;
   const int tid = threadIdx.x, tx = tid & 15, ty = tid >> 4;
   cplx acc[4][4];
@@ -32,7 +45,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int j = 0; j < 4; ++j) acc[i][j] = mkc(0.0, 0.0);
 
-  for (int k0 = 0; k0 < K; k0 += GB_K) {
+  for (int k0 = kbeg; k0 < kend; k0 += GB_K) {
 #pragma unroll
     for (int e = tid; e < GB_M * GB_K; e += 256) {
       int m, k;
@@ -45,7 +58,7 @@ __global__ void __launch_bounds__(256)
       }
       const int gm = m0 + m, gk = k0 + k;
       cplx v = mkc(0.0, 0.0);
-      if (gm < M && gk < K) {
+      if (gm < M && gk < kend) {
         v = (OPA == OP_N || OPA == OP_R) ? A[(long long)gm * lda + gk] : A[(long long)gk * lda + gm];
         if (OPA == OP_C || OPA == OP_R) v.y = -v.y;
       }
@@ -63,7 +76,7 @@ __global__ void __launch_bounds__(256)
       }
       const int gn = n0 + n, gk = k0 + k;
       cplx v = mkc(0.0, 0.0);
-      if (gn < N && gk < K) {
+      if (gn < N && gk < kend) {
         v = (OPB == OP_N || OPB == OP_R) ? B[(long long)gk * ldb + gn] : B[(long long)gn * ldb + gk];
         if (OPB == OP_C || OPB == OP_R) v.y = -v.y;
       }
@@ -101,22 +114,39 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+#define ZG_ARGS M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, ns, kc, nb, P
 template <int OPA>
 void zgemm_b(int opB, dim3 g, cudaStream_t st, int M, int N, int K, cplx alpha, const cplx* A,
              long long lda, long long sA, const cplx* B, long long ldb, long long sB, cplx beta,
-             cplx* C, long long ldc, long long sC) {
+             cplx* C, long long ldc, long long sC, int ns, int kc, int nb, cplx* P) {
   switch (opB) {
-    case OP_N: k_zgemm<OPA, OP_N><<<g, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC); break;
-    case OP_T: k_zgemm<OPA, OP_T><<<g, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC); break;
-    case OP_C: k_zgemm<OPA, OP_C><<<g, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC); break;
-    default:   k_zgemm<OPA, OP_R><<<g, 256, 0, st>>>(M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC); break;
+    case OP_N: k_zgemm<OPA, OP_N><<<g, 256, 0, st>>>(ZG_ARGS); break;
+    case OP_T: k_zgemm<OPA, OP_T><<<g, 256, 0, st>>>(ZG_ARGS); break;
+    case OP_C: k_zgemm<OPA, OP_C><<<g, 256, 0, st>>>(ZG_ARGS); break;
+    default:   k_zgemm<OPA, OP_R><<<g, 256, 0, st>>>(ZG_ARGS); break;
   }
+}
+#undef ZG_ARGS
+
+// C[b][m][n] = sum_s P[s][b][m][n] + beta C[b][m][n]  (fixed summation order)
+__global__ void k_splitk_reduce(const cplx* __restrict__ P, int nsplit, int nbatch, int M, int N, cplx beta,
+                                cplx* __restrict__ C, long long ldc, long long sC) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  const long long per = (long long)M * N;
+  if (e >= per * nbatch) return;
+  const long long b = e / per, r = e % per;
+  const int m = r / N, n = r % N;
+  cplx acc = mkc(0.0, 0.0);
+  for (int s = 0; s < nsplit; ++s) acc = cadd(acc, P[((long long)s * nbatch + b) * per + r]);
+  cplx* c = C + b * sC + (long long)m * ldc + n;
+  if (beta.x != 0.0 || beta.y != 0.0) acc = cadd(acc, cmul(beta, *c));
+  *c = acc;
 }
 }  // namespace
 
 void zgemm(cudaStream_t st, int opA, int opB, int M, int N, int K, cplx alpha, const cplx* A,
            long long lda, const cplx* B, long long ldb, cplx beta, cplx* C, long long ldc,
-           int batch, long long sA, long long sB, long long sC) {
+           int batch, long long sA, long long sB, long long sC, DevicePool* ws) {
   if (M <= 0 || N <= 0 || batch <= 0) return;
   tdvp_require(batch <= 65535, TDVP_ERR_INVALID_ARG, "zgemm: batch too large");
   tdvp_require(ceil_div(M, GB_M) <= 65535, TDVP_ERR_INVALID_ARG, "zgemm: M too large");
@@ -127,14 +157,39 @@ void zgemm(cudaStream_t st, int opA, int opB, int M, int N, int K, cplx alpha, c
         TDVP_CUDA(cudaMemsetAsync(C + b * sC + (long long)r * ldc, 0, sizeof(cplx) * N, st));
     return;
   }
-  dim3 g(ceil_div(N, GB_N), ceil_div(M, GB_M), batch);
+  // FP64 throughput per SM is low on this part: a GEMM with few output tiles and a
+  // long K is split along K over enough blocks to occupy the GPU (needs a pool).
+  const long long tiles = (long long)ceil_div(N, GB_N) * ceil_div(M, GB_M) * batch;
+  int ns = 1, kc = K;
+  static int sms = 0;
+  if (!sms) {
+    int dev = 0;
+    cudaGetDevice(&dev);
+    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+    if (sms <= 0) sms = 148;
+  }
+  if (ws && tiles < 2LL * sms && K >= 32) {
+    ns = (int)std::min<long long>((2LL * sms + tiles - 1) / tiles, (K + 15) / 16);
+    ns = std::max(1, std::min(ns, 65535 / batch));
+    kc = ((K + ns - 1) / ns + GB_K - 1) / GB_K * GB_K;
+    ns = (K + kc - 1) / kc;
+  }
+  DArr part;
+  if (ns > 1) part.reset(ws, (size_t)ns * batch * M * N);
+  dim3 g(ceil_div(N, GB_N), ceil_div(M, GB_M), batch * ns);
+  cplx* P = part.data();
   switch (opA) {
-    case OP_N: zgemm_b<OP_N>(opB, g, st, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC); break;
-    case OP_T: zgemm_b<OP_T>(opB, g, st, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC); break;
-    case OP_C: zgemm_b<OP_C>(opB, g, st, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC); break;
-    default:   zgemm_b<OP_R>(opB, g, st, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC); break;
+    case OP_N: zgemm_b<OP_N>(opB, g, st, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, ns, kc, batch, P); break;
+    case OP_T: zgemm_b<OP_T>(opB, g, st, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, ns, kc, batch, P); break;
+    case OP_C: zgemm_b<OP_C>(opB, g, st, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, ns, kc, batch, P); break;
+    default:   zgemm_b<OP_R>(opB, g, st, M, N, K, alpha, A, lda, sA, B, ldb, sB, beta, C, ldc, sC, ns, kc, batch, P); break;
   }
   TDVP_CHECK_LAUNCH();
+  if (ns > 1) {
+    const long long n = (long long)M * N * batch;
+    k_splitk_reduce<<<ceil_div(n, 256), 256, 0, st>>>(P, ns, batch, M, N, beta, C, ldc, sC);
+    TDVP_CHECK_LAUNCH();
+  }
 }
 
 // ============================================================================
@@ -416,10 +471,132 @@ __global__ void k_copy_real(const cplx* c, int j, double* alpha) { alpha[j] = c[
 __global__ void k_store_beta(const double* nrm2, double* slot) { *slot = sqrt(*nrm2); }
 }  // namespace
 
+static int red_blocks(long long n, int max_blocks);
+
 void Blas1::init(DevicePool* p, int sm_count) {
   pool = p;
   max_blocks = 2 * sm_count;
   partial.reset(pool, (size_t)max_blocks * 64);
+  if (!counter) {
+    TDVP_CUDA(cudaMalloc(&counter, sizeof(unsigned)));
+    TDVP_CUDA(cudaMemset(counter, 0, sizeof(unsigned)));
+  }
+}
+
+void Blas1::release() {
+  if (counter) cudaFree(counter);
+  counter = nullptr;
+  partial.release();
+}
+
+// ---------------------------------------------------------------------------
+// Fused Lanczos re-orthogonalisation steps.  Each kernel writes per-block
+// partial sums; the last block to finish (atomic ticket, no waiting) reduces
+// them in a fixed order, so results are deterministic and no block spins.
+namespace {
+__device__ __forceinline__ bool last_block(unsigned* counter) {
+  __shared__ bool is_last;
+  __threadfence();
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    const unsigned t = atomicAdd(counter, 1u);
+    is_last = (t == gridDim.x - 1);
+  }
+  __syncthreads();
+  return is_last;
+}
+
+// mode 0: c = V^H w                        (alpha[j] = Re c[j])
+// mode 1: w -= V cin;  c = V^H w
+// mode 2: w -= V cin;  nrm2 = |w|^2, beta_slot = sqrt(nrm2)
+__global__ void __launch_bounds__(RED_THREADS)
+    k_lanczos_fused(int mode, const cplx* __restrict__ V, long long ldv, int nvec, cplx* __restrict__ w, long long n,
+                    const cplx* __restrict__ cin, cplx* __restrict__ cout, double* __restrict__ alpha, int j,
+                    double* __restrict__ nrm2, double* __restrict__ beta_slot, cplx* __restrict__ partial,
+                    unsigned* __restrict__ counter) {
+  __shared__ cplx cs[64];
+  __shared__ cplx red[MD_CH][RED_THREADS / 32];
+  __shared__ double dred[RED_THREADS / 32];
+  const int G = gridDim.x, warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  if (mode >= 1) {
+    for (int k = threadIdx.x; k < nvec; k += blockDim.x) cs[k] = cin[k];
+    __syncthreads();
+    for (long long i = (long long)blockIdx.x * RED_THREADS + threadIdx.x; i < n; i += (long long)G * RED_THREADS) {
+      cplx acc = mkc(0.0, 0.0);
+      for (int k = 0; k < nvec; ++k) cfma(acc, V[(long long)k * ldv + i], cs[k]);
+      w[i] = csub(w[i], acc);
+    }
+    // each thread re-reads only the w[i] it wrote: no block-wide barrier needed
+  }
+  if (mode <= 1) {
+    for (int k0 = 0; k0 < nvec; k0 += MD_CH) {
+      cplx acc[MD_CH];
+#pragma unroll
+      for (int q = 0; q < MD_CH; ++q) acc[q] = mkc(0.0, 0.0);
+      for (long long i = (long long)blockIdx.x * RED_THREADS + threadIdx.x; i < n; i += (long long)G * RED_THREADS) {
+        const cplx wi = w[i];
+#pragma unroll
+        for (int q = 0; q < MD_CH; ++q)
+          if (k0 + q < nvec) cfma_conj(acc[q], V[(long long)(k0 + q) * ldv + i], wi);
+      }
+#pragma unroll
+      for (int q = 0; q < MD_CH; ++q) {
+        cplx t = warp_sum(acc[q]);
+        if (lane == 0) red[q][warp] = t;
+      }
+      __syncthreads();
+      if (threadIdx.x < MD_CH && k0 + (int)threadIdx.x < nvec) {
+        cplx t = mkc(0.0, 0.0);
+        for (int u = 0; u < RED_THREADS / 32; ++u) t = cadd(t, red[threadIdx.x][u]);
+        partial[(long long)(k0 + threadIdx.x) * G + blockIdx.x] = t;
+      }
+      __syncthreads();
+    }
+    if (last_block(counter)) {
+      for (int k = warp; k < nvec; k += RED_THREADS / 32) {
+        cplx t = mkc(0.0, 0.0);
+        for (int g = lane; g < G; g += 32) t = cadd(t, partial[(long long)k * G + g]);
+        t = warp_sum(t);
+        if (lane == 0) {
+          cout[k] = t;
+          if (mode == 0 && k == j) alpha[j] = t.x;
+        }
+      }
+      if (threadIdx.x == 0) *counter = 0;
+    }
+  } else {
+    double a = 0.0;
+    for (long long i = (long long)blockIdx.x * RED_THREADS + threadIdx.x; i < n; i += (long long)G * RED_THREADS)
+      a += cabs2(w[i]);
+    a = warp_sum(a);
+    if (lane == 0) dred[warp] = a;
+    __syncthreads();
+    double* dpart = reinterpret_cast<double*>(partial);
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int u = 0; u < RED_THREADS / 32; ++u) t += dred[u];
+      dpart[blockIdx.x] = t;
+    }
+    if (last_block(counter)) {
+      if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int g = 0; g < G; ++g) t += dpart[g];
+        *nrm2 = t;
+        *beta_slot = sqrt(t);
+        *counter = 0;
+      }
+    }
+  }
+}
+}  // namespace
+
+void Blas1::lanczos_fused(cudaStream_t st, int mode, const cplx* V, long long ldv, int nvec, cplx* w, long long n,
+                          const cplx* cin, cplx* cout, double* alpha, int j, double* nrm2, double* beta_slot) {
+  tdvp_require(nvec >= 1 && nvec <= 64, TDVP_ERR_INVALID_ARG, "lanczos_fused: nvec out of range");
+  const int G = red_blocks(n, max_blocks);
+  k_lanczos_fused<<<G, RED_THREADS, 0, st>>>(mode, V, ldv, nvec, w, n, cin, cout, alpha, j, nrm2, beta_slot,
+                                             partial.data(), counter);
+  TDVP_CHECK_LAUNCH();
 }
 
 static int red_blocks(long long n, int max_blocks) {
@@ -1163,4 +1340,197 @@ void copy_block(cudaStream_t st, cplx* dst, long long ldd, const cplx* src, long
   if (!n) return;
   k_copy_block<<<ceil_div(n, 256), 256, 0, st>>>(dst, ldd, src, lds, rows, cols);
   TDVP_CHECK_LAUNCH();
+}
+
+// ============================================================================
+// Block-structured SVD.  Quantum numbers that the dynamics conserves (S^z for
+// the Heisenberg models) make every matrix factorised by the method block
+// diagonal up to a permutation, with the forbidden entries exactly zero in
+// floating point (they are sums of products with a zero factor).  Rows and
+// columns linked by nonzero entries form connected components; each component
+// is an independent, much smaller SVD.  Singular values from all components are
+// merged and sorted, so the selection rule sees the same spectrum as the dense
+// SVD; U and Vh are scattered back in that global order.
+// ============================================================================
+namespace {
+__global__ void k_nonzero_mask(const cplx* __restrict__ M, int rows, int cols, int words,
+                               unsigned* __restrict__ mask) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)rows * words) return;
+  const int w = e % words;
+  const long long r = e / words;
+  unsigned bits = 0;
+  for (int b = 0; b < 32; ++b) {
+    const int c = w * 32 + b;
+    if (c < cols) {
+      const cplx v = M[r * cols + c];
+      if (v.x != 0.0 || v.y != 0.0) bits |= 1u << b;
+    }
+  }
+  mask[e] = bits;
+}
+
+__global__ void k_gather_block(const cplx* __restrict__ M, int cols, const int* __restrict__ rmap,
+                               const int* __restrict__ cmap, int pb, int qb, cplx* __restrict__ out) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)pb * qb) return;
+  const int i = e / qb, j = e % qb;
+  out[e] = M[(long long)rmap[i] * cols + cmap[j]];
+}
+
+// dst[map[i] * ld + col[l]] = src[i * lds + l] for the listed local columns l
+__global__ void k_scatter_cols(const cplx* __restrict__ src, int nrows, int lds, const int* __restrict__ rowmap,
+                               const int* __restrict__ sel_local, const int* __restrict__ sel_global, int nsel,
+                               cplx* __restrict__ dst, int ld, int transpose) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)nrows * nsel) return;
+  const int i = e / nsel, k = e % nsel;
+  const cplx v = transpose ? src[(long long)sel_local[k] * lds + i] : src[(long long)i * lds + sel_local[k]];
+  if (transpose)
+    dst[(long long)sel_global[k] * ld + rowmap[i]] = v;   // Vh: rows = kept index, cols = global column
+  else
+    dst[(long long)rowmap[i] * ld + sel_global[k]] = v;   // U: rows = global row, cols = kept index
+}
+
+struct DSU {
+  std::vector<int> p;
+  explicit DSU(int n) : p(n) { std::iota(p.begin(), p.end(), 0); }
+  int find(int x) {
+    while (p[x] != x) {
+      p[x] = p[p[x]];
+      x = p[x];
+    }
+    return x;
+  }
+  void unite(int a, int b) {
+    a = find(a);
+    b = find(b);
+    if (a != b) p[std::max(a, b)] = std::min(a, b);
+  }
+};
+
+int keep_all_rule(const std::vector<double>& s, void*) { return (int)s.size(); }
+}  // namespace
+
+void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows, int cols,
+                      int (*select)(const std::vector<double>& s, void* ctx), void* ctx, SvdOut& out, bool want_u,
+                      bool want_v) {
+  const long long n = (long long)rows * cols;
+  if (rows <= 1 || cols <= 1 || n > (1LL << 22)) {
+    svd_jacobi_keep(st, pool, M, rows, cols, select, ctx, out, want_u, want_v);
+    return;
+  }
+  const int words = (cols + 31) / 32;
+  std::vector<unsigned> mask((size_t)rows * words);
+  {
+    RawBuf dm;
+    dm.ensure(pool, sizeof(unsigned) * mask.size());
+    const long long e = (long long)rows * words;
+    k_nonzero_mask<<<ceil_div(e, 256), 256, 0, st>>>(M, rows, cols, words, dm.as<unsigned>());
+    TDVP_CHECK_LAUNCH();
+    TDVP_CUDA(cudaMemcpyAsync(mask.data(), dm.as<unsigned>(), sizeof(unsigned) * mask.size(),
+                              cudaMemcpyDeviceToHost, st));
+    TDVP_CUDA(cudaStreamSynchronize(st));
+  }
+  DSU dsu(rows + cols);
+  std::vector<char> row_nz(rows, 0), col_nz(cols, 0);
+  for (int r = 0; r < rows; ++r)
+    for (int w = 0; w < words; ++w) {
+      unsigned bits = mask[(size_t)r * words + w];
+      while (bits) {
+        const int b = __builtin_ctz(bits);
+        bits &= bits - 1;
+        const int c = w * 32 + b;
+        dsu.unite(r, rows + c);
+        row_nz[r] = col_nz[c] = 1;
+      }
+    }
+  std::map<int, std::pair<std::vector<int>, std::vector<int>>> comp;
+  for (int r = 0; r < rows; ++r)
+    if (row_nz[r]) comp[dsu.find(r)].first.push_back(r);
+  for (int c = 0; c < cols; ++c)
+    if (col_nz[c]) comp[dsu.find(rows + c)].second.push_back(c);
+  if (comp.size() <= 1) {
+    svd_jacobi_keep(st, pool, M, rows, cols, select, ctx, out, want_u, want_v);
+    return;
+  }
+  // per-component SVDs, every singular value kept
+  struct Part {
+    std::vector<int> r, c;
+    SvdOut sv;
+    int* d_r = nullptr;
+    int* d_c = nullptr;
+  };
+  std::vector<Part> parts;
+  parts.reserve(comp.size());
+  for (auto& kv : comp) {
+    Part pt;
+    pt.r = std::move(kv.second.first);
+    pt.c = std::move(kv.second.second);
+    parts.push_back(std::move(pt));
+  }
+  std::vector<std::pair<double, std::pair<int, int>>> all;  // (s, (part, local index))
+  for (int b = 0; b < (int)parts.size(); ++b) {
+    Part& pt = parts[b];
+    const int pb = (int)pt.r.size(), qb = (int)pt.c.size();
+    TDVP_CUDA(cudaMallocAsync(&pt.d_r, sizeof(int) * pb, st));
+    TDVP_CUDA(cudaMallocAsync(&pt.d_c, sizeof(int) * qb, st));
+    TDVP_CUDA(cudaMemcpyAsync(pt.d_r, pt.r.data(), sizeof(int) * pb, cudaMemcpyHostToDevice, st));
+    TDVP_CUDA(cudaMemcpyAsync(pt.d_c, pt.c.data(), sizeof(int) * qb, cudaMemcpyHostToDevice, st));
+    DArr blk(pool, (size_t)pb * qb);
+    k_gather_block<<<ceil_div((long long)pb * qb, 256), 256, 0, st>>>(M, cols, pt.d_r, pt.d_c, pb, qb, blk.data());
+    TDVP_CHECK_LAUNCH();
+    svd_jacobi_keep(st, pool, blk.data(), pb, qb, keep_all_rule, nullptr, pt.sv, want_u, want_v);
+    for (int k = 0; k < (int)pt.sv.s.size(); ++k) all.push_back({pt.sv.s[k], {b, k}});
+  }
+  std::stable_sort(all.begin(), all.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+  out.rows = rows;
+  out.cols = cols;
+  out.s.resize(std::min(rows, cols), 0.0);
+  for (size_t k = 0; k < all.size() && k < out.s.size(); ++k) out.s[k] = all[k].first;
+  const int keep = std::max(0, std::min((int)all.size(), select(out.s, ctx)));
+  out.rank = keep;
+  out.sweeps = 0;
+  out.U.release();
+  out.Vh.release();
+  if (keep > 0) {
+    if (want_u) {
+      out.U.reset(pool, (size_t)rows * keep);
+      fill_zero(st, out.U.data(), (long long)rows * keep);
+    }
+    if (want_v) {
+      out.Vh.reset(pool, (size_t)keep * cols);
+      fill_zero(st, out.Vh.data(), (long long)keep * cols);
+    }
+    for (int b = 0; b < (int)parts.size(); ++b) {
+      std::vector<int> sl, sg;
+      for (int k = 0; k < keep; ++k)
+        if (all[k].second.first == b) {
+          sl.push_back(all[k].second.second);
+          sg.push_back(k);
+        }
+      if (sl.empty()) continue;
+      Part& pt = parts[b];
+      const int pb = (int)pt.r.size(), qb = (int)pt.c.size(), kb = pt.sv.rank;
+      int *d_sl = nullptr, *d_sg = nullptr;
+      TDVP_CUDA(cudaMallocAsync(&d_sl, sizeof(int) * sl.size(), st));
+      TDVP_CUDA(cudaMallocAsync(&d_sg, sizeof(int) * sg.size(), st));
+      TDVP_CUDA(cudaMemcpyAsync(d_sl, sl.data(), sizeof(int) * sl.size(), cudaMemcpyHostToDevice, st));
+      TDVP_CUDA(cudaMemcpyAsync(d_sg, sg.data(), sizeof(int) * sg.size(), cudaMemcpyHostToDevice, st));
+      const int ns = (int)sl.size();
+      if (want_u)
+        k_scatter_cols<<<ceil_div((long long)pb * ns, 256), 256, 0, st>>>(pt.sv.U.data(), pb, kb, pt.d_r, d_sl, d_sg,
+                                                                          ns, out.U.data(), keep, 0);
+      if (want_v)
+        k_scatter_cols<<<ceil_div((long long)qb * ns, 256), 256, 0, st>>>(pt.sv.Vh.data(), qb, qb, pt.d_c, d_sl, d_sg,
+                                                                          ns, out.Vh.data(), cols, 1);
+      TDVP_CHECK_LAUNCH();
+      TDVP_CUDA(cudaFreeAsync(d_sl, st));
+      TDVP_CUDA(cudaFreeAsync(d_sg, st));
+    }
+  }
+  for (auto& pt : parts) {
+    TDVP_CUDA(cudaFreeAsync(pt.d_r, st));
+    TDVP_CUDA(cudaFreeAsync(pt.d_c, st));
+  }
 }

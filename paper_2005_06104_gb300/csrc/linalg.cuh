@@ -6,10 +6,12 @@ enum GemmOp { OP_N = 0, OP_T = 1, OP_C = 2, OP_R = 3 };  // R = conjugate, not t
 
 // C[m,n] = alpha * sum_k opA(A)[m,k] opB(B)[k,n] + beta * C[m,n], all row-major.
 // opA(A)[m,k] = A[m*lda+k] (N), A[k*lda+m] (T), conj(A[k*lda+m]) (C), conj(A[m*lda+k]) (R).
-// batch > 1 uses strides sA, sB, sC (elements).
+// batch > 1 uses strides sA, sB, sC (elements).  With a pool `ws`, GEMMs with few
+// output tiles split K over more blocks (partials reduced in a fixed order);
+// without one nothing is allocated.
 void zgemm(cudaStream_t st, int opA, int opB, int M, int N, int K, cplx alpha, const cplx* A,
            long long lda, const cplx* B, long long ldb, cplx beta, cplx* C, long long ldc,
-           int batch = 1, long long sA = 0, long long sB = 0, long long sC = 0);
+           int batch = 1, long long sA = 0, long long sB = 0, long long sC = 0, DevicePool* ws = nullptr);
 
 // Sparse description of one MPO site tensor W[w][s][t][v] for the contraction
 // stages: entries grouped by output (s, v) for left moves and by (s, w) for
@@ -56,6 +58,14 @@ struct Blas1 {
                  long long n, cplx* out);
   // *out = sum_i |x_i|^2 (double in device memory)
   void norm2(cudaStream_t st, const cplx* x, long long n, double* out);
+  // One launch of a fused Lanczos step (partials reduced by the last block):
+  //   mode 0: cout = V^H w, alpha[j] = Re cout[j]
+  //   mode 1: w -= V cin, then cout = V^H w
+  //   mode 2: w -= V cin, then *nrm2 = |w|^2, *beta_slot = sqrt(*nrm2)
+  void lanczos_fused(cudaStream_t st, int mode, const cplx* V, long long ldv, int nvec, cplx* w, long long n,
+                     const cplx* cin, cplx* cout, double* alpha, int j, double* nrm2, double* beta_slot);
+  unsigned* counter = nullptr;  // ticket of the last-block reductions (reset by that block)
+  void release();
 };
 // w[i] -= sum_k V[k*ldv+i] c[k]
 void multi_axpy_sub(cudaStream_t st, cplx* w, const cplx* V, long long ldv, int nvec,
@@ -94,13 +104,18 @@ void svd_jacobi(cudaStream_t st, DevicePool* pool, const cplx* M, int rows, int 
 void svd_jacobi_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows, int cols,
                      int (*select)(const std::vector<double>& s, void* ctx), void* ctx,
                      SvdOut& out, bool want_u, bool want_v);
+// The same contract, exploiting block structure (exact zeros from conserved
+// quantum numbers): independent SVDs per connected block, merged spectrum.
+void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows, int cols,
+                      int (*select)(const std::vector<double>& s, void* ctx), void* ctx,
+                      SvdOut& out, bool want_u, bool want_v);
 template <class Select>
 inline void svd_jacobi(cudaStream_t st, DevicePool* pool, const cplx* M, int rows, int cols,
                        Select select, SvdOut& out, bool want_u, bool want_v) {
   auto thunk = [](const std::vector<double>& s, void* ctx) -> int {
     return (*static_cast<Select*>(ctx))(s);
   };
-  svd_jacobi_keep(st, pool, M, rows, cols, thunk, &select, out, want_u, want_v);
+  svd_blocked_keep(st, pool, M, rows, cols, thunk, &select, out, want_u, want_v);
 }
 
 // rows-of-Vh scaling helpers: out[r][c] = s[r] * Vh[r][c]; out[i][r] = U[i][r] * s[r]

@@ -433,6 +433,46 @@ void gemm_tf32x3(cudaStream_t st, const float* Ahi, const float* Alo, const floa
 
 inline int pad32(int k) { return (k + 31) / 32 * 32; }
 inline int pad128(int k) { return (k + 127) / 128 * 128; }
+
+// A operand of a general complex GEMM: hi/lo[m][k2] = split(opA(A)[m][k2/2] re|im),
+// zero outside M x 2K (rows padded to Mp, row length ld)
+__global__ void k_split_opa(const cplx* __restrict__ A, long long lda, int opA, int M, int K, int Mp, int ld,
+                            float* __restrict__ hi, float* __restrict__ lo) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)Mp * ld) return;
+  const int k2 = e % ld;
+  const long long m = e / ld;
+  float h = 0.f, l = 0.f;
+  if (m < M && k2 < 2 * K) {
+    const int k = k2 >> 1;
+    cplx v = (opA == OP_N || opA == OP_R) ? A[m * lda + k] : A[(long long)k * lda + m];
+    if (opA == OP_C || opA == OP_R) v.y = -v.y;
+    split2((k2 & 1) ? v.y : v.x, h, l);
+  }
+  hi[e] = h;
+  lo[e] = l;
+}
+
+// B operand expanded to the real (2N x 2K) form from opB(B)[k][n]
+__global__ void k_expand_opb(const cplx* __restrict__ B, long long ldb, int opB, int K, int N, int rows_pad, int ld,
+                             float* __restrict__ hi, float* __restrict__ lo) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)rows_pad * ld) return;
+  const int k2 = e % ld;
+  const long long n2 = e / ld;
+  float h = 0.f, l = 0.f;
+  if (k2 < 2 * K && n2 < 2LL * N) {
+    const int k = k2 >> 1, c = k2 & 1;
+    const long long n = n2 >> 1;
+    const int cp = (int)(n2 & 1);
+    cplx v = (opB == OP_N || opB == OP_R) ? B[(long long)k * ldb + n] : B[n * ldb + k];
+    if (opB == OP_C || opB == OP_R) v.y = -v.y;
+    const double x = (cp == 0) ? ((c == 0) ? v.x : -v.y) : ((c == 0) ? v.y : v.x);
+    split2(x, h, l);
+  }
+  hi[e] = h;
+  lo[e] = l;
+}
 }  // namespace tc
 
 using namespace tc;
@@ -499,6 +539,32 @@ void heff_tf32x3(cudaStream_t st, Scratch& s, const SiteOp& op, const cplx* x, c
   // stage 3: y[(a,s)][(b,c)] = T2 R^T  (FP64 output, interleaved complex)
   gemm_tf32x3(st, c.T2hi.as<float>(), c.T2lo.as<float>(), c.Rhi.as<float>(), c.Rlo.as<float>(), M3, N3, K3p,
               reinterpret_cast<double*>(y), N3, true, c.err.as<int>());
+  c.pending = true;
+}
+
+void zgemm_tc(cudaStream_t st, Scratch& s, int opA, int opB, int M, int N, int K, const cplx* A, long long lda,
+              const cplx* B, long long ldb, cplx* C, long long ldc) {
+  if (M <= 0 || N <= 0) return;
+  DevicePool* pool = s.pool;
+  TcEnvCache& c = s.tc;
+  if (c.err.bytes() == 0) {
+    c.err.ensure(pool, sizeof(int));
+    TDVP_CUDA(cudaMemsetAsync(c.err.as<int>(), 0, sizeof(int), st));
+  }
+  const int Kp = pad32(std::max(1, 2 * K)), Mp = pad128(M), Np = pad128(2 * N);
+  RawBuf ahi, alo, bhi, blo;
+  ahi.ensure(pool, sizeof(float) * (size_t)Mp * Kp);
+  alo.ensure(pool, sizeof(float) * (size_t)Mp * Kp);
+  bhi.ensure(pool, sizeof(float) * (size_t)Np * Kp);
+  blo.ensure(pool, sizeof(float) * (size_t)Np * Kp);
+  long long n = (long long)Mp * Kp;
+  k_split_opa<<<ceil_div(n, 256), 256, 0, st>>>(A, lda, opA, M, K, Mp, Kp, ahi.as<float>(), alo.as<float>());
+  TDVP_CHECK_LAUNCH();
+  n = (long long)Np * Kp;
+  k_expand_opb<<<ceil_div(n, 256), 256, 0, st>>>(B, ldb, opB, K, N, Np, Kp, bhi.as<float>(), blo.as<float>());
+  TDVP_CHECK_LAUNCH();
+  gemm_tf32x3(st, ahi.as<float>(), alo.as<float>(), bhi.as<float>(), blo.as<float>(), M, 2 * N, Kp,
+              reinterpret_cast<double*>(C), 2 * ldc, true, c.err.as<int>());
   c.pending = true;
 }
 

@@ -22,7 +22,7 @@ if not os.path.exists(LIB_PATH):
 _lib = C.CDLL(LIB_PATH)
 
 REAL, IMAG = 0, 1
-PREC_FP64, PREC_TF32X3 = 0, 1
+PREC_FP64, PREC_TF32X3, PREC_TF32X3_ENV = 0, 1, 2
 STATUS = {0: "ok", 1: "invalid argument", 2: "shape mismatch", 3: "out of memory",
           4: "Lanczos not converged", 5: "non-finite value", 6: "device wait timed out",
           7: "CUDA error", 8: "SVD not converged"}
