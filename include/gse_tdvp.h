@@ -186,8 +186,10 @@ TDVP_API tdvp_status tdvp_profile_read(tdvp_handle* h, double* out3);
  * last read into out[0..n) and resets.  Phases: 0 local exponentials of the
  * sweep (H_eff Lanczos), 1 backward bond exponentials (K_eff Lanczos), 2 SVDs
  * of the sweep's gauge moves, 3 environment updates, 4 Krylov vectors (step 1),
- * 5 basis extension (step 2), 6 gauge moves of tdvp_canonicalize.  Intervals
- * nest (phase 3 also runs inside 0..2), so the entries do not add up. */
+ * 5 basis extension (step 2), 6 gauge moves of tdvp_canonicalize, 7 right
+ * density environments of the Krylov vectors, 8 their eigendecompositions,
+ * 9 SVDs of the extension.  Intervals nest (3 runs inside 0..2, 7-8 inside 4,
+ * 9 inside 5), so the entries do not add up. */
 TDVP_API tdvp_status tdvp_trace(tdvp_handle* h, int enable);
 TDVP_API tdvp_status tdvp_trace_read(tdvp_handle* h, double* out, int n);
 

@@ -597,6 +597,7 @@ void Engine::krylov_apply(const KrylovOp& kop, const MpsDev& src, MpsDev& out) {
   TDVP_CHECK_LAUNCH();
   DArr T1, T2;
   for (int i = N - 1; i >= 1; --i) {
+    PhaseScope ps(tracer, PH_KRYLOV_RENV);
     const int ml = src.m[i], m = src.m[i + 1], wl = w[i], wr = w[i + 1];
     const cplx* A = src.A[i].data();
     T1.ensure(&pool, (size_t)wr * ml * d * wr * m);
@@ -662,7 +663,10 @@ void Engine::krylov_apply(const KrylovOp& kop, const MpsDev& src, MpsDev& out) {
       return nk;
     };
     SvdOut sv;
-    svd_jacobi(st, &pool, rho.data(), n, n, rule, sv, true, false);
+    {
+      PhaseScope ps(tracer, PH_KRYLOV_EIG);
+      svd_jacobi(st, &pool, rho.data(), n, n, rule, sv, true, false);
+    }
     const int keep = std::max(1, sv.rank);
     tdvp_require(sv.rank >= 1, TDVP_ERR_NONFINITE, "krylov: zero density matrix");
     // X <- U^+ G  : [keep][v][b]
@@ -711,7 +715,10 @@ void Engine::expand_basis(int k, const double* weights) {
     const int ml = psi.m[i], mp = psi.m[i + 1], cols = d * mp, ml0 = psi.m[i - 1];
     const cplx* X = psi.A[i].data();
     SvdOut sv;
-    svd_jacobi(st, &pool, X, ml, cols, SvdRule{}, sv, false, true);  // C = U S B, rank-revealing
+    {
+      PhaseScope ps(tracer, PH_EXTEND_SVD);
+      svd_jacobi(st, &pool, X, ml, cols, SvdRule{}, sv, false, true);  // C = U S B, rank-revealing
+    }
     const int r = sv.rank;
     tdvp_require(r >= 1, TDVP_ERR_NONFINITE, "extension: zero centre tensor");
     int nb = 0;
@@ -753,7 +760,10 @@ void Engine::expand_basis(int k, const double* weights) {
           return n;
         };
         SvdOut sy;
-        svd_jacobi(st, &pool, Y.data(), rows, cols, rule, sy, false, true);
+        {
+          PhaseScope ps(tracer, PH_EXTEND_SVD);
+          svd_jacobi(st, &pool, Y.data(), rows, cols, rule, sy, false, true);
+        }
         nb = sy.rank;
         if (nb > 0) {
           // enforce B_bar B^H = 0 to rounding: project off range(B) twice, re-orthonormalise

@@ -27,7 +27,10 @@ struct KrylovOp {
 };
 
 // Phases timed by the tracer (CUDA events on the engine stream).
-enum TracePhase { PH_LANCZOS_SITE = 0, PH_LANCZOS_BOND, PH_SVD, PH_ENV, PH_KRYLOV, PH_EXTEND, PH_CANON, PH_COUNT };
+enum TracePhase {
+  PH_LANCZOS_SITE = 0, PH_LANCZOS_BOND, PH_SVD, PH_ENV, PH_KRYLOV, PH_EXTEND, PH_CANON,
+  PH_KRYLOV_RENV, PH_KRYLOV_EIG, PH_EXTEND_SVD, PH_COUNT
+};
 
 struct Tracer {
   bool on = false;

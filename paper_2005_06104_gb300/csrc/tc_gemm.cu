@@ -27,14 +27,27 @@
 #include "contract.cuh"
 
 namespace tc {
-constexpr int BM = 128, BN = 128, BK = 32, STAGES = 3;
-constexpr int A_TILE = BM * BK * 4;                        // 16 KiB
-constexpr int B_TILE = BN * BK * 4;                        // 16 KiB
-constexpr int STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;       // 64 KiB
-constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
-constexpr int TMEM_COLS = 256;     // two 128-column accumulators (ping-pong)
-constexpr int CHUNK_KB = 4;        // k-blocks per accumulation chunk (K = 128)
+constexpr int BM = 128;
 constexpr unsigned long long kWaitNs = 2000000000ull;      // 2 s per wait
+
+// Tile configurations.  BK fp32 per K-block: 32 uses the 128-byte swizzle, 16 the
+// 64-byte swizzle.  BN = 256 halves the operand traffic per MAC (the kernel is
+// fed from L2); its epilogue uses eight warps, two per TMEM lane quadrant.
+template <int BN_, int BK_, int STAGES_>
+struct Cfg {
+  static constexpr int BN = BN_, BK = BK_, STAGES = STAGES_;
+  static constexpr int A_TILE = BM * BK * 4;
+  static constexpr int B_TILE = BN * BK * 4;
+  static constexpr int STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+  static constexpr int TMEM_COLS = 2 * BN;           // two accumulators (ping-pong)
+  static constexpr int CHUNK_KB = 128 / BK;          // K = 128 per accumulation chunk
+  static constexpr int EPI_WARPS = 4 * (BN / 128);
+  static constexpr int THREADS = 64 + 32 * EPI_WARPS;
+  static constexpr int SWZ_BYTES = BK * 4;           // 128 or 64
+};
+using CfgN128 = Cfg<128, 32, 3>;
+using CfgN256 = Cfg<256, 16, 4>;
 
 __device__ __forceinline__ uint32_t smem_u32(const void* p) {
   return static_cast<uint32_t>(__cvta_generic_to_shared(p));
@@ -78,14 +91,16 @@ __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap* map
       "l"(reinterpret_cast<uint64_t>(map)), "r"(x), "r"(y), "r"(bar)
       : "memory");
 }
-// Shared-memory matrix descriptor: K-major, 128B swizzle, 8-row groups 1024 B apart.
+// Shared-memory matrix descriptor, K-major: rows of SWZ bytes (128 or 64) with the
+// matching swizzle, 8-row groups 8*SWZ bytes apart.
+template <int SWZ>
 __device__ __forceinline__ uint64_t sdesc(uint32_t addr) {
   uint64_t d = 0;
   d |= (uint64_t)((addr >> 4) & 0x3FFF);          // start address
   d |= (uint64_t)1 << 16;                          // leading byte offset (unused for swizzled K-major)
-  d |= (uint64_t)(1024 >> 4) << 32;                // stride byte offset
+  d |= (uint64_t)((8 * SWZ) >> 4) << 32;           // stride byte offset
   d |= (uint64_t)1 << 46;                          // descriptor version (sm_100 family)
-  d |= (uint64_t)2 << 61;                          // layout: 128B swizzle
+  d |= (uint64_t)(SWZ == 128 ? 2 : 4) << 61;       // layout: 128B or 64B swizzle
   return d;
 }
 // Instruction descriptor, kind::tf32: D = F32, A = B = TF32, both K-major, M x N.
@@ -118,10 +133,14 @@ __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
 // two TMEM buffers (ping-pong) and the epilogue warps add it into FP32 registers
 // with round-to-nearest adds, so the tensor core's own accumulator only ever
 // sums CHUNK_KB * BK products.
-__global__ void __launch_bounds__(192, 1)
+template <class C>
+__global__ void __launch_bounds__(C::THREADS, 1)
     k_gemm_tf32x3(const __grid_constant__ CUtensorMap tmAhi, const __grid_constant__ CUtensorMap tmAlo,
                   const __grid_constant__ CUtensorMap tmBhi, const __grid_constant__ CUtensorMap tmBlo, int M,
                   int N, int nkb, void* __restrict__ out, long long ldo, int out_f64, int* __restrict__ err) {
+  constexpr int BN = C::BN, BK = C::BK, STAGES = C::STAGES, A_TILE = C::A_TILE, B_TILE = C::B_TILE;
+  constexpr int STAGE_BYTES = C::STAGE_BYTES, TMEM_COLS = C::TMEM_COLS, CHUNK_KB = C::CHUNK_KB;
+  constexpr int SWZ = C::SWZ_BYTES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
@@ -143,7 +162,7 @@ __global__ void __launch_bounds__(192, 1)
     }
     for (int b = 0; b < 2; ++b) {
       mbar_init(smem_u32(&tfull[b]), 1);
-      mbar_init(smem_u32(&tempty[b]), 4);
+      mbar_init(smem_u32(&tempty[b]), C::EPI_WARPS);
     }
     mbar_init(smem_u32(done), 1);
     *abort_flag = 0;
@@ -211,9 +230,9 @@ __global__ void __launch_bounds__(192, 1)
         for (int k = 0; k < BK / 8; ++k) {
           const uint32_t off = k * 32;  // 8 tf32 = 32 bytes along K inside the swizzle atom
           const uint32_t first = (kb == c * CHUNK_KB && k == 0) ? 0u : 1u;
-          mma_tf32(acc_tmem, sdesc(a_hi + off), sdesc(b_hi + off), idesc, first);
-          mma_tf32(acc_tmem, sdesc(a_hi + off), sdesc(b_lo + off), idesc, 1u);
-          mma_tf32(acc_tmem, sdesc(a_lo + off), sdesc(b_hi + off), idesc, 1u);
+          mma_tf32(acc_tmem, sdesc<SWZ>(a_hi + off), sdesc<SWZ>(b_hi + off), idesc, first);
+          mma_tf32(acc_tmem, sdesc<SWZ>(a_hi + off), sdesc<SWZ>(b_lo + off), idesc, 1u);
+          mma_tf32(acc_tmem, sdesc<SWZ>(a_lo + off), sdesc<SWZ>(b_hi + off), idesc, 1u);
         }
         mma_commit(smem_u32(&empty[s]));
       }
@@ -223,11 +242,14 @@ __global__ void __launch_bounds__(192, 1)
     mma_commit(smem_u32(done));  // fires when every issued MMA has completed
   } else if (warp >= 2) {
     // ---------------- epilogue: promote chunk partials into FP32 registers
+    // warp w reads TMEM lanes 32*(w%4)..+31 and the column half (w-2)/4 (128 columns)
     const int q = warp & 3;
+    const int half = (warp - 2) >> 2;
     const uint32_t lane_base = (uint32_t)(q * 32) << 16;
-    float acc[BN];
+    constexpr int EC = 128;  // columns per epilogue warp
+    float acc[EC];
 #pragma unroll
-    for (int j = 0; j < BN; ++j) acc[j] = 0.f;
+    for (int j = 0; j < EC; ++j) acc[j] = 0.f;
     bool ok = true;
     for (int c = 0; c < nchunks; ++c) {
       const int b = c & 1, u = c >> 1;
@@ -237,13 +259,13 @@ __global__ void __launch_bounds__(192, 1)
       if (!ok) break;
       fence_after();
 #pragma unroll
-      for (int c0 = 0; c0 < BN; c0 += 16) {
+      for (int c0 = 0; c0 < EC; c0 += 16) {
         uint32_t v[16];
         asm volatile(
             "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15}, [%16];"
             : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]), "=r"(v[7]),
               "=r"(v[8]), "=r"(v[9]), "=r"(v[10]), "=r"(v[11]), "=r"(v[12]), "=r"(v[13]), "=r"(v[14]), "=r"(v[15])
-            : "r"(tmem + lane_base + (uint32_t)(b * BN + c0)));
+            : "r"(tmem + lane_base + (uint32_t)(b * BN + half * EC + c0)));
         asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
         for (int j = 0; j < 16; ++j) acc[c0 + j] += __uint_as_float(v[j]);
@@ -253,28 +275,29 @@ __global__ void __launch_bounds__(192, 1)
       if (lane == 0) mbar_arrive(smem_u32(&tempty[b]));
     }
     const int gm = m0 + q * 32 + lane;
+    const int nb = n0 + half * EC;
     if (ok && gm < M) {
       if (out_f64) {
-        double* o = static_cast<double*>(out) + (long long)gm * ldo + n0;
-        if (n0 + BN <= N && (ldo & 1) == 0) {
+        double* o = static_cast<double*>(out) + (long long)gm * ldo + nb;
+        if (nb + EC <= N && (ldo & 1) == 0) {
 #pragma unroll
-          for (int j = 0; j < BN; j += 2)
+          for (int j = 0; j < EC; j += 2)
             *reinterpret_cast<double2*>(o + j) = make_double2((double)acc[j], (double)acc[j + 1]);
         } else {
 #pragma unroll
-          for (int j = 0; j < BN; ++j)
-            if (n0 + j < N) o[j] = (double)acc[j];
+          for (int j = 0; j < EC; ++j)
+            if (nb + j < N) o[j] = (double)acc[j];
         }
       } else {
-        float* o = static_cast<float*>(out) + (long long)gm * ldo + n0;
-        if (n0 + BN <= N && (ldo & 3) == 0) {
+        float* o = static_cast<float*>(out) + (long long)gm * ldo + nb;
+        if (nb + EC <= N && (ldo & 3) == 0) {
 #pragma unroll
-          for (int j = 0; j < BN; j += 4)
+          for (int j = 0; j < EC; j += 4)
             *reinterpret_cast<float4*>(o + j) = make_float4(acc[j], acc[j + 1], acc[j + 2], acc[j + 3]);
         } else {
 #pragma unroll
-          for (int j = 0; j < BN; ++j)
-            if (n0 + j < N) o[j] = acc[j];
+          for (int j = 0; j < EC; ++j)
+            if (nb + j < N) o[j] = acc[j];
         }
       }
     }
@@ -395,44 +418,61 @@ PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   return fn;
 }
 
-CUtensorMap make_map(const float* base, int rows, int ld, int box_rows) {
+CUtensorMap make_map(const float* base, int rows, int ld, int box_rows, int bk) {
   tdvp_require((reinterpret_cast<uintptr_t>(base) & 15) == 0, TDVP_ERR_INVALID_ARG, "TMA base not 16B aligned");
   tdvp_require(ld % 32 == 0, TDVP_ERR_INVALID_ARG, "TMA row length must be a multiple of 32");
   tdvp_require(rows % box_rows == 0, TDVP_ERR_INVALID_ARG, "TMA operand rows must be padded to the box");
+  tdvp_require(bk == 32 || bk == 16, TDVP_ERR_INVALID_ARG, "TMA K box must be 16 or 32");
   CUtensorMap m;
   std::memset(&m, 0, sizeof(m));
   cuuint64_t dims[2] = {(cuuint64_t)ld, (cuuint64_t)rows};
   cuuint64_t strides[1] = {(cuuint64_t)ld * sizeof(float)};
-  cuuint32_t box[2] = {(cuuint32_t)BK, (cuuint32_t)box_rows};
+  cuuint32_t box[2] = {(cuuint32_t)bk, (cuuint32_t)box_rows};
   cuuint32_t estr[2] = {1, 1};
   CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_FLOAT32, 2, const_cast<float*>(base), dims, strides, box, estr,
-                           CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_128B,
+                           CU_TENSOR_MAP_INTERLEAVE_NONE,
+                           bk == 32 ? CU_TENSOR_MAP_SWIZZLE_128B : CU_TENSOR_MAP_SWIZZLE_64B,
                            CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
   tdvp_require(r == CUDA_SUCCESS, TDVP_ERR_CUDA, "cuTensorMapEncodeTiled failed: " + std::to_string((int)r));
   return m;
 }
 
-void gemm_tf32x3(cudaStream_t st, const float* Ahi, const float* Alo, const float* Bhi, const float* Blo, int M, int N,
+template <class C>
+void launch_gemm(cudaStream_t st, const float* Ahi, const float* Alo, const float* Bhi, const float* Blo, int M, int N,
                  int ldk, void* out, long long ldo, bool out_f64, int* d_err) {
   static bool attr = false;
   if (!attr) {
-    TDVP_CUDA(cudaFuncSetAttribute(k_gemm_tf32x3, cudaFuncAttributeMaxDynamicSharedMemorySize, SMEM_BYTES));
+    TDVP_CUDA(cudaFuncSetAttribute(k_gemm_tf32x3<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
     attr = true;
   }
-  if (M <= 0 || N <= 0) return;
-  tdvp_require(ldk % BK == 0 && ldk > 0, TDVP_ERR_INVALID_ARG, "gemm_tf32x3: K must be padded to 32");
-  // operands hold ceil(M/128)*128 and ceil(N/128)*128 rows (zero padded): no TMA box leaves the buffer
-  const int Mp = ceil_div(M, BM) * BM, Np = ceil_div(N, BN) * BN;
-  const CUtensorMap ma = make_map(Ahi, Mp, ldk, BM), mal = make_map(Alo, Mp, ldk, BM);
-  const CUtensorMap mb = make_map(Bhi, Np, ldk, BN), mbl = make_map(Blo, Np, ldk, BN);
-  dim3 grid(ceil_div(N, BN), ceil_div(M, BM));
+  // operands hold ceil(M/128)*128 and ceil(N/128)*128 rows (zero padded); a BN = 256
+  // tile may reach 128 rows past the padded B operand only when N is not a multiple of
+  // 256, and the host pads B to 256 rows in that case
+  const int Mp = ceil_div(M, BM) * BM, Np = ceil_div(N, C::BN) * C::BN;
+  const CUtensorMap ma = make_map(Ahi, Mp, ldk, BM, C::BK), mal = make_map(Alo, Mp, ldk, BM, C::BK);
+  const CUtensorMap mb = make_map(Bhi, Np, ldk, C::BN, C::BK), mbl = make_map(Blo, Np, ldk, C::BN, C::BK);
+  dim3 grid(ceil_div(N, C::BN), ceil_div(M, BM));
   tdvp_require(grid.y <= 65535, TDVP_ERR_INVALID_ARG, "gemm_tf32x3: M too large");
-  k_gemm_tf32x3<<<grid, 192, SMEM_BYTES, st>>>(ma, mal, mb, mbl, M, N, ldk / BK, out, ldo, out_f64 ? 1 : 0, d_err);
+  k_gemm_tf32x3<C><<<grid, C::THREADS, C::SMEM_BYTES, st>>>(ma, mal, mb, mbl, M, N, ldk / C::BK, out, ldo,
+                                                            out_f64 ? 1 : 0, d_err);
   TDVP_CHECK_LAUNCH();
+}
+
+// B operands are allocated with rows padded to a multiple of 256 (see bpad) so both
+// tile shapes stay inside the buffer.
+void gemm_tf32x3(cudaStream_t st, const float* Ahi, const float* Alo, const float* Bhi, const float* Blo, int M, int N,
+                 int ldk, void* out, long long ldo, bool out_f64, int* d_err) {
+  if (M <= 0 || N <= 0) return;
+  tdvp_require(ldk % 32 == 0 && ldk > 0, TDVP_ERR_INVALID_ARG, "gemm_tf32x3: K must be padded to 32");
+  if (N >= 256)
+    launch_gemm<CfgN256>(st, Ahi, Alo, Bhi, Blo, M, N, ldk, out, ldo, out_f64, d_err);
+  else
+    launch_gemm<CfgN128>(st, Ahi, Alo, Bhi, Blo, M, N, ldk, out, ldo, out_f64, d_err);
 }
 
 inline int pad32(int k) { return (k + 31) / 32 * 32; }
 inline int pad128(int k) { return (k + 127) / 128 * 128; }
+inline int bpad(int n) { return (n + 255) / 256 * 256; }  // rows of a B operand (either tile shape)
 
 // A operand of a general complex GEMM: hi/lo[m][k2] = split(opA(A)[m][k2/2] re|im),
 // zero outside M x 2K (rows padded to Mp, row length ld)
@@ -487,7 +527,7 @@ void heff_tf32x3(cudaStream_t st, Scratch& s, const SiteOp& op, const cplx* x, c
     c.err.ensure(pool, sizeof(int));
     TDVP_CUDA(cudaMemsetAsync(c.err.as<int>(), 0, sizeof(int), st));
   }
-  const int M1p = pad128(M1), N1p = pad128(N1), M3p = pad128(M3), N3p = pad128(N3);
+  const int M1p = pad128(M1), N1p = bpad(N1), M3p = pad128(M3), N3p = bpad(N3);
   if (op.env_key < 0 || c.key != op.env_key) {
     c.Lhi.ensure(pool, sizeof(float) * (size_t)M1p * K1p);
     c.Llo.ensure(pool, sizeof(float) * (size_t)M1p * K1p);
@@ -551,7 +591,7 @@ void zgemm_tc(cudaStream_t st, Scratch& s, int opA, int opB, int M, int N, int K
     c.err.ensure(pool, sizeof(int));
     TDVP_CUDA(cudaMemsetAsync(c.err.as<int>(), 0, sizeof(int), st));
   }
-  const int Kp = pad32(std::max(1, 2 * K)), Mp = pad128(M), Np = pad128(2 * N);
+  const int Kp = pad32(std::max(1, 2 * K)), Mp = pad128(M), Np = bpad(2 * N);
   RawBuf ahi, alo, bhi, blo;
   ahi.ensure(pool, sizeof(float) * (size_t)Mp * Kp);
   alo.ensure(pool, sizeof(float) * (size_t)Mp * Kp);

@@ -4,16 +4,10 @@ oracle on identical seeded inputs.
 Tensors differ by gauge between the two implementations, so states are
 compared through gauge-invariant quantities: |<psi_gpu|psi_oracle>|, energies,
 norms, local expectation values and bond dimensions.  FP64 agreement target
-is 1e-10 (relative for energies, absolute for overlaps and <S^z>) for single
-steps.  Over many truncated steps the method itself amplifies differences at
-the Lanczos tolerance: the oracle against itself with tol 1e-12 vs 1e-13 on
-the 10-site chain differs by 1.8e-9 in <S^z> and 6e-12 in overlap after 10
-steps, and a singular value at the rank threshold can then be kept on one side
-and dropped on the other.  Multi-step tests therefore hold <S^z> to 1e-8,
-overlaps to 1e-9, energy conservation to 1e-10, and bond dimensions to +-2
-(the 10-site chain shows such flips at steps 5 and 6 of its trajectory: the two
-implementations agree exactly from a common input, and differ by one retained
-direction of weight ~1e-20 once their inputs differ at the 1e-12 level).
+is 1e-10 (relative for energies, absolute for overlaps and <S^z>).  Both sides
+factorise block-diagonal matrices block by block, so the conserved S^z stays
+exact; the oracle against itself with Lanczos tol 1e-12 vs 1e-13 then differs
+by ~1e-14 after 10 steps of the 10-site chain, well inside these bounds.
 """
 import numpy as np
 import pytest
@@ -131,13 +125,12 @@ def test_gse_real_time_heisenberg_chain(g):
     for _ in range(p["steps"]):
         st.step(p["dt"], g.REAL, p["k"])
         ref = O.gse_tdvp1_step(ref, W, p)
-        diff = [abs(a - b) for a, b in zip(st.bond_dims(), wl.mps_bond_dims(ref))]
-        assert max(diff) <= 2 and sum(diff) <= 4, (st.bond_dims(), wl.mps_bond_dims(ref))
+        assert st.bond_dims() == wl.mps_bond_dims(ref)
         assert abs(st.energy() - e0) < 1e-10                 # real time conserves energy
     mine = st.get_mps()
-    assert abs(abs(O.mps_overlap(mine, ref)) - 1) < 1e-9
+    assert abs(abs(O.mps_overlap(mine, ref)) - 1) < 1e-10
     for i in range(10):
-        assert abs(st.expect_local(wl.SZ, i).real - O.expect_local(ref, wl.SZ, i).real) < 1e-8
+        assert abs(st.expect_local(wl.SZ, i).real - O.expect_local(ref, wl.SZ, i).real) < 1e-10
     st.close()
 
 
