@@ -54,7 +54,7 @@ typedef enum { TDVP_REAL = 0, TDVP_IMAG = 1 } tdvp_time;
 typedef enum {
   TDVP_PREC_FP64 = 0,       /* FP64 on CUDA cores                                       */
   TDVP_PREC_TF32X3 = 1,     /* tcgen05 kind::tf32, operands split hi+lo, 3 products,
-                               FP32 accumulation in 128-deep chunks: H_eff and the
+                               FP32 accumulation in 32-deep chunks: H_eff and the
                                Krylov-vector GEMMs; environments stay FP64             */
   TDVP_PREC_TF32X3_ENV = 2  /* as TF32X3, and the sweep's environment updates too      */
 } tdvp_precision;
@@ -165,8 +165,10 @@ TDVP_API tdvp_status tdvp_bond_dims(tdvp_handle* h, int* out);  /* N + 1 ints   
 TDVP_API tdvp_status tdvp_center(tdvp_handle* h, int* site);
 /* out[0..3]: discarded weight sums of the last call for eps_k, eps_m, eps, and the
  * number of basis states added by the last extension; out[4]: total Lanczos
- * iterations of the last sweep; out[5]: Lanczos calls of the last sweep. */
-TDVP_API tdvp_status tdvp_trunc_stats(tdvp_handle* h, double* out6);
+ * iterations of the last sweep; out[5]: Lanczos calls of the last sweep;
+ * out[6..8]: process-wide SVD calls, calls that split into independent blocks
+ * (conserved quantum numbers), and blocks solved. */
+TDVP_API tdvp_status tdvp_trunc_stats(tdvp_handle* h, double* out9);
 
 /* Copies the state to host buffers the caller allocated from tdvp_bond_dims
  * (site i: 2 * m_i * d * m_{i+1} doubles). */

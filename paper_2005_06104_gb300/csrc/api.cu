@@ -233,6 +233,9 @@ tdvp_status tdvp_trunc_stats(tdvp_handle* h, double* out) {
     out[3] = e.added_states;
     out[4] = (double)e.lanczos_iters;
     out[5] = (double)e.lanczos_calls;
+    out[6] = (double)g_svd_counters.calls;
+    out[7] = (double)g_svd_counters.blocked;
+    out[8] = (double)g_svd_counters.blocks;
   });
 }
 

@@ -12,7 +12,6 @@ namespace {
 constexpr double kRankRtol = 1e-10;     // "SVD without truncation": keep s > 1e-10 s_max
 constexpr double kClusterRtol = 1e-8;   // never split a cluster of near-equal weights
 constexpr double kEigFloorRtol = 1e-12; // mixed density-matrix eigenvalues <= 1e-12 tr never count
-constexpr double kBreakdown = 1e-13;    // Lanczos invariant-subspace threshold
 const cplx kOne = {1.0, 0.0};
 const cplx kZero = {0.0, 0.0};
 const cplx kMinusOne = {-1.0, 0.0};
@@ -65,26 +64,6 @@ struct SvdRule {
     return n;
   }
 };
-
-__global__ void k_apply_mpo_site(const cplx* __restrict__ W, const cplx* __restrict__ A, int ml, int wl,
-                                 int d, int mr, int wr, cplx* __restrict__ out) {
-  // out[(a,w), s, (b,v)] = sum_t W[w,s,t,v] A[a,t,b]
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  const long long total = (long long)ml * wl * d * mr * wr;
-  if (e >= total) return;
-  const int v = e % wr;
-  long long r = e / wr;
-  const int b = r % mr;
-  r /= mr;
-  const int s = r % d;
-  r /= d;
-  const int w = r % wl;
-  const int a = r / wl;
-  cplx acc = mkc(0.0, 0.0);
-  for (int t = 0; t < d; ++t)
-    cfma(acc, W[(((long long)w * d + s) * d + t) * wr + v], A[((long long)a * d + t) * mr + b]);
-  out[e] = acc;
-}
 
 __global__ void k_apply_op_site(const cplx* __restrict__ op, const cplx* __restrict__ A, int ml, int d,
                                 int mr, cplx* __restrict__ out) {

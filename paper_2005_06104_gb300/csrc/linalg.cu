@@ -685,7 +685,7 @@ __global__ void __launch_bounds__(TRI_MAX)
                    double delta, int kind, const double* __restrict__ nrm2_next,
                    cplx* __restrict__ y, double* __restrict__ err) {
   __shared__ double d[TRI_MAX], o[TRI_MAX + 1];
-  __shared__ double tk[TRI_MAX], tkm[TRI_MAX];
+  __shared__ double tk[TRI_MAX];
   __shared__ double coef[CHEB_MAX + 1];
   __shared__ double sh_c, sh_h, sh_lo, sh_hi;
   __shared__ int sh_K, sh_bad;
@@ -785,7 +785,6 @@ __global__ void __launch_bounds__(TRI_MAX)
     prev = cur;
     cur = nxt;
   }
-  (void)tkm;
   if (i < n) {
     double fre, fim;
     if (kind == 0) {
@@ -947,16 +946,6 @@ __device__ bool jacobi_pair_block(cplx* __restrict__ X, cplx* __restrict__ V, in
     }
   }
   return true;
-}
-
-// Large path, one launch per round: one block per pair.
-__global__ void __launch_bounds__(256)
-    k_jacobi_round(cplx* __restrict__ X, cplx* __restrict__ V, int p, int q, int qpad, int round,
-                   double tol, const double* __restrict__ fro2, int want_v, int* __restrict__ rotated) {
-  int P, Q;
-  rr_pair(round, blockIdx.x, qpad, P, Q);
-  if (Q >= q) return;
-  if (jacobi_pair_block(X, V, p, q, P, Q, tol, 1e-32 * (*fro2), want_v) && threadIdx.x == 0) *rotated = 1;
 }
 
 // Grid-wide barrier for the cooperative path (all blocks co-resident by cooperative
@@ -1392,6 +1381,148 @@ __global__ void k_scatter_cols(const cplx* __restrict__ src, int nrows, int lds,
     dst[(long long)rowmap[i] * ld + sel_global[k]] = v;   // U: rows = global row, cols = kept index
 }
 
+// Batched small blocks: descriptor per block.  Block b is gathered as the column-major
+// working matrix X_b (p x q, p >= q; transposed and conjugated when orient = 1) and
+// solved by one CTA with X_b, V_b in shared memory.
+struct BlkDesc {
+  int orient, p, q, nr, nc;  // nr/nc: rows/cols of the block in M
+  long long x_off, v_off;
+  int s_off, r_off, c_off;
+};
+
+__global__ void k_gather_batched(const cplx* __restrict__ M, int cols, const BlkDesc* __restrict__ desc,
+                                 const int* __restrict__ ridx, const int* __restrict__ cidx, cplx* __restrict__ X,
+                                 cplx* __restrict__ V) {
+  const BlkDesc d = desc[blockIdx.x];
+  cplx* Xb = X + d.x_off;
+  cplx* Vb = V + d.v_off;
+  for (int e = threadIdx.x; e < d.p * d.q; e += blockDim.x) {
+    const int i = e % d.p, j = e / d.p;  // X_b[i + j p]
+    cplx v;
+    if (d.orient == 0)
+      v = M[(long long)ridx[d.r_off + i] * cols + cidx[d.c_off + j]];
+    else
+      v = cconj(M[(long long)ridx[d.r_off + j] * cols + cidx[d.c_off + i]]);
+    Xb[e] = v;
+  }
+  for (int e = threadIdx.x; e < d.q * d.q; e += blockDim.x) Vb[e] = mkc((e % d.q) == (e / d.q) ? 1.0 : 0.0, 0.0);
+}
+
+__global__ void __launch_bounds__(256)
+    k_jacobi_batched(cplx* __restrict__ X, cplx* __restrict__ V, const BlkDesc* __restrict__ desc, int max_sweeps,
+                     double* __restrict__ s_out, int* __restrict__ bad) {
+  extern __shared__ cplx sm[];
+  __shared__ int s_rot;
+  __shared__ double s_fro[8];
+  const BlkDesc d = desc[blockIdx.x];
+  const int p = d.p, q = d.q, qpad = q + (q & 1);
+  cplx* Xs = sm;
+  cplx* Vs = sm + (long long)p * q;
+  cplx* Xg = X + d.x_off;
+  cplx* Vg = V + d.v_off;
+  double f = 0.0;
+  for (int e = threadIdx.x; e < p * q; e += blockDim.x) {
+    Xs[e] = Xg[e];
+    f += cabs2(Xs[e]);
+  }
+  for (int e = threadIdx.x; e < q * q; e += blockDim.x) Vs[e] = Vg[e];
+  f = warp_sum(f);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (lane == 0) s_fro[warp] = f;
+  __syncthreads();
+  double fro2 = 0.0;
+  for (int u = 0; u < nw; ++u) fro2 += s_fro[u];
+  const double floor2 = 1e-32 * fro2;
+  const double tol = fmax(1e-15, sqrt((double)p) * 2.2e-16);
+  int sweep = 0;
+  for (; sweep < max_sweeps && q > 1; ++sweep) {
+    if (threadIdx.x == 0) s_rot = 0;
+    __syncthreads();
+    for (int round = 0; round < qpad - 1; ++round) {
+      for (int k = warp; k < qpad / 2; k += nw) {
+        int P, Q;
+        rr_pair(round, k, qpad, P, Q);
+        if (Q >= q) continue;
+        cplx* xp = Xs + P * p;
+        cplx* xq = Xs + Q * p;
+        double a = 0.0, b = 0.0;
+        cplx c = mkc(0.0, 0.0);
+        for (int r = lane; r < p; r += 32) {
+          const cplx u = xp[r], v = xq[r];
+          a += cabs2(u);
+          b += cabs2(v);
+          cfma_conj(c, u, v);
+        }
+#pragma unroll
+        for (int o = 16; o > 0; o >>= 1) {
+          a += __shfl_xor_sync(0xffffffffu, a, o);
+          b += __shfl_xor_sync(0xffffffffu, b, o);
+          c.x += __shfl_xor_sync(0xffffffffu, c.x, o);
+          c.y += __shfl_xor_sync(0xffffffffu, c.y, o);
+        }
+        double cs;
+        cplx sne;
+        if (!jacobi_params(a, b, c, tol, floor2, cs, sne)) continue;
+        if (lane == 0) s_rot = 1;
+        for (int r = lane; r < p; r += 32) {
+          cplx u = xp[r], v = xq[r];
+          rotate_pair(u, v, cs, sne);
+          xp[r] = u;
+          xq[r] = v;
+        }
+        cplx* vp = Vs + P * q;
+        cplx* vq = Vs + Q * q;
+        for (int r = lane; r < q; r += 32) {
+          cplx u = vp[r], v = vq[r];
+          rotate_pair(u, v, cs, sne);
+          vp[r] = u;
+          vq[r] = v;
+        }
+      }
+      __syncthreads();
+    }
+    const int rot = s_rot;
+    __syncthreads();
+    if (!rot) break;
+  }
+  if (threadIdx.x == 0 && sweep >= max_sweeps) *bad = 1;
+  for (int e = threadIdx.x; e < p * q; e += blockDim.x) Xg[e] = Xs[e];
+  for (int e = threadIdx.x; e < q * q; e += blockDim.x) Vg[e] = Vs[e];
+  __syncthreads();
+  for (int j = warp; j < q; j += nw) {
+    double t = 0.0;
+    for (int r = lane; r < p; r += 32) t += cabs2(Xs[j * p + r]);
+    t = warp_sum(t);
+    if (lane == 0) s_out[d.s_off + j] = sqrt(t);
+  }
+}
+
+// One kept singular triple per CTA: U[:, k] over the block's rows, Vh[k, :] over its columns.
+struct SelEntry {
+  int blk, j, k;
+  double s;
+};
+__global__ void k_scatter_batched(const cplx* __restrict__ X, const cplx* __restrict__ V,
+                                  const BlkDesc* __restrict__ desc, const SelEntry* __restrict__ sel,
+                                  const int* __restrict__ ridx, const int* __restrict__ cidx, cplx* __restrict__ U,
+                                  int keep, cplx* __restrict__ Vh, int cols, int want_u, int want_v) {
+  const SelEntry e = sel[blockIdx.x];
+  const BlkDesc d = desc[e.blk];
+  const cplx* Xb = X + d.x_off + (long long)e.j * d.p;  // column j of X_b
+  const cplx* Vb = V + d.v_off + (long long)e.j * d.q;  // column j of V_b
+  const double inv = 1.0 / e.s;
+  if (want_u)
+    for (int i = threadIdx.x; i < d.nr; i += blockDim.x) {
+      const cplx v = (d.orient == 0) ? cscale(Xb[i], inv) : Vb[i];
+      U[(long long)ridx[d.r_off + i] * keep + e.k] = v;
+    }
+  if (want_v)
+    for (int i = threadIdx.x; i < d.nc; i += blockDim.x) {
+      const cplx v = (d.orient == 0) ? cconj(Vb[i]) : cscale(cconj(Xb[i]), inv);
+      Vh[(long long)e.k * cols + cidx[d.c_off + i]] = v;
+    }
+}
+
 struct DSU {
   std::vector<int> p;
   explicit DSU(int n) : p(n) { std::iota(p.begin(), p.end(), 0); }
@@ -1412,9 +1543,12 @@ struct DSU {
 int keep_all_rule(const std::vector<double>& s, void*) { return (int)s.size(); }
 }  // namespace
 
+SvdCounters g_svd_counters;
+
 void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows, int cols,
                       int (*select)(const std::vector<double>& s, void* ctx), void* ctx, SvdOut& out, bool want_u,
                       bool want_v) {
+  g_svd_counters.calls++;
   const long long n = (long long)rows * cols;
   if (rows <= 1 || cols <= 1 || n > (1LL << 22)) {
     svd_jacobi_keep(st, pool, M, rows, cols, select, ctx, out, want_u, want_v);
@@ -1454,40 +1588,110 @@ void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows
     svd_jacobi_keep(st, pool, M, rows, cols, select, ctx, out, want_u, want_v);
     return;
   }
-  // per-component SVDs, every singular value kept
-  struct Part {
-    std::vector<int> r, c;
-    SvdOut sv;
-    int* d_r = nullptr;
-    int* d_c = nullptr;
-  };
-  std::vector<Part> parts;
-  parts.reserve(comp.size());
+  g_svd_counters.blocked++;
+  g_svd_counters.blocks += (long long)comp.size();
+  // small blocks: one batched launch (X_b, V_b in shared memory); large ones one by one
+  constexpr size_t kSmemCap = 200 * 1024;
+  std::vector<BlkDesc> desc;
+  std::vector<int> ridx, cidx;
+  std::vector<std::pair<std::vector<int>, std::vector<int>>> large;
+  long long xo = 0, vo = 0;
+  int so = 0;
+  size_t smem_need = 0;
   for (auto& kv : comp) {
-    Part pt;
-    pt.r = std::move(kv.second.first);
-    pt.c = std::move(kv.second.second);
-    parts.push_back(std::move(pt));
+    auto& rr = kv.second.first;
+    auto& cc = kv.second.second;
+    const int nr = (int)rr.size(), nc = (int)cc.size();
+    const int p = std::max(nr, nc), q = std::min(nr, nc);
+    const size_t bytes = ((size_t)p * q + (size_t)q * q) * sizeof(cplx);
+    if (bytes > kSmemCap) {
+      large.push_back({rr, cc});
+      continue;
+    }
+    BlkDesc d;
+    d.orient = nr >= nc ? 0 : 1;
+    d.p = p;
+    d.q = q;
+    d.nr = nr;
+    d.nc = nc;
+    d.x_off = xo;
+    d.v_off = vo;
+    d.s_off = so;
+    d.r_off = (int)ridx.size();
+    d.c_off = (int)cidx.size();
+    ridx.insert(ridx.end(), rr.begin(), rr.end());
+    cidx.insert(cidx.end(), cc.begin(), cc.end());
+    xo += (long long)p * q;
+    vo += (long long)q * q;
+    so += q;
+    smem_need = std::max(smem_need, bytes);
+    desc.push_back(d);
   }
-  std::vector<std::pair<double, std::pair<int, int>>> all;  // (s, (part, local index))
-  for (int b = 0; b < (int)parts.size(); ++b) {
-    Part& pt = parts[b];
-    const int pb = (int)pt.r.size(), qb = (int)pt.c.size();
-    TDVP_CUDA(cudaMallocAsync(&pt.d_r, sizeof(int) * pb, st));
-    TDVP_CUDA(cudaMallocAsync(&pt.d_c, sizeof(int) * qb, st));
-    TDVP_CUDA(cudaMemcpyAsync(pt.d_r, pt.r.data(), sizeof(int) * pb, cudaMemcpyHostToDevice, st));
-    TDVP_CUDA(cudaMemcpyAsync(pt.d_c, pt.c.data(), sizeof(int) * qb, cudaMemcpyHostToDevice, st));
-    DArr blk(pool, (size_t)pb * qb);
-    k_gather_block<<<ceil_div((long long)pb * qb, 256), 256, 0, st>>>(M, cols, pt.d_r, pt.d_c, pb, qb, blk.data());
+  const int nsmall = (int)desc.size();
+  std::vector<SvdOut> lout(large.size());
+  std::vector<int*> l_r(large.size()), l_c(large.size());
+  struct Cand {
+    double s;
+    int blk, j;  // blk >= 0: small block; blk < 0: large block -(blk+1)
+  };
+  std::vector<Cand> all;
+  DArr Xs, Vs;
+  BlkDesc* d_desc = nullptr;
+  int *d_ridx = nullptr, *d_cidx = nullptr, *d_bad = nullptr;
+  double* d_s = nullptr;
+  if (nsmall) {
+    Xs.reset(pool, (size_t)std::max<long long>(1, xo));
+    Vs.reset(pool, (size_t)std::max<long long>(1, vo));
+    TDVP_CUDA(cudaMallocAsync(&d_desc, sizeof(BlkDesc) * nsmall, st));
+    TDVP_CUDA(cudaMallocAsync(&d_ridx, sizeof(int) * std::max<size_t>(1, ridx.size()), st));
+    TDVP_CUDA(cudaMallocAsync(&d_cidx, sizeof(int) * std::max<size_t>(1, cidx.size()), st));
+    TDVP_CUDA(cudaMallocAsync(&d_s, sizeof(double) * std::max(1, so) + sizeof(int), st));
+    d_bad = reinterpret_cast<int*>(d_s + std::max(1, so));
+    TDVP_CUDA(cudaMemcpyAsync(d_desc, desc.data(), sizeof(BlkDesc) * nsmall, cudaMemcpyHostToDevice, st));
+    TDVP_CUDA(cudaMemcpyAsync(d_ridx, ridx.data(), sizeof(int) * ridx.size(), cudaMemcpyHostToDevice, st));
+    TDVP_CUDA(cudaMemcpyAsync(d_cidx, cidx.data(), sizeof(int) * cidx.size(), cudaMemcpyHostToDevice, st));
+    TDVP_CUDA(cudaMemsetAsync(d_bad, 0, sizeof(int), st));
+    k_gather_batched<<<nsmall, 256, 0, st>>>(M, cols, d_desc, d_ridx, d_cidx, Xs.data(), Vs.data());
     TDVP_CHECK_LAUNCH();
-    svd_jacobi_keep(st, pool, blk.data(), pb, qb, keep_all_rule, nullptr, pt.sv, want_u, want_v);
-    for (int k = 0; k < (int)pt.sv.s.size(); ++k) all.push_back({pt.sv.s[k], {b, k}});
+    static bool attr = false;
+    if (!attr) {
+      TDVP_CUDA(cudaFuncSetAttribute(k_jacobi_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap));
+      attr = true;
+    }
+    k_jacobi_batched<<<nsmall, 256, smem_need, st>>>(Xs.data(), Vs.data(), d_desc, 60, d_s, d_bad);
+    TDVP_CHECK_LAUNCH();
+    std::vector<double> hs(so);
+    int hbad = 0;
+    TDVP_CUDA(cudaMemcpyAsync(hs.data(), d_s, sizeof(double) * so, cudaMemcpyDeviceToHost, st));
+    TDVP_CUDA(cudaMemcpyAsync(&hbad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TDVP_CUDA(cudaStreamSynchronize(st));
+    tdvp_require(hbad == 0, TDVP_ERR_SVD_NOT_CONVERGED, "batched Jacobi SVD did not converge");
+    for (int b = 0; b < nsmall; ++b)
+      for (int j = 0; j < desc[b].q; ++j) {
+        const double v = hs[desc[b].s_off + j];
+        tdvp_require(std::isfinite(v), TDVP_ERR_NONFINITE, "SVD: non-finite singular value");
+        all.push_back({v, b, j});
+      }
   }
-  std::stable_sort(all.begin(), all.end(), [](const auto& a, const auto& b) { return a.first > b.first; });
+  for (size_t L = 0; L < large.size(); ++L) {
+    auto& rr = large[L].first;
+    auto& cc = large[L].second;
+    const int pb = (int)rr.size(), qb = (int)cc.size();
+    TDVP_CUDA(cudaMallocAsync(&l_r[L], sizeof(int) * pb, st));
+    TDVP_CUDA(cudaMallocAsync(&l_c[L], sizeof(int) * qb, st));
+    TDVP_CUDA(cudaMemcpyAsync(l_r[L], rr.data(), sizeof(int) * pb, cudaMemcpyHostToDevice, st));
+    TDVP_CUDA(cudaMemcpyAsync(l_c[L], cc.data(), sizeof(int) * qb, cudaMemcpyHostToDevice, st));
+    DArr blk(pool, (size_t)pb * qb);
+    k_gather_block<<<ceil_div((long long)pb * qb, 256), 256, 0, st>>>(M, cols, l_r[L], l_c[L], pb, qb, blk.data());
+    TDVP_CHECK_LAUNCH();
+    svd_jacobi_keep(st, pool, blk.data(), pb, qb, keep_all_rule, nullptr, lout[L], want_u, want_v);
+    for (int k = 0; k < (int)lout[L].s.size(); ++k) all.push_back({lout[L].s[k], -(int)L - 1, k});
+  }
+  std::stable_sort(all.begin(), all.end(), [](const Cand& a, const Cand& b) { return a.s > b.s; });
   out.rows = rows;
   out.cols = cols;
-  out.s.resize(std::min(rows, cols), 0.0);
-  for (size_t k = 0; k < all.size() && k < out.s.size(); ++k) out.s[k] = all[k].first;
+  out.s.assign(std::min(rows, cols), 0.0);
+  for (size_t k = 0; k < all.size() && k < out.s.size(); ++k) out.s[k] = all[k].s;
   const int keep = std::max(0, std::min((int)all.size(), select(out.s, ctx)));
   out.rank = keep;
   out.sweeps = 0;
@@ -1502,35 +1706,56 @@ void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows
       out.Vh.reset(pool, (size_t)keep * cols);
       fill_zero(st, out.Vh.data(), (long long)keep * cols);
     }
-    for (int b = 0; b < (int)parts.size(); ++b) {
-      std::vector<int> sl, sg;
-      for (int k = 0; k < keep; ++k)
-        if (all[k].second.first == b) {
-          sl.push_back(all[k].second.second);
-          sg.push_back(k);
-        }
-      if (sl.empty()) continue;
-      Part& pt = parts[b];
-      const int pb = (int)pt.r.size(), qb = (int)pt.c.size(), kb = pt.sv.rank;
+    std::vector<SelEntry> sel;
+    std::vector<std::vector<int>> lsl(large.size()), lsg(large.size());
+    for (int k = 0; k < keep; ++k) {
+      if (all[k].blk >= 0)
+        sel.push_back({all[k].blk, all[k].j, k, all[k].s});
+      else {
+        const int L = -all[k].blk - 1;
+        lsl[L].push_back(all[k].j);
+        lsg[L].push_back(k);
+      }
+    }
+    if (!sel.empty()) {
+      SelEntry* d_sel = nullptr;
+      TDVP_CUDA(cudaMallocAsync(&d_sel, sizeof(SelEntry) * sel.size(), st));
+      TDVP_CUDA(cudaMemcpyAsync(d_sel, sel.data(), sizeof(SelEntry) * sel.size(), cudaMemcpyHostToDevice, st));
+      k_scatter_batched<<<(int)sel.size(), 128, 0, st>>>(Xs.data(), Vs.data(), d_desc, d_sel, d_ridx, d_cidx,
+                                                          want_u ? out.U.data() : nullptr, keep,
+                                                          want_v ? out.Vh.data() : nullptr, cols, want_u ? 1 : 0,
+                                                          want_v ? 1 : 0);
+      TDVP_CHECK_LAUNCH();
+      TDVP_CUDA(cudaFreeAsync(d_sel, st));
+    }
+    for (size_t L = 0; L < large.size(); ++L) {
+      if (lsl[L].empty()) continue;
+      const int pb = (int)large[L].first.size(), qb = (int)large[L].second.size(), kb = lout[L].rank;
       int *d_sl = nullptr, *d_sg = nullptr;
-      TDVP_CUDA(cudaMallocAsync(&d_sl, sizeof(int) * sl.size(), st));
-      TDVP_CUDA(cudaMallocAsync(&d_sg, sizeof(int) * sg.size(), st));
-      TDVP_CUDA(cudaMemcpyAsync(d_sl, sl.data(), sizeof(int) * sl.size(), cudaMemcpyHostToDevice, st));
-      TDVP_CUDA(cudaMemcpyAsync(d_sg, sg.data(), sizeof(int) * sg.size(), cudaMemcpyHostToDevice, st));
-      const int ns = (int)sl.size();
+      TDVP_CUDA(cudaMallocAsync(&d_sl, sizeof(int) * lsl[L].size(), st));
+      TDVP_CUDA(cudaMallocAsync(&d_sg, sizeof(int) * lsg[L].size(), st));
+      TDVP_CUDA(cudaMemcpyAsync(d_sl, lsl[L].data(), sizeof(int) * lsl[L].size(), cudaMemcpyHostToDevice, st));
+      TDVP_CUDA(cudaMemcpyAsync(d_sg, lsg[L].data(), sizeof(int) * lsg[L].size(), cudaMemcpyHostToDevice, st));
+      const int ns = (int)lsl[L].size();
       if (want_u)
-        k_scatter_cols<<<ceil_div((long long)pb * ns, 256), 256, 0, st>>>(pt.sv.U.data(), pb, kb, pt.d_r, d_sl, d_sg,
-                                                                          ns, out.U.data(), keep, 0);
+        k_scatter_cols<<<ceil_div((long long)pb * ns, 256), 256, 0, st>>>(lout[L].U.data(), pb, kb, l_r[L], d_sl,
+                                                                          d_sg, ns, out.U.data(), keep, 0);
       if (want_v)
-        k_scatter_cols<<<ceil_div((long long)qb * ns, 256), 256, 0, st>>>(pt.sv.Vh.data(), qb, qb, pt.d_c, d_sl, d_sg,
-                                                                          ns, out.Vh.data(), cols, 1);
+        k_scatter_cols<<<ceil_div((long long)qb * ns, 256), 256, 0, st>>>(lout[L].Vh.data(), qb, qb, l_c[L], d_sl,
+                                                                          d_sg, ns, out.Vh.data(), cols, 1);
       TDVP_CHECK_LAUNCH();
       TDVP_CUDA(cudaFreeAsync(d_sl, st));
       TDVP_CUDA(cudaFreeAsync(d_sg, st));
     }
   }
-  for (auto& pt : parts) {
-    TDVP_CUDA(cudaFreeAsync(pt.d_r, st));
-    TDVP_CUDA(cudaFreeAsync(pt.d_c, st));
+  if (nsmall) {
+    TDVP_CUDA(cudaFreeAsync(d_desc, st));
+    TDVP_CUDA(cudaFreeAsync(d_ridx, st));
+    TDVP_CUDA(cudaFreeAsync(d_cidx, st));
+    TDVP_CUDA(cudaFreeAsync(d_s, st));
+  }
+  for (size_t L = 0; L < large.size(); ++L) {
+    TDVP_CUDA(cudaFreeAsync(l_r[L], st));
+    TDVP_CUDA(cudaFreeAsync(l_c[L], st));
   }
 }

@@ -104,6 +104,12 @@ void svd_jacobi(cudaStream_t st, DevicePool* pool, const cplx* M, int rows, int 
 void svd_jacobi_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows, int cols,
                      int (*select)(const std::vector<double>& s, void* ctx), void* ctx,
                      SvdOut& out, bool want_u, bool want_v);
+// Process-wide counters of the SVD driver (calls, calls that split into blocks, blocks).
+struct SvdCounters {
+  long long calls = 0, blocked = 0, blocks = 0;
+};
+extern SvdCounters g_svd_counters;
+
 // The same contract, exploiting block structure (exact zeros from conserved
 // quantum numbers): independent SVDs per connected block, merged spectrum.
 void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows, int cols,

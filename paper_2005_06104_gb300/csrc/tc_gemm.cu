@@ -14,7 +14,7 @@
 //   warps 2..5  epilogue: tcgen05.ld from TMEM lanes 32*(warp%4) .. +31
 // The tensor core's FP32 accumulation error grows linearly with the number of
 // products summed in one accumulator (measured); K is therefore split into
-// chunks of 128 that alternate between two TMEM accumulators, and the epilogue
+// chunks of 32 that alternate between two TMEM accumulators, and the epilogue
 // warps add each finished chunk into FP32 registers.
 // Every mbarrier wait is bounded by a wall-clock limit; on expiry the CTA
 // records an error word, drains its own copies and MMAs (bounded) and frees
@@ -41,7 +41,7 @@ struct Cfg {
   static constexpr int STAGE_BYTES = 2 * A_TILE + 2 * B_TILE;
   static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
   static constexpr int TMEM_COLS = 2 * BN;           // two accumulators (ping-pong)
-  static constexpr int CHUNK_KB = 128 / BK;          // K = 128 per accumulation chunk
+  static constexpr int CHUNK_KB = 32 / BK;           // K = 32 per accumulation chunk
   static constexpr int EPI_WARPS = 4 * (BN / 128);
   static constexpr int THREADS = 64 + 32 * EPI_WARPS;
   static constexpr int SWZ_BYTES = BK * 4;           // 128 or 64
