@@ -49,7 +49,27 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--heff-probe", action="store_true",
                     help="only time the tensor-core H_eff apply at --heff-chi (the profiling target)")
+    ap.add_argument("--precision", default="bf16x10", choices=sorted(PRECISIONS),
+                    help="arithmetic of the dense contractions (Lanczos, SVDs, observables stay FP64)")
+    ap.add_argument("--step-only", action="store_true",
+                    help="stop after the timed steps (no FP64 comparison, e2e, probe or CPU baseline): "
+                         "the short command a launch-list profile runs")
     return ap.parse_args()
+
+
+PRECISIONS = {"fp64": "PREC_FP64", "tf32x3": "PREC_TF32X3", "tf32x3_env": "PREC_TF32X3_ENV",
+              "bf16x10": "PREC_BF16X10", "bf16x6": "PREC_BF16X6"}
+PRECISION_TEXT = {
+    "fp64": "FP64 on CUDA cores throughout",
+    "tf32x3": "tcgen05 split TF32 x3 (H_eff, K_eff, Krylov GEMMs); FP64 environments, Lanczos, SVD",
+    "tf32x3_env": "tcgen05 split TF32 x3 (H_eff, K_eff, environments, Krylov GEMMs); FP64 Lanczos, SVD",
+    "bf16x10": "tcgen05 BF16 exact slices x10 (H_eff, K_eff, environments, Krylov GEMMs); FP64 Lanczos, SVD",
+    "bf16x6": "tcgen05 BF16 exact slices x6 (H_eff, K_eff, environments, Krylov GEMMs); FP64 Lanczos, SVD",
+}
+
+
+def prec_code(g, name):
+    return getattr(g, PRECISIONS[name])
 
 
 def workload(args):
@@ -64,7 +84,7 @@ def workload(args):
            "lattice": "4x16 cylinder (periodic in y), snake path, J=1", "n_sites": lat.n,
            "mpo_bond_dim_max": int(max(wl.mpo_bond_dims(W))), "chi_max": args.chi_max,
            "krylov_order_k": args.k, "dt": args.dt, "tau": args.dt, "eps_k": 1e-8, "eps_m": 1e-8, "eps": 0.0,
-           "time": "real", "precision_form": "tf32x3 (H_eff, environments, Krylov GEMMs); FP64 Lanczos/SVD",
+           "time": "real", "precision_form": PRECISION_TEXT[args.precision],
            "start_state": "Neel with the spin at (8,0) flipped", "prep_steps": args.prep_steps,
            "l2": "working set of a step (environments, Krylov vectors, density environments) > L2; no flush"}
     return lat, W, psi, cfg
@@ -203,7 +223,7 @@ def run_reference(args):
     print(json.dumps(line), flush=True)
 
 
-def heff_roofline(g, torch, chi, W):
+def heff_roofline(g, torch, chi, W, prec):
     """Timed H_eff applies at bond dimension chi on the 14-wide MPO site (tensor-core path),
     CUDA events on the launching stream."""
     gen = torch.Generator(device="cuda").manual_seed(7)
@@ -217,13 +237,13 @@ def heff_roofline(g, torch, chi, W):
     flops = 8.0 * (chi * 2 * chi * (chi * W.shape[0] + chi * W.shape[3]) + chi * chi * nnz)
     st = torch.cuda.current_stream()
     for _ in range(3):
-        g.heff_contract(L, W, R, x, y, g.PREC_TF32X3, stream=st.cuda_stream)
+        g.heff_contract(L, W, R, x, y, prec, stream=st.cuda_stream)
     reps = 10
     a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.synchronize()
     a.record(st)
     for _ in range(reps):
-        g.heff_contract(L, W, R, x, y, g.PREC_TF32X3, stream=st.cuda_stream)
+        g.heff_contract(L, W, R, x, y, prec, stream=st.cuda_stream)
     b.record(st)
     b.synchronize()
     ms = a.elapsed_time(b) / reps
@@ -242,7 +262,8 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     from paper_2005_06104_gb300 import gse_tdvp as g
     lat, W, psi0, cfg = workload(args)
-    opts = dict(tau=args.dt, eps_k=1e-8, eps_m=1e-8, eps=0.0, chi_max=args.chi_max, precision=g.PREC_TF32X3)
+    opts = dict(tau=args.dt, eps_k=1e-8, eps_m=1e-8, eps=0.0, chi_max=args.chi_max,
+                precision=prec_code(g, args.precision))
     stream = torch.cuda.current_stream().cuda_stream
     st = g.GseTdvp(psi0, W, stream=stream, **opts)
     e_init = st.energy()
@@ -264,6 +285,7 @@ def run_gpu(args):
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
+    launches0 = g.launch_count()
     for _ in range(args.steps):
         st.profile(True)
         st.trace(True)
@@ -283,6 +305,7 @@ def run_gpu(args):
         heff_n += pr["applies"]
         nfo = st.trunc_stats()
     torch.cuda.synchronize()
+    launches = g.launch_count() - launches0
     if world > 1:
         dist.barrier()
     ck = clocks.stop()
@@ -297,6 +320,14 @@ def run_gpu(args):
     e_end = st.energy()
     st.close()
     if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    if args.step_only:
+        print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
+                          "warmup": args.warmup, "ms_per_step": sum(ts) / len(ts), "step_only": True,
+                          "config": dict(cfg, parallelism=f"replicas{world}"), "gpu_launches": launches,
+                          "phases_ms_per_step": phases, "step_stats": nfo}), flush=True)
         if world > 1:
             dist.destroy_process_group()
         return
@@ -323,11 +354,24 @@ def run_gpu(args):
         e2e_ts.append(time.perf_counter() - t)
         d2h = sum(x.nbytes for x in out)
     Wmax = max(W, key=lambda w: w.shape[0] * w.shape[3])
-    pflops, pms = heff_roofline(g, torch, args.heff_chi, Wmax)
+    pflops, pms = heff_roofline(g, torch, args.heff_chi, Wmax, prec_code(g, args.precision))
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     peaks = json.load(open(peaks_path)) if os.path.exists(peaks_path) else None
     bf16 = peaks["bf16_tflops"] if peaks else 1900.0
-    tf32_peak = bf16 * (1.1 / 2.25)  # measured bf16 x nominal tf32/bf16 ratio
+    if args.precision.startswith("bf16"):
+        # a contraction in BF16 slices: the measured dense BF16 peak; each algorithmic
+        # flop costs `products` tensor-core flops
+        products = 10 if args.precision == "bf16x10" else 6
+        peak, peak_src = bf16, "measured bf16_tflops (MEASURED_PEAKS.json)" if peaks else "fallback 1900 TF/s bf16"
+        kern = f"H_eff apply (tcgen05 kind::f16, BF16 exact slices, {products} products) at chi={args.heff_chi}, w=14"
+    elif args.precision.startswith("tf32"):
+        products = 3
+        peak = bf16 * (1.1 / 2.25)  # measured bf16 x nominal tf32/bf16 ratio
+        peak_src = "measured bf16_tflops x 1.1/2.25 (nominal tf32/bf16)"
+        kern = f"H_eff apply (tcgen05 kind::tf32, 3 split products) at chi={args.heff_chi}, w=14"
+    else:
+        products, peak, peak_src = 1, 1.25, "nominal FP64 (no tensor cores)"
+        kern = f"H_eff apply (FP64 CUDA cores) at chi={args.heff_chi}, w=14"
     cpu = None
     if not args.no_cpu_baseline:
         try:
@@ -339,16 +383,16 @@ def run_gpu(args):
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": sum(ts) / len(ts), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "c128 state / tf32x3 contractions", "data": "synthetic",
-        "config": dict(cfg, parallelism=f"replicas{world}"),
-        "roofline": {"bound": "tensor", "achieved": achieved, "peak": tf32_peak, "unit": "TFLOP/s",
-                     "frac": achieved / tf32_peak, "traffic": None,
-                     "kernel": f"H_eff apply (tcgen05 kind::tf32, 3 split products) at chi={args.heff_chi}, w=14",
-                     "peak_source": "measured bf16_tflops x 1.1/2.25 (nominal tf32/bf16)",
+        "scaling": "weak", "vs_baseline": None, "dtype": f"c128 state / {args.precision} contractions",
+        "data": "synthetic", "config": dict(cfg, parallelism=f"replicas{world}"),
+        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+                     "frac": achieved / peak, "traffic": None, "kernel": kern, "peak_source": peak_src,
+                     "tensor_flops_per_algorithmic_flop": products,
+                     "tensor_frac_executed": achieved * products / peak,
                      "ms_per_apply": pms, "algorithmic_flops_per_apply": pflops},
         "heff_in_step": {"applies": heff_n, "ms": heff_ms, "tflops_algorithmic": achieved_step,
                          "share_of_step": heff_ms / sum(ts) if ts else None},
-        "precision_vs_fp64": {"energy_tf32x3": e_tc, "energy_fp64": e_64,
+        "precision_vs_fp64": {"precision": args.precision, "energy_precision_form": e_tc, "energy_fp64": e_64,
                               "rel_energy_err": abs(e_tc - e_64) / abs(e_64), "norm_drift": abs(n_tc - 1.0)},
         "energy_conservation": {"E_initial": e_init, "E_after_timed_steps": e_end, "abs_drift": abs(e_end - e_init)},
         "step_stats": nfo,
@@ -357,7 +401,7 @@ def run_gpu(args):
         "e2e": {"value": len(e2e_ts) / sum(e2e_ts), "unit": UNIT, "h2d_bytes_per_step": h2d,
                 "d2h_bytes_per_step": d2h,
                 "what": "tdvp_create from host MPS + expand + sweep + tdvp_get_mps + destroy"},
-        "gpu_launches": None,
+        "gpu_launches": launches,
         "clocks": ck,
     }
     print(json.dumps(line), flush=True)
@@ -370,8 +414,9 @@ def run_heff_probe(args):
     from paper_2005_06104_gb300 import gse_tdvp as g
     from paper_2005_06104_gb300 import workloads as wl
     W = max(wl.heisenberg_mpo(wl.cylinder_snake(16, 4)), key=lambda w: w.shape[0] * w.shape[3])
-    flops, ms = heff_roofline(g, torch, args.heff_chi, W)
-    print(json.dumps({"heff_chi": args.heff_chi, "w": int(W.shape[0]), "ms_per_apply": ms,
+    flops, ms = heff_roofline(g, torch, args.heff_chi, W, prec_code(g, args.precision))
+    print(json.dumps({"heff_chi": args.heff_chi, "w": int(W.shape[0]), "precision": args.precision,
+                      "ms_per_apply": ms,
                       "algorithmic_tflops": flops / ms / 1e9}), flush=True)
 
 

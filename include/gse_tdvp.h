@@ -56,7 +56,14 @@ typedef enum {
   TDVP_PREC_TF32X3 = 1,     /* tcgen05 kind::tf32, operands split hi+lo, 3 products,
                                FP32 accumulation in 32-deep chunks: H_eff and the
                                Krylov-vector GEMMs; environments stay FP64             */
-  TDVP_PREC_TF32X3_ENV = 2  /* as TF32X3, and the sweep's environment updates too      */
+  TDVP_PREC_TF32X3_ENV = 2, /* as TF32X3, and the sweep's environment updates too      */
+  TDVP_PREC_BF16X10 = 3,    /* tcgen05 kind::f16: each operand cut into 4 fixed-point
+                               BF16 slices per row and 128-deep K chunk (power-of-two
+                               chunk scale), 10 slice products, the leading one summed
+                               exactly, chunks promoted into FP32 (hi, lo) pairs:
+                               resolves about 2^-33 of the chunk maxima.  H_eff,
+                               K_eff, environments and Krylov-vector GEMMs           */
+  TDVP_PREC_BF16X6 = 4      /* as BF16X10 with 3 slices and 6 products (about 2^-25)   */
 } tdvp_precision;
 
 typedef struct tdvp_handle tdvp_handle;
@@ -194,6 +201,12 @@ TDVP_API tdvp_status tdvp_profile_read(tdvp_handle* h, double* out3);
  * 9 inside 5), so the entries do not add up. */
 TDVP_API tdvp_status tdvp_trace(tdvp_handle* h, int enable);
 TDVP_API tdvp_status tdvp_trace_read(tdvp_handle* h, double* out, int n);
+
+/* Number of CUDA kernels this library has launched in this process, over all
+ * handles and handle-free calls (a relaxed atomic counter bumped at every
+ * launch site).  Differences of two reads count the launches in between.
+ * Returns TDVP_ERR_INVALID_ARG for a null pointer. */
+TDVP_API tdvp_status tdvp_launch_count(long long* out);
 
 /* ---------------------------------------------------------------------------
  * Handle-free contractions of one site on caller buffers (kernel-level entry

@@ -37,7 +37,7 @@ void check_options(const tdvp_options& o) {
   tdvp_require(o.chi_max >= 1, TDVP_ERR_INVALID_ARG, "chi_max must be >= 1");
   tdvp_require(o.lanczos_tol > 0 && o.lanczos_max >= 1 && o.lanczos_max <= 63, TDVP_ERR_INVALID_ARG,
                "lanczos_tol > 0 and 1 <= lanczos_max <= 63 required");
-  tdvp_require(o.precision >= TDVP_PREC_FP64 && o.precision <= TDVP_PREC_TF32X3_ENV, TDVP_ERR_INVALID_ARG,
+  tdvp_require(o.precision >= TDVP_PREC_FP64 && o.precision <= TDVP_PREC_BF16X6, TDVP_ERR_INVALID_ARG,
                "unknown precision");
 }
 }  // namespace
@@ -143,7 +143,7 @@ tdvp_status tdvp_heff_apply(tdvp_handle* h, int site, const void* x, void* y, in
     Engine& e = h->eng;
     tdvp_require(x && y && x != y, TDVP_ERR_INVALID_ARG, "x, y must be distinct device buffers");
     tdvp_require(site >= 0 && site < e.N, TDVP_ERR_INVALID_ARG, "site out of range");
-    tdvp_require(precision >= TDVP_PREC_FP64 && precision <= TDVP_PREC_TF32X3_ENV, TDVP_ERR_INVALID_ARG,
+    tdvp_require(precision >= TDVP_PREC_FP64 && precision <= TDVP_PREC_BF16X6, TDVP_ERR_INVALID_ARG,
                  "unknown precision");
     e.ensure_L(site);
     e.ensure_R(site);
@@ -290,6 +290,12 @@ tdvp_status tdvp_trace_read(tdvp_handle* h, double* out, int n) {
   });
 }
 
+tdvp_status tdvp_launch_count(long long* out) {
+  if (!out) return TDVP_ERR_INVALID_ARG;
+  *out = g_kernel_launches.load(std::memory_order_relaxed);
+  return TDVP_OK;
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------
@@ -359,7 +365,7 @@ tdvp_status tdvp_heff_contract(const tdvp_site_dims* dims, const void* L, const 
   return raw_guarded([&](RawCtx& c) {
     check_dims(dims);
     tdvp_require(L && R && x && y && x != y, TDVP_ERR_INVALID_ARG, "null or aliased buffers");
-    tdvp_require(precision >= TDVP_PREC_FP64 && precision <= TDVP_PREC_TF32X3_ENV, TDVP_ERR_INVALID_ARG,
+    tdvp_require(precision >= TDVP_PREC_FP64 && precision <= TDVP_PREC_BF16X6, TDVP_ERR_INVALID_ARG,
                  "unknown precision");
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     WSparse w = make_w(dims, W);
@@ -418,7 +424,7 @@ tdvp_status tdvp_expm_contract(const tdvp_site_dims* dims, const void* L, const 
     check_dims(dims);
     tdvp_require(L && R && x && y && x != y, TDVP_ERR_INVALID_ARG, "null or aliased buffers");
     tdvp_require(kind == TDVP_REAL || kind == TDVP_IMAG, TDVP_ERR_INVALID_ARG, "bad time kind");
-    tdvp_require(precision >= TDVP_PREC_FP64 && precision <= TDVP_PREC_TF32X3_ENV, TDVP_ERR_INVALID_ARG,
+    tdvp_require(precision >= TDVP_PREC_FP64 && precision <= TDVP_PREC_BF16X6, TDVP_ERR_INVALID_ARG,
                  "unknown precision");
     tdvp_require(tol > 0 && nmax >= 1 && nmax <= 63 && std::isfinite(delta), TDVP_ERR_INVALID_ARG,
                  "bad Lanczos parameters");

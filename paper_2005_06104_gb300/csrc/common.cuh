@@ -1,6 +1,7 @@
 // Shared device/host helpers of libgsetdvp: complex FP64 arithmetic, error
 // handling, a caching device allocator and launch helpers.
 #pragma once
+#include <atomic>
 #include <cuda_runtime.h>
 
 #include <cmath>
@@ -52,7 +53,14 @@ struct TdvpError : public std::runtime_error {
     }                                                                                \
   } while (0)
 
-#define TDVP_CHECK_LAUNCH() TDVP_CUDA(cudaGetLastError())
+// Process-wide count of kernel launches made by this library.  Every launch
+// site is followed by exactly one TDVP_CHECK_LAUNCH, which bumps it.
+extern std::atomic<long long> g_kernel_launches;
+#define TDVP_CHECK_LAUNCH()                                             \
+  do {                                                                  \
+    g_kernel_launches.fetch_add(1, std::memory_order_relaxed);          \
+    TDVP_CUDA(cudaGetLastError());                                      \
+  } while (0)
 
 inline void tdvp_require(bool ok, tdvp_status s, const std::string& msg) {
   if (!ok) throw TdvpError(s, msg);

@@ -27,8 +27,12 @@ void heff_fp64(cudaStream_t st, Scratch& s, const SiteOp& op, const cplx* x, cpl
         y, mr, 1, 0, 0, 0, s.pool);
 }
 
+bool prec_is_bf16(int precision) { return precision == TDVP_PREC_BF16X10 || precision == TDVP_PREC_BF16X6; }
+
 void heff_apply_prec(cudaStream_t st, Scratch& s, const SiteOp& op, const cplx* x, cplx* y, int precision) {
-  if (precision != TDVP_PREC_FP64)
+  if (prec_is_bf16(precision))
+    heff_bf16s(st, s, op, x, y, bf16_slices(precision));
+  else if (precision != TDVP_PREC_FP64)
     heff_tf32x3(st, s, op, x, y);
   else
     heff_fp64(st, s, op, x, y);
@@ -36,7 +40,10 @@ void heff_apply_prec(cudaStream_t st, Scratch& s, const SiteOp& op, const cplx* 
 
 void zgemm_prec(cudaStream_t st, Scratch& s, int precision, int opA, int opB, int M, int N, int K, const cplx* A,
                 long long lda, const cplx* B, long long ldb, cplx* C, long long ldc) {
-  if (precision != TDVP_PREC_FP64 && (long long)M * N * K >= (1LL << 21) && M >= 64 && N >= 32)
+  const bool big = (long long)M * N * K >= (1LL << 21) && M >= 64 && N >= 32;
+  if (big && prec_is_bf16(precision))
+    zgemm_bf16s(st, s, bf16_slices(precision), opA, opB, M, N, K, A, lda, B, ldb, C, ldc);
+  else if (big && precision != TDVP_PREC_FP64)
     zgemm_tc(st, s, opA, opB, M, N, K, A, lda, B, ldb, C, ldc);
   else
     zgemm(st, opA, opB, M, N, K, kOne, A, lda, B, ldb, kZero, C, ldc, 1, 0, 0, 0, s.pool);

@@ -3,6 +3,7 @@
 // The engine and the handle-free C-ABI entry points share them.
 #pragma once
 #include <functional>
+#include <memory>
 
 #include "linalg.cuh"
 #include "tc_gemm.cuh"
@@ -16,11 +17,14 @@ struct SiteOp {
   long long env_key = -1;      // identifies the (L, R) content for operand caching; -1 = never cache
 };
 
+struct TcSliceCache;  // sliced operands of the BF16 tensor-core path (tc_bf16.cu)
+
 // Work buffers reused across calls (drawn from a pool).
 struct Scratch {
   DevicePool* pool = nullptr;
   DArr t1, t2, t3;
   TcEnvCache tc;
+  std::shared_ptr<TcSliceCache> tcs;
 };
 
 // Algorithmic flop count of one H_eff apply (8 real flops per complex multiply-add):
@@ -30,13 +34,22 @@ double heff_flops(const SiteOp& op);
 // y[a,s,b] = sum L[a,w,a'] W[w,s,s',v] x[a',s',b'] R[b,v,b']
 void heff_fp64(cudaStream_t st, Scratch& s, const SiteOp& op, const cplx* x, cplx* y);
 void heff_tf32x3(cudaStream_t st, Scratch& s, const SiteOp& op, const cplx* x, cplx* y);
+// The same on the BF16 exact-slice tensor-core GEMM with S = 3 or 4 slices per operand.
+void heff_bf16s(cudaStream_t st, Scratch& s, const SiteOp& op, const cplx* x, cplx* y, int S);
+// Slices per operand of a BF16 precision mode (BF16X6: 3, BF16X10: 4).
+int bf16_slices(int precision);
+bool prec_is_bf16(int precision);
 void heff_apply_prec(cudaStream_t st, Scratch& s, const SiteOp& op, const cplx* x, cplx* y, int precision);
 // C = opA(A) opB(B) (complex, alpha = 1, beta = 0) on the tensor cores (split TF32,
 // FP32 accumulation, FP64 output).
 void zgemm_tc(cudaStream_t st, Scratch& s, int opA, int opB, int M, int N, int K, const cplx* A, long long lda,
               const cplx* B, long long ldb, cplx* C, long long ldc);
-// zgemm_tc when `precision` is TF32X3 and the product is large enough to fill
-// tensor-core tiles, the FP64 GEMM otherwise (alpha = 1, beta = 0).
+// C = opA(A) opB(B) on the BF16 exact-slice tensor-core GEMM (S slices, FP64 output).
+void zgemm_bf16s(cudaStream_t st, Scratch& s, int S, int opA, int opB, int M, int N, int K, const cplx* A,
+                 long long lda, const cplx* B, long long ldb, cplx* C, long long ldc);
+// The tensor-core GEMM of `precision` (zgemm_tc for the TF32 modes, zgemm_bf16s for
+// the BF16 modes) when the product is large enough to fill its tiles, the FP64
+// GEMM otherwise (alpha = 1, beta = 0).
 void zgemm_prec(cudaStream_t st, Scratch& s, int precision, int opA, int opB, int M, int N, int K, const cplx* A,
                 long long lda, const cplx* B, long long ldb, cplx* C, long long ldc);
 // Reads the tensor-core error word of the launches since the last check (synchronises);

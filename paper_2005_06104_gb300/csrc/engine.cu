@@ -366,7 +366,7 @@ void Engine::sweep(double dt, int kind) {
   const double delta = 0.5 * dt;
   const bool imag = kind == TDVP_IMAG;
   const int prec = opt.precision;
-  env_prec = (prec == TDVP_PREC_TF32X3_ENV) ? TDVP_PREC_TF32X3 : TDVP_PREC_FP64;
+  env_prec = (prec == TDVP_PREC_TF32X3_ENV) ? TDVP_PREC_TF32X3 : prec_is_bf16(prec) ? prec : TDVP_PREC_FP64;
   lanczos_iters = lanczos_calls = 0;
   disc_eps = 0.0;
   DArr y;

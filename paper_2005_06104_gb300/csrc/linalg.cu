@@ -1215,6 +1215,7 @@ void svd_jacobi_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows,
       const double* fr = d_fro2;
       void* args[] = {&xp, &vp, &pp, &qq, &qp, &tl, &fr, &wv, &ms, &bar, &d_flag};
       TDVP_CUDA(cudaLaunchCooperativeKernel((void*)k_jacobi_coop, dim3(nblk), dim3(256), args, 0, st));
+      g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
       GridBar hb;
       TDVP_CUDA(cudaMemcpyAsync(&sweeps, d_flag, sizeof(int), cudaMemcpyDeviceToHost, st));
       TDVP_CUDA(cudaMemcpyAsync(&hb, bar, sizeof(GridBar), cudaMemcpyDeviceToHost, st));
@@ -1544,6 +1545,7 @@ int keep_all_rule(const std::vector<double>& s, void*) { return (int)s.size(); }
 }  // namespace
 
 SvdCounters g_svd_counters;
+std::atomic<long long> g_kernel_launches{0};
 
 void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows, int cols,
                       int (*select)(const std::vector<double>& s, void* ctx), void* ctx, SvdOut& out, bool want_u,
@@ -1737,13 +1739,16 @@ void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows
       TDVP_CUDA(cudaMemcpyAsync(d_sl, lsl[L].data(), sizeof(int) * lsl[L].size(), cudaMemcpyHostToDevice, st));
       TDVP_CUDA(cudaMemcpyAsync(d_sg, lsg[L].data(), sizeof(int) * lsg[L].size(), cudaMemcpyHostToDevice, st));
       const int ns = (int)lsl[L].size();
-      if (want_u)
+      if (want_u) {
         k_scatter_cols<<<ceil_div((long long)pb * ns, 256), 256, 0, st>>>(lout[L].U.data(), pb, kb, l_r[L], d_sl,
                                                                           d_sg, ns, out.U.data(), keep, 0);
-      if (want_v)
+        TDVP_CHECK_LAUNCH();
+      }
+      if (want_v) {
         k_scatter_cols<<<ceil_div((long long)qb * ns, 256), 256, 0, st>>>(lout[L].Vh.data(), qb, qb, l_c[L], d_sl,
                                                                           d_sg, ns, out.Vh.data(), cols, 1);
-      TDVP_CHECK_LAUNCH();
+        TDVP_CHECK_LAUNCH();
+      }
       TDVP_CUDA(cudaFreeAsync(d_sl, st));
       TDVP_CUDA(cudaFreeAsync(d_sg, st));
     }

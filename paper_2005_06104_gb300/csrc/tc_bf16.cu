@@ -1,0 +1,627 @@
+// Tensor-core complex GEMMs with BF16 "exact slices" (sm_103a, tcgen05 kind::f16).
+//
+// Each real operand (the 4M embedding of the complex one, as in the TF32 path)
+// is cut into fixed-point slices.  For one scaling group, with 2^e the smallest
+// power of two above its largest magnitude, every entry is written as
+//   x = 2^e (a1 2^-8 + a2 2^-16 + a3 2^-24 + a4 2^-32) + r,   |r| <= 2^(e-33),
+// with integers |a1| <= 256 and |a_s| <= 128 (s > 1), exact in BF16.  Slice s is
+// stored as a_s 2^(-8(s-1)) (exact) and the group scale as the float 2^(e-8).
+// A-operand groups are one row and one chunk of 128 along K; B-operand groups
+// are whole rows, so the B scale is one factor per output column, applied once.
+//
+// The products of slices s, t (0-based) with s + t <= S - 1 are summed: the
+// leading product a1 b1 in accumulator P, all others in accumulator Q.  Within a
+// chunk P is a sum of at most 128 integers of magnitude <= 2^16, so every partial
+// sum is an integer below 2^24 and the tensor core's FP32 accumulation of P is
+// exact whatever its rounding.  Q is about 2^-7 of P; its rounding stays near
+// 2^-31 of P per chunk.  The epilogue scales each chunk by its A chunk scale
+// (a power of two: exact) and adds it into a double-float (hi, lo) pair per output
+// with Knuth's two-sum, so no error accrues across chunks.  GB300 runs FP64 at a
+// small fraction of its FP32 rate, which is why the promotion uses FP32 pairs.
+// S = 4 (10 products) resolves about 2^-33 of the chunk maxima; S = 3 (6 products)
+// about 2^-25.
+//
+// Kernel layout (one CTA per 128 x 128 output tile, three warpgroups):
+//   warp 0       TMA producer: one 3-D box per operand and stage (all S slices)
+//   warp 1       TMEM allocator and single-thread tcgen05.mma issuer
+//   warps 2, 3   idle
+//   warps 4..11  epilogue: warp w reads TMEM lanes 32*(w%4)..+31, columns 64*((w-4)/4)..+63
+// The first warpgroup gives registers back (setmaxnreg 40) so that the epilogue
+// warpgroups can hold 64 (hi, lo) pairs per thread (setmaxnreg 232):
+// 128 * 40 + 256 * 232 = 384 * 168, the launch's own allocation.
+// Tensor memory: two chunk buffers (ping-pong) x (P, Q) x 128 columns = 512 columns.
+// Every mbarrier wait is bounded; on expiry the CTA records an error word, drains
+// its copies and MMAs (bounded) and frees its tensor memory.
+#include <cuda_bf16.h>
+
+#include <cstring>
+
+#include "contract.cuh"
+#include "tc_ptx.cuh"
+
+namespace tcb {
+using namespace tc;
+
+constexpr int BM = 128, BN = 128, BK = 32, STAGES = 3;
+constexpr int KC = 128;                 // K elements per chunk (exactness bound of P: 128 * 2^16 < 2^24)
+constexpr int KC_KB = KC / BK;          // k-blocks per chunk
+constexpr int EPI_WARPS = 8;
+constexpr int EPI_WARP0 = 4;            // first epilogue warp (second warpgroup)
+constexpr int THREADS = 128 + 32 * EPI_WARPS;
+constexpr int REGS_LAUNCH = 168, REGS_LOW = 40, REGS_HIGH = 232;
+static_assert(128 * REGS_LOW + 32 * EPI_WARPS * REGS_HIGH <= THREADS * REGS_LAUNCH, "register split");
+constexpr int TILE = BM * BK * 2;       // one slice of one operand tile (bytes); BM == BN
+constexpr int TMEM_COLS = 512;
+constexpr int EC = 64;                  // output columns per epilogue thread
+
+template <int S>
+struct SCfg {
+  static constexpr int STAGE_BYTES = 2 * S * TILE;
+  static constexpr int SMEM_BYTES = STAGES * STAGE_BYTES + 1024 + 256;
+};
+
+// Instruction descriptor, kind::f16: D = F32, A = B = BF16, both K-major, M x N.
+__host__ __device__ constexpr uint32_t idesc_bf16(int M, int N) {
+  return (1u << 4) | (1u << 7) | (1u << 10) | ((uint32_t)(N >> 3) << 17) | ((uint32_t)(M >> 4) << 24);
+}
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc, uint32_t acc) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}\n" ::"r"(tmem_d),
+      "l"(da), "l"(db), "r"(idesc), "r"(acc)
+      : "memory");
+}
+
+// hi + lo += v without loss (Knuth's two-sum into hi, its error into lo)
+__device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
+  const float s = __fadd_rn(hi, v);
+  const float bb = __fadd_rn(s, -hi);
+  const float e = __fadd_rn(__fadd_rn(hi, -__fadd_rn(s, -bb)), __fadd_rn(v, -bb));
+  hi = s;
+  lo = __fadd_rn(lo, e);
+}
+
+template <int S>
+__global__ void __launch_bounds__(THREADS, 1)
+    k_gemm_bf16s(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
+                 int nkb, const float* __restrict__ sA, long long lsA, const float* __restrict__ sB,
+                 double* __restrict__ out, long long ldo, int* __restrict__ err) {
+  constexpr int STAGE_BYTES = SCfg<S>::STAGE_BYTES;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  uint64_t* bars = reinterpret_cast<uint64_t*>(smem + STAGES * STAGE_BYTES);
+  uint64_t* full = bars;
+  uint64_t* empty = bars + STAGES;
+  uint64_t* tfull = bars + 2 * STAGES;
+  uint64_t* tempty = bars + 2 * STAGES + 2;
+  uint64_t* done = bars + 2 * STAGES + 4;
+  uint32_t* tmem_slot = reinterpret_cast<uint32_t*>(bars + 2 * STAGES + 5);
+  volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  const int nchunks = (nkb + KC_KB - 1) / KC_KB;
+
+  if (threadIdx.x == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), 1);
+    }
+    for (int b = 0; b < 2; ++b) {
+      mbar_init(smem_u32(&tfull[b]), 1);
+      mbar_init(smem_u32(&tempty[b]), EPI_WARPS);
+    }
+    mbar_init(smem_u32(done), 1);
+    *abort_flag = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 1) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(smem_u32(tmem_slot)),
+                 "r"(TMEM_COLS)
+                 : "memory");
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+  }
+  fence_before();
+  __syncthreads();
+  fence_after();
+  const uint32_t tmem = *tmem_slot;
+  if (warp < EPI_WARP0) {
+    asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(REGS_LOW));
+  if (warp == 0 && lane == 0) {
+    // ---------------- TMA producer: all S slices of the A and B tiles of one k-block
+    int issued = 0;
+    for (int kb = 0; kb < nkb; ++kb) {
+      const int s = kb % STAGES, it = kb / STAGES;
+      if (it > 0 && !mbar_wait(smem_u32(&empty[s]), (it - 1) & 1)) {
+        *abort_flag = 1;
+        break;
+      }
+      if (*abort_flag) break;
+      uint8_t* st = smem + s * STAGE_BYTES;
+      const uint32_t fb = smem_u32(&full[s]);
+      mbar_expect_tx(fb, STAGE_BYTES);
+      tma_load_3d(smem_u32(st), &tmA, fb, kb * BK, m0, 0);
+      tma_load_3d(smem_u32(st + S * TILE), &tmB, fb, kb * BK, n0, 0);
+      issued = kb + 1;
+    }
+    if (*abort_flag) {
+      for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
+        (void)mbar_wait(smem_u32(&full[kb % STAGES]), (kb / STAGES) & 1);
+    }
+  } else if (warp == 1 && lane == 0) {
+    // ---------------- MMA issuer
+    const uint32_t idesc = idesc_bf16(BM, BN);
+    for (int c = 0; c < nchunks && !*abort_flag; ++c) {
+      const int b = c & 1, u = c >> 1;
+      if (u > 0 && !mbar_wait(smem_u32(&tempty[b]), (u - 1) & 1)) {
+        *abort_flag = 1;
+        break;
+      }
+      fence_after();
+      const uint32_t accP = tmem + (uint32_t)(b * 2 * BN);
+      const uint32_t accQ = accP + BN;
+      const int kb_end = min(nkb, (c + 1) * KC_KB);
+      for (int kb = c * KC_KB; kb < kb_end; ++kb) {
+        const int s = kb % STAGES, it = kb / STAGES;
+        if (!mbar_wait(smem_u32(&full[s]), it & 1)) {
+          *abort_flag = 1;
+          break;
+        }
+        fence_after();
+        const uint32_t a0 = smem_u32(smem + s * STAGE_BYTES);
+        const uint32_t b0 = a0 + S * TILE;
+#pragma unroll
+        for (int k = 0; k < BK / 16; ++k) {
+          const uint32_t off = k * 32;  // 16 bf16 = 32 bytes along K inside the 64-byte swizzle atom
+          const uint32_t first = (kb == c * KC_KB && k == 0) ? 0u : 1u;
+          mma_bf16(accP, sdesc<64>(a0 + off), sdesc<64>(b0 + off), idesc, first);
+          uint32_t qacc = first;
+#pragma unroll
+          for (int sa = 0; sa < S; ++sa)
+#pragma unroll
+            for (int sb = 0; sb + sa < S; ++sb) {
+              if (sa == 0 && sb == 0) continue;
+              mma_bf16(accQ, sdesc<64>(a0 + sa * TILE + off), sdesc<64>(b0 + sb * TILE + off), idesc, qacc);
+              qacc = 1u;
+            }
+        }
+        mma_commit(smem_u32(&empty[s]));
+      }
+      if (*abort_flag) break;
+      mma_commit(smem_u32(&tfull[b]));
+    }
+    mma_commit(smem_u32(done));
+  }
+  } else {
+    asm volatile("setmaxnreg.inc.sync.aligned.u32 %0;" ::"n"(REGS_HIGH));
+    // ---------------- epilogue: scale each chunk and add it into (hi, lo) pairs
+    const int q = warp & 3;
+    const int half = (warp - EPI_WARP0) >> 2;
+    const uint32_t lane_base = (uint32_t)(q * 32) << 16;
+    const int gm = m0 + q * 32 + lane;
+    const int nb = n0 + half * EC;
+    float hi[EC], lo[EC];
+#pragma unroll
+    for (int j = 0; j < EC; ++j) hi[j] = lo[j] = 0.f;
+    bool ok = true;
+    for (int c = 0; c < nchunks; ++c) {
+      const int b = c & 1, u = c >> 1;
+      bool got = mbar_wait(smem_u32(&tfull[b]), u & 1);
+      if (!got) *abort_flag = 1;
+      ok = __all_sync(0xffffffffu, got && !*abort_flag);
+      if (!ok) break;
+      fence_after();
+      const float sa = sA[(long long)c * lsA + gm];
+#pragma unroll
+      for (int c0 = 0; c0 < EC; c0 += 8) {
+        uint32_t vp[8], vq[8];
+        const uint32_t col = tmem + lane_base + (uint32_t)(b * 2 * BN + half * EC + c0);
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(vp[0]), "=r"(vp[1]), "=r"(vp[2]), "=r"(vp[3]), "=r"(vp[4]), "=r"(vp[5]), "=r"(vp[6]),
+                       "=r"(vp[7])
+                     : "r"(col));
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(vq[0]), "=r"(vq[1]), "=r"(vq[2]), "=r"(vq[3]), "=r"(vq[4]), "=r"(vq[5]), "=r"(vq[6]),
+                       "=r"(vq[7])
+                     : "r"(col + BN));
+        asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+#pragma unroll
+        for (int j = 0; j < 8; ++j) {
+          two_sum_acc(hi[c0 + j], lo[c0 + j], __fmul_rn(__uint_as_float(vp[j]), sa));
+          two_sum_acc(hi[c0 + j], lo[c0 + j], __fmul_rn(__uint_as_float(vq[j]), sa));
+        }
+      }
+      fence_before();
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&tempty[b]));
+    }
+    if (ok) {  // warp-uniform
+      // column scales: lane i holds those of columns nb + 2i, nb + 2i + 1 (inside the padded rows)
+      const float2 sbv = __ldg(reinterpret_cast<const float2*>(sB + nb) + lane);
+      double* o = out + (long long)gm * ldo + nb;
+      const bool row_ok = gm < M;
+      const bool vec = nb + EC <= N && (ldo & 1) == 0;
+#pragma unroll
+      for (int j = 0; j < EC; j += 2) {
+        const float s0 = __shfl_sync(0xffffffffu, sbv.x, j >> 1);
+        const float s1 = __shfl_sync(0xffffffffu, sbv.y, j >> 1);
+        const double d0 = ((double)hi[j] + (double)lo[j]) * (double)s0;
+        const double d1 = ((double)hi[j + 1] + (double)lo[j + 1]) * (double)s1;
+        if (row_ok) {
+          if (vec) {
+            *reinterpret_cast<double2*>(o + j) = make_double2(d0, d1);
+          } else {
+            if (nb + j < N) o[j] = d0;
+            if (nb + j + 1 < N) o[j + 1] = d1;
+          }
+        }
+      }
+    }
+  }
+  fence_before();
+  __syncthreads();
+  if (warp == 1) {
+    (void)mbar_wait(smem_u32(done), 0);
+    fence_after();
+    asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(TMEM_COLS) : "memory");
+  }
+  if (threadIdx.x == 0 && *abort_flag) atomicExch(err, 1);
+}
+
+// ---------------------------------------------------------------- operand slicing
+// Sources: each gives the real operand entries (k2, k2+1, k2+2, k2+3) of one row
+// (k2 a multiple of 4), zero outside the logical matrix.
+
+// Rows m of opA(A) with K interleaved (re, im): the A operand of the 4M form.
+struct SrcA {
+  const cplx* p;
+  long long ld;
+  int rows, K, op;
+  __device__ void load4(long long m, int k2, double v[4]) const {
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = (k2 >> 1) + h;
+      double re = 0.0, im = 0.0;
+      if (m < rows && k < K) {
+        const cplx z = (op == OP_N || op == OP_R) ? p[m * ld + k] : p[(long long)k * ld + m];
+        re = z.x;
+        im = (op == OP_C || op == OP_R) ? -z.y : z.y;
+      }
+      v[2 * h] = re;
+      v[2 * h + 1] = im;
+    }
+  }
+};
+// Rows (n, c') of the expanded real B operand built from opB(B)[k][n]:
+//   row (n, re): (Re, -Im) over K index (k, re/im); row (n, im): (Im, Re).
+struct SrcB {
+  const cplx* p;
+  long long ld;
+  int K, N, op;
+  __device__ void load4(long long n2, int k2, double v[4]) const {
+    const long long n = n2 >> 1;
+    const int cp = (int)(n2 & 1);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = (k2 >> 1) + h;
+      double re = 0.0, im = 0.0;
+      if (n < N && k < K) {
+        const cplx z = (op == OP_N || op == OP_R) ? p[(long long)k * ld + n] : p[n * ld + k];
+        re = z.x;
+        im = (op == OP_C || op == OP_R) ? -z.y : z.y;
+      }
+      v[2 * h] = cp == 0 ? re : im;
+      v[2 * h + 1] = cp == 0 ? -im : re;
+    }
+  }
+};
+// Rows (a, s) of the stage-3 A operand of H_eff: K index (v, b', re/im),
+//   T2[(a,s)][(v,b')] = sum_{(w,t)} W[w,s,t,v] T1[a][w][t][b']   (T1 complex FP64)
+struct SrcStage2 {
+  const cplx* T1;
+  const int* off;
+  const int* idx;
+  const cplx* val;
+  int ML, WL, WR, D, MR;
+  __device__ void load4(long long row, int k2, double v[4]) const {
+    const long long a = row / D;
+    const int s = (int)(row % D);
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int j = (k2 >> 1) + h;
+      const int vv = j / MR, b = j % MR;
+      double re = 0.0, im = 0.0;
+      if (a < ML && vv < WR) {
+        const int sv = s * WR + vv;
+        for (int e = off[sv]; e < off[sv + 1]; ++e) {
+          const int w = idx[2 * e], t = idx[2 * e + 1];
+          const cplx x = T1[((a * WL + w) * D + t) * (long long)MR + b];
+          const cplx c = val[e];
+          re += c.x * x.x - c.y * x.y;
+          im += c.x * x.y + c.y * x.x;
+        }
+      }
+      v[2 * h] = re;
+      v[2 * h + 1] = im;
+    }
+  }
+};
+
+// Scale of one group from its largest magnitude m: 2^e with m < 2^e, stored as
+// 2^(e-8).  Groups below 2^-100 are taken as zero; a non-finite entry makes the
+// scale NaN, so that it shows in the output.
+struct GroupScale {
+  int e = 0;
+  bool live = false;
+  float sc = 0.f;
+};
+__device__ __forceinline__ GroupScale group_scale(double m, bool bad) {
+  GroupScale g;
+  if (bad) {
+    g.sc = __int_as_float(0x7fc00000);
+  } else if (m >= 0x1p-100) {
+    g.live = true;
+    g.e = ilogb(m) + 1;
+    g.sc = ldexpf(1.f, g.e - 8);
+  }
+  return g;
+}
+__device__ __forceinline__ bool any_nonfinite(const double v[4]) {
+  return !(v[0] - v[0] == 0.0 && v[1] - v[1] == 0.0 && v[2] - v[2] == 0.0 && v[3] - v[3] == 0.0);
+}
+__device__ __forceinline__ double max_abs4(const double v[4]) {
+  return fmax(fmax(fabs(v[0]), fabs(v[1])), fmax(fabs(v[2]), fabs(v[3])));
+}
+// writes the S slices of 4 consecutive entries of one row: out + s * slice_stride
+template <int S>
+__device__ __forceinline__ void write_slices(const double v[4], const GroupScale& g, __nv_bfloat16* out,
+                                             long long slice_stride) {
+  __nv_bfloat16 sl[S][4];
+#pragma unroll
+  for (int i = 0; i < 4; ++i) {
+    double t = g.live ? ldexp(v[i], 8 - g.e) : 0.0;  // |t| < 256
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      const double a = rint(t);
+      t = (t - a) * 256.0;
+      sl[s][i] = __float2bfloat16_rn((float)ldexp(a, -8 * s));
+    }
+  }
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    __nv_bfloat162 lo2, hi2;
+    lo2.x = sl[s][0];
+    lo2.y = sl[s][1];
+    hi2.x = sl[s][2];
+    hi2.y = sl[s][3];
+    uint2 pk;
+    pk.x = *reinterpret_cast<uint32_t*>(&lo2);
+    pk.y = *reinterpret_cast<uint32_t*>(&hi2);
+    *reinterpret_cast<uint2*>(out + s * slice_stride) = pk;
+  }
+}
+
+// A operands: one warp per (row, chunk of 128 K entries).
+// out: [S][rows_pad][ldk] bf16; scale: [nch][rows_pad] float.
+template <int S, class Src>
+__global__ void k_slice_chunks(Src src, int rows_pad, int ldk, int nch, __nv_bfloat16* __restrict__ out,
+                               float* __restrict__ scale) {
+  const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (gw >= (long long)rows_pad * nch) return;  // warp-uniform
+  const long long row = gw / nch;
+  const int ch = (int)(gw % nch);
+  const int k2 = ch * KC + 4 * lane;
+  double v[4] = {0.0, 0.0, 0.0, 0.0};
+  if (k2 < ldk) src.load4(row, k2, v);
+  double m = max_abs4(v);
+  bool bad = any_nonfinite(v);
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  bad = __any_sync(0xffffffffu, bad);
+  const GroupScale g = group_scale(m, bad);
+  if (k2 < ldk) write_slices<S>(v, g, out + row * ldk + k2, (long long)rows_pad * ldk);
+  if (lane == 0) scale[(long long)ch * rows_pad + row] = g.sc;
+}
+
+// B operands: one 128-thread block per row, one scale per row (two passes over
+// the source: the largest magnitude, then the slices).  scale: [rows_pad] float.
+template <int S, class Src>
+__global__ void __launch_bounds__(128) k_slice_rows(Src src, int rows_pad, int ldk, __nv_bfloat16* __restrict__ out,
+                                                    float* __restrict__ scale) {
+  __shared__ double red_m[4];
+  __shared__ int red_bad[4];
+  const long long row = blockIdx.x;
+  const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
+  double m = 0.0;
+  bool bad = false;
+  for (int k2 = 4 * tid; k2 < ldk; k2 += 512) {
+    double v[4];
+    src.load4(row, k2, v);
+    m = fmax(m, max_abs4(v));
+    bad = bad || any_nonfinite(v);
+  }
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
+  bad = __any_sync(0xffffffffu, bad);
+  if (lane == 0) {
+    red_m[wid] = m;
+    red_bad[wid] = bad ? 1 : 0;
+  }
+  __syncthreads();
+  m = fmax(fmax(red_m[0], red_m[1]), fmax(red_m[2], red_m[3]));
+  bad = (red_bad[0] | red_bad[1] | red_bad[2] | red_bad[3]) != 0;
+  const GroupScale g = group_scale(m, bad);
+  for (int k2 = 4 * tid; k2 < ldk; k2 += 512) {
+    double v[4];
+    src.load4(row, k2, v);
+    write_slices<S>(v, g, out + row * ldk + k2, (long long)rows_pad * ldk);
+  }
+  if (tid == 0) scale[row] = g.sc;
+}
+
+// ---------------------------------------------------------------- host side
+inline int pad32(int k) { return (k + 31) / 32 * 32; }
+inline int pad128(int k) { return (k + 127) / 128 * 128; }
+
+// A sliced operand: bf16 slices [S][rows_pad][ldk] and scales, per (chunk, row)
+// ([nch][rows_pad], A operands) or per row ([rows_pad], B operands).
+struct Sliced {
+  RawBuf data, scale;
+  int rows_pad = 0, ldk = 0, nch = 0, S = 0;
+  bool row_scale = false;
+  void shape(DevicePool* pool, int S_, int rows, int K2, bool per_row) {
+    S = S_;
+    row_scale = per_row;
+    rows_pad = pad128(std::max(rows, 1));
+    ldk = pad32(std::max(K2, 1));
+    nch = (ldk + KC - 1) / KC;
+    data.ensure(pool, sizeof(__nv_bfloat16) * (size_t)S * rows_pad * ldk);
+    scale.ensure(pool, sizeof(float) * (size_t)(per_row ? 1 : nch) * rows_pad);
+  }
+};
+
+template <class Src>
+void slice(cudaStream_t st, const Src& src, Sliced& o) {
+  __nv_bfloat16* d = o.data.as<__nv_bfloat16>();
+  float* sc = o.scale.as<float>();
+  if (o.row_scale) {
+    if (o.S == 4)
+      k_slice_rows<4, Src><<<o.rows_pad, 128, 0, st>>>(src, o.rows_pad, o.ldk, d, sc);
+    else
+      k_slice_rows<3, Src><<<o.rows_pad, 128, 0, st>>>(src, o.rows_pad, o.ldk, d, sc);
+  } else {
+    const int blocks = ceil_div((long long)o.rows_pad * o.nch * 32, 256);
+    if (o.S == 4)
+      k_slice_chunks<4, Src><<<blocks, 256, 0, st>>>(src, o.rows_pad, o.ldk, o.nch, d, sc);
+    else
+      k_slice_chunks<3, Src><<<blocks, 256, 0, st>>>(src, o.rows_pad, o.ldk, o.nch, d, sc);
+  }
+  TDVP_CHECK_LAUNCH();
+}
+
+CUtensorMap make_map3(const Sliced& o, int box_rows) {
+  const void* base = o.data.as<void>();
+  tdvp_require((reinterpret_cast<uintptr_t>(base) & 15) == 0, TDVP_ERR_INVALID_ARG, "TMA base not 16B aligned");
+  tdvp_require(o.ldk % 32 == 0 && o.rows_pad % box_rows == 0, TDVP_ERR_INVALID_ARG, "sliced operand not padded");
+  CUtensorMap m;
+  std::memset(&m, 0, sizeof(m));
+  cuuint64_t dims[3] = {(cuuint64_t)o.ldk, (cuuint64_t)o.rows_pad, (cuuint64_t)o.S};
+  cuuint64_t strides[2] = {(cuuint64_t)o.ldk * 2, (cuuint64_t)o.rows_pad * o.ldk * 2};
+  cuuint32_t box[3] = {(cuuint32_t)BK, (cuuint32_t)box_rows, (cuuint32_t)o.S};
+  cuuint32_t estr[3] = {1, 1, 1};
+  CUresult r = encode_fn()(&m, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 3, const_cast<void*>(base), dims, strides, box,
+                           estr, CU_TENSOR_MAP_INTERLEAVE_NONE, CU_TENSOR_MAP_SWIZZLE_64B,
+                           CU_TENSOR_MAP_L2_PROMOTION_L2_256B, CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+  tdvp_require(r == CUDA_SUCCESS, TDVP_ERR_CUDA, "cuTensorMapEncodeTiled (bf16) failed: " + std::to_string((int)r));
+  return m;
+}
+
+template <int S>
+void launch_bf16s(cudaStream_t st, const CUtensorMap& ma, const CUtensorMap& mb, int M, int N, int nkb,
+                  const float* sA, long long lsA, const float* sB, double* out, long long ldo,
+                  int* d_err) {
+  static bool attr = false;
+  if (!attr) {
+    // the register hand-over inside the kernel is sized for exactly this launch allocation
+    cudaFuncAttributes fa;
+    TDVP_CUDA(cudaFuncGetAttributes(&fa, k_gemm_bf16s<S>));
+    tdvp_require(fa.numRegs == REGS_LAUNCH, TDVP_ERR_CUDA,
+                 "gemm_bf16s: kernel built with " + std::to_string(fa.numRegs) + " registers, expected " +
+                     std::to_string(REGS_LAUNCH));
+    TDVP_CUDA(cudaFuncSetAttribute(k_gemm_bf16s<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                   SCfg<S>::SMEM_BYTES));
+    attr = true;
+  }
+  dim3 grid(ceil_div(N, BN), ceil_div(M, BM));
+  tdvp_require(grid.y <= 65535, TDVP_ERR_INVALID_ARG, "gemm_bf16s: M too large");
+  k_gemm_bf16s<S><<<grid, THREADS, SCfg<S>::SMEM_BYTES, st>>>(ma, mb, M, N, nkb, sA, lsA, sB, out, ldo, d_err);
+  TDVP_CHECK_LAUNCH();
+}
+
+// out[M x N] (FP64, row-major, ldo) = A B^T over the sliced real operands
+void gemm_bf16s(cudaStream_t st, const Sliced& A, const Sliced& B, int M, int N, double* out, long long ldo,
+                int* d_err) {
+  if (M <= 0 || N <= 0) return;
+  tdvp_require(A.ldk == B.ldk && A.S == B.S, TDVP_ERR_INVALID_ARG, "gemm_bf16s: operand K or slices differ");
+  tdvp_require(M <= A.rows_pad && N <= B.rows_pad, TDVP_ERR_INVALID_ARG, "gemm_bf16s: operand rows");
+  tdvp_require(!A.row_scale && B.row_scale, TDVP_ERR_INVALID_ARG, "gemm_bf16s: operand scaling groups");
+  const CUtensorMap ma = make_map3(A, BM), mb = make_map3(B, BN);
+  const int nkb = A.ldk / BK;
+  if (A.S == 4)
+    launch_bf16s<4>(st, ma, mb, M, N, nkb, A.scale.as<float>(), A.rows_pad, B.scale.as<float>(), out,
+                    ldo, d_err);
+  else
+    launch_bf16s<3>(st, ma, mb, M, N, nkb, A.scale.as<float>(), A.rows_pad, B.scale.as<float>(), out,
+                    ldo, d_err);
+}
+}  // namespace tcb
+
+using namespace tcb;
+
+struct TcSliceCache {
+  long long key = -1;
+  int S = 0;
+  Sliced L, R, X, T2;
+  RawBuf T1;
+};
+
+namespace {
+TcSliceCache& slice_cache(Scratch& s) {
+  if (!s.tcs) s.tcs = std::make_shared<TcSliceCache>();
+  return *s.tcs;
+}
+int* tc_err(cudaStream_t st, Scratch& s) {
+  TcEnvCache& c = s.tc;
+  if (c.err.bytes() == 0) {
+    c.err.ensure(s.pool, sizeof(int));
+    TDVP_CUDA(cudaMemsetAsync(c.err.as<int>(), 0, sizeof(int), st));
+  }
+  c.pending = true;
+  return c.err.as<int>();
+}
+}  // namespace
+
+int bf16_slices(int precision) { return precision == TDVP_PREC_BF16X6 ? 3 : 4; }
+
+void heff_bf16s(cudaStream_t st, Scratch& s, const SiteOp& op, const cplx* x, cplx* y, int S) {
+  const int ml = op.ml, mr = op.mr, wl = op.wl, wr = op.wr, d = op.d;
+  TcSliceCache& c = slice_cache(s);
+  DevicePool* pool = s.pool;
+  int* err = tc_err(st, s);
+  if (op.env_key < 0 || c.key != op.env_key || c.S != S) {
+    // L as the A operand: rows (a, w), K = (a', re/im)
+    c.L.shape(pool, S, ml * wl, 2 * ml, false);
+    slice(st, SrcA{op.L, ml, ml * wl, ml, OP_N}, c.L);
+    // R[b][(v,b')] is B[k=(v,b')][n=b] stored n-major (op T)
+    c.R.shape(pool, S, 2 * mr, 2 * wr * mr, true);
+    slice(st, SrcB{op.R, (long long)wr * mr, wr * mr, mr, OP_T}, c.R);
+    c.key = op.env_key;
+    c.S = S;
+  }
+  // stage 1: T1[(a,w)][(s',b',c)] = L x     (x[a'][(s',b')] is B[k=a'][n=(s',b')])
+  c.X.shape(pool, S, 2 * d * mr, 2 * ml, true);
+  slice(st, SrcB{x, (long long)d * mr, ml, d * mr, OP_N}, c.X);
+  const int M1 = ml * wl, N1 = 2 * d * mr;
+  c.T1.ensure(pool, sizeof(double) * (size_t)M1 * N1);
+  gemm_bf16s(st, c.L, c.X, M1, N1, c.T1.as<double>(), N1, err);
+  // stage 2: MPO tensor, sliced straight into the stage-3 A operand
+  const WSparse& ws = *op.W;
+  c.T2.shape(pool, S, ml * d, 2 * wr * mr, false);
+  slice(st, SrcStage2{c.T1.as<cplx>(), ws.d_l_off, ws.d_l_idx, ws.d_l_val, ml, wl, wr, d, mr}, c.T2);
+  // stage 3: y[(a,s)][(b,c)] = T2 R^T
+  gemm_bf16s(st, c.T2, c.R, ml * d, 2 * mr, reinterpret_cast<double*>(y), 2 * mr, err);
+}
+
+void zgemm_bf16s(cudaStream_t st, Scratch& s, int S, int opA, int opB, int M, int N, int K, const cplx* A,
+                 long long lda, const cplx* B, long long ldb, cplx* C, long long ldc) {
+  if (M <= 0 || N <= 0) return;
+  DevicePool* pool = s.pool;
+  int* err = tc_err(st, s);
+  Sliced a, b;
+  a.shape(pool, S, M, 2 * std::max(K, 1), false);
+  slice(st, SrcA{A, lda, M, K, opA}, a);
+  b.shape(pool, S, 2 * N, 2 * std::max(K, 1), true);
+  slice(st, SrcB{B, ldb, K, N, opB}, b);
+  gemm_bf16s(st, a, b, M, 2 * N, reinterpret_cast<double*>(C), 2 * ldc, err);
+}

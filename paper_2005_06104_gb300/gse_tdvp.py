@@ -22,7 +22,7 @@ if not os.path.exists(LIB_PATH):
 _lib = C.CDLL(LIB_PATH)
 
 REAL, IMAG = 0, 1
-PREC_FP64, PREC_TF32X3, PREC_TF32X3_ENV = 0, 1, 2
+PREC_FP64, PREC_TF32X3, PREC_TF32X3_ENV, PREC_BF16X10, PREC_BF16X6 = 0, 1, 2, 3, 4
 STATUS = {0: "ok", 1: "invalid argument", 2: "shape mismatch", 3: "out of memory",
           4: "Lanczos not converged", 5: "non-finite value", 6: "device wait timed out",
           7: "CUDA error", 8: "SVD not converged"}
@@ -81,6 +81,17 @@ _lib.tdvp_status_string.argtypes = [C.c_int]
 _lib.tdvp_status_string.restype = C.c_char_p
 _lib.tdvp_contract_last_error.argtypes = []
 _lib.tdvp_contract_last_error.restype = C.c_char_p
+_lib.tdvp_launch_count.argtypes = [C.POINTER(C.c_longlong)]
+_lib.tdvp_launch_count.restype = C.c_int
+
+
+def launch_count():
+    """Kernels the library has launched in this process (all handles and calls)."""
+    out = C.c_longlong(0)
+    s = _lib.tdvp_launch_count(C.byref(out))
+    if s != 0:
+        raise TDVPError(s, "tdvp_launch_count")
+    return out.value
 
 
 class SiteDims(C.Structure):

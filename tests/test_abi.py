@@ -51,3 +51,11 @@ def test_default_options_struct(lib):
     assert o.chi_max == 77 and o.tau_im == -0.25 and o.tau_re == 0.0
     assert o.lanczos_tol == 1e-12 and o.lanczos_max == 40 and o.precision == g.PREC_FP64
     assert g.declared_symbols() == declared()
+
+
+def test_launch_counter_reads_without_a_gpu(lib):
+    from paper_2005_06104_gb300 import gse_tdvp as g
+    assert lib.tdvp_launch_count(None) == 1
+    n0 = g.launch_count()
+    assert isinstance(n0, int) and n0 >= 0
+    assert g.launch_count() == n0  # nothing launched in between

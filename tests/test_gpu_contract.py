@@ -6,6 +6,13 @@ tensor-core form is held to relative 1e-5: each product keeps about 22
 significant bits (hi + lo, the lo*lo term dropped, |x - hi - lo| <= 2^-22 |x|),
 FP32 accumulation adds about 2^-24 sqrt(K) per output, and two GEMMs are
 chained, which bounds the norm-wise error near 3e-6 for these shapes.
+
+The BF16 exact-slice forms represent every operand entry to 2^-33 (4 slices)
+or 2^-25 (3 slices) of its scaling group's largest magnitude; the leading
+slice product is summed exactly and the rest carries about 2^-31 of it per
+128-deep chunk.  For these operands (entries within a few standard deviations
+of their group maxima, two chained GEMMs) that bounds the norm-wise error near
+1e-9 and 3e-7: the tests hold them to 1e-8 and 3e-6.
 """
 import numpy as np
 import pytest
@@ -18,6 +25,8 @@ from paper_2005_06104_gb300 import workloads as wl
 
 TOL64 = 1e-12
 TOL_TC = 1e-5
+TOL_BF16X10 = 1e-8
+TOL_BF16X6 = 3e-6
 
 
 @pytest.fixture(scope="module")
@@ -48,7 +57,7 @@ SHAPES = [  # (ml, mr, W site) -- several tiles with ragged tails, the boundary 
 
 
 @pytest.mark.parametrize("ml,mr,W", SHAPES, ids=lambda v: str(v) if np.isscalar(v) else "W")
-@pytest.mark.parametrize("prec", ["fp64", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp64", "tf32x3", "bf16x10", "bf16x6"])
 def test_heff_contract_matches_oracle(g, ml, mr, W, prec):
     rng = np.random.default_rng(ml * 1000 + mr)
     L = _rand(rng, ml, W.shape[0], ml)
@@ -56,10 +65,38 @@ def test_heff_contract_matches_oracle(g, ml, mr, W, prec):
     x = _rand(rng, ml, W.shape[1], mr)
     Ld, Rd, xd = _dev(L, R, x)
     yd = torch.empty_like(xd)
-    g.heff_contract(Ld, W, Rd, xd, yd, precision=g.PREC_FP64 if prec == "fp64" else g.PREC_TF32X3)
+    g.heff_contract(Ld, W, Rd, xd, yd, precision=PREC[prec](g))
     ref = O.heff_apply(L, W, R, x)
     err = _rel(yd.cpu().numpy(), ref)
-    assert err < (TOL64 if prec == "fp64" else TOL_TC), err
+    assert err < TOL[prec], err
+
+
+PREC = {"fp64": lambda g: g.PREC_FP64, "tf32x3": lambda g: g.PREC_TF32X3,
+        "bf16x10": lambda g: g.PREC_BF16X10, "bf16x6": lambda g: g.PREC_BF16X6}
+TOL = {"fp64": TOL64, "tf32x3": TOL_TC, "bf16x10": TOL_BF16X10, "bf16x6": TOL_BF16X6}
+
+
+@pytest.mark.parametrize("prec", ["bf16x10", "bf16x6"])
+def test_heff_bf16_groups_with_wide_range(g, prec):
+    """Rows whose entries span many orders of magnitude, a zero row and a zero
+    chunk: the fixed-point slices keep every entry to 2^-33 (2^-25) of its
+    group's largest magnitude, so the output error stays at that level of the
+    output's scale."""
+    rng = np.random.default_rng(17)
+    W = W_LADDER[6]
+    ml, mr = 160, 136
+    L = _rand(rng, ml, W.shape[0], ml) * np.exp(rng.uniform(-12, 3, size=(ml, W.shape[0], 1)))
+    R = _rand(rng, mr, W.shape[3], mr) * np.exp(rng.uniform(-12, 3, size=(1, W.shape[3], mr)))
+    x = _rand(rng, ml, W.shape[1], mr) * np.exp(rng.uniform(-8, 0, size=(ml, 1, 1)))
+    L[3] = 0.0
+    x[:, :, 5] = 0.0
+    L[:, :, 64:] *= 1e-9
+    Ld, Rd, xd = _dev(L, R, x)
+    yd = torch.empty_like(xd)
+    g.heff_contract(Ld, W, Rd, xd, yd, precision=PREC[prec](g))
+    ref = O.heff_apply(L, W, R, x)
+    assert _rel(yd.cpu().numpy(), ref) < 10 * TOL[prec]
+    assert np.all(yd.cpu().numpy()[3] == 0.0)
 
 
 @pytest.mark.parametrize("ml,mr,w", [(1, 1, 1), (3, 5, 5), (70, 66, 8), (130, 129, 14)])
@@ -92,7 +129,7 @@ def test_env_updates_match_oracle(g, ml, mr, W):
 
 
 @pytest.mark.parametrize("kind", ["real", "imag"])
-@pytest.mark.parametrize("prec", ["fp64", "tf32x3"])
+@pytest.mark.parametrize("prec", ["fp64", "tf32x3", "bf16x10"])
 def test_lanczos_exponential_matches_oracle(g, kind, prec):
     # environments of a random canonical MPS make H_eff Hermitian, as in the sweep
     lat = wl.zigzag_ladder(5, 1.0, 1.0)
@@ -111,10 +148,12 @@ def test_lanczos_exponential_matches_oracle(g, kind, prec):
     Ld, Rd, xd = _dev(Ls[c], Rs[c], x)
     yd = torch.empty_like(xd)
     it = g.expm_contract(Ld, W[c], Rd, xd, yd, delta, kind=g.REAL if kind == "real" else g.IMAG,
-                         precision=g.PREC_FP64 if prec == "fp64" else g.PREC_TF32X3)
+                         precision=PREC[prec](g))
     err = _rel(yd.cpu().numpy(), ref)
     if prec == "fp64":
         assert err < 1e-11 and it == it_ref
+    elif prec == "bf16x10":
+        assert err < TOL_BF16X10 and abs(it - it_ref) <= 1
     else:
         assert err < TOL_TC and abs(it - it_ref) <= 2
 
@@ -148,8 +187,10 @@ def test_heff_full_size_sampled(g):
     Ld, Rd, xd = rnd(m, 14, m), rnd(m, 14, m), rnd(m, 2, m)
     y64 = torch.empty_like(xd)
     ytc = torch.empty_like(xd)
+    ybf = torch.empty_like(xd)
     g.heff_contract(Ld, W, Rd, xd, y64, precision=g.PREC_FP64)
     g.heff_contract(Ld, W, Rd, xd, ytc, precision=g.PREC_TF32X3)
+    g.heff_contract(Ld, W, Rd, xd, ybf, precision=g.PREC_BF16X10)
     L, R, x = Ld.cpu().numpy(), Rd.cpu().numpy(), xd.cpu().numpy()
     rng = np.random.default_rng(1)
     entries = [(int(rng.integers(m)), int(rng.integers(2)), int(rng.integers(m))) for _ in range(12)]
@@ -157,8 +198,11 @@ def test_heff_full_size_sampled(g):
     ref = O.heff_apply_entries(L, W, R, x, entries)
     got64 = np.array([y64[a, s, b].item() for a, s, b in entries])
     gottc = np.array([ytc[a, s, b].item() for a, s, b in entries])
+    gotbf = np.array([ybf[a, s, b].item() for a, s, b in entries])
     scale = np.linalg.norm(ref) / np.sqrt(len(ref))
     assert np.max(np.abs(got64 - ref)) < 1e-11 * scale
     assert np.max(np.abs(gottc - ref)) < 3e-5 * scale
-    # the whole output: the two GPU forms agree norm-wise
+    assert np.max(np.abs(gotbf - ref)) < 3e-8 * scale
+    # the whole output: the GPU forms agree norm-wise
     assert (torch.linalg.norm(ytc - y64) / torch.linalg.norm(y64)).item() < TOL_TC
+    assert (torch.linalg.norm(ybf - y64) / torch.linalg.norm(y64)).item() < TOL_BF16X10

@@ -152,15 +152,16 @@ def test_gse_imaginary_time_decoupled_ladder(g):
     st.close()
 
 
-def test_precision_form_energy_and_norm(g):
-    """Split-TF32 sweeps hold relative energy error <= 1e-7 and norm drift <= 1e-10 per step
+@pytest.mark.parametrize("prec", ["tf32x3", "bf16x10"])
+def test_precision_form_energy_and_norm(g, prec):
+    """Tensor-core sweeps hold relative energy error <= 1e-7 and norm drift <= 1e-10 per step
     against the FP64 GPU form (real time, rung-coupled ladder, Neel with one flipped spin)."""
     lat = wl.zigzag_ladder(8, 1.0, 1.0)
     W = wl.heisenberg_mpo(lat)
     psi = wl.neel_state(lat, flip=(4, 0))
     kw = dict(tau=0.1, eps_k=1e-8, eps_m=1e-8, chi_max=48)
     a = g.GseTdvp(psi, W, precision=g.PREC_FP64, **kw)
-    b = g.GseTdvp(psi, W, precision=g.PREC_TF32X3, **kw)
+    b = g.GseTdvp(psi, W, precision=g.PREC_TF32X3 if prec == "tf32x3" else g.PREC_BF16X10, **kw)
     e0 = a.energy()
     for _ in range(4):
         a.step(0.1, g.REAL, 3)
