@@ -60,9 +60,11 @@ typedef enum {
   TDVP_PREC_BF16X10 = 3,    /* tcgen05 kind::f16: each operand cut into 4 fixed-point
                                BF16 slices per row and 128-deep K chunk (power-of-two
                                chunk scale), 10 slice products, the leading one summed
-                               exactly, chunks promoted into FP32 (hi, lo) pairs:
-                               resolves about 2^-33 of the chunk maxima.  H_eff,
-                               K_eff, environments and Krylov-vector GEMMs           */
+                               exactly, the other 9 in one FP32 accumulator per
+                               chunk, chunks promoted into FP32 (hi, lo) pairs:
+                               operands to 2^-33 of their group maxima, products to
+                               about 2^-24 (measured 1e-8 relative per H_eff apply).
+                               H_eff, K_eff, environments and Krylov-vector GEMMs  */
   TDVP_PREC_BF16X6 = 4      /* as BF16X10 with 3 slices and 6 products (about 2^-25)   */
 } tdvp_precision;
 
@@ -182,6 +184,26 @@ TDVP_API tdvp_status tdvp_trunc_stats(tdvp_handle* h, double* out9);
 TDVP_API tdvp_status tdvp_get_mps(tdvp_handle* h, double* const* sites_out);
 
 /* ---------------------------------------------------------------------------
+ * Checkpoints.  A file holds one MPS: magic "GSETDVP1", int32 {version 1, N, d,
+ * 0}, int32 bond_dims[N + 1], the site tensors as complex128 [m_i][d][m_{i+1}]
+ * row-major, and a 64-bit FNV-1a hash of all preceding bytes (little-endian).
+ * Writers go through "<path>.tmp" and rename it over <path>.  Readers reject a
+ * wrong magic or version, inconsistent dimensions, a truncated file or a hash
+ * mismatch with TDVP_ERR_INVALID_ARG / TDVP_ERR_SHAPE; tdvp_checkpoint_last_error()
+ * (per thread) gives the reason.  The checkpoint_* calls are host-only. */
+/* Saves the current state of h (its gauge as it stands). */
+TDVP_API tdvp_status tdvp_save(tdvp_handle* h, const char* path);
+/* Creates a handle from a saved state, as tdvp_create does from host arrays. */
+TDVP_API tdvp_status tdvp_load(const char* path, const tdvp_mpo_desc* mpo, const tdvp_options* opt, void* stream,
+                               tdvp_handle** out);
+TDVP_API tdvp_status tdvp_checkpoint_write(const char* path, const tdvp_mps_desc* mps);
+/* N and d, and bond_dims (N + 1 ints) when non-null. */
+TDVP_API tdvp_status tdvp_checkpoint_read_header(const char* path, int* n_sites, int* d, int* bond_dims);
+/* Site tensors into caller buffers sized from the header (2 m_i d m_{i+1} doubles). */
+TDVP_API tdvp_status tdvp_checkpoint_read(const char* path, double* const* sites_out);
+TDVP_API const char* tdvp_checkpoint_last_error(void);
+
+/* ---------------------------------------------------------------------------
  * Timing of the H_eff applies inside a handle (CUDA events on the handle's
  * stream).  tdvp_profile(h, 1) starts recording, 0 stops.  tdvp_profile_read
  * writes out3 = {applies, total milliseconds, total algorithmic flops} since
@@ -221,6 +243,16 @@ typedef struct { int ml, mr, wl, wr, d; } tdvp_site_dims;
 TDVP_API tdvp_status tdvp_heff_contract(const tdvp_site_dims* dims, const void* L_dev, const double* W_host,
                                         const void* R_dev, const void* x_dev, void* y_dev, int precision,
                                         void* stream);
+/* As tdvp_heff_contract, for repeated applies with the same environments (a
+ * Lanczos run).  env_tag >= 0 names the content of (L, R, W, dims): when the
+ * previous tensor-core call used the same tag, the tensor-core operand forms of
+ * L and R built then are reused instead of being rebuilt from L_dev and R_dev.
+ * The caller must give a new tag whenever L, R, W or dims change; -1 never
+ * reuses (the behaviour of tdvp_heff_contract).  FP64 ignores the tag.
+ * TDVP_ERR_INVALID_ARG for env_tag < -1. */
+TDVP_API tdvp_status tdvp_heff_contract_cached(const tdvp_site_dims* dims, const void* L_dev,
+                                               const double* W_host, const void* R_dev, const void* x_dev,
+                                               void* y_dev, int precision, long long env_tag, void* stream);
 /* y[a,c] = sum L[a,w,a'] x[a',b'] R[c,w,b']; L: ml*w*ml, R: mr*w*mr, x, y: ml*mr. */
 TDVP_API tdvp_status tdvp_keff_contract(int ml, int mr, int w, const void* L_dev, const void* R_dev,
                                         const void* x_dev, void* y_dev, void* stream);

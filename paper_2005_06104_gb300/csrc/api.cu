@@ -6,10 +6,6 @@
 
 #include "engine.cuh"
 
-struct tdvp_handle {
-  Engine eng;
-  std::string err;
-};
 
 namespace {
 template <class F>
@@ -362,7 +358,13 @@ extern "C" {
 
 tdvp_status tdvp_heff_contract(const tdvp_site_dims* dims, const void* L, const double* W, const void* R,
                                const void* x, void* y, int precision, void* stream) {
+  return tdvp_heff_contract_cached(dims, L, W, R, x, y, precision, -1, stream);
+}
+
+tdvp_status tdvp_heff_contract_cached(const tdvp_site_dims* dims, const void* L, const double* W, const void* R,
+                                      const void* x, void* y, int precision, long long env_tag, void* stream) {
   return raw_guarded([&](RawCtx& c) {
+    tdvp_require(env_tag >= -1, TDVP_ERR_INVALID_ARG, "env_tag must be >= -1");
     check_dims(dims);
     tdvp_require(L && R && x && y && x != y, TDVP_ERR_INVALID_ARG, "null or aliased buffers");
     tdvp_require(precision >= TDVP_PREC_FP64 && precision <= TDVP_PREC_BF16X6, TDVP_ERR_INVALID_ARG,
@@ -378,7 +380,9 @@ tdvp_status tdvp_heff_contract(const tdvp_site_dims* dims, const void* L, const 
     op.wl = dims->wl;
     op.wr = dims->wr;
     op.d = dims->d;
-    op.env_key = -1;
+    // a tag names the (L, R) content for the operand caches of the tensor-core paths;
+    // tags are kept apart from nothing else (this context serves only these calls)
+    op.env_key = env_tag;
     heff_apply_prec(st, c.scr, op, static_cast<const cplx*>(x), static_cast<cplx*>(y), precision);
     TDVP_CUDA(cudaStreamSynchronize(st));
     w.free_device();

@@ -159,3 +159,9 @@ struct Engine {
   cplx expect_local(const double* op, int site);
   void sync() { TDVP_CUDA(cudaStreamSynchronize(st)); }
 };
+
+// The opaque handle of the C ABI: one engine and the text of its last error.
+struct tdvp_handle {
+  Engine eng;
+  std::string err;
+};

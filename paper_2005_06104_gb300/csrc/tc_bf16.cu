@@ -13,13 +13,13 @@
 // leading product a1 b1 in accumulator P, all others in accumulator Q.  Within a
 // chunk P is a sum of at most 128 integers of magnitude <= 2^16, so every partial
 // sum is an integer below 2^24 and the tensor core's FP32 accumulation of P is
-// exact whatever its rounding.  Q is about 2^-7 of P; its rounding stays near
-// 2^-31 of P per chunk.  The epilogue scales each chunk by its A chunk scale
+// exact whatever its rounding.  Q is about 2^-7 of P; its 72 (S = 4) MMA
+// accumulations per chunk, each rounding near 2^-23 of Q, leave about 2^-24 of P.  The epilogue scales each chunk by its A chunk scale
 // (a power of two: exact) and adds it into a double-float (hi, lo) pair per output
 // with Knuth's two-sum, so no error accrues across chunks.  GB300 runs FP64 at a
 // small fraction of its FP32 rate, which is why the promotion uses FP32 pairs.
-// S = 4 (10 products) resolves about 2^-33 of the chunk maxima; S = 3 (6 products)
-// about 2^-25.
+// S = 4 (10 products) represents the operands to 2^-33 of their group maxima and
+// the products to about 2^-24 (the rounding of Q); S = 3 (6 products) to 2^-25.
 //
 // Kernel layout (one CTA per 128 x 128 output tile, three warpgroups):
 //   warp 0       TMA producer: one 3-D box per operand and stage (all S slices)

@@ -101,6 +101,8 @@ class SiteDims(C.Structure):
 _raw = {
     "tdvp_heff_contract": [C.POINTER(SiteDims), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                            C.c_int, C.c_void_p],
+    "tdvp_heff_contract_cached": [C.POINTER(SiteDims), C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
+                                  C.c_void_p, C.c_int, C.c_longlong, C.c_void_p],
     "tdvp_keff_contract": [C.c_int, C.c_int, C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p],
     "tdvp_env_contract": [C.POINTER(SiteDims), C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p,
                           C.c_void_p],
@@ -131,14 +133,20 @@ def _stream(stream):
     return C.c_void_p(stream or 0)
 
 
-def heff_contract(L, W, R, x, y, precision=PREC_FP64, stream=None):
-    """y = H_eff x on caller tensors: L, R, x, y torch CUDA complex128; W numpy [wl, d, d, wr]."""
+def heff_contract(L, W, R, x, y, precision=PREC_FP64, stream=None, env_tag=None):
+    """y = H_eff x on caller tensors: L, R, x, y torch CUDA complex128; W numpy [wl, d, d, wr].
+    env_tag (int >= 0): reuse the tensor-core operand forms of L and R across calls with
+    the same tag (the caller guarantees L, R, W unchanged)."""
     ml, wl, _ = L.shape
     mr, wr, _ = R.shape
     d = W.shape[1]
     Wc, wp = _host(W)
-    _raw_chk(_lib.tdvp_heff_contract(C.byref(SiteDims(ml, mr, wl, wr, d)), _ptr(L), wp, _ptr(R), _ptr(x), _ptr(y),
-                                     precision, _stream(stream)))
+    dims = C.byref(SiteDims(ml, mr, wl, wr, d))
+    if env_tag is None:
+        _raw_chk(_lib.tdvp_heff_contract(dims, _ptr(L), wp, _ptr(R), _ptr(x), _ptr(y), precision, _stream(stream)))
+    else:
+        _raw_chk(_lib.tdvp_heff_contract_cached(dims, _ptr(L), wp, _ptr(R), _ptr(x), _ptr(y), precision,
+                                                int(env_tag), _stream(stream)))
 
 
 def keff_contract(L, R, x, y, stream=None):
@@ -183,6 +191,50 @@ def heff_contract_noalloc(L, W, R, x, y, stream=None):
                                         _ptr(y), _stream(stream), buf, 512)
     if s != 0:
         raise TDVPError(s, buf.value.decode())
+
+
+_lib.tdvp_checkpoint_write.argtypes = [C.c_char_p, C.c_void_p]
+_lib.tdvp_checkpoint_write.restype = C.c_int
+_lib.tdvp_checkpoint_read_header.argtypes = [C.c_char_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_void_p]
+_lib.tdvp_checkpoint_read_header.restype = C.c_int
+_lib.tdvp_checkpoint_read.argtypes = [C.c_char_p, C.POINTER(C.c_void_p)]
+_lib.tdvp_checkpoint_read.restype = C.c_int
+_lib.tdvp_checkpoint_last_error.argtypes = []
+_lib.tdvp_checkpoint_last_error.restype = C.c_char_p
+_lib.tdvp_save.argtypes = [_h, C.c_char_p]
+_lib.tdvp_save.restype = C.c_int
+_lib.tdvp_load.argtypes = [C.c_char_p, C.c_void_p, C.c_void_p, C.c_void_p, C.POINTER(_h)]
+_lib.tdvp_load.restype = C.c_int
+
+
+def _ckpt_chk(s):
+    if s != 0:
+        raise TDVPError(s, _lib.tdvp_checkpoint_last_error().decode())
+
+
+def write_checkpoint(path, mps):
+    """Writes host site tensors (complex128 [m_i, d, m_{i+1}]) to a checkpoint file (host only)."""
+    dims = [mps[0].shape[0]] + [a.shape[2] for a in mps]
+    pinned = _Pinned(mps, dims)
+    _ckpt_chk(_lib.tdvp_checkpoint_write(os.fsencode(path), C.cast(C.pointer(pinned.desc(mps[0].shape[1])),
+                                                                  C.c_void_p)))
+
+
+def checkpoint_header(path):
+    n, d = C.c_int(0), C.c_int(0)
+    _ckpt_chk(_lib.tdvp_checkpoint_read_header(os.fsencode(path), C.byref(n), C.byref(d), None))
+    dims = (C.c_int * (n.value + 1))()
+    _ckpt_chk(_lib.tdvp_checkpoint_read_header(os.fsencode(path), C.byref(n), C.byref(d), C.cast(dims, C.c_void_p)))
+    return n.value, d.value, list(dims)
+
+
+def read_checkpoint(path):
+    """The site tensors of a checkpoint file (host only)."""
+    n, d, m = checkpoint_header(path)
+    arrs = [np.empty((m[i], d, m[i + 1]), dtype=np.complex128) for i in range(n)]
+    ptrs = (C.c_void_p * n)(*[a.ctypes.data for a in arrs])
+    _ckpt_chk(_lib.tdvp_checkpoint_read(os.fsencode(path), ptrs))
+    return arrs
 
 
 def declared_symbols(header=HEADER):
@@ -235,6 +287,28 @@ class GseTdvp:
             raise TDVPError(s, "tdvp_create failed")
         self.h = h
         del self._m, self._w
+
+    @classmethod
+    def load(cls, path, mpo, stream=None, **opts):
+        """A handle created from a checkpoint file (tdvp_load)."""
+        self = cls.__new__(cls)
+        mpo_dims = [mpo[0].shape[0]] + [w.shape[3] for w in mpo]
+        n, d, _ = checkpoint_header(path)
+        self.n, self.d = n, d
+        self._w = _Pinned(mpo, mpo_dims)
+        self.opts = default_options(**opts)
+        h = _h()
+        st = _lib.tdvp_load(os.fsencode(path), C.byref(self._w.desc(d)), C.byref(self.opts), C.c_void_p(stream or 0),
+                            C.byref(h))
+        del self._w
+        if st != 0:
+            raise TDVPError(st, _lib.tdvp_checkpoint_last_error().decode() or "tdvp_load failed")
+        self.h = h
+        return self
+
+    def save(self, path):
+        """Writes the current state to a checkpoint file (tdvp_save)."""
+        self._chk(_lib.tdvp_save(self.h, os.fsencode(path)))
 
     def _chk(self, s):
         if s != 0:
