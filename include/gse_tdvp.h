@@ -176,8 +176,9 @@ TDVP_API tdvp_status tdvp_center(tdvp_handle* h, int* site);
  * number of basis states added by the last extension; out[4]: total Lanczos
  * iterations of the last sweep; out[5]: Lanczos calls of the last sweep;
  * out[6..8]: process-wide SVD calls, calls that split into independent blocks
- * (conserved quantum numbers), and blocks solved. */
-TDVP_API tdvp_status tdvp_trunc_stats(tdvp_handle* h, double* out9);
+ * (conserved quantum numbers), and blocks solved; out[9..10]: process-wide
+ * Jacobi sweeps summed over all blocks, and the most sweeps one block took. */
+TDVP_API tdvp_status tdvp_trunc_stats(tdvp_handle* h, double* out11);
 
 /* Copies the state to host buffers the caller allocated from tdvp_bond_dims
  * (site i: 2 * m_i * d * m_{i+1} doubles). */

@@ -232,6 +232,8 @@ tdvp_status tdvp_trunc_stats(tdvp_handle* h, double* out) {
     out[6] = (double)g_svd_counters.calls;
     out[7] = (double)g_svd_counters.blocked;
     out[8] = (double)g_svd_counters.blocks;
+    out[9] = (double)g_svd_counters.sweeps;
+    out[10] = (double)g_svd_counters.max_sweeps;
   });
 }
 

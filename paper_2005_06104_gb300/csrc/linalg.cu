@@ -247,6 +247,12 @@ void WSparse::upload() {
   up(l_off, &d_l_off);
   up(l_idx, &d_l_idx);
   up(l_val, &d_l_val);
+  l_val_df.resize(l_val.size());
+  for (size_t e = 0; e < l_val.size(); ++e) {
+    const float rh = (float)l_val[e].x, ih = (float)l_val[e].y;
+    l_val_df[e] = make_float4(rh, (float)(l_val[e].x - (double)rh), ih, (float)(l_val[e].y - (double)ih));
+  }
+  up(l_val_df, &d_l_val_df);
   up(r_off, &d_r_off);
   up(r_idx, &d_r_idx);
   up(r_val, &d_r_val);
@@ -256,6 +262,8 @@ void WSparse::free_device() {
   cudaFree(d_l_off);
   cudaFree(d_l_idx);
   cudaFree(d_l_val);
+  cudaFree(d_l_val_df);
+  d_l_val_df = nullptr;
   cudaFree(d_r_off);
   cudaFree(d_r_idx);
   cudaFree(d_r_val);
@@ -1233,6 +1241,8 @@ void svd_jacobi_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows,
   }
   TDVP_CUDA(cudaFreeAsync(d_flag, st));
   out.sweeps = sweeps;
+  g_svd_counters.sweeps += sweeps;
+  g_svd_counters.max_sweeps = std::max<long long>(g_svd_counters.max_sweeps, sweeps);
   // singular values = column norms
   double* d_s = nullptr;
   TDVP_CUDA(cudaMallocAsync(&d_s, sizeof(double) * q, st));
@@ -1486,7 +1496,11 @@ __global__ void __launch_bounds__(256)
     __syncthreads();
     if (!rot) break;
   }
-  if (threadIdx.x == 0 && sweep >= max_sweeps) *bad = 1;
+  if (threadIdx.x == 0) {
+    if (sweep >= max_sweeps) bad[0] = 1;
+    atomicMax(&bad[1], sweep);  // sweep statistics: largest and total
+    atomicAdd(&bad[2], sweep);
+  }
   for (int e = threadIdx.x; e < p * q; e += blockDim.x) Xg[e] = Xs[e];
   for (int e = threadIdx.x; e < q * q; e += blockDim.x) Vg[e] = Vs[e];
   __syncthreads();
@@ -1647,12 +1661,12 @@ void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows
     TDVP_CUDA(cudaMallocAsync(&d_desc, sizeof(BlkDesc) * nsmall, st));
     TDVP_CUDA(cudaMallocAsync(&d_ridx, sizeof(int) * std::max<size_t>(1, ridx.size()), st));
     TDVP_CUDA(cudaMallocAsync(&d_cidx, sizeof(int) * std::max<size_t>(1, cidx.size()), st));
-    TDVP_CUDA(cudaMallocAsync(&d_s, sizeof(double) * std::max(1, so) + sizeof(int), st));
+    TDVP_CUDA(cudaMallocAsync(&d_s, sizeof(double) * std::max(1, so) + 3 * sizeof(int), st));
     d_bad = reinterpret_cast<int*>(d_s + std::max(1, so));
     TDVP_CUDA(cudaMemcpyAsync(d_desc, desc.data(), sizeof(BlkDesc) * nsmall, cudaMemcpyHostToDevice, st));
     TDVP_CUDA(cudaMemcpyAsync(d_ridx, ridx.data(), sizeof(int) * ridx.size(), cudaMemcpyHostToDevice, st));
     TDVP_CUDA(cudaMemcpyAsync(d_cidx, cidx.data(), sizeof(int) * cidx.size(), cudaMemcpyHostToDevice, st));
-    TDVP_CUDA(cudaMemsetAsync(d_bad, 0, sizeof(int), st));
+    TDVP_CUDA(cudaMemsetAsync(d_bad, 0, 3 * sizeof(int), st));
     k_gather_batched<<<nsmall, 256, 0, st>>>(M, cols, d_desc, d_ridx, d_cidx, Xs.data(), Vs.data());
     TDVP_CHECK_LAUNCH();
     static bool attr = false;
@@ -1663,11 +1677,13 @@ void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows
     k_jacobi_batched<<<nsmall, 256, smem_need, st>>>(Xs.data(), Vs.data(), d_desc, 60, d_s, d_bad);
     TDVP_CHECK_LAUNCH();
     std::vector<double> hs(so);
-    int hbad = 0;
+    int hbad[3] = {0, 0, 0};
     TDVP_CUDA(cudaMemcpyAsync(hs.data(), d_s, sizeof(double) * so, cudaMemcpyDeviceToHost, st));
-    TDVP_CUDA(cudaMemcpyAsync(&hbad, d_bad, sizeof(int), cudaMemcpyDeviceToHost, st));
+    TDVP_CUDA(cudaMemcpyAsync(hbad, d_bad, 3 * sizeof(int), cudaMemcpyDeviceToHost, st));
     TDVP_CUDA(cudaStreamSynchronize(st));
-    tdvp_require(hbad == 0, TDVP_ERR_SVD_NOT_CONVERGED, "batched Jacobi SVD did not converge");
+    tdvp_require(hbad[0] == 0, TDVP_ERR_SVD_NOT_CONVERGED, "batched Jacobi SVD did not converge");
+    g_svd_counters.sweeps += hbad[2];
+    g_svd_counters.max_sweeps = std::max<long long>(g_svd_counters.max_sweeps, hbad[1]);
     for (int b = 0; b < nsmall; ++b)
       for (int j = 0; j < desc[b].q; ++j) {
         const double v = hs[desc[b].s_off + j];

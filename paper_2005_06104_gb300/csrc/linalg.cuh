@@ -23,6 +23,7 @@ struct WSparse {
   std::vector<int> l_off;           // d*wr + 1
   std::vector<int> l_idx;           // 2*nnz: (w, t)
   std::vector<cplx> l_val;
+  std::vector<float4> l_val_df;     // l_val as double-float pairs (re hi, re lo, im hi, im lo)
   // right grouping: for out row (s, w): entries (v, t)
   std::vector<int> r_off;           // d*wl + 1
   std::vector<int> r_idx;
@@ -31,6 +32,7 @@ struct WSparse {
   int* d_l_off = nullptr;
   int* d_l_idx = nullptr;
   cplx* d_l_val = nullptr;
+  float4* d_l_val_df = nullptr;
   int* d_r_off = nullptr;
   int* d_r_idx = nullptr;
   cplx* d_r_val = nullptr;
@@ -107,6 +109,7 @@ void svd_jacobi_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows,
 // Process-wide counters of the SVD driver (calls, calls that split into blocks, blocks).
 struct SvdCounters {
   long long calls = 0, blocked = 0, blocks = 0;
+  long long sweeps = 0, max_sweeps = 0;  // Jacobi sweeps over all (blocks of) calls, and the most in one
 };
 extern SvdCounters g_svd_counters;
 

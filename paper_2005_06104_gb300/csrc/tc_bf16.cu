@@ -86,7 +86,7 @@ template <int S>
 __global__ void __launch_bounds__(THREADS, 1)
     k_gemm_bf16s(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
                  int nkb, const float* __restrict__ sA, long long lsA, const float* __restrict__ sB,
-                 double* __restrict__ out, long long ldo, int* __restrict__ err) {
+                 void* __restrict__ out, long long ldo, int out_df, int* __restrict__ err) {
   constexpr int STAGE_BYTES = SCfg<S>::STAGE_BYTES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -238,21 +238,41 @@ __global__ void __launch_bounds__(THREADS, 1)
     if (ok) {  // warp-uniform
       // column scales: lane i holds those of columns nb + 2i, nb + 2i + 1 (inside the padded rows)
       const float2 sbv = __ldg(reinterpret_cast<const float2*>(sB + nb) + lane);
-      double* o = out + (long long)gm * ldo + nb;
       const bool row_ok = gm < M;
       const bool vec = nb + EC <= N && (ldo & 1) == 0;
+      if (out_df) {
+        // double-float output: (hi, lo) FP32 pairs, scaled exactly by the power-of-two column scale
+        float2* o = static_cast<float2*>(out) + (long long)gm * ldo + nb;
 #pragma unroll
-      for (int j = 0; j < EC; j += 2) {
-        const float s0 = __shfl_sync(0xffffffffu, sbv.x, j >> 1);
-        const float s1 = __shfl_sync(0xffffffffu, sbv.y, j >> 1);
-        const double d0 = ((double)hi[j] + (double)lo[j]) * (double)s0;
-        const double d1 = ((double)hi[j + 1] + (double)lo[j + 1]) * (double)s1;
-        if (row_ok) {
-          if (vec) {
-            *reinterpret_cast<double2*>(o + j) = make_double2(d0, d1);
-          } else {
-            if (nb + j < N) o[j] = d0;
-            if (nb + j + 1 < N) o[j + 1] = d1;
+        for (int j = 0; j < EC; j += 2) {
+          const float s0 = __shfl_sync(0xffffffffu, sbv.x, j >> 1);
+          const float s1 = __shfl_sync(0xffffffffu, sbv.y, j >> 1);
+          const float4 v = make_float4(__fmul_rn(hi[j], s0), __fmul_rn(lo[j], s0), __fmul_rn(hi[j + 1], s1),
+                                       __fmul_rn(lo[j + 1], s1));
+          if (row_ok) {
+            if (vec) {
+              *reinterpret_cast<float4*>(o + j) = v;
+            } else {
+              if (nb + j < N) o[j] = make_float2(v.x, v.y);
+              if (nb + j + 1 < N) o[j + 1] = make_float2(v.z, v.w);
+            }
+          }
+        }
+      } else {
+        double* o = static_cast<double*>(out) + (long long)gm * ldo + nb;
+#pragma unroll
+        for (int j = 0; j < EC; j += 2) {
+          const float s0 = __shfl_sync(0xffffffffu, sbv.x, j >> 1);
+          const float s1 = __shfl_sync(0xffffffffu, sbv.y, j >> 1);
+          const double d0 = ((double)hi[j] + (double)lo[j]) * (double)s0;
+          const double d1 = ((double)hi[j + 1] + (double)lo[j + 1]) * (double)s1;
+          if (row_ok) {
+            if (vec) {
+              *reinterpret_cast<double2*>(o + j) = make_double2(d0, d1);
+            } else {
+              if (nb + j < N) o[j] = d0;
+              if (nb + j + 1 < N) o[j + 1] = d1;
+            }
           }
         }
       }
@@ -269,11 +289,18 @@ __global__ void __launch_bounds__(THREADS, 1)
 }
 
 // ---------------------------------------------------------------- operand slicing
-// Sources: each gives the real operand entries (k2, k2+1, k2+2, k2+3) of one row
-// (k2 a multiple of 4), zero outside the logical matrix.
+// GB300 executes FP64 at a small fraction of its FP32 and integer rates, so the
+// slicing runs without FP64 arithmetic: FP64 sources are cut into digits with
+// integer operations on their bit patterns, double-float sources (FP32 hi, lo
+// pairs) with exact FP32 operations.
+//
+// Sources give the real operand entries (k2, k2+1, k2+2, k2+3) of one row (k2 a
+// multiple of 4), zero outside the logical matrix.  FP64 sources (kDF = false)
+// fill double v[4]; double-float sources (kDF = true) fill float hi[4], lo[4].
 
 // Rows m of opA(A) with K interleaved (re, im): the A operand of the 4M form.
 struct SrcA {
+  static constexpr bool kDF = false;
   const cplx* p;
   long long ld;
   int rows, K, op;
@@ -295,6 +322,7 @@ struct SrcA {
 // Rows (n, c') of the expanded real B operand built from opB(B)[k][n]:
 //   row (n, re): (Re, -Im) over K index (k, re/im); row (n, im): (Im, Re).
 struct SrcB {
+  static constexpr bool kDF = false;
   const cplx* p;
   long long ld;
   int K, N, op;
@@ -315,89 +343,239 @@ struct SrcB {
     }
   }
 };
+
+// s_hi + s_lo += (a_hi + a_lo)(b_hi + b_lo) in double-float arithmetic (about 2^-48)
+__device__ __forceinline__ void df_mac(float& sh, float& sl, float ah, float al, float bh, float bl) {
+  const float p = __fmul_rn(ah, bh);
+  const float pe = __fmaf_rn(ah, bh, -p);  // exact rounding error of ah * bh
+  const float cross = __fmaf_rn(ah, bl, __fmul_rn(al, bh));
+  const float s = __fadd_rn(sh, p);
+  const float bb = __fadd_rn(s, -sh);
+  const float err = __fadd_rn(__fadd_rn(sh, -__fadd_rn(s, -bb)), __fadd_rn(p, -bb));
+  sh = s;
+  sl = __fadd_rn(sl, __fadd_rn(err, __fadd_rn(pe, cross)));
+}
+
 // Rows (a, s) of the stage-3 A operand of H_eff: K index (v, b', re/im),
-//   T2[(a,s)][(v,b')] = sum_{(w,t)} W[w,s,t,v] T1[a][w][t][b']   (T1 complex FP64)
+//   T2[(a,s)][(v,b')] = sum_{(w,t)} W[w,s,t,v] T1[a][w][t][b']
+// with T1 and W as double-float complex (re hi, re lo, im hi, im lo).
 struct SrcStage2 {
-  const cplx* T1;
+  static constexpr bool kDF = true;
+  const float4* T1;
   const int* off;
   const int* idx;
-  const cplx* val;
+  const float4* val;
   int ML, WL, WR, D, MR;
-  __device__ void load4(long long row, int k2, double v[4]) const {
+  __device__ void load4(long long row, int k2, float hi[4], float lo[4]) const {
     const long long a = row / D;
     const int s = (int)(row % D);
 #pragma unroll
     for (int h = 0; h < 2; ++h) {
       const int j = (k2 >> 1) + h;
       const int vv = j / MR, b = j % MR;
-      double re = 0.0, im = 0.0;
+      float rh = 0.f, rl = 0.f, ih = 0.f, il = 0.f;
       if (a < ML && vv < WR) {
         const int sv = s * WR + vv;
         for (int e = off[sv]; e < off[sv + 1]; ++e) {
           const int w = idx[2 * e], t = idx[2 * e + 1];
-          const cplx x = T1[((a * WL + w) * D + t) * (long long)MR + b];
-          const cplx c = val[e];
-          re += c.x * x.x - c.y * x.y;
-          im += c.x * x.y + c.y * x.x;
+          const float4 x = T1[((a * WL + w) * D + t) * (long long)MR + b];
+          const float4 c = val[e];
+          df_mac(rh, rl, c.x, c.y, x.x, x.y);     // + Re c Re x
+          df_mac(rh, rl, -c.z, -c.w, x.z, x.w);   // - Im c Im x
+          df_mac(ih, il, c.x, c.y, x.z, x.w);     // + Re c Im x
+          df_mac(ih, il, c.z, c.w, x.x, x.y);     // + Im c Re x
         }
       }
-      v[2 * h] = re;
-      v[2 * h + 1] = im;
+      // renormalise so that |lo| <= ulp(hi) / 2
+      float t = __fadd_rn(rh, rl);
+      rl = __fadd_rn(rl, -__fadd_rn(t, -rh));
+      rh = t;
+      t = __fadd_rn(ih, il);
+      il = __fadd_rn(il, -__fadd_rn(t, -ih));
+      ih = t;
+      hi[2 * h] = rh;
+      lo[2 * h] = rl;
+      hi[2 * h + 1] = ih;
+      lo[2 * h + 1] = il;
     }
   }
 };
 
-// Scale of one group from its largest magnitude m: 2^e with m < 2^e, stored as
-// 2^(e-8).  Groups below 2^-100 are taken as zero; a non-finite entry makes the
-// scale NaN, so that it shows in the output.
+// Group exponent: the smallest e with (largest magnitude) < 2^e.  Groups whose largest
+// magnitude is below 2^-100 (or zero) are taken as zero (live = false); a non-finite
+// entry makes the scale NaN, so that it shows in the output.
 struct GroupScale {
   int e = 0;
   bool live = false;
-  float sc = 0.f;
+  float sc = 0.f;  // 2^(e-8)
 };
-__device__ __forceinline__ GroupScale group_scale(double m, bool bad) {
+__device__ __forceinline__ GroupScale scale_from_exponent(int unbiased, bool bad) {
   GroupScale g;
   if (bad) {
     g.sc = __int_as_float(0x7fc00000);
-  } else if (m >= 0x1p-100) {
+  } else if (unbiased >= -100) {
     g.live = true;
-    g.e = ilogb(m) + 1;
+    g.e = unbiased + 1;
     g.sc = ldexpf(1.f, g.e - 8);
   }
   return g;
 }
-__device__ __forceinline__ bool any_nonfinite(const double v[4]) {
-  return !(v[0] - v[0] == 0.0 && v[1] - v[1] == 0.0 && v[2] - v[2] == 0.0 && v[3] - v[3] == 0.0);
+// |x| as an ordered integer key (larger magnitude, larger key; NaN/Inf above all finite)
+__device__ __forceinline__ unsigned long long abs_key(double x) {
+  return (unsigned long long)__double_as_longlong(x) & 0x7fffffffffffffffull;
 }
-__device__ __forceinline__ double max_abs4(const double v[4]) {
-  return fmax(fmax(fabs(v[0]), fabs(v[1])), fmax(fabs(v[2]), fabs(v[3])));
+__device__ __forceinline__ GroupScale scale_from_key(unsigned long long key) {
+  const int ex = (int)(key >> 52);
+  if (ex == 0x7ff) return scale_from_exponent(0, true);
+  if (ex == 0) return scale_from_exponent(-2000, false);  // zero or subnormal
+  return scale_from_exponent(ex - 1023, false);
 }
-// writes the S slices of 4 consecutive entries of one row: out + s * slice_stride
+__device__ __forceinline__ GroupScale scale_from_float(float m, bool bad) {
+  const int ex = (int)((__float_as_uint(m) >> 23) & 0xff);
+  if (bad || ex == 0xff) return scale_from_exponent(0, true);
+  if (ex == 0) return scale_from_exponent(-2000, false);
+  return scale_from_exponent(ex - 127, false);
+}
+
+// integer value a (|a| < 2^22) as an exact float
+__device__ __forceinline__ float int_to_float_exact(int a) {
+  return __fadd_rn(__int_as_float(0x4B400000 + a), -12582912.0f);
+}
+
+// Digits of an FP64 entry: X = round(|x| 2^(32-e)) (|X| <= 2^32) from the bit pattern,
+// then X = a1 2^24 + a2 2^16 + a3 2^8 + a4 with rounded signed digits; out[s] = a_{s+1} 2^(-8s).
 template <int S>
-__device__ __forceinline__ void write_slices(const double v[4], const GroupScale& g, __nv_bfloat16* out,
-                                             long long slice_stride) {
-  __nv_bfloat16 sl[S][4];
-#pragma unroll
-  for (int i = 0; i < 4; ++i) {
-    double t = g.live ? ldexp(v[i], 8 - g.e) : 0.0;  // |t| < 256
-#pragma unroll
-    for (int s = 0; s < S; ++s) {
-      const double a = rint(t);
-      t = (t - a) * 256.0;
-      sl[s][i] = __float2bfloat16_rn((float)ldexp(a, -8 * s));
+__device__ __forceinline__ void digits_fp64(double x, const GroupScale& g, float out[S]) {
+  long long X = 0;
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const int ex = (int)((b >> 52) & 0x7ff);
+  if (g.live && ex != 0) {
+    const int shift = 20 + g.e - (ex - 1023);  // >= 21
+    if (shift < 64) {
+      const unsigned long long m53 = (b & 0xfffffffffffffull) | (1ull << 52);
+      X = (long long)((m53 + (1ull << (shift - 1))) >> shift);
+      if (b >> 63) X = -X;
     }
   }
+  const int a1 = (int)((X + (1ll << 23)) >> 24);
+  int r = (int)(X - ((long long)a1 << 24));  // [-2^23, 2^23)
+  const int a2 = (r + (1 << 15)) >> 16;
+  r -= a2 << 16;
+  int a3, a4;
+  if (S == 4) {
+    a3 = (r + (1 << 7)) >> 8;
+    a4 = r - (a3 << 8);
+  } else {
+    a3 = (r + (1 << 7)) >> 8;
+    a4 = 0;
+  }
+  const int dg[4] = {a1, a2, a3, a4};
+#pragma unroll
+  for (int s = 0; s < S; ++s) out[s] = __fmul_rn(int_to_float_exact(dg[s]), __int_as_float((127 - 8 * s) << 23));
+}
+
+// Digits of a double-float entry hi + lo with exact FP32 steps: peel the rounded
+// top digit off the head, fold the tail back in with a two-sum, repeat.
+template <int S>
+__device__ __forceinline__ void digits_df(float hi, float lo, const GroupScale& g, float out[S]) {
+  if (!g.live) {
+#pragma unroll
+    for (int s = 0; s < S; ++s) out[s] = 0.f;
+    return;
+  }
+  const float up = ldexpf(1.f, 32 - g.e);
+  float H = __fmul_rn(hi, up), L = __fmul_rn(lo, up);  // |H + L| < 2^32
 #pragma unroll
   for (int s = 0; s < S; ++s) {
-    __nv_bfloat162 lo2, hi2;
-    lo2.x = sl[s][0];
-    lo2.y = sl[s][1];
-    hi2.x = sl[s][2];
-    hi2.y = sl[s][3];
+    const int sh = 24 - 8 * s;                          // digit weight 2^sh
+    const float w = __int_as_float((127 + sh) << 23), iw = __int_as_float((127 - sh) << 23);
+    const float a = rintf(__fmul_rn(H, iw));
+    out[s] = __fmul_rn(a, __int_as_float((127 - 8 * s) << 23));
+    const float r = __fmaf_rn(-a, w, H);  // exact
+    const float t = __fadd_rn(r, L);
+    const float bb = __fadd_rn(t, -r);
+    L = __fadd_rn(__fadd_rn(r, -__fadd_rn(t, -bb)), __fadd_rn(L, -bb));
+    H = t;
+  }
+}
+
+template <int S>
+__device__ __forceinline__ void store_slices(const float d[4][S], __nv_bfloat16* out, long long slice_stride) {
+#pragma unroll
+  for (int s = 0; s < S; ++s) {
+    // every digit has at most 8 significant bits: the top half of its FP32 pattern is its BF16
     uint2 pk;
-    pk.x = *reinterpret_cast<uint32_t*>(&lo2);
-    pk.y = *reinterpret_cast<uint32_t*>(&hi2);
+    pk.x = (__float_as_uint(d[0][s]) >> 16) | (__float_as_uint(d[1][s]) & 0xffff0000u);
+    pk.y = (__float_as_uint(d[2][s]) >> 16) | (__float_as_uint(d[3][s]) & 0xffff0000u);
     *reinterpret_cast<uint2*>(out + s * slice_stride) = pk;
+  }
+}
+
+// The entries of one row segment: group-max contribution and the source values.
+template <class Src>
+struct Seg {
+  double v[4];
+  float hi[4], lo[4];
+  __device__ void load(const Src& src, long long row, int k2) {
+    if constexpr (Src::kDF) {
+      src.load4(row, k2, hi, lo);
+    } else {
+      src.load4(row, k2, v);
+    }
+  }
+  __device__ void zero() {
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      v[i] = 0.0;
+      hi[i] = lo[i] = 0.f;
+    }
+  }
+  // max key (FP64) or max |hi| (double-float); bad = non-finite seen
+  __device__ unsigned long long key() const {
+    unsigned long long k = 0;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) k = max(k, abs_key(v[i]));
+    return k;
+  }
+  __device__ float fmaxabs(bool& bad) const {
+    float m = 0.f;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      const float a = fabsf(hi[i]);
+      bad = bad || !(a <= 3.0e38f) || !(fabsf(lo[i]) <= 3.0e38f);
+      m = fmaxf(m, a);
+    }
+    return m;
+  }
+  template <int S>
+  __device__ void write(const GroupScale& g, __nv_bfloat16* out, long long slice_stride) const {
+    float d[4][S];
+#pragma unroll
+    for (int i = 0; i < 4; ++i) {
+      if constexpr (Src::kDF)
+        digits_df<S>(hi[i], lo[i], g, d[i]);
+      else
+        digits_fp64<S>(v[i], g, d[i]);
+    }
+    store_slices<S>(d, out, slice_stride);
+  }
+};
+
+// warp-wide group scale of the segments held by the 32 lanes
+template <class Src>
+__device__ __forceinline__ GroupScale warp_scale(const Seg<Src>& sg) {
+  if constexpr (Src::kDF) {
+    bool bad = false;
+    float m = sg.fmaxabs(bad);
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_xor_sync(0xffffffffu, m, o));
+    bad = __any_sync(0xffffffffu, bad);
+    return scale_from_float(m, bad);
+  } else {
+    unsigned long long k = sg.key();
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) k = max(k, __shfl_xor_sync(0xffffffffu, k, o));
+    return scale_from_key(k);
   }
 }
 
@@ -412,15 +590,11 @@ __global__ void k_slice_chunks(Src src, int rows_pad, int ldk, int nch, __nv_bfl
   const long long row = gw / nch;
   const int ch = (int)(gw % nch);
   const int k2 = ch * KC + 4 * lane;
-  double v[4] = {0.0, 0.0, 0.0, 0.0};
-  if (k2 < ldk) src.load4(row, k2, v);
-  double m = max_abs4(v);
-  bool bad = any_nonfinite(v);
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  bad = __any_sync(0xffffffffu, bad);
-  const GroupScale g = group_scale(m, bad);
-  if (k2 < ldk) write_slices<S>(v, g, out + row * ldk + k2, (long long)rows_pad * ldk);
+  Seg<Src> sg;
+  sg.zero();
+  if (k2 < ldk) sg.load(src, row, k2);
+  const GroupScale g = warp_scale(sg);
+  if (k2 < ldk) sg.template write<S>(g, out + row * ldk + k2, (long long)rows_pad * ldk);
   if (lane == 0) scale[(long long)ch * rows_pad + row] = g.sc;
 }
 
@@ -429,33 +603,25 @@ __global__ void k_slice_chunks(Src src, int rows_pad, int ldk, int nch, __nv_bfl
 template <int S, class Src>
 __global__ void __launch_bounds__(128) k_slice_rows(Src src, int rows_pad, int ldk, __nv_bfloat16* __restrict__ out,
                                                     float* __restrict__ scale) {
-  __shared__ double red_m[4];
-  __shared__ int red_bad[4];
+  static_assert(!Src::kDF, "row-scaled operands come from FP64 sources");
+  __shared__ unsigned long long red[4];
   const long long row = blockIdx.x;
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  double m = 0.0;
-  bool bad = false;
+  unsigned long long k = 0;
+  Seg<Src> sg;
   for (int k2 = 4 * tid; k2 < ldk; k2 += 512) {
-    double v[4];
-    src.load4(row, k2, v);
-    m = fmax(m, max_abs4(v));
-    bad = bad || any_nonfinite(v);
+    sg.load(src, row, k2);
+    k = max(k, sg.key());
   }
 #pragma unroll
-  for (int o = 16; o > 0; o >>= 1) m = fmax(m, __shfl_xor_sync(0xffffffffu, m, o));
-  bad = __any_sync(0xffffffffu, bad);
-  if (lane == 0) {
-    red_m[wid] = m;
-    red_bad[wid] = bad ? 1 : 0;
-  }
+  for (int o = 16; o > 0; o >>= 1) k = max(k, __shfl_xor_sync(0xffffffffu, k, o));
+  if (lane == 0) red[wid] = k;
   __syncthreads();
-  m = fmax(fmax(red_m[0], red_m[1]), fmax(red_m[2], red_m[3]));
-  bad = (red_bad[0] | red_bad[1] | red_bad[2] | red_bad[3]) != 0;
-  const GroupScale g = group_scale(m, bad);
+  k = max(max(red[0], red[1]), max(red[2], red[3]));
+  const GroupScale g = scale_from_key(k);
   for (int k2 = 4 * tid; k2 < ldk; k2 += 512) {
-    double v[4];
-    src.load4(row, k2, v);
-    write_slices<S>(v, g, out + row * ldk + k2, (long long)rows_pad * ldk);
+    sg.load(src, row, k2);
+    sg.template write<S>(g, out + row * ldk + k2, (long long)rows_pad * ldk);
   }
   if (tid == 0) scale[row] = g.sc;
 }
@@ -486,10 +652,14 @@ void slice(cudaStream_t st, const Src& src, Sliced& o) {
   __nv_bfloat16* d = o.data.as<__nv_bfloat16>();
   float* sc = o.scale.as<float>();
   if (o.row_scale) {
-    if (o.S == 4)
-      k_slice_rows<4, Src><<<o.rows_pad, 128, 0, st>>>(src, o.rows_pad, o.ldk, d, sc);
-    else
-      k_slice_rows<3, Src><<<o.rows_pad, 128, 0, st>>>(src, o.rows_pad, o.ldk, d, sc);
+    if constexpr (Src::kDF) {
+      throw TdvpError(TDVP_ERR_INVALID_ARG, "slice: row-scaled operands come from FP64 sources");
+    } else {
+      if (o.S == 4)
+        k_slice_rows<4, Src><<<o.rows_pad, 128, 0, st>>>(src, o.rows_pad, o.ldk, d, sc);
+      else
+        k_slice_rows<3, Src><<<o.rows_pad, 128, 0, st>>>(src, o.rows_pad, o.ldk, d, sc);
+    }
   } else {
     const int blocks = ceil_div((long long)o.rows_pad * o.nch * 32, 256);
     if (o.S == 4)
@@ -519,7 +689,7 @@ CUtensorMap make_map3(const Sliced& o, int box_rows) {
 
 template <int S>
 void launch_bf16s(cudaStream_t st, const CUtensorMap& ma, const CUtensorMap& mb, int M, int N, int nkb,
-                  const float* sA, long long lsA, const float* sB, double* out, long long ldo,
+                  const float* sA, long long lsA, const float* sB, void* out, long long ldo, int out_df,
                   int* d_err) {
   static bool attr = false;
   if (!attr) {
@@ -535,13 +705,15 @@ void launch_bf16s(cudaStream_t st, const CUtensorMap& ma, const CUtensorMap& mb,
   }
   dim3 grid(ceil_div(N, BN), ceil_div(M, BM));
   tdvp_require(grid.y <= 65535, TDVP_ERR_INVALID_ARG, "gemm_bf16s: M too large");
-  k_gemm_bf16s<S><<<grid, THREADS, SCfg<S>::SMEM_BYTES, st>>>(ma, mb, M, N, nkb, sA, lsA, sB, out, ldo, d_err);
+  k_gemm_bf16s<S><<<grid, THREADS, SCfg<S>::SMEM_BYTES, st>>>(ma, mb, M, N, nkb, sA, lsA, sB, out, ldo, out_df,
+                                                              d_err);
   TDVP_CHECK_LAUNCH();
 }
 
-// out[M x N] (FP64, row-major, ldo) = A B^T over the sliced real operands
-void gemm_bf16s(cudaStream_t st, const Sliced& A, const Sliced& B, int M, int N, double* out, long long ldo,
-                int* d_err) {
+// out[M x N] (row-major, ldo) = A B^T over the sliced real operands; FP64 entries, or
+// double-float (hi, lo) FP32 pairs when out_df
+void gemm_bf16s(cudaStream_t st, const Sliced& A, const Sliced& B, int M, int N, void* out, long long ldo,
+                bool out_df, int* d_err) {
   if (M <= 0 || N <= 0) return;
   tdvp_require(A.ldk == B.ldk && A.S == B.S, TDVP_ERR_INVALID_ARG, "gemm_bf16s: operand K or slices differ");
   tdvp_require(M <= A.rows_pad && N <= B.rows_pad, TDVP_ERR_INVALID_ARG, "gemm_bf16s: operand rows");
@@ -550,10 +722,10 @@ void gemm_bf16s(cudaStream_t st, const Sliced& A, const Sliced& B, int M, int N,
   const int nkb = A.ldk / BK;
   if (A.S == 4)
     launch_bf16s<4>(st, ma, mb, M, N, nkb, A.scale.as<float>(), A.rows_pad, B.scale.as<float>(), out,
-                    ldo, d_err);
+                    ldo, out_df ? 1 : 0, d_err);
   else
     launch_bf16s<3>(st, ma, mb, M, N, nkb, A.scale.as<float>(), A.rows_pad, B.scale.as<float>(), out,
-                    ldo, d_err);
+                    ldo, out_df ? 1 : 0, d_err);
 }
 }  // namespace tcb
 
@@ -603,14 +775,15 @@ void heff_bf16s(cudaStream_t st, Scratch& s, const SiteOp& op, const cplx* x, cp
   c.X.shape(pool, S, 2 * d * mr, 2 * ml, true);
   slice(st, SrcB{x, (long long)d * mr, ml, d * mr, OP_N}, c.X);
   const int M1 = ml * wl, N1 = 2 * d * mr;
-  c.T1.ensure(pool, sizeof(double) * (size_t)M1 * N1);
-  gemm_bf16s(st, c.L, c.X, M1, N1, c.T1.as<double>(), N1, err);
+  c.T1.ensure(pool, sizeof(float2) * (size_t)M1 * N1);  // double-float
+  gemm_bf16s(st, c.L, c.X, M1, N1, c.T1.as<void>(), N1, true, err);
   // stage 2: MPO tensor, sliced straight into the stage-3 A operand
   const WSparse& ws = *op.W;
   c.T2.shape(pool, S, ml * d, 2 * wr * mr, false);
-  slice(st, SrcStage2{c.T1.as<cplx>(), ws.d_l_off, ws.d_l_idx, ws.d_l_val, ml, wl, wr, d, mr}, c.T2);
+  tdvp_require(ws.d_l_val_df != nullptr, TDVP_ERR_INVALID_ARG, "heff_bf16s: MPO site without double-float values");
+  slice(st, SrcStage2{c.T1.as<float4>(), ws.d_l_off, ws.d_l_idx, ws.d_l_val_df, ml, wl, wr, d, mr}, c.T2);
   // stage 3: y[(a,s)][(b,c)] = T2 R^T
-  gemm_bf16s(st, c.T2, c.R, ml * d, 2 * mr, reinterpret_cast<double*>(y), 2 * mr, err);
+  gemm_bf16s(st, c.T2, c.R, ml * d, 2 * mr, y, 2 * mr, false, err);
 }
 
 void zgemm_bf16s(cudaStream_t st, Scratch& s, int S, int opA, int opB, int M, int N, int K, const cplx* A,
@@ -623,5 +796,5 @@ void zgemm_bf16s(cudaStream_t st, Scratch& s, int S, int opA, int opB, int M, in
   slice(st, SrcA{A, lda, M, K, opA}, a);
   b.shape(pool, S, 2 * N, 2 * std::max(K, 1), true);
   slice(st, SrcB{B, ldb, K, N, opB}, b);
-  gemm_bf16s(st, a, b, M, 2 * N, reinterpret_cast<double*>(C), 2 * ldc, err);
+  gemm_bf16s(st, a, b, M, 2 * N, C, 2 * ldc, false, err);
 }

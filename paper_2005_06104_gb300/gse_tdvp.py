@@ -396,11 +396,12 @@ class GseTdvp:
         return v.value
 
     def trunc_stats(self):
-        out = (C.c_double * 9)()
+        out = (C.c_double * 11)()
         self._chk(_lib.tdvp_trunc_stats(self.h, out))
         return dict(disc_k=out[0], disc_m=out[1], disc_eps=out[2], added=int(out[3]),
                     lanczos_iters=int(out[4]), lanczos_calls=int(out[5]), svd_calls=int(out[6]),
-                    svd_blocked_calls=int(out[7]), svd_blocks=int(out[8]))
+                    svd_blocked_calls=int(out[7]), svd_blocks=int(out[8]), svd_sweeps=int(out[9]),
+                    svd_max_sweeps=int(out[10]))
 
     def profile(self, enable=True):
         self._chk(_lib.tdvp_profile(self.h, 1 if enable else 0))
