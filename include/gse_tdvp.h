@@ -177,12 +177,40 @@ TDVP_API tdvp_status tdvp_center(tdvp_handle* h, int* site);
  * iterations of the last sweep; out[5]: Lanczos calls of the last sweep;
  * out[6..8]: process-wide SVD calls, calls that split into independent blocks
  * (conserved quantum numbers), and blocks solved; out[9..10]: process-wide
- * Jacobi sweeps summed over all blocks, and the most sweeps one block took. */
-TDVP_API tdvp_status tdvp_trunc_stats(tdvp_handle* h, double* out11);
+ * Jacobi sweeps summed over all blocks, and the most sweeps one block took;
+ * out[11..12]: blocks too large for the shared-memory batched path, and the
+ * widest block (smaller dimension) seen. */
+TDVP_API tdvp_status tdvp_trunc_stats(tdvp_handle* h, double* out13);
 
 /* Copies the state to host buffers the caller allocated from tdvp_bond_dims
  * (site i: 2 * m_i * d * m_{i+1} doubles). */
 TDVP_API tdvp_status tdvp_get_mps(tdvp_handle* h, double* const* sites_out);
+
+/* ---------------------------------------------------------------------------
+ * Batches of independent chains on one GPU (many chains of uneven length and
+ * bond dimension, e.g. disorder realisations).  One engine per chain, each on
+ * its own CUDA stream; a batch call runs the per-chain call for every chain on
+ * n_threads host workers (<= 0: the number of host cores), longest chains
+ * first, so the chains' kernels overlap on the device.  Arrays of n descriptors;
+ * opts may be NULL (defaults for all) or n options.  Per-chain status codes go
+ * to status[n] when non-null; the return value is the first non-OK status
+ * (tdvp_batch_last_error names the chain).  A failing chain does not stop or
+ * change the others.  tdvp_batch_handle lends the handle of chain i for any
+ * per-chain call (observables, tdvp_get_mps); the batch keeps ownership. */
+typedef struct tdvp_batch tdvp_batch;
+TDVP_API tdvp_status tdvp_batch_create(int n, const tdvp_mps_desc* mps, const tdvp_mpo_desc* mpo,
+                                       const tdvp_options* opts, int n_threads, tdvp_batch** out);
+TDVP_API tdvp_status tdvp_batch_destroy(tdvp_batch* b);
+TDVP_API tdvp_status tdvp_batch_size(const tdvp_batch* b, int* n);
+TDVP_API tdvp_status tdvp_batch_handle(tdvp_batch* b, int i, tdvp_handle** h);
+TDVP_API tdvp_status tdvp_batch_expand_basis(tdvp_batch* b, int krylov_order_k, const double* weights, int* status);
+TDVP_API tdvp_status tdvp_batch_sweep(tdvp_batch* b, double dt, tdvp_time kind, int* status);
+/* expand_basis then sweep on every chain: one GSE-TDVP1 step each */
+TDVP_API tdvp_status tdvp_batch_step(tdvp_batch* b, int krylov_order_k, const double* weights, double dt,
+                                     tdvp_time kind, int* status);
+TDVP_API tdvp_status tdvp_batch_energy(tdvp_batch* b, double* out_n);
+TDVP_API tdvp_status tdvp_batch_norm(tdvp_batch* b, double* out_n);
+TDVP_API const char* tdvp_batch_last_error(const tdvp_batch* b);
 
 /* ---------------------------------------------------------------------------
  * Checkpoints.  A file holds one MPS: magic "GSETDVP1", int32 {version 1, N, d,

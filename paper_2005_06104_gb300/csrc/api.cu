@@ -234,6 +234,8 @@ tdvp_status tdvp_trunc_stats(tdvp_handle* h, double* out) {
     out[8] = (double)g_svd_counters.blocks;
     out[9] = (double)g_svd_counters.sweeps;
     out[10] = (double)g_svd_counters.max_sweeps;
+    out[11] = (double)g_svd_counters.large_blocks;
+    out[12] = (double)g_svd_counters.max_q;
   });
 }
 

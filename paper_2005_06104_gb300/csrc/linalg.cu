@@ -161,13 +161,12 @@ void zgemm(cudaStream_t st, int opA, int opB, int M, int N, int K, cplx alpha, c
   // long K is split along K over enough blocks to occupy the GPU (needs a pool).
   const long long tiles = (long long)ceil_div(N, GB_N) * ceil_div(M, GB_M) * batch;
   int ns = 1, kc = K;
-  static int sms = 0;
-  if (!sms) {
-    int dev = 0;
+  static const int sms = [] {  // thread-safe one-time initialisation
+    int dev = 0, n = 0;
     cudaGetDevice(&dev);
-    cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
-    if (sms <= 0) sms = 148;
-  }
+    cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev);
+    return n > 0 ? n : 148;
+  }();
   if (ws && tiles < 2LL * sms && K >= 32) {
     ns = (int)std::min<long long>((2LL * sms + tiles - 1) / tiles, (K + 15) / 16);
     ns = std::max(1, std::min(ns, 65535 / batch));
@@ -1168,6 +1167,7 @@ void svd_jacobi_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows,
   const int p = orient == 0 ? rows : cols;
   const int q = orient == 0 ? cols : rows;
   const int qpad = q + (q & 1);
+  atomic_max(g_svd_counters.max_q, q);
   // accumulated rotations are needed for V (orient 0) or U (orient 1)
   const bool need_acc = orient == 0 ? want_v : want_u;
   DArr X(pool, (size_t)p * q), Vx(pool, need_acc ? (size_t)q * q : 1);
@@ -1188,12 +1188,12 @@ void svd_jacobi_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows,
   int sweeps = 0;
   if (q > 1) {
     if (small_bytes <= 96 * 1024) {
-      static bool attr_set = false;
-      if (!attr_set) {
+      static const bool attr_set = [] {
         TDVP_CUDA(cudaFuncSetAttribute(k_jacobi_small, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        96 * 1024));
-        attr_set = true;
-      }
+        return true;
+      }();
+      (void)attr_set;
       k_jacobi_small<<<1, 256, small_bytes, st>>>(X.data(), Vx.data(), p, q, qpad, tol, d_fro2,
                                                    need_acc ? 1 : 0, max_sweeps, d_flag);
       TDVP_CHECK_LAUNCH();
@@ -1204,14 +1204,13 @@ void svd_jacobi_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows,
         throw TdvpError(TDVP_ERR_SVD_NOT_CONVERGED, "Jacobi SVD did not converge");
       }
     } else {
-      static int coop_blocks = 0;
-      if (coop_blocks == 0) {
+      static const int coop_blocks = [] {
         int dev = 0, sms = 0, per_sm = 0;
         TDVP_CUDA(cudaGetDevice(&dev));
         TDVP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
         TDVP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_coop, 256, 0));
-        coop_blocks = std::max(1, sms * std::max(1, per_sm));
-      }
+        return std::max(1, sms * std::max(1, per_sm));
+      }();
       const int nblk = std::max(1, std::min(qpad / 2, coop_blocks));
       GridBar* bar = nullptr;
       TDVP_CUDA(cudaMallocAsync(&bar, sizeof(GridBar), st));
@@ -1242,7 +1241,7 @@ void svd_jacobi_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows,
   TDVP_CUDA(cudaFreeAsync(d_flag, st));
   out.sweeps = sweeps;
   g_svd_counters.sweeps += sweeps;
-  g_svd_counters.max_sweeps = std::max<long long>(g_svd_counters.max_sweeps, sweeps);
+  atomic_max(g_svd_counters.max_sweeps, sweeps);
   // singular values = column norms
   double* d_s = nullptr;
   TDVP_CUDA(cudaMallocAsync(&d_s, sizeof(double) * q, st));
@@ -1370,27 +1369,7 @@ __global__ void k_nonzero_mask(const cplx* __restrict__ M, int rows, int cols, i
   mask[e] = bits;
 }
 
-__global__ void k_gather_block(const cplx* __restrict__ M, int cols, const int* __restrict__ rmap,
-                               const int* __restrict__ cmap, int pb, int qb, cplx* __restrict__ out) {
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (long long)pb * qb) return;
-  const int i = e / qb, j = e % qb;
-  out[e] = M[(long long)rmap[i] * cols + cmap[j]];
-}
 
-// dst[map[i] * ld + col[l]] = src[i * lds + l] for the listed local columns l
-__global__ void k_scatter_cols(const cplx* __restrict__ src, int nrows, int lds, const int* __restrict__ rowmap,
-                               const int* __restrict__ sel_local, const int* __restrict__ sel_global, int nsel,
-                               cplx* __restrict__ dst, int ld, int transpose) {
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (long long)nrows * nsel) return;
-  const int i = e / nsel, k = e % nsel;
-  const cplx v = transpose ? src[(long long)sel_local[k] * lds + i] : src[(long long)i * lds + sel_local[k]];
-  if (transpose)
-    dst[(long long)sel_global[k] * ld + rowmap[i]] = v;   // Vh: rows = kept index, cols = global column
-  else
-    dst[(long long)rowmap[i] * ld + sel_global[k]] = v;   // U: rows = global row, cols = kept index
-}
 
 // Batched small blocks: descriptor per block.  Block b is gathered as the column-major
 // working matrix X_b (p x q, p >= q; transposed and conjugated when orient = 1) and
@@ -1512,6 +1491,120 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Many blocks at once over the whole GPU: the FP64 pipe of one SM is a small
+// fraction of the device's (about 8 GFLOP/s of 1.2 TFLOP/s on this part), so a
+// block wider than a few dozen columns must not sit on one SM.  One cooperative
+// launch runs every block's Jacobi sweeps; each round's pairs of all unconverged
+// blocks are work items spread over the CTAs, which meet at a bounded grid
+// barrier between rounds.  A block that completes a sweep without a rotation is
+// done; its sweeps stop while the others continue.
+// flags: rot[nblk][3] | done[nblk] | sweeps[nblk]; stat: bad, max sweeps, total sweeps.
+__global__ void __launch_bounds__(256)
+    k_jacobi_multi(cplx* __restrict__ X, cplx* __restrict__ V, const BlkDesc* __restrict__ desc,
+                   const int* __restrict__ pair_off, int nblk, int total_pairs, int max_rounds, int max_sweeps,
+                   double* __restrict__ fro2, int* __restrict__ flags, GridBar* bar, double* __restrict__ s_out,
+                   int* __restrict__ stat) {
+  int* rot = flags;
+  int* done = flags + 3 * nblk;
+  int* nsw = flags + 4 * nblk;
+  __shared__ double red[8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  // Frobenius norms (the floor below which a pair is numerical zero)
+  for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
+    const BlkDesc d = desc[b];
+    const cplx* Xb = X + d.x_off;
+    double f = 0.0;
+    for (long long e = threadIdx.x; e < (long long)d.p * d.q; e += blockDim.x) f += cabs2(Xb[e]);
+    f = warp_sum(f);
+    if (lane == 0) red[warp] = f;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int u = 0; u < (int)(blockDim.x >> 5); ++u) t += red[u];
+      fro2[b] = t;
+      for (int k = 0; k < 3; ++k) rot[3 * b + k] = 0;
+      done[b] = d.q <= 1 ? 1 : 0;
+      nsw[b] = 0;
+    }
+    __syncthreads();
+  }
+  if (!grid_sync(bar, gridDim.x)) return;
+  int sweep = 0;
+  for (; sweep < max_sweeps; ++sweep) {
+    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += gridDim.x * blockDim.x)
+      rot[3 * b + (sweep + 1) % 3] = 0;
+    for (int round = 0; round < max_rounds; ++round) {
+      for (int it = blockIdx.x; it < total_pairs; it += gridDim.x) {
+        int lo = 0, hi = nblk - 1;  // last block with pair_off[b] <= it
+        while (lo < hi) {
+          const int mid = (lo + hi + 1) >> 1;
+          if (pair_off[mid] <= it) lo = mid; else hi = mid - 1;
+        }
+        const int b = lo;
+        if (((volatile int*)done)[b]) continue;
+        const BlkDesc d = desc[b];
+        const int qpad = d.q + (d.q & 1);
+        if (round >= qpad - 1) continue;
+        int P, Q;
+        rr_pair(round, it - pair_off[b], qpad, P, Q);
+        if (Q >= d.q) continue;
+        const double tol = fmax(1e-15, sqrt((double)d.p) * 2.2e-16);
+        if (jacobi_pair_block(X + d.x_off, V + d.v_off, d.p, d.q, P, Q, tol, 1e-32 * fro2[b], 1) &&
+            threadIdx.x == 0)
+          rot[3 * b + sweep % 3] = 1;
+      }
+      if (!grid_sync(bar, gridDim.x)) return;
+    }
+    if (blockIdx.x == 0 && threadIdx.x == 0)
+      for (int b = 0; b < nblk; ++b)
+        if (!done[b] && !((volatile int*)rot)[3 * b + sweep % 3]) {
+          done[b] = 1;
+          nsw[b] = sweep + 1;
+        }
+    if (!grid_sync(bar, gridDim.x)) return;
+    int all = 1;
+    for (int b = 0; b < nblk && all; ++b) all = ((volatile int*)done)[b];
+    if (all) break;
+  }
+  // singular values: column norms of every block
+  for (int it = blockIdx.x; it < total_pairs * 2; it += gridDim.x) {
+    // columns enumerated block by block: column j of block b is item 2 * pair_off[b] + j
+    int lo = 0, hi = nblk - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (2 * pair_off[mid] <= it) lo = mid; else hi = mid - 1;
+    }
+    const int b = lo;
+    const BlkDesc d = desc[b];
+    const int j = it - 2 * pair_off[b];
+    if (j >= d.q) continue;
+    const cplx* col = X + d.x_off + (long long)j * d.p;
+    double t = 0.0;
+    for (int r = threadIdx.x; r < d.p; r += blockDim.x) t += cabs2(col[r]);
+    t = warp_sum(t);
+    if (lane == 0) red[warp] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double u = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) u += red[w];
+      s_out[d.s_off + j] = sqrt(u);
+    }
+    __syncthreads();
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    int mx = 0, tot = 0, bad = 0;
+    for (int b = 0; b < nblk; ++b) {
+      const int n = done[b] ? nsw[b] : max_sweeps;
+      if (!done[b]) bad = 1;
+      mx = max(mx, n);
+      tot += n;
+    }
+    stat[0] = bad;
+    stat[1] = mx;
+    stat[2] = tot;
+  }
+}
+
 // One kept singular triple per CTA: U[:, k] over the block's rows, Vh[k, :] over its columns.
 struct SelEntry {
   int blk, j, k;
@@ -1555,18 +1648,66 @@ struct DSU {
   }
 };
 
-int keep_all_rule(const std::vector<double>& s, void*) { return (int)s.size(); }
 }  // namespace
 
 SvdCounters g_svd_counters;
 std::atomic<long long> g_kernel_launches{0};
+
+namespace {
+// Host side of k_jacobi_multi: pair offsets, one cooperative launch, bounded-wait check.
+// d_stat receives {bad, max sweeps, total sweeps} like the batched kernel.
+void run_jacobi_multi(cudaStream_t st, cplx* Xs, cplx* Vs, const std::vector<BlkDesc>& desc, const BlkDesc* d_desc,
+                      double* d_s, int* d_stat) {
+  const int nblk = (int)desc.size();
+  std::vector<int> pair_off(nblk);
+  int total = 0, rounds = 0;
+  for (int b = 0; b < nblk; ++b) {
+    const int qpad = desc[b].q + (desc[b].q & 1);
+    pair_off[b] = total;
+    total += qpad / 2;
+    rounds = std::max(rounds, qpad - 1);
+  }
+  static const int max_ctas = [] {
+    int dev = 0, sms = 0, per_sm = 0;
+    TDVP_CUDA(cudaGetDevice(&dev));
+    TDVP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    TDVP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_multi, 256, 0));
+    return std::max(1, sms * std::min(2, std::max(1, per_sm)));
+  }();
+  const int nctas = std::max(1, std::min(std::max(total, nblk), max_ctas));
+  int* d_off = nullptr;
+  int* d_flags = nullptr;
+  double* d_fro2 = nullptr;
+  GridBar* bar = nullptr;
+  TDVP_CUDA(cudaMallocAsync(&d_off, sizeof(int) * nblk, st));
+  TDVP_CUDA(cudaMallocAsync(&d_flags, sizeof(int) * 5 * nblk, st));
+  TDVP_CUDA(cudaMallocAsync(&d_fro2, sizeof(double) * nblk, st));
+  TDVP_CUDA(cudaMallocAsync(&bar, sizeof(GridBar), st));
+  TDVP_CUDA(cudaMemsetAsync(bar, 0, sizeof(GridBar), st));
+  TDVP_CUDA(cudaMemcpyAsync(d_off, pair_off.data(), sizeof(int) * nblk, cudaMemcpyHostToDevice, st));
+  int nb = nblk, tp = total, mr = rounds, ms = 60;
+  const BlkDesc* dd = d_desc;
+  const int* po = d_off;
+  void* args[] = {&Xs, &Vs, &dd, &po, &nb, &tp, &mr, &ms, &d_fro2, &d_flags, &bar, &d_s, &d_stat};
+  TDVP_CUDA(cudaLaunchCooperativeKernel((void*)k_jacobi_multi, dim3(nctas), dim3(256), args, 0, st));
+  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+  GridBar hb;
+  TDVP_CUDA(cudaMemcpyAsync(&hb, bar, sizeof(GridBar), cudaMemcpyDeviceToHost, st));
+  TDVP_CUDA(cudaStreamSynchronize(st));
+  TDVP_CUDA(cudaFreeAsync(d_off, st));
+  TDVP_CUDA(cudaFreeAsync(d_flags, st));
+  TDVP_CUDA(cudaFreeAsync(d_fro2, st));
+  TDVP_CUDA(cudaFreeAsync(bar, st));
+  if (hb.err) throw TdvpError(TDVP_ERR_TIMEOUT, "Jacobi SVD: a grid barrier wait ran out");
+}
+}  // namespace
 
 void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows, int cols,
                       int (*select)(const std::vector<double>& s, void* ctx), void* ctx, SvdOut& out, bool want_u,
                       bool want_v) {
   g_svd_counters.calls++;
   const long long n = (long long)rows * cols;
-  if (rows <= 1 || cols <= 1 || n > (1LL << 22)) {
+  if (rows <= 1 || cols <= 1 || n > (1LL << 27)) {
     svd_jacobi_keep(st, pool, M, rows, cols, select, ctx, out, want_u, want_v);
     return;
   }
@@ -1600,17 +1741,28 @@ void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows
     if (row_nz[r]) comp[dsu.find(r)].first.push_back(r);
   for (int c = 0; c < cols; ++c)
     if (col_nz[c]) comp[dsu.find(rows + c)].second.push_back(c);
-  if (comp.size() <= 1) {
+  if (comp.empty()) {
     svd_jacobi_keep(st, pool, M, rows, cols, select, ctx, out, want_u, want_v);
     return;
   }
-  g_svd_counters.blocked++;
-  g_svd_counters.blocks += (long long)comp.size();
-  // small blocks: one batched launch (X_b, V_b in shared memory); large ones one by one
+  if (comp.size() > 1) {
+    g_svd_counters.blocked++;
+    g_svd_counters.blocks += (long long)comp.size();
+  }
+  // Narrow blocks: one batched launch, one CTA per block with X_b, V_b in shared
+  // memory.  As soon as one block is kMultiQ columns wide (or too large for shared
+  // memory), every block goes to the cooperative launch that spreads each round's
+  // pairs over the whole GPU.
   constexpr size_t kSmemCap = 200 * 1024;
+  constexpr int kMultiQ = 24;
+  bool multi = false;
+  for (auto& kv : comp) {
+    const int nr = (int)kv.second.first.size(), nc = (int)kv.second.second.size();
+    const int p = std::max(nr, nc), q = std::min(nr, nc);
+    if (q >= kMultiQ || ((size_t)p * q + (size_t)q * q) * sizeof(cplx) > kSmemCap) multi = true;
+  }
   std::vector<BlkDesc> desc;
   std::vector<int> ridx, cidx;
-  std::vector<std::pair<std::vector<int>, std::vector<int>>> large;
   long long xo = 0, vo = 0;
   int so = 0;
   size_t smem_need = 0;
@@ -1620,10 +1772,8 @@ void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows
     const int nr = (int)rr.size(), nc = (int)cc.size();
     const int p = std::max(nr, nc), q = std::min(nr, nc);
     const size_t bytes = ((size_t)p * q + (size_t)q * q) * sizeof(cplx);
-    if (bytes > kSmemCap) {
-      large.push_back({rr, cc});
-      continue;
-    }
+    atomic_max(g_svd_counters.max_q, q);
+    if (multi && q >= kMultiQ) g_svd_counters.large_blocks++;
     BlkDesc d;
     d.orient = nr >= nc ? 0 : 1;
     d.p = p;
@@ -1644,11 +1794,9 @@ void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows
     desc.push_back(d);
   }
   const int nsmall = (int)desc.size();
-  std::vector<SvdOut> lout(large.size());
-  std::vector<int*> l_r(large.size()), l_c(large.size());
   struct Cand {
     double s;
-    int blk, j;  // blk >= 0: small block; blk < 0: large block -(blk+1)
+    int blk, j;
   };
   std::vector<Cand> all;
   DArr Xs, Vs;
@@ -1669,13 +1817,18 @@ void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows
     TDVP_CUDA(cudaMemsetAsync(d_bad, 0, 3 * sizeof(int), st));
     k_gather_batched<<<nsmall, 256, 0, st>>>(M, cols, d_desc, d_ridx, d_cidx, Xs.data(), Vs.data());
     TDVP_CHECK_LAUNCH();
-    static bool attr = false;
-    if (!attr) {
-      TDVP_CUDA(cudaFuncSetAttribute(k_jacobi_batched, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kSmemCap));
-      attr = true;
+    if (!multi) {
+      static const bool attr = [] {
+        TDVP_CUDA(cudaFuncSetAttribute(k_jacobi_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       (int)kSmemCap));
+        return true;
+      }();
+      (void)attr;
+      k_jacobi_batched<<<nsmall, 256, smem_need, st>>>(Xs.data(), Vs.data(), d_desc, 60, d_s, d_bad);
+      TDVP_CHECK_LAUNCH();
+    } else {
+      run_jacobi_multi(st, Xs.data(), Vs.data(), desc, d_desc, d_s, d_bad);
     }
-    k_jacobi_batched<<<nsmall, 256, smem_need, st>>>(Xs.data(), Vs.data(), d_desc, 60, d_s, d_bad);
-    TDVP_CHECK_LAUNCH();
     std::vector<double> hs(so);
     int hbad[3] = {0, 0, 0};
     TDVP_CUDA(cudaMemcpyAsync(hs.data(), d_s, sizeof(double) * so, cudaMemcpyDeviceToHost, st));
@@ -1683,27 +1836,13 @@ void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows
     TDVP_CUDA(cudaStreamSynchronize(st));
     tdvp_require(hbad[0] == 0, TDVP_ERR_SVD_NOT_CONVERGED, "batched Jacobi SVD did not converge");
     g_svd_counters.sweeps += hbad[2];
-    g_svd_counters.max_sweeps = std::max<long long>(g_svd_counters.max_sweeps, hbad[1]);
+    atomic_max(g_svd_counters.max_sweeps, hbad[1]);
     for (int b = 0; b < nsmall; ++b)
       for (int j = 0; j < desc[b].q; ++j) {
         const double v = hs[desc[b].s_off + j];
         tdvp_require(std::isfinite(v), TDVP_ERR_NONFINITE, "SVD: non-finite singular value");
         all.push_back({v, b, j});
       }
-  }
-  for (size_t L = 0; L < large.size(); ++L) {
-    auto& rr = large[L].first;
-    auto& cc = large[L].second;
-    const int pb = (int)rr.size(), qb = (int)cc.size();
-    TDVP_CUDA(cudaMallocAsync(&l_r[L], sizeof(int) * pb, st));
-    TDVP_CUDA(cudaMallocAsync(&l_c[L], sizeof(int) * qb, st));
-    TDVP_CUDA(cudaMemcpyAsync(l_r[L], rr.data(), sizeof(int) * pb, cudaMemcpyHostToDevice, st));
-    TDVP_CUDA(cudaMemcpyAsync(l_c[L], cc.data(), sizeof(int) * qb, cudaMemcpyHostToDevice, st));
-    DArr blk(pool, (size_t)pb * qb);
-    k_gather_block<<<ceil_div((long long)pb * qb, 256), 256, 0, st>>>(M, cols, l_r[L], l_c[L], pb, qb, blk.data());
-    TDVP_CHECK_LAUNCH();
-    svd_jacobi_keep(st, pool, blk.data(), pb, qb, keep_all_rule, nullptr, lout[L], want_u, want_v);
-    for (int k = 0; k < (int)lout[L].s.size(); ++k) all.push_back({lout[L].s[k], -(int)L - 1, k});
   }
   std::stable_sort(all.begin(), all.end(), [](const Cand& a, const Cand& b) { return a.s > b.s; });
   out.rows = rows;
@@ -1725,16 +1864,7 @@ void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows
       fill_zero(st, out.Vh.data(), (long long)keep * cols);
     }
     std::vector<SelEntry> sel;
-    std::vector<std::vector<int>> lsl(large.size()), lsg(large.size());
-    for (int k = 0; k < keep; ++k) {
-      if (all[k].blk >= 0)
-        sel.push_back({all[k].blk, all[k].j, k, all[k].s});
-      else {
-        const int L = -all[k].blk - 1;
-        lsl[L].push_back(all[k].j);
-        lsg[L].push_back(k);
-      }
-    }
+    for (int k = 0; k < keep; ++k) sel.push_back({all[k].blk, all[k].j, k, all[k].s});
     if (!sel.empty()) {
       SelEntry* d_sel = nullptr;
       TDVP_CUDA(cudaMallocAsync(&d_sel, sizeof(SelEntry) * sel.size(), st));
@@ -1746,37 +1876,11 @@ void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows
       TDVP_CHECK_LAUNCH();
       TDVP_CUDA(cudaFreeAsync(d_sel, st));
     }
-    for (size_t L = 0; L < large.size(); ++L) {
-      if (lsl[L].empty()) continue;
-      const int pb = (int)large[L].first.size(), qb = (int)large[L].second.size(), kb = lout[L].rank;
-      int *d_sl = nullptr, *d_sg = nullptr;
-      TDVP_CUDA(cudaMallocAsync(&d_sl, sizeof(int) * lsl[L].size(), st));
-      TDVP_CUDA(cudaMallocAsync(&d_sg, sizeof(int) * lsg[L].size(), st));
-      TDVP_CUDA(cudaMemcpyAsync(d_sl, lsl[L].data(), sizeof(int) * lsl[L].size(), cudaMemcpyHostToDevice, st));
-      TDVP_CUDA(cudaMemcpyAsync(d_sg, lsg[L].data(), sizeof(int) * lsg[L].size(), cudaMemcpyHostToDevice, st));
-      const int ns = (int)lsl[L].size();
-      if (want_u) {
-        k_scatter_cols<<<ceil_div((long long)pb * ns, 256), 256, 0, st>>>(lout[L].U.data(), pb, kb, l_r[L], d_sl,
-                                                                          d_sg, ns, out.U.data(), keep, 0);
-        TDVP_CHECK_LAUNCH();
-      }
-      if (want_v) {
-        k_scatter_cols<<<ceil_div((long long)qb * ns, 256), 256, 0, st>>>(lout[L].Vh.data(), qb, qb, l_c[L], d_sl,
-                                                                          d_sg, ns, out.Vh.data(), cols, 1);
-        TDVP_CHECK_LAUNCH();
-      }
-      TDVP_CUDA(cudaFreeAsync(d_sl, st));
-      TDVP_CUDA(cudaFreeAsync(d_sg, st));
-    }
   }
   if (nsmall) {
     TDVP_CUDA(cudaFreeAsync(d_desc, st));
     TDVP_CUDA(cudaFreeAsync(d_ridx, st));
     TDVP_CUDA(cudaFreeAsync(d_cidx, st));
     TDVP_CUDA(cudaFreeAsync(d_s, st));
-  }
-  for (size_t L = 0; L < large.size(); ++L) {
-    TDVP_CUDA(cudaFreeAsync(l_r[L], st));
-    TDVP_CUDA(cudaFreeAsync(l_c[L], st));
   }
 }

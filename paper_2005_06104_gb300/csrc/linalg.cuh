@@ -108,9 +108,15 @@ void svd_jacobi_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows,
                      SvdOut& out, bool want_u, bool want_v);
 // Process-wide counters of the SVD driver (calls, calls that split into blocks, blocks).
 struct SvdCounters {
-  long long calls = 0, blocked = 0, blocks = 0;
-  long long sweeps = 0, max_sweeps = 0;  // Jacobi sweeps over all (blocks of) calls, and the most in one
+  std::atomic<long long> calls{0}, blocked{0}, blocks{0};
+  std::atomic<long long> sweeps{0}, max_sweeps{0};  // Jacobi sweeps over all (blocks of) calls, and the most in one
+  std::atomic<long long> large_blocks{0}, max_q{0};  // blocks too large for the batched path; widest block
 };
+inline void atomic_max(std::atomic<long long>& a, long long v) {
+  long long cur = a.load(std::memory_order_relaxed);
+  while (v > cur && !a.compare_exchange_weak(cur, v, std::memory_order_relaxed)) {
+  }
+}
 extern SvdCounters g_svd_counters;
 
 // The same contract, exploiting block structure (exact zeros from conserved

@@ -691,8 +691,7 @@ template <int S>
 void launch_bf16s(cudaStream_t st, const CUtensorMap& ma, const CUtensorMap& mb, int M, int N, int nkb,
                   const float* sA, long long lsA, const float* sB, void* out, long long ldo, int out_df,
                   int* d_err) {
-  static bool attr = false;
-  if (!attr) {
+  static const bool attr = [] {
     // the register hand-over inside the kernel is sized for exactly this launch allocation
     cudaFuncAttributes fa;
     TDVP_CUDA(cudaFuncGetAttributes(&fa, k_gemm_bf16s<S>));
@@ -701,8 +700,9 @@ void launch_bf16s(cudaStream_t st, const CUtensorMap& ma, const CUtensorMap& mb,
                      std::to_string(REGS_LAUNCH));
     TDVP_CUDA(cudaFuncSetAttribute(k_gemm_bf16s<S>, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                    SCfg<S>::SMEM_BYTES));
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   dim3 grid(ceil_div(N, BN), ceil_div(M, BM));
   tdvp_require(grid.y <= 65535, TDVP_ERR_INVALID_ARG, "gemm_bf16s: M too large");
   k_gemm_bf16s<S><<<grid, THREADS, SCfg<S>::SMEM_BYTES, st>>>(ma, mb, M, N, nkb, sA, lsA, sB, out, ldo, out_df,

@@ -327,14 +327,13 @@ __global__ void k_zero_pad_cols(float* __restrict__ hi, float* __restrict__ lo, 
 
 // ---------------------------------------------------------------- host side
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
-  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
-  if (!fn) {
+  static const PFN_cuTensorMapEncodeTiled_v12000 fn = [] {
     cudaDriverEntryPointQueryResult q;
     void* p = nullptr;
     TDVP_CUDA(cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q));
     tdvp_require(q == cudaDriverEntryPointSuccess && p, TDVP_ERR_CUDA, "cuTensorMapEncodeTiled unavailable");
-    fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
-  }
+    return reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }();
   return fn;
 }
 
@@ -360,11 +359,11 @@ CUtensorMap make_map(const float* base, int rows, int ld, int box_rows, int bk) 
 template <class C>
 void launch_gemm(cudaStream_t st, const float* Ahi, const float* Alo, const float* Bhi, const float* Blo, int M, int N,
                  int ldk, void* out, long long ldo, bool out_f64, int* d_err) {
-  static bool attr = false;
-  if (!attr) {
+  static const bool attr = [] {
     TDVP_CUDA(cudaFuncSetAttribute(k_gemm_tf32x3<C>, cudaFuncAttributeMaxDynamicSharedMemorySize, C::SMEM_BYTES));
-    attr = true;
-  }
+    return true;
+  }();
+  (void)attr;
   // operands hold ceil(M/128)*128 and ceil(N/128)*128 rows (zero padded); a BN = 256
   // tile may reach 128 rows past the padded B operand only when N is not a multiple of
   // 256, and the host pads B to 256 rows in that case

@@ -396,12 +396,12 @@ class GseTdvp:
         return v.value
 
     def trunc_stats(self):
-        out = (C.c_double * 11)()
+        out = (C.c_double * 13)()
         self._chk(_lib.tdvp_trunc_stats(self.h, out))
         return dict(disc_k=out[0], disc_m=out[1], disc_eps=out[2], added=int(out[3]),
                     lanczos_iters=int(out[4]), lanczos_calls=int(out[5]), svd_calls=int(out[6]),
                     svd_blocked_calls=int(out[7]), svd_blocks=int(out[8]), svd_sweeps=int(out[9]),
-                    svd_max_sweeps=int(out[10]))
+                    svd_max_sweeps=int(out[10]), svd_large_blocks=int(out[11]), svd_max_block=int(out[12]))
 
     def profile(self, enable=True):
         self._chk(_lib.tdvp_profile(self.h, 1 if enable else 0))
@@ -428,3 +428,111 @@ class GseTdvp:
         ptrs = (C.c_void_p * self.n)(*[a.ctypes.data for a in arrs])
         self._chk(_lib.tdvp_get_mps(self.h, ptrs))
         return arrs
+
+
+_lib.tdvp_batch_create.argtypes = [C.c_int, C.c_void_p, C.c_void_p, C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]
+_lib.tdvp_batch_create.restype = C.c_int
+_lib.tdvp_batch_destroy.argtypes = [C.c_void_p]
+_lib.tdvp_batch_destroy.restype = C.c_int
+_lib.tdvp_batch_handle.argtypes = [C.c_void_p, C.c_int, C.POINTER(C.c_void_p)]
+_lib.tdvp_batch_handle.restype = C.c_int
+_lib.tdvp_batch_step.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_int)]
+_lib.tdvp_batch_step.restype = C.c_int
+_lib.tdvp_batch_expand_basis.argtypes = [C.c_void_p, C.c_int, C.c_void_p, C.POINTER(C.c_int)]
+_lib.tdvp_batch_expand_basis.restype = C.c_int
+_lib.tdvp_batch_sweep.argtypes = [C.c_void_p, C.c_double, C.c_int, C.POINTER(C.c_int)]
+_lib.tdvp_batch_sweep.restype = C.c_int
+_lib.tdvp_batch_energy.argtypes = [C.c_void_p, C.POINTER(C.c_double)]
+_lib.tdvp_batch_energy.restype = C.c_int
+_lib.tdvp_batch_norm.argtypes = [C.c_void_p, C.POINTER(C.c_double)]
+_lib.tdvp_batch_norm.restype = C.c_int
+_lib.tdvp_batch_last_error.argtypes = [C.c_void_p]
+_lib.tdvp_batch_last_error.restype = C.c_char_p
+
+
+class _Borrowed(GseTdvp):
+    """A chain handle owned by a batch (never destroyed through this object)."""
+
+    def close(self):
+        self.h = None
+
+
+class GseTdvpBatch:
+    """Independent chains on one GPU, each on its own stream (tdvp_batch_*).
+
+    chains: list of (mps, mpo, options dict).  n_threads <= 0: one host worker per core."""
+
+    def __init__(self, chains, n_threads=0):
+        n = len(chains)
+        pins, descs_m, descs_w, opts = [], (_Desc * n)(), (_Desc * n)(), (Options * n)()
+        self.d = chains[0][0][0].shape[1]
+        for i, (mps, mpo, kw) in enumerate(chains):
+            pm = _Pinned(mps, [mps[0].shape[0]] + [a.shape[2] for a in mps])
+            pw = _Pinned(mpo, [mpo[0].shape[0]] + [w.shape[3] for w in mpo])
+            pins += [pm, pw]
+            descs_m[i] = pm.desc(mps[0].shape[1])
+            descs_w[i] = pw.desc(mps[0].shape[1])
+            opts[i] = default_options(**kw)
+        b = C.c_void_p()
+        s = _lib.tdvp_batch_create(n, C.cast(descs_m, C.c_void_p), C.cast(descs_w, C.c_void_p),
+                                   C.cast(opts, C.c_void_p), int(n_threads), C.byref(b))
+        if s != 0:
+            raise TDVPError(s, "tdvp_batch_create failed")
+        self.b = b
+        self.n = n
+        self.sizes = [len(c[0]) for c in chains]
+
+    def _chk(self, s, status=None):
+        if s != 0:
+            raise TDVPError(s, _lib.tdvp_batch_last_error(self.b).decode())
+
+    def _status(self):
+        return (C.c_int * self.n)()
+
+    def step(self, dt, kind, k, weights=None):
+        st = self._status()
+        w = None if weights is None else C.cast((C.c_double * len(weights))(*weights), C.c_void_p)
+        self._chk(_lib.tdvp_batch_step(self.b, k, w, dt, kind, st))
+        return list(st)
+
+    def expand_basis(self, k, weights=None):
+        st = self._status()
+        w = None if weights is None else C.cast((C.c_double * len(weights))(*weights), C.c_void_p)
+        self._chk(_lib.tdvp_batch_expand_basis(self.b, k, w, st))
+        return list(st)
+
+    def sweep(self, dt, kind=REAL):
+        st = self._status()
+        self._chk(_lib.tdvp_batch_sweep(self.b, dt, kind, st))
+        return list(st)
+
+    def energies(self):
+        out = (C.c_double * self.n)()
+        self._chk(_lib.tdvp_batch_energy(self.b, out))
+        return list(out)
+
+    def norms(self):
+        out = (C.c_double * self.n)()
+        self._chk(_lib.tdvp_batch_norm(self.b, out))
+        return list(out)
+
+    def chain(self, i):
+        """The handle of chain i (owned by the batch; valid while the batch is open)."""
+        h = C.c_void_p()
+        s = _lib.tdvp_batch_handle(self.b, i, C.byref(h))
+        if s != 0:
+            raise TDVPError(s, "tdvp_batch_handle")
+        c = _Borrowed.__new__(_Borrowed)
+        c.h, c.n, c.d = h, self.sizes[i], self.d
+        return c
+
+    def close(self):
+        if getattr(self, "b", None):
+            _lib.tdvp_batch_destroy(self.b)
+            self.b = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
