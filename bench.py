@@ -51,6 +51,10 @@ def parse():
                     help="only time the tensor-core H_eff apply at --heff-chi (the profiling target)")
     ap.add_argument("--precision", default="bf16x10", choices=sorted(PRECISIONS),
                     help="arithmetic of the dense contractions (Lanczos, SVDs, observables stay FP64)")
+    ap.add_argument("--batch-chains", type=int, default=0,
+                    help="time the batch workload instead: this many random-field chains (lengths 20-60, "
+                         "chi_max 32-128, dt 0.05, k 2) stepped together, against the same chains one at a time")
+    ap.add_argument("--batch-threads", type=int, default=0, help="host workers of the batch (0: all cores)")
     ap.add_argument("--step-only", action="store_true",
                     help="stop after the timed steps (no FP64 comparison, e2e, probe or CPU baseline): "
                          "the short command a launch-list profile runs")
@@ -423,8 +427,55 @@ def run_heff_probe(args):
                       "algorithmic_tflops": flops / ms / 1e9}), flush=True)
 
 
+def run_batch(args):
+    """Independent random-field chains stepped as one batch (one stream per chain, host worker
+    pool) against the same chains stepped one after another on one stream each, same steps."""
+    import torch
+    from paper_2005_06104_gb300 import gse_tdvp as g
+    from paper_2005_06104_gb300 import workloads as wl
+    torch.cuda.set_device(0)
+    spec = wl.random_field_chains(args.batch_chains, seed=0)
+    chains = [(c["psi"], c["mpo"], dict(tau=c["tau"], eps_k=1e-8, eps_m=1e-8, chi_max=c["chi_max"],
+                                        precision=prec_code(g, args.precision))) for c in spec]
+    dt, k = spec[0]["dt"], spec[0]["k"]
+
+    def timed(n_threads):
+        b = g.GseTdvpBatch(chains, n_threads=n_threads)
+        for _ in range(args.prep_steps + args.warmup):
+            b.step(dt, g.REAL, k)
+        torch.cuda.synchronize()
+        l0 = g.launch_count()
+        t = time.perf_counter()
+        for _ in range(args.steps):
+            b.step(dt, g.REAL, k)
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t
+        dims = [max(b.chain(i).bond_dims()) for i in range(len(chains))]
+        e = b.energies()
+        b.close()
+        return el, g.launch_count() - l0, dims, e
+
+    t_b, l_b, dims, e_b = timed(args.batch_threads)
+    t_1, _, _, e_1 = timed(1)
+    n = len(chains)
+    print(json.dumps({
+        "metric": "GSE-TDVP1 chain steps/s, batch of independent random-field chains", "unit": "chain steps/s",
+        "value": n * args.steps / t_b, "sequential_value": n * args.steps / t_1, "speedup": t_1 / t_b,
+        "n_gpus": 1, "steps": args.steps, "warmup": args.warmup, "prep_steps": args.prep_steps,
+        "higher_is_better": True, "dtype": f"c128 state / {args.precision} contractions", "data": "synthetic",
+        "config": {"workload": f"random_field_heisenberg_chains_{n}", "lengths": "U{20..60}", "fields": "U[-2,2]",
+                   "chi_max": "U{32..128}", "dt": dt, "k": k, "seed": 0, "start": "Neel",
+                   "batch_threads": args.batch_threads or os.cpu_count()},
+        "gpu_launches": l_b, "bond_dim_max_per_chain": dims,
+        "max_energy_difference_batch_vs_sequential": max(abs(a - b) for a, b in zip(e_b, e_1)),
+        "timing": "host wall clock around the timed batch steps, synchronised on both sides"}), flush=True)
+
+
 def main():
     args = parse()
+    if args.batch_chains > 0:
+        run_batch(args)
+        return
     if args.heff_probe:
         run_heff_probe(args)
     elif args.impl == "reference":
