@@ -848,13 +848,17 @@ __device__ __forceinline__ void rr_pair(int round, int k, int qpad, int& P, int&
 
 // Rotation from a = |x_p|^2, b = |x_q|^2, c = x_p^H x_q:
 //   x_p' = cs x_p - sn e^{-i phi} x_q,  x_q' = sn e^{i phi} x_p + cs x_q,  c = |c| e^{i phi}
-// Pairs whose larger column is below floor2 (1e-32 |M|_F^2, i.e. numerically zero next
-// to the matrix) or whose smaller column is negligible next to the larger one
-// are left alone: rotating rounding noise never converges.
+// Pairs whose larger column is below floor2 (kJacobiFloor |M|_F^2) or whose smaller
+// column is below kJacobiFloor times the larger (norms squared) are left alone.  Such
+// columns hold singular values below 1e-15 of their neighbours, under every keep rule
+// of the method (rank 1e-10 s_max, eigenvalue floor 1e-14 lambda_max), and rotating
+// them against each other chases rounding noise for extra sweeps while moving the
+// kept columns by at most 1e-15.
+constexpr double kJacobiFloor = 1e-30;
 __device__ __forceinline__ bool jacobi_params(double a, double b, cplx c, double tol, double floor2,
                                               double& cs, cplx& sne) {
   const double big = fmax(a, b), small = fmin(a, b);
-  if (big <= floor2 || small <= 1e-32 * big) return false;
+  if (big <= floor2 || small <= kJacobiFloor * big) return false;
   const double ac = sqrt(cabs2(c));
   if (!(ac > tol * sqrt(a * b)) || ac == 0.0) return false;
   const double zeta = (b - a) / (2.0 * ac);
@@ -1011,7 +1015,7 @@ __global__ void __launch_bounds__(256)
     k_jacobi_coop(cplx* __restrict__ X, cplx* __restrict__ V, int p, int q, int qpad, double tol,
                   const double* __restrict__ fro2, int want_v, int max_sweeps, GridBar* bar,
                   int* __restrict__ sweeps_out) {
-  const double floor2 = 1e-32 * (*fro2);
+  const double floor2 = kJacobiFloor * (*fro2);
   for (int sweep = 0; sweep < max_sweeps; ++sweep) {
     if (blockIdx.x == 0 && threadIdx.x == 0) bar->rot[(sweep + 1) % 3] = 0;
     for (int round = 0; round < qpad - 1; ++round) {
@@ -1037,7 +1041,7 @@ __global__ void __launch_bounds__(256)
     k_jacobi_small(cplx* __restrict__ Xg, cplx* __restrict__ Vg, int p, int q, int qpad,
                    double tol, const double* __restrict__ fro2, int want_v, int max_sweeps,
                    int* __restrict__ sweeps_out) {
-  const double floor2 = 1e-32 * (*fro2);
+  const double floor2 = kJacobiFloor * (*fro2);
   extern __shared__ cplx sm[];
   cplx* X = sm;
   cplx* V = sm + (long long)p * q;
@@ -1422,7 +1426,7 @@ __global__ void __launch_bounds__(256)
   __syncthreads();
   double fro2 = 0.0;
   for (int u = 0; u < nw; ++u) fro2 += s_fro[u];
-  const double floor2 = 1e-32 * fro2;
+  const double floor2 = kJacobiFloor * fro2;
   const double tol = fmax(1e-15, sqrt((double)p) * 2.2e-16);
   int sweep = 0;
   for (; sweep < max_sweeps && q > 1; ++sweep) {
@@ -1549,7 +1553,7 @@ __global__ void __launch_bounds__(256)
         rr_pair(round, it - pair_off[b], qpad, P, Q);
         if (Q >= d.q) continue;
         const double tol = fmax(1e-15, sqrt((double)d.p) * 2.2e-16);
-        if (jacobi_pair_block(X + d.x_off, V + d.v_off, d.p, d.q, P, Q, tol, 1e-32 * fro2[b], 1) &&
+        if (jacobi_pair_block(X + d.x_off, V + d.v_off, d.p, d.q, P, Q, tol, kJacobiFloor * fro2[b], 1) &&
             threadIdx.x == 0)
           rot[3 * b + sweep % 3] = 1;
       }
