@@ -106,6 +106,7 @@ int lanczos_expm(cudaStream_t st, DevicePool* pool, Blas1& blas, LanczosWork& lw
   double* alpha = lw.real;
   double* beta = lw.real + 64;
   double* nrm2 = lw.real + 130;
+  double* err = lw.real + 132;
   lw.V.ensure(pool, (size_t)(nmax + 1) * n);
   lw.w.ensure(pool, (size_t)n);
   cplx* V = lw.V.data();
@@ -121,36 +122,24 @@ int lanczos_expm(cudaStream_t st, DevicePool* pool, Blas1& blas, LanczosWork& lw
     return 0;
   }
   scale_by_inv_sqrt(st, V, x, nrm2, n);
-  // The stopping test needs the host.  Small problems (latency-bound) run a few
-  // iterations between tests: every iteration stores its error estimate, the host
-  // then takes the first iteration that passes, and the coefficients are
-  // recomputed for it, so the result is the one a test after every iteration gives.
-  const int group = n <= (1LL << 16) ? 4 : (n <= (1LL << 18) ? 2 : 1);
-  double* errs = lw.real + 256;  // errs[2j], errs[2j+1]: estimate and beta of iteration j
-  int used = 0, checked = 0;
+  int used = 0;
   double last_err = 0.0;
-  double h_err[128];
-  for (int j = 0; j < nmax && used == 0; ++j) {
+  for (int j = 0; j < nmax; ++j) {
     op(V + (long long)j * n, wv);
     // alpha_j = Re <v_j, w>; w -= V (V^H w), twice (full re-orthogonalisation); beta = |w|
     blas.lanczos_fused(st, 0, V, n, j + 1, wv, n, nullptr, lw.c.data(), alpha, j, nullptr, nullptr);
     blas.lanczos_fused(st, 1, V, n, j + 1, wv, n, lw.c.data(), lw.c.data() + 64, nullptr, j, nullptr, nullptr);
     blas.lanczos_fused(st, 2, V, n, j + 1, wv, n, lw.c.data() + 64, nullptr, nullptr, j, nrm2, beta + j + 1);
-    tridiag_expv(st, alpha, beta, j + 1, delta, kind, nrm2, lw.y.data(), errs + 2 * j);
-    const bool test = (j + 1) % group == 0 || j + 1 == nmax || j + 1 == n;
-    if (test) {
-      const int cnt = j + 1 - checked;
-      TDVP_CUDA(cudaMemcpyAsync(h_err + 2 * checked, errs + 2 * checked, sizeof(double) * 2 * cnt,
-                                cudaMemcpyDeviceToHost, st));
-      TDVP_CUDA(cudaStreamSynchronize(st));
-      for (int i = checked; i <= j && used == 0; ++i) {
-        tdvp_require(std::isfinite(h_err[2 * i]) && std::isfinite(h_err[2 * i + 1]), TDVP_ERR_NONFINITE,
-                     "Lanczos: non-finite coefficient");
-        last_err = h_err[2 * i];
-        if (h_err[2 * i] <= tol || h_err[2 * i + 1] <= kBreakdown || i + 1 == n) used = i + 1;
-      }
-      checked = j + 1;
-      if (used) break;
+    tridiag_expv(st, alpha, beta, j + 1, delta, kind, nrm2, lw.y.data(), err);
+    double h_err[2];
+    TDVP_CUDA(cudaMemcpyAsync(h_err, err, sizeof(h_err), cudaMemcpyDeviceToHost, st));
+    TDVP_CUDA(cudaStreamSynchronize(st));
+    tdvp_require(std::isfinite(h_err[0]) && std::isfinite(h_err[1]), TDVP_ERR_NONFINITE,
+                 "Lanczos: non-finite coefficient");
+    last_err = h_err[0];
+    if (h_err[0] <= tol || h_err[1] <= kBreakdown || j + 1 == n) {
+      used = j + 1;
+      break;
     }
     if (j + 1 == nmax) break;
     scale_by_inv_sqrt(st, V + (long long)(j + 1) * n, wv, nrm2, n);
@@ -159,8 +148,6 @@ int lanczos_expm(cudaStream_t st, DevicePool* pool, Blas1& blas, LanczosWork& lw
     throw TdvpError(TDVP_ERR_LANCZOS_NOT_CONVERGED,
                     "Lanczos error estimate " + std::to_string(last_err) + " above tolerance after " +
                         std::to_string(nmax) + " steps");
-  if (used < checked)  // a later iteration of the group ran last: coefficients of the one taken
-    tridiag_expv(st, alpha, beta, used, delta, kind, nrm2, lw.y.data(), errs + 2 * (used - 1));
   multi_combine(st, out, V, n, used, lw.y.data(), beta0, n);
   return used;
 }

@@ -73,7 +73,7 @@ void env_right_fp64(cudaStream_t st, Scratch& s, const cplx* R, const WSparse& W
 // steps do not bring the error estimate below tol.
 struct LanczosWork {
   DArr V, w, c, y;
-  double* real = nullptr;  // device: alpha[64], beta[65], nrm2, err[2]; from 256: err of step j at 2j
+  double* real = nullptr;  // device: alpha[64], beta[65], nrm2, err[2], scratch norms
   void init(DevicePool* pool);
   void release();
 };

@@ -627,7 +627,7 @@ void Engine::krylov_apply(const KrylovOp& kop, const MpsDev& src, MpsDev& out) {
     rho.ensure(&pool, (size_t)n * n);
     zgemm_prec(st, scr, kp, OP_N, OP_C, n, n, K, H1.data(), K, G.data(), K, rho.data(), n);
     F[i].release();
-    // eigen-decomposition of the Hermitian PSD rho through its SVD (singular values = eigenvalues)
+    // eigendecomposition of the Hermitian PSD rho: Jacobi SVD of its pivoted Cholesky factor
     const double eps_k = opt.eps_k;
     const int cap = opt.chi_max;
     double* disc = &disc_k;
@@ -644,7 +644,7 @@ void Engine::krylov_apply(const KrylovOp& kop, const MpsDev& src, MpsDev& out) {
     SvdOut sv;
     {
       PhaseScope ps(tracer, PH_KRYLOV_EIG);
-      svd_jacobi(st, &pool, rho.data(), n, n, rule, sv, true, false);
+      eig_psd_jacobi(st, &pool, rho.data(), n, rule, sv);
     }
     const int keep = std::max(1, sv.rank);
     tdvp_require(sv.rank >= 1, TDVP_ERR_NONFINITE, "krylov: zero density matrix");

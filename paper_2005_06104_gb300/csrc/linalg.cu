@@ -1609,6 +1609,123 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Hermitian positive semidefinite blocks: pivoted Cholesky, in place, one CTA per
+// block.  X_b (n x n, column-major) becomes L (n x rank) with A[piv][:, piv] = L L^H;
+// elimination stops when the largest remaining diagonal entry is below
+// rel_floor times the block's largest diagonal entry, and desc[b].q becomes the
+// rank.  The one-sided Jacobi SVD of L then gives the eigenvectors (its left
+// singular vectors) and eigenvalues (singular values squared) of the block.  L's
+// singular values span half the decades of A's eigenvalues, so the sweeps that
+// follow are far fewer than those of a Jacobi SVD of A itself.
+__global__ void __launch_bounds__(256)
+    k_pchol_batched(cplx* __restrict__ X, BlkDesc* __restrict__ desc, int* __restrict__ piv, double rel_floor) {
+  __shared__ double s_val[8];
+  __shared__ int s_idx[8];
+  __shared__ double s_thr, s_piv;
+  __shared__ int s_k;
+  BlkDesc& dref = desc[blockIdx.x];
+  const int n = dref.p;
+  cplx* A = X + dref.x_off;
+  int* pv = piv + dref.r_off;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  for (int i = tid; i < n; i += blockDim.x) pv[i] = i;
+  // largest diagonal entry from row `from` on: value and index (block-wide)
+  auto argmax_diag = [&](int from, double& val, int& idx) {
+    double v = -1.0;
+    int k = from;
+    for (int i = from + tid; i < n; i += blockDim.x) {
+      const double t = A[(long long)i * n + i].x;
+      if (t > v) {
+        v = t;
+        k = i;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+      const int ok = __shfl_xor_sync(0xffffffffu, k, o);
+      if (ov > v || (ov == v && ok < k)) {
+        v = ov;
+        k = ok;
+      }
+    }
+    if (lane == 0) {
+      s_val[warp] = v;
+      s_idx[warp] = k;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double bv = s_val[0];
+      int bk = s_idx[0];
+      for (int u = 1; u < nw; ++u)
+        if (s_val[u] > bv || (s_val[u] == bv && s_idx[u] < bk)) {
+          bv = s_val[u];
+          bk = s_idx[u];
+        }
+      s_piv = bv;
+      s_k = bk;
+    }
+    __syncthreads();
+    val = s_piv;
+    idx = s_k;
+    __syncthreads();
+  };
+  double dmax;
+  int k0;
+  argmax_diag(0, dmax, k0);
+  if (tid == 0) s_thr = rel_floor * dmax;
+  __syncthreads();
+  const double thr = s_thr;
+  int rank = 0;
+  for (int j = 0; j < n; ++j) {
+    double val;
+    int k;
+    argmax_diag(j, val, k);
+    if (!(val > thr)) break;  // uniform: every thread read the same shared values
+    if (k != j) {
+      for (int l = tid; l < n; l += blockDim.x) {  // rows j and k, every column
+        const cplx t = A[(long long)l * n + j];
+        A[(long long)l * n + j] = A[(long long)l * n + k];
+        A[(long long)l * n + k] = t;
+      }
+      __syncthreads();
+      for (int i = tid; i < n; i += blockDim.x) {  // columns j and k, every row
+        const cplx t = A[(long long)j * n + i];
+        A[(long long)j * n + i] = A[(long long)k * n + i];
+        A[(long long)k * n + i] = t;
+      }
+      if (tid == 0) {
+        const int t = pv[j];
+        pv[j] = pv[k];
+        pv[k] = t;
+      }
+      __syncthreads();
+    }
+    const double ljj = sqrt(A[(long long)j * n + j].x);
+    const double inv = 1.0 / ljj;
+    __syncthreads();
+    for (int i = tid; i < n; i += blockDim.x) {
+      cplx& a = A[(long long)j * n + i];
+      if (i > j)
+        a = cscale(a, inv);
+      else if (i < j)
+        a = mkc(0.0, 0.0);
+      else
+        a = mkc(ljj, 0.0);
+    }
+    __syncthreads();
+    const int m = n - j - 1;
+    for (long long e = tid; e < (long long)m * m; e += blockDim.x) {
+      const int i = j + 1 + (int)(e % m), l = j + 1 + (int)(e / m);
+      const cplx li = A[(long long)j * n + i], ll = A[(long long)j * n + l];
+      cplx& a = A[(long long)l * n + i];
+      a = csub(a, cmul(li, cconj(ll)));
+    }
+    __syncthreads();
+    rank = j + 1;
+  }
+  if (tid == 0) dref.q = rank;
+}
+
 // One kept singular triple per CTA: U[:, k] over the block's rows, Vh[k, :] over its columns.
 struct SelEntry {
   int blk, j, k;
@@ -1617,7 +1734,8 @@ struct SelEntry {
 __global__ void k_scatter_batched(const cplx* __restrict__ X, const cplx* __restrict__ V,
                                   const BlkDesc* __restrict__ desc, const SelEntry* __restrict__ sel,
                                   const int* __restrict__ ridx, const int* __restrict__ cidx, cplx* __restrict__ U,
-                                  int keep, cplx* __restrict__ Vh, int cols, int want_u, int want_v) {
+                                  int keep, cplx* __restrict__ Vh, int cols, int want_u, int want_v,
+                                  const int* __restrict__ piv) {
   const SelEntry e = sel[blockIdx.x];
   const BlkDesc d = desc[e.blk];
   const cplx* Xb = X + d.x_off + (long long)e.j * d.p;  // column j of X_b
@@ -1626,7 +1744,8 @@ __global__ void k_scatter_batched(const cplx* __restrict__ X, const cplx* __rest
   if (want_u)
     for (int i = threadIdx.x; i < d.nr; i += blockDim.x) {
       const cplx v = (d.orient == 0) ? cscale(Xb[i], inv) : Vb[i];
-      U[(long long)ridx[d.r_off + i] * keep + e.k] = v;
+      const int li = piv ? piv[d.r_off + i] : i;  // row i of a pivoted factor is local row piv[i]
+      U[(long long)ridx[d.r_off + li] * keep + e.k] = v;
     }
   if (want_v)
     for (int i = threadIdx.x; i < d.nc; i += blockDim.x) {
@@ -1708,7 +1827,7 @@ void run_jacobi_multi(cudaStream_t st, cplx* Xs, cplx* Vs, const std::vector<Blk
 
 void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows, int cols,
                       int (*select)(const std::vector<double>& s, void* ctx), void* ctx, SvdOut& out, bool want_u,
-                      bool want_v) {
+                      bool want_v, bool psd) {
   g_svd_counters.calls++;
   const long long n = (long long)rows * cols;
   if (rows <= 1 || cols <= 1 || n > (1LL << 27)) {
@@ -1805,8 +1924,9 @@ void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows
   std::vector<Cand> all;
   DArr Xs, Vs;
   BlkDesc* d_desc = nullptr;
-  int *d_ridx = nullptr, *d_cidx = nullptr, *d_bad = nullptr;
+  int *d_ridx = nullptr, *d_cidx = nullptr, *d_bad = nullptr, *d_piv = nullptr;
   double* d_s = nullptr;
+  psd = psd && rows == cols && !want_v;
   if (nsmall) {
     Xs.reset(pool, (size_t)std::max<long long>(1, xo));
     Vs.reset(pool, (size_t)std::max<long long>(1, vo));
@@ -1821,6 +1941,15 @@ void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows
     TDVP_CUDA(cudaMemsetAsync(d_bad, 0, 3 * sizeof(int), st));
     k_gather_batched<<<nsmall, 256, 0, st>>>(M, cols, d_desc, d_ridx, d_cidx, Xs.data(), Vs.data());
     TDVP_CHECK_LAUNCH();
+    if (psd) {
+      // eigendecomposition of a Hermitian PSD matrix: Jacobi SVD of its pivoted Cholesky
+      // factor per block; eigenvalues below 1e-15 of the block's largest diagonal entry
+      // (under every keep floor of the method) end the factorisation
+      TDVP_CUDA(cudaMallocAsync(&d_piv, sizeof(int) * std::max<size_t>(1, ridx.size()), st));
+      TDVP_CUDA(cudaMemsetAsync(d_s, 0, sizeof(double) * std::max(1, so), st));
+      k_pchol_batched<<<nsmall, 256, 0, st>>>(Xs.data(), d_desc, d_piv, 1e-15);
+      TDVP_CHECK_LAUNCH();
+    }
     if (!multi) {
       static const bool attr = [] {
         TDVP_CUDA(cudaFuncSetAttribute(k_jacobi_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1845,7 +1974,11 @@ void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows
       for (int j = 0; j < desc[b].q; ++j) {
         const double v = hs[desc[b].s_off + j];
         tdvp_require(std::isfinite(v), TDVP_ERR_NONFINITE, "SVD: non-finite singular value");
-        all.push_back({v, b, j});
+        if (psd) {
+          if (v > 0.0) all.push_back({v * v, b, j});  // eigenvalue = (singular value of L)^2
+        } else {
+          all.push_back({v, b, j});
+        }
       }
   }
   std::stable_sort(all.begin(), all.end(), [](const Cand& a, const Cand& b) { return a.s > b.s; });
@@ -1868,7 +2001,7 @@ void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows
       fill_zero(st, out.Vh.data(), (long long)keep * cols);
     }
     std::vector<SelEntry> sel;
-    for (int k = 0; k < keep; ++k) sel.push_back({all[k].blk, all[k].j, k, all[k].s});
+    for (int k = 0; k < keep; ++k) sel.push_back({all[k].blk, all[k].j, k, psd ? std::sqrt(all[k].s) : all[k].s});
     if (!sel.empty()) {
       SelEntry* d_sel = nullptr;
       TDVP_CUDA(cudaMallocAsync(&d_sel, sizeof(SelEntry) * sel.size(), st));
@@ -1876,7 +2009,7 @@ void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows
       k_scatter_batched<<<(int)sel.size(), 128, 0, st>>>(Xs.data(), Vs.data(), d_desc, d_sel, d_ridx, d_cidx,
                                                           want_u ? out.U.data() : nullptr, keep,
                                                           want_v ? out.Vh.data() : nullptr, cols, want_u ? 1 : 0,
-                                                          want_v ? 1 : 0);
+                                                          want_v ? 1 : 0, psd ? d_piv : nullptr);
       TDVP_CHECK_LAUNCH();
       TDVP_CUDA(cudaFreeAsync(d_sel, st));
     }
@@ -1886,5 +2019,6 @@ void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows
     TDVP_CUDA(cudaFreeAsync(d_ridx, st));
     TDVP_CUDA(cudaFreeAsync(d_cidx, st));
     TDVP_CUDA(cudaFreeAsync(d_s, st));
+    if (d_piv) TDVP_CUDA(cudaFreeAsync(d_piv, st));
   }
 }

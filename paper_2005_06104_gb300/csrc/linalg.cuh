@@ -121,9 +121,12 @@ extern SvdCounters g_svd_counters;
 
 // The same contract, exploiting block structure (exact zeros from conserved
 // quantum numbers): independent SVDs per connected block, merged spectrum.
+// psd: M is Hermitian positive semidefinite and only U is wanted; the blocks are then
+// factorised by pivoted Cholesky and the Jacobi SVD runs on the factor (fewer sweeps);
+// out.s holds eigenvalues.
 void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows, int cols,
                       int (*select)(const std::vector<double>& s, void* ctx), void* ctx,
-                      SvdOut& out, bool want_u, bool want_v);
+                      SvdOut& out, bool want_u, bool want_v, bool psd = false);
 template <class Select>
 inline void svd_jacobi(cudaStream_t st, DevicePool* pool, const cplx* M, int rows, int cols,
                        Select select, SvdOut& out, bool want_u, bool want_v) {
@@ -131,6 +134,15 @@ inline void svd_jacobi(cudaStream_t st, DevicePool* pool, const cplx* M, int row
     return (*static_cast<Select*>(ctx))(s);
   };
   svd_blocked_keep(st, pool, M, rows, cols, thunk, &select, out, want_u, want_v);
+}
+// Eigendecomposition of a Hermitian positive semidefinite n x n matrix: out.s the
+// eigenvalues (descending), out.U the kept eigenvectors (n x keep).
+template <class Select>
+inline void eig_psd_jacobi(cudaStream_t st, DevicePool* pool, const cplx* M, int n, Select select, SvdOut& out) {
+  auto thunk = [](const std::vector<double>& s, void* ctx) -> int {
+    return (*static_cast<Select*>(ctx))(s);
+  };
+  svd_blocked_keep(st, pool, M, n, n, thunk, &select, out, true, false, true);
 }
 
 // rows-of-Vh scaling helpers: out[r][c] = s[r] * Vh[r][c]; out[i][r] = U[i][r] * s[r]
