@@ -1548,9 +1548,12 @@ __global__ void __launch_bounds__(256)
         if (((volatile int*)done)[b]) continue;
         const BlkDesc d = desc[b];
         const int qpad = d.q + (d.q & 1);
-        if (round >= qpad - 1) continue;
+        const int k = it - pair_off[b];
+        // the device q may be below the host's (a block's rank after pivoted Cholesky):
+        // only the first qpad / 2 pair slots of the block are pairs of this round
+        if (round >= qpad - 1 || k >= qpad / 2) continue;
         int P, Q;
-        rr_pair(round, it - pair_off[b], qpad, P, Q);
+        rr_pair(round, k, qpad, P, Q);
         if (Q >= d.q) continue;
         const double tol = fmax(1e-15, sqrt((double)d.p) * 2.2e-16);
         if (jacobi_pair_block(X + d.x_off, V + d.v_off, d.p, d.q, P, Q, tol, kJacobiFloor * fro2[b], 1) &&
@@ -1927,6 +1930,9 @@ void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows
   int *d_ridx = nullptr, *d_cidx = nullptr, *d_bad = nullptr, *d_piv = nullptr;
   double* d_s = nullptr;
   psd = psd && rows == cols && !want_v;
+  // the factorisation reads each block as a square n x n matrix: a Hermitian pattern
+  // gives square blocks; anything else takes the plain SVD (same eigen data for PSD)
+  for (const BlkDesc& d : desc) psd = psd && d.nr == d.nc;
   if (nsmall) {
     Xs.reset(pool, (size_t)std::max<long long>(1, xo));
     Vs.reset(pool, (size_t)std::max<long long>(1, vo));
