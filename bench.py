@@ -40,8 +40,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--chi-max", type=int, default=128)
-    ap.add_argument("--prep-steps", type=int, default=6,
+    ap.add_argument("--chi-max", type=int, default=256)
+    ap.add_argument("--prep-steps", type=int, default=8,
                     help="untimed GSE-TDVP1 steps that grow the bond dimension before warm-up")
     ap.add_argument("--k", type=int, default=3)
     ap.add_argument("--dt", type=float, default=0.1)

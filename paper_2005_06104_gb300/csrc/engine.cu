@@ -334,8 +334,8 @@ void Engine::canonicalize(int c) {
     move_left(center, 0.0, 1 << 30, false);
     --center;
   }
-  ensure_L(c);
-  ensure_R(c);
+  // environments are built on demand by their users (sweep, energy, heff): the Krylov
+  // step, the extension and the local observables need none
 }
 
 // ============================================================================
@@ -361,12 +361,16 @@ int Engine::lanczos(const std::function<void(const cplx*, cplx*)>& op, const cpl
 // ============================================================================
 void Engine::sweep(double dt, int kind) {
   canonicalize(0);
-  for (int i = 0; i < N; ++i) ensure_R(i);
-  ensure_L(0);
   const double delta = 0.5 * dt;
   const bool imag = kind == TDVP_IMAG;
   const int prec = opt.precision;
-  env_prec = (prec == TDVP_PREC_TF32X3_ENV) ? TDVP_PREC_TF32X3 : prec_is_bf16(prec) ? prec : TDVP_PREC_FP64;
+  // the sweep's environments (the initial right ones included) in the precision form
+  const int want_env = (prec == TDVP_PREC_TF32X3_ENV) ? TDVP_PREC_TF32X3 : prec_is_bf16(prec) ? prec : TDVP_PREC_FP64;
+  if (want_env != TDVP_PREC_FP64)  // FP64 environments left by observables are rebuilt in that form
+    for (int j = 0; j < N; ++j) Lok[j] = Rok[j] = 0;
+  env_prec = want_env;
+  for (int i = 0; i < N; ++i) ensure_R(i);
+  ensure_L(0);
   lanczos_iters = lanczos_calls = 0;
   disc_eps = 0.0;
   DArr y;
