@@ -256,6 +256,19 @@ def heff_roofline(g, torch, chi, W, prec):
     return flops, timed(7), timed(None)
 
 
+def max_over_ranks(x, dist, device):
+    """The largest of every rank's x (all ranks receive it)."""
+    import torch
+    t = torch.tensor([float(x)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return t.item()
+
+
+def job_throughput(world, steps, t_max):
+    """Whole-job steps per second: every replica runs `steps` steps; the slowest rank's time counts."""
+    return world * steps / t_max
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -316,10 +329,8 @@ def run_gpu(args):
     ck = clocks.stop()
     t_rank = sum(ts) / 1e3
     if world > 1:
-        tt = torch.tensor([t_rank], device="cuda")
-        dist.all_reduce(tt, op=dist.ReduceOp.MAX)
-        t_rank = tt.item()
-    value = world * args.steps / t_rank
+        t_rank = max_over_ranks(t_rank, dist, "cuda")
+    value = job_throughput(world, args.steps, t_rank)
     nfo["bond_dim_max"] = max(st.bond_dims())
     nfo["bond_dims_start"] = dims_start
     e_end = st.energy()
@@ -336,13 +347,20 @@ def run_gpu(args):
         if world > 1:
             dist.destroy_process_group()
         return
-    # precision form vs FP64 GPU form: one step of each from the same state
+    # precision form vs FP64 GPU form: one step of each from the same state (device time)
+    def timed_step(h):
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ea.record()
+        step(h)
+        eb.record()
+        eb.synchronize()
+        return ea.elapsed_time(eb)
     a = g.GseTdvp(start_state, W, stream=stream, **dict(opts, precision=g.PREC_FP64))
-    step(a)
+    ms_64 = timed_step(a)
     e_64 = a.energy()
     a.close()
     b_ = g.GseTdvp(start_state, W, stream=stream, **opts)
-    step(b_)
+    ms_tc = timed_step(b_)
     e_tc, n_tc = b_.energy(), b_.norm()
     b_.close()
     # e2e through the public API: host state in, one step, full state out
@@ -377,6 +395,13 @@ def run_gpu(args):
     else:
         products, peak, peak_src = 1, 1.25, "nominal FP64 (no tensor cores)"
         kern = f"H_eff apply (FP64 CUDA cores) at chi={args.heff_chi}, w=14"
+    # DRAM bytes of one apply (its 4 launches), from the ncu capture of these kernels at
+    # chi = 1024, w = 14 in BF16X10; other configurations have no capture
+    traffic, traffic_src = None, None
+    if args.precision == "bf16x10" and args.heff_chi == 1024:
+        traffic = 4.70e9
+        traffic_src = ("ncu dram__bytes_read.sum + dram__bytes_write.sum over the 4 launches of one cached "
+                       "apply (slice x, GEMM 1, MPO stage, GEMM 3) of these kernels")
     cpu = None
     if not args.no_cpu_baseline:
         try:
@@ -391,7 +416,8 @@ def run_gpu(args):
         "scaling": "weak", "vs_baseline": None, "dtype": f"c128 state / {args.precision} contractions",
         "data": "synthetic", "config": dict(cfg, parallelism=f"replicas{world}"),
         "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": None, "kernel": kern, "peak_source": peak_src,
+                     "frac": achieved / peak, "traffic": traffic, "kernel": kern, "peak_source": peak_src,
+                     "traffic_source": traffic_src,
                      "tensor_flops_per_algorithmic_flop": products,
                      "tensor_frac_executed": achieved * products / peak,
                      "ms_per_apply": pms, "algorithmic_flops_per_apply": pflops,
@@ -400,6 +426,8 @@ def run_gpu(args):
         "heff_in_step": {"applies": heff_n, "ms": heff_ms, "tflops_algorithmic": achieved_step,
                          "share_of_step": heff_ms / sum(ts) if ts else None},
         "precision_vs_fp64": {"precision": args.precision, "energy_precision_form": e_tc, "energy_fp64": e_64,
+                              "step_ms_precision_form": ms_tc, "step_ms_fp64": ms_64,
+                              "speedup_over_fp64": ms_64 / ms_tc,
                               "rel_energy_err": abs(e_tc - e_64) / abs(e_64), "norm_drift": abs(n_tc - 1.0)},
         "energy_conservation": {"E_initial": e_init, "E_after_timed_steps": e_end, "abs_drift": abs(e_end - e_init)},
         "step_stats": nfo,
