@@ -1495,123 +1495,6 @@ __global__ void __launch_bounds__(256)
   }
 }
 
-// Many blocks at once over the whole GPU: the FP64 pipe of one SM is a small
-// fraction of the device's (about 8 GFLOP/s of 1.2 TFLOP/s on this part), so a
-// block wider than a few dozen columns must not sit on one SM.  One cooperative
-// launch runs every block's Jacobi sweeps; each round's pairs of all unconverged
-// blocks are work items spread over the CTAs, which meet at a bounded grid
-// barrier between rounds.  A block that completes a sweep without a rotation is
-// done; its sweeps stop while the others continue.
-// flags: rot[nblk][3] | done[nblk] | sweeps[nblk]; stat: bad, max sweeps, total sweeps.
-__global__ void __launch_bounds__(256)
-    k_jacobi_multi(cplx* __restrict__ X, cplx* __restrict__ V, const BlkDesc* __restrict__ desc,
-                   const int* __restrict__ pair_off, int nblk, int total_pairs, int max_rounds, int max_sweeps,
-                   double* __restrict__ fro2, int* __restrict__ flags, GridBar* bar, double* __restrict__ s_out,
-                   int* __restrict__ stat) {
-  int* rot = flags;
-  int* done = flags + 3 * nblk;
-  int* nsw = flags + 4 * nblk;
-  __shared__ double red[8];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  // Frobenius norms (the floor below which a pair is numerical zero)
-  for (int b = blockIdx.x; b < nblk; b += gridDim.x) {
-    const BlkDesc d = desc[b];
-    const cplx* Xb = X + d.x_off;
-    double f = 0.0;
-    for (long long e = threadIdx.x; e < (long long)d.p * d.q; e += blockDim.x) f += cabs2(Xb[e]);
-    f = warp_sum(f);
-    if (lane == 0) red[warp] = f;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double t = 0.0;
-      for (int u = 0; u < (int)(blockDim.x >> 5); ++u) t += red[u];
-      fro2[b] = t;
-      for (int k = 0; k < 3; ++k) rot[3 * b + k] = 0;
-      done[b] = d.q <= 1 ? 1 : 0;
-      nsw[b] = 0;
-    }
-    __syncthreads();
-  }
-  if (!grid_sync(bar, gridDim.x)) return;
-  int sweep = 0;
-  for (; sweep < max_sweeps; ++sweep) {
-    for (int b = blockIdx.x * blockDim.x + threadIdx.x; b < nblk; b += gridDim.x * blockDim.x)
-      rot[3 * b + (sweep + 1) % 3] = 0;
-    for (int round = 0; round < max_rounds; ++round) {
-      for (int it = blockIdx.x; it < total_pairs; it += gridDim.x) {
-        int lo = 0, hi = nblk - 1;  // last block with pair_off[b] <= it
-        while (lo < hi) {
-          const int mid = (lo + hi + 1) >> 1;
-          if (pair_off[mid] <= it) lo = mid; else hi = mid - 1;
-        }
-        const int b = lo;
-        if (((volatile int*)done)[b]) continue;
-        const BlkDesc d = desc[b];
-        const int qpad = d.q + (d.q & 1);
-        const int k = it - pair_off[b];
-        // the device q may be below the host's (a block's rank after pivoted Cholesky):
-        // only the first qpad / 2 pair slots of the block are pairs of this round
-        if (round >= qpad - 1 || k >= qpad / 2) continue;
-        int P, Q;
-        rr_pair(round, k, qpad, P, Q);
-        if (Q >= d.q) continue;
-        const double tol = fmax(1e-15, sqrt((double)d.p) * 2.2e-16);
-        if (jacobi_pair_block(X + d.x_off, V + d.v_off, d.p, d.q, P, Q, tol, kJacobiFloor * fro2[b], 1) &&
-            threadIdx.x == 0)
-          rot[3 * b + sweep % 3] = 1;
-      }
-      if (!grid_sync(bar, gridDim.x)) return;
-    }
-    if (blockIdx.x == 0 && threadIdx.x == 0)
-      for (int b = 0; b < nblk; ++b)
-        if (!done[b] && !((volatile int*)rot)[3 * b + sweep % 3]) {
-          done[b] = 1;
-          nsw[b] = sweep + 1;
-        }
-    if (!grid_sync(bar, gridDim.x)) return;
-    int all = 1;
-    for (int b = 0; b < nblk && all; ++b) all = ((volatile int*)done)[b];
-    if (all) break;
-  }
-  // singular values: column norms of every block
-  for (int it = blockIdx.x; it < total_pairs * 2; it += gridDim.x) {
-    // columns enumerated block by block: column j of block b is item 2 * pair_off[b] + j
-    int lo = 0, hi = nblk - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (2 * pair_off[mid] <= it) lo = mid; else hi = mid - 1;
-    }
-    const int b = lo;
-    const BlkDesc d = desc[b];
-    const int j = it - 2 * pair_off[b];
-    if (j >= d.q) continue;
-    const cplx* col = X + d.x_off + (long long)j * d.p;
-    double t = 0.0;
-    for (int r = threadIdx.x; r < d.p; r += blockDim.x) t += cabs2(col[r]);
-    t = warp_sum(t);
-    if (lane == 0) red[warp] = t;
-    __syncthreads();
-    if (threadIdx.x == 0) {
-      double u = 0.0;
-      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) u += red[w];
-      s_out[d.s_off + j] = sqrt(u);
-    }
-    __syncthreads();
-  }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    int mx = 0, tot = 0, bad = 0;
-    for (int b = 0; b < nblk; ++b) {
-      const int n = done[b] ? nsw[b] : max_sweeps;
-      if (!done[b]) bad = 1;
-      mx = max(mx, n);
-      tot += n;
-    }
-    stat[0] = bad;
-    stat[1] = mx;
-    stat[2] = tot;
-  }
-}
-
 // Hermitian positive semidefinite blocks: pivoted Cholesky, in place, one CTA per
 // block.  X_b (n x n, column-major) becomes L (n x rank) with A[piv][:, piv] = L L^H;
 // elimination stops when the largest remaining diagonal entry is below
@@ -1779,52 +1662,188 @@ struct DSU {
 SvdCounters g_svd_counters;
 std::atomic<long long> g_kernel_launches{0};
 
+// Barrier of the n CTAs that work on one block (all co-resident: cooperative launch).
+// Bounded like grid_sync; a wait that runs out, or an error raised by any other
+// group (gerr), makes every waiter return false.
+__device__ bool group_sync(GridBar* b, unsigned n, int* gerr) {
+  __shared__ int ok;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    ok = 1;
+    if (n > 1) {
+      volatile unsigned* vgen = &b->gen;
+      volatile int* verr = gerr;
+      const unsigned g = *vgen;
+      __threadfence();
+      const unsigned arrived = atomicAdd(&b->count, 1u);
+      if (arrived == n - 1) {
+        atomicExch(&b->count, 0u);
+        __threadfence();
+        atomicAdd(&b->gen, 1u);
+      } else {
+        const unsigned long long t0 = gtimer();
+        while (*vgen == g) {
+          if (*verr) {
+            ok = 0;
+            break;
+          }
+          if (gtimer() - t0 > 2000000000ull) {
+            atomicExch(gerr, 1);
+            ok = 0;
+            break;
+          }
+        }
+      }
+      __threadfence();
+    }
+    if (*(volatile int*)gerr) ok = 0;
+  }
+  __syncthreads();
+  return ok != 0;
+}
+
+// Many blocks at once over the whole GPU.  The FP64 pipe of one SM is a small
+// fraction of the device's (about 8 GFLOP/s of 1.2 TFLOP/s on this part), so a block
+// wider than a few dozen columns must not sit on one SM.  One cooperative launch
+// runs the blocks of one call, each on its own group of CTAs.  Blocks are independent,
+// so a group synchronises only its own CTAs between rounds (few participants, no
+// waiting for wider blocks) and leaves as soon as its block has converged.  Group
+// b holds CTAs [cta_off[b], cta_off[b+1]); its CTA lc takes the pairs lc, lc + n_b, ...
+// of every round.  flags per block: rot[3] | sweeps; bars: one barrier per block;
+// stat: bad, max sweeps, total sweeps (atomics); gerr: any barrier that ran out.
+__global__ void __launch_bounds__(256)
+    k_jacobi_groups(cplx* __restrict__ X, cplx* __restrict__ V, const BlkDesc* __restrict__ desc,
+                    const int* __restrict__ cta_off, int nblk, int max_sweeps, double* __restrict__ fro2,
+                    int* __restrict__ flags, GridBar* __restrict__ bars, int* __restrict__ gerr,
+                    double* __restrict__ s_out, int* __restrict__ stat) {
+  __shared__ double red[8];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  int lo = 0, hi = nblk - 1;  // the block whose group holds this CTA
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (cta_off[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+  }
+  const int b = lo;
+  const int lc = blockIdx.x - cta_off[b];
+  const unsigned n_b = (unsigned)(cta_off[b + 1] - cta_off[b]);
+  const BlkDesc d = desc[b];
+  int* rot = flags + 4 * b;
+  GridBar* bar = bars + b;
+  if (lc == 0) {
+    const cplx* Xb = X + d.x_off;
+    double f = 0.0;
+    for (long long e = threadIdx.x; e < (long long)d.p * d.q; e += blockDim.x) f += cabs2(Xb[e]);
+    f = warp_sum(f);
+    if (lane == 0) red[warp] = f;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0.0;
+      for (int u = 0; u < (int)(blockDim.x >> 5); ++u) t += red[u];
+      fro2[b] = t;
+      rot[0] = rot[1] = rot[2] = 0;
+    }
+    __syncthreads();
+  }
+  if (!group_sync(bar, n_b, gerr)) return;
+  const double floor2 = kJacobiFloor * fro2[b];
+  const double tol = fmax(1e-15, sqrt((double)d.p) * 2.2e-16);
+  const int qpad = d.q + (d.q & 1);
+  int sweep = 0;
+  bool converged = d.q <= 1;
+  for (; sweep < max_sweeps && !converged; ++sweep) {
+    if (lc == 0 && threadIdx.x == 0) rot[(sweep + 1) % 3] = 0;
+    for (int round = 0; round < qpad - 1; ++round) {
+      for (int k = lc; k < qpad / 2; k += n_b) {
+        int P, Q;
+        rr_pair(round, k, qpad, P, Q);
+        if (Q >= d.q) continue;
+        if (jacobi_pair_block(X + d.x_off, V + d.v_off, d.p, d.q, P, Q, tol, floor2, 1) && threadIdx.x == 0)
+          rot[sweep % 3] = 1;
+      }
+      if (!group_sync(bar, n_b, gerr)) return;
+    }
+    converged = ((volatile int*)rot)[sweep % 3] == 0;  // every CTA of the group reads it after the barrier
+  }
+  // singular values: column norms, spread over the group
+  for (int j = lc; j < d.q; j += n_b) {
+    const cplx* col = X + d.x_off + (long long)j * d.p;
+    double t = 0.0;
+    for (int r = threadIdx.x; r < d.p; r += blockDim.x) t += cabs2(col[r]);
+    t = warp_sum(t);
+    if (lane == 0) red[warp] = t;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double u = 0.0;
+      for (int w = 0; w < (int)(blockDim.x >> 5); ++w) u += red[w];
+      s_out[d.s_off + j] = sqrt(u);
+    }
+    __syncthreads();
+  }
+  if (lc == 0 && threadIdx.x == 0) {
+    const int used = converged ? sweep : max_sweeps;
+    if (!converged) atomicExch(&stat[0], 1);
+    atomicMax(&stat[1], used);
+    atomicAdd(&stat[2], used);
+  }
+}
+
 namespace {
-// Host side of k_jacobi_multi: pair offsets, one cooperative launch, bounded-wait check.
+// Host side of k_jacobi_groups: CTA groups per block, one cooperative launch, bounded-wait check.
 // d_stat receives {bad, max sweeps, total sweeps} like the batched kernel.
 void run_jacobi_multi(cudaStream_t st, cplx* Xs, cplx* Vs, const std::vector<BlkDesc>& desc, const BlkDesc* d_desc,
                       double* d_s, int* d_stat) {
   const int nblk = (int)desc.size();
-  std::vector<int> pair_off(nblk);
-  int total = 0, rounds = 0;
-  for (int b = 0; b < nblk; ++b) {
-    const int qpad = desc[b].q + (desc[b].q & 1);
-    pair_off[b] = total;
-    total += qpad / 2;
-    rounds = std::max(rounds, qpad - 1);
-  }
   static const int max_ctas = [] {
     int dev = 0, sms = 0, per_sm = 0;
     TDVP_CUDA(cudaGetDevice(&dev));
     TDVP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    TDVP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_multi, 256, 0));
+    TDVP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_groups, 256, 0));
     return std::max(1, sms * std::min(2, std::max(1, per_sm)));
   }();
-  const int nctas = std::max(1, std::min(std::max(total, nblk), max_ctas));
+  // CTAs per block: one per pair of a round, scaled down together when they do not all fit
+  std::vector<long long> pairs(nblk);
+  long long total = 0;
+  for (int b = 0; b < nblk; ++b) {
+    pairs[b] = std::max(1, (desc[b].q + (desc[b].q & 1)) / 2);
+    total += pairs[b];
+  }
+  std::vector<int> cta_off(nblk + 1, 0);
+  const int budget = std::max(max_ctas, nblk);
+  for (int b = 0; b < nblk; ++b) {
+    long long nb = pairs[b];
+    if (total > budget - nblk) nb = std::max<long long>(1, pairs[b] * (budget - nblk) / total);
+    cta_off[b + 1] = cta_off[b] + (int)nb;
+  }
+  tdvp_require(cta_off[nblk] <= budget, TDVP_ERR_INVALID_ARG, "Jacobi groups exceed the co-resident CTAs");
+  const int nctas = cta_off[nblk];
   int* d_off = nullptr;
   int* d_flags = nullptr;
+  int* d_gerr = nullptr;
   double* d_fro2 = nullptr;
-  GridBar* bar = nullptr;
-  TDVP_CUDA(cudaMallocAsync(&d_off, sizeof(int) * nblk, st));
-  TDVP_CUDA(cudaMallocAsync(&d_flags, sizeof(int) * 5 * nblk, st));
+  GridBar* bars = nullptr;
+  TDVP_CUDA(cudaMallocAsync(&d_off, sizeof(int) * (nblk + 1), st));
+  TDVP_CUDA(cudaMallocAsync(&d_flags, sizeof(int) * 4 * nblk + sizeof(int), st));
   TDVP_CUDA(cudaMallocAsync(&d_fro2, sizeof(double) * nblk, st));
-  TDVP_CUDA(cudaMallocAsync(&bar, sizeof(GridBar), st));
-  TDVP_CUDA(cudaMemsetAsync(bar, 0, sizeof(GridBar), st));
-  TDVP_CUDA(cudaMemcpyAsync(d_off, pair_off.data(), sizeof(int) * nblk, cudaMemcpyHostToDevice, st));
-  int nb = nblk, tp = total, mr = rounds, ms = 60;
+  TDVP_CUDA(cudaMallocAsync(&bars, sizeof(GridBar) * nblk, st));
+  d_gerr = d_flags + 4 * nblk;
+  TDVP_CUDA(cudaMemsetAsync(bars, 0, sizeof(GridBar) * nblk, st));
+  TDVP_CUDA(cudaMemsetAsync(d_flags, 0, sizeof(int) * 4 * nblk + sizeof(int), st));
+  TDVP_CUDA(cudaMemsetAsync(d_stat, 0, 3 * sizeof(int), st));
+  TDVP_CUDA(cudaMemcpyAsync(d_off, cta_off.data(), sizeof(int) * (nblk + 1), cudaMemcpyHostToDevice, st));
+  int nb = nblk, ms = 60;
   const BlkDesc* dd = d_desc;
   const int* po = d_off;
-  void* args[] = {&Xs, &Vs, &dd, &po, &nb, &tp, &mr, &ms, &d_fro2, &d_flags, &bar, &d_s, &d_stat};
-  TDVP_CUDA(cudaLaunchCooperativeKernel((void*)k_jacobi_multi, dim3(nctas), dim3(256), args, 0, st));
+  void* args[] = {&Xs, &Vs, &dd, &po, &nb, &ms, &d_fro2, &d_flags, &bars, &d_gerr, &d_s, &d_stat};
+  TDVP_CUDA(cudaLaunchCooperativeKernel((void*)k_jacobi_groups, dim3(nctas), dim3(256), args, 0, st));
   g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
-  GridBar hb;
-  TDVP_CUDA(cudaMemcpyAsync(&hb, bar, sizeof(GridBar), cudaMemcpyDeviceToHost, st));
+  int herr = 0;
+  TDVP_CUDA(cudaMemcpyAsync(&herr, d_gerr, sizeof(int), cudaMemcpyDeviceToHost, st));
   TDVP_CUDA(cudaStreamSynchronize(st));
   TDVP_CUDA(cudaFreeAsync(d_off, st));
   TDVP_CUDA(cudaFreeAsync(d_flags, st));
   TDVP_CUDA(cudaFreeAsync(d_fro2, st));
-  TDVP_CUDA(cudaFreeAsync(bar, st));
-  if (hb.err) throw TdvpError(TDVP_ERR_TIMEOUT, "Jacobi SVD: a grid barrier wait ran out");
+  TDVP_CUDA(cudaFreeAsync(bars, st));
+  if (herr) throw TdvpError(TDVP_ERR_TIMEOUT, "Jacobi SVD: a group barrier wait ran out");
 }
 }  // namespace
 
