@@ -910,10 +910,12 @@ __device__ bool jacobi_pair_block(cplx* __restrict__ X, cplx* __restrict__ V, in
     b += cabs2(v);
     cfma_conj(c, u, v);
   }
-  a = warp_sum(a);
-  b = warp_sum(b);
-  c = warp_sum(c);
   const int warp = threadIdx.x >> 5;
+  if (warp * 32 < p) {  // warps past the last row hold zeros: no FP64 reduction for them
+    a = warp_sum(a);
+    b = warp_sum(b);
+    c = warp_sum(c);
+  }
   if ((threadIdx.x & 31) == 0) {
     ra[warp] = a;
     rb[warp] = b;
@@ -1382,6 +1384,7 @@ struct BlkDesc {
   int orient, p, q, nr, nc;  // nr/nc: rows/cols of the block in M
   long long x_off, v_off;
   int s_off, r_off, c_off;
+  int need_v;  // the accumulated rotations are read (V for orient 0, U for orient 1)
 };
 
 __global__ void k_gather_batched(const cplx* __restrict__ M, int cols, const BlkDesc* __restrict__ desc,
@@ -1464,13 +1467,15 @@ __global__ void __launch_bounds__(256)
           xp[r] = u;
           xq[r] = v;
         }
-        cplx* vp = Vs + P * q;
-        cplx* vq = Vs + Q * q;
-        for (int r = lane; r < q; r += 32) {
-          cplx u = vp[r], v = vq[r];
-          rotate_pair(u, v, cs, sne);
-          vp[r] = u;
-          vq[r] = v;
+        if (d.need_v) {
+          cplx* vp = Vs + P * q;
+          cplx* vq = Vs + Q * q;
+          for (int r = lane; r < q; r += 32) {
+            cplx u = vp[r], v = vq[r];
+            rotate_pair(u, v, cs, sne);
+            vp[r] = u;
+            vq[r] = v;
+          }
         }
       }
       __syncthreads();
@@ -1757,7 +1762,7 @@ __global__ void __launch_bounds__(256)
         int P, Q;
         rr_pair(round, k, qpad, P, Q);
         if (Q >= d.q) continue;
-        if (jacobi_pair_block(X + d.x_off, V + d.v_off, d.p, d.q, P, Q, tol, floor2, 1) && threadIdx.x == 0)
+        if (jacobi_pair_block(X + d.x_off, V + d.v_off, d.p, d.q, P, Q, tol, floor2, d.need_v) && threadIdx.x == 0)
           rot[sweep % 3] = 1;
       }
       if (!group_sync(bar, n_b, gerr)) return;
@@ -1921,6 +1926,7 @@ void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows
     if (multi && q >= kMultiQ) g_svd_counters.large_blocks++;
     BlkDesc d;
     d.orient = nr >= nc ? 0 : 1;
+    d.need_v = d.orient == 0 ? (want_v ? 1 : 0) : (want_u ? 1 : 0);
     d.p = p;
     d.q = q;
     d.nr = nr;
