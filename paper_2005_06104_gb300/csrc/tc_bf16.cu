@@ -85,8 +85,9 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
 template <int S>
 __global__ void __launch_bounds__(THREADS, 1)
     k_gemm_bf16s(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
-                 int nkb, const float* __restrict__ sA, long long lsA, const float* __restrict__ sB,
-                 void* __restrict__ out, long long ldo, int out_df, int* __restrict__ err) {
+                 int nkb_total, int kb_split, const float* __restrict__ sA, long long lsA,
+                 const float* __restrict__ sB, void* __restrict__ out, long long ldo, long long split_stride,
+                 int out_df, int* __restrict__ err) {
   constexpr int STAGE_BYTES = SCfg<S>::STAGE_BYTES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -100,6 +101,10 @@ __global__ void __launch_bounds__(THREADS, 1)
   volatile int* abort_flag = reinterpret_cast<volatile int*>(tmem_slot + 1);
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   const int m0 = blockIdx.y * BM, n0 = blockIdx.x * BN;
+  // split K: this CTA takes k-blocks [kb0, kb0 + nkb) (kb0 a multiple of a chunk)
+  const int kb0 = blockIdx.z * kb_split;
+  const int nkb = min(nkb_total, kb0 + kb_split) - kb0;
+  const int c0 = kb0 / KC_KB;
   const int nchunks = (nkb + KC_KB - 1) / KC_KB;
 
   if (threadIdx.x == 0) {
@@ -140,8 +145,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       uint8_t* st = smem + s * STAGE_BYTES;
       const uint32_t fb = smem_u32(&full[s]);
       mbar_expect_tx(fb, STAGE_BYTES);
-      tma_load_3d(smem_u32(st), &tmA, fb, kb * BK, m0, 0);
-      tma_load_3d(smem_u32(st + S * TILE), &tmB, fb, kb * BK, n0, 0);
+      tma_load_3d(smem_u32(st), &tmA, fb, (kb0 + kb) * BK, m0, 0);
+      tma_load_3d(smem_u32(st + S * TILE), &tmB, fb, (kb0 + kb) * BK, n0, 0);
       issued = kb + 1;
     }
     if (*abort_flag) {
@@ -211,7 +216,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       ok = __all_sync(0xffffffffu, got && !*abort_flag);
       if (!ok) break;
       fence_after();
-      const float sa = sA[(long long)c * lsA + gm];
+      const float sa = sA[(long long)(c0 + c) * lsA + gm];
 #pragma unroll
       for (int c0 = 0; c0 < EC; c0 += 8) {
         uint32_t vp[8], vq[8];
@@ -242,7 +247,7 @@ __global__ void __launch_bounds__(THREADS, 1)
       const bool vec = nb + EC <= N && (ldo & 1) == 0;
       if (out_df) {
         // double-float output: (hi, lo) FP32 pairs, scaled exactly by the power-of-two column scale
-        float2* o = static_cast<float2*>(out) + (long long)gm * ldo + nb;
+        float2* o = static_cast<float2*>(out) + blockIdx.z * split_stride + (long long)gm * ldo + nb;
 #pragma unroll
         for (int j = 0; j < EC; j += 2) {
           const float s0 = __shfl_sync(0xffffffffu, sbv.x, j >> 1);
@@ -689,8 +694,8 @@ CUtensorMap make_map3(const Sliced& o, int box_rows) {
 
 template <int S>
 void launch_bf16s(cudaStream_t st, const CUtensorMap& ma, const CUtensorMap& mb, int M, int N, int nkb,
-                  const float* sA, long long lsA, const float* sB, void* out, long long ldo, int out_df,
-                  int* d_err) {
+                  int kb_split, int splits, const float* sA, long long lsA, const float* sB, void* out,
+                  long long ldo, long long split_stride, int out_df, int* d_err) {
   static const bool attr = [] {
     // the register hand-over inside the kernel is sized for exactly this launch allocation
     cudaFuncAttributes fa;
@@ -703,29 +708,93 @@ void launch_bf16s(cudaStream_t st, const CUtensorMap& ma, const CUtensorMap& mb,
     return true;
   }();
   (void)attr;
-  dim3 grid(ceil_div(N, BN), ceil_div(M, BM));
-  tdvp_require(grid.y <= 65535, TDVP_ERR_INVALID_ARG, "gemm_bf16s: M too large");
-  k_gemm_bf16s<S><<<grid, THREADS, SCfg<S>::SMEM_BYTES, st>>>(ma, mb, M, N, nkb, sA, lsA, sB, out, ldo, out_df,
-                                                              d_err);
+  dim3 grid(ceil_div(N, BN), ceil_div(M, BM), splits);
+  tdvp_require(grid.y <= 65535 && splits <= 65535, TDVP_ERR_INVALID_ARG, "gemm_bf16s: grid too large");
+  k_gemm_bf16s<S><<<grid, THREADS, SCfg<S>::SMEM_BYTES, st>>>(ma, mb, M, N, nkb, kb_split, sA, lsA, sB, out, ldo,
+                                                              split_stride, out_df, d_err);
   TDVP_CHECK_LAUNCH();
 }
 
+// Sum of the split-K partials (double-float pairs, one [M][N] slab per split) into
+// the output: FP64, or double-float pairs when out_df.
+__global__ void k_splitk_df(const float2* __restrict__ ws, int splits, int M, int N, void* __restrict__ out,
+                            long long ldo, int out_df) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)M * N) return;
+  const long long m = e / N, n = e % N;
+  double sum = 0.0;
+  for (int z = 0; z < splits; ++z) {
+    const float2 v = ws[(long long)z * M * N + e];
+    sum += (double)v.x + (double)v.y;
+  }
+  if (out_df) {
+    const float hi = (float)sum;
+    static_cast<float2*>(out)[m * ldo + n] = make_float2(hi, (float)(sum - (double)hi));
+  } else {
+    static_cast<double*>(out)[m * ldo + n] = sum;
+  }
+}
+
+// Splits of K (whole 128-deep chunks) that minimise waves of CTAs x work per CTA:
+// few output tiles (a narrow product or a long K) would otherwise leave most SMs idle.
+int choose_splits(long long tiles, int nchunks) {
+  static const int sms = [] {
+    int dev = 0, n = 0;
+    TDVP_CUDA(cudaGetDevice(&dev));
+    TDVP_CUDA(cudaDeviceGetAttribute(&n, cudaDevAttrMultiProcessorCount, dev));
+    return n > 0 ? n : 148;
+  }();
+  int best = 1;
+  double best_t = (double)((tiles + sms - 1) / sms);
+  for (int sp = 2; sp <= std::min(32, nchunks); ++sp) {
+    const int cps = (nchunks + sp - 1) / sp;
+    const int real = (nchunks + cps - 1) / cps;
+    const double t = (double)((tiles * real + sms - 1) / sms) * cps / nchunks + 0.02;  // + reduction pass
+    if (t < 0.9 * best_t) {
+      best_t = t;
+      best = real;
+    }
+  }
+  return best;
+}
+
 // out[M x N] (row-major, ldo) = A B^T over the sliced real operands; FP64 entries, or
-// double-float (hi, lo) FP32 pairs when out_df
-void gemm_bf16s(cudaStream_t st, const Sliced& A, const Sliced& B, int M, int N, void* out, long long ldo,
-                bool out_df, int* d_err) {
+// double-float (hi, lo) FP32 pairs when out_df.  Products with few output tiles split
+// K over more CTAs (partials in a pool workspace, summed by k_splitk_df).
+void gemm_bf16s(cudaStream_t st, DevicePool* pool, const Sliced& A, const Sliced& B, int M, int N, void* out,
+                long long ldo, bool out_df, int* d_err) {
   if (M <= 0 || N <= 0) return;
   tdvp_require(A.ldk == B.ldk && A.S == B.S, TDVP_ERR_INVALID_ARG, "gemm_bf16s: operand K or slices differ");
   tdvp_require(M <= A.rows_pad && N <= B.rows_pad, TDVP_ERR_INVALID_ARG, "gemm_bf16s: operand rows");
   tdvp_require(!A.row_scale && B.row_scale, TDVP_ERR_INVALID_ARG, "gemm_bf16s: operand scaling groups");
   const CUtensorMap ma = make_map3(A, BM), mb = make_map3(B, BN);
   const int nkb = A.ldk / BK;
+  const int nchunks = (nkb + KC_KB - 1) / KC_KB;
+  const long long tiles = (long long)ceil_div(N, BN) * ceil_div(M, BM);
+  const int splits = pool ? choose_splits(tiles, nchunks) : 1;
+  const int kb_split = splits > 1 ? ((nchunks + splits - 1) / splits) * KC_KB : nkb;
+  RawBuf ws;
+  void* dst = out;
+  long long ld = ldo, stride = 0;
+  int df = out_df ? 1 : 0;
+  if (splits > 1) {
+    ws.ensure(pool, sizeof(float2) * (size_t)splits * M * N);
+    dst = ws.as<void>();
+    ld = N;
+    stride = (long long)M * N;
+    df = 1;
+  }
   if (A.S == 4)
-    launch_bf16s<4>(st, ma, mb, M, N, nkb, A.scale.as<float>(), A.rows_pad, B.scale.as<float>(), out,
-                    ldo, out_df ? 1 : 0, d_err);
+    launch_bf16s<4>(st, ma, mb, M, N, nkb, kb_split, splits, A.scale.as<float>(), A.rows_pad, B.scale.as<float>(),
+                    dst, ld, stride, df, d_err);
   else
-    launch_bf16s<3>(st, ma, mb, M, N, nkb, A.scale.as<float>(), A.rows_pad, B.scale.as<float>(), out,
-                    ldo, out_df ? 1 : 0, d_err);
+    launch_bf16s<3>(st, ma, mb, M, N, nkb, kb_split, splits, A.scale.as<float>(), A.rows_pad, B.scale.as<float>(),
+                    dst, ld, stride, df, d_err);
+  if (splits > 1) {
+    const long long n = (long long)M * N;
+    k_splitk_df<<<ceil_div(n, 256), 256, 0, st>>>(ws.as<float2>(), splits, M, N, out, ldo, out_df ? 1 : 0);
+    TDVP_CHECK_LAUNCH();
+  }
 }
 }  // namespace tcb
 
@@ -776,14 +845,14 @@ void heff_bf16s(cudaStream_t st, Scratch& s, const SiteOp& op, const cplx* x, cp
   slice(st, SrcB{x, (long long)d * mr, ml, d * mr, OP_N}, c.X);
   const int M1 = ml * wl, N1 = 2 * d * mr;
   c.T1.ensure(pool, sizeof(float2) * (size_t)M1 * N1);  // double-float
-  gemm_bf16s(st, c.L, c.X, M1, N1, c.T1.as<void>(), N1, true, err);
+  gemm_bf16s(st, pool, c.L, c.X, M1, N1, c.T1.as<void>(), N1, true, err);
   // stage 2: MPO tensor, sliced straight into the stage-3 A operand
   const WSparse& ws = *op.W;
   c.T2.shape(pool, S, ml * d, 2 * wr * mr, false);
   tdvp_require(ws.d_l_val_df != nullptr, TDVP_ERR_INVALID_ARG, "heff_bf16s: MPO site without double-float values");
   slice(st, SrcStage2{c.T1.as<float4>(), ws.d_l_off, ws.d_l_idx, ws.d_l_val_df, ml, wl, wr, d, mr}, c.T2);
   // stage 3: y[(a,s)][(b,c)] = T2 R^T
-  gemm_bf16s(st, c.T2, c.R, ml * d, 2 * mr, y, 2 * mr, false, err);
+  gemm_bf16s(st, pool, c.T2, c.R, ml * d, 2 * mr, y, 2 * mr, false, err);
 }
 
 void zgemm_bf16s(cudaStream_t st, Scratch& s, int S, int opA, int opB, int M, int N, int K, const cplx* A,
@@ -796,5 +865,5 @@ void zgemm_bf16s(cudaStream_t st, Scratch& s, int S, int opA, int opB, int M, in
   slice(st, SrcA{A, lda, M, K, opA}, a);
   b.shape(pool, S, 2 * N, 2 * std::max(K, 1), true);
   slice(st, SrcB{B, ldb, K, N, opB}, b);
-  gemm_bf16s(st, a, b, M, 2 * N, C, 2 * ldc, false, err);
+  gemm_bf16s(st, pool, a, b, M, 2 * N, C, 2 * ldc, false, err);
 }
