@@ -395,13 +395,13 @@ def run_gpu(args):
     else:
         products, peak, peak_src = 1, 1.25, "nominal FP64 (no tensor cores)"
         kern = f"H_eff apply (FP64 CUDA cores) at chi={args.heff_chi}, w=14"
-    # DRAM bytes of one apply (its 4 launches), from the ncu capture of these kernels at
+    # DRAM bytes of one apply (its 5 launches), from the ncu capture of these kernels at
     # chi = 1024, w = 14 in BF16X10; other configurations have no capture
     traffic, traffic_src = None, None
     if args.precision == "bf16x10" and args.heff_chi == 1024:
-        traffic = 4.70e9
-        traffic_src = ("ncu dram__bytes_read.sum + dram__bytes_write.sum over the 4 launches of one cached "
-                       "apply (slice x, GEMM 1, MPO stage, GEMM 3) of these kernels")
+        traffic = 5.11e9
+        traffic_src = ("ncu dram__bytes_read.sum + dram__bytes_write.sum over the 5 launches of one cached "
+                       "apply (slice x, GEMM 1, MPO stage, GEMM 3 split 4 ways, split-K sum) of these kernels")
     cpu = None
     if not args.no_cpu_baseline:
         try:

@@ -152,6 +152,30 @@ def test_gse_imaginary_time_decoupled_ladder(g):
     st.close()
 
 
+def test_precision_form_imaginary_time(g):
+    """Imaginary time on the rung-coupled ladder (config 2's kind of run): the BF16X10 form
+    follows the FP64 form to relative 1e-7 in energy at every step and both approach the
+    ground state from above."""
+    lat = wl.zigzag_ladder(6, 1.0, 1.0)
+    W = wl.heisenberg_mpo(lat)
+    psi = wl.random_product_state(lat.n, 1)
+    lam = wl.lambda_top(lat)
+    kw = dict(tau=-1j / lam, eps_k=1e-10, eps_m=1e-8, chi_max=48, eps=1e-10)
+    a = g.GseTdvp(psi, W, precision=g.PREC_FP64, **kw)
+    b = g.GseTdvp(psi, W, precision=g.PREC_BF16X10, **kw)
+    e_prev = a.energy()
+    for _ in range(6):
+        a.step(0.2, g.IMAG, 3)
+        b.step(0.2, g.IMAG, 3)
+        ea, eb = a.energy(), b.energy()
+        assert abs(eb - ea) <= 1e-7 * abs(ea)
+        assert abs(b.norm() - 1) < 1e-10
+        assert ea <= e_prev + 1e-12
+        e_prev = ea
+    a.close()
+    b.close()
+
+
 @pytest.mark.parametrize("prec", ["tf32x3", "bf16x10"])
 def test_precision_form_energy_and_norm(g, prec):
     """Tensor-core sweeps hold relative energy error <= 1e-7 and norm drift <= 1e-10 per step
