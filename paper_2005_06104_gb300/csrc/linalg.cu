@@ -859,13 +859,15 @@ __device__ __forceinline__ bool jacobi_params(double a, double b, cplx c, double
                                               double& cs, cplx& sne) {
   const double big = fmax(a, b), small = fmin(a, b);
   if (big <= floor2 || small <= kJacobiFloor * big) return false;
-  const double ac = sqrt(cabs2(c));
-  if (!(ac > tol * sqrt(a * b)) || ac == 0.0) return false;
-  const double zeta = (b - a) / (2.0 * ac);
+  const double ac2 = cabs2(c);
+  // |c| > tol sqrt(a b), squared (no square root on the common no-rotation path)
+  if (!(ac2 > tol * tol * a * b)) return false;
+  const double inv_ac = rsqrt(ac2);
+  const double zeta = 0.5 * (b - a) * inv_ac;
   const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-  cs = 1.0 / sqrt(1.0 + t * t);
-  const double sn = cs * t;
-  sne = mkc(sn * c.x / ac, sn * c.y / ac);  // sn e^{i phi}
+  cs = rsqrt(1.0 + t * t);
+  const double sn_ac = cs * t * inv_ac;
+  sne = mkc(sn_ac * c.x, sn_ac * c.y);  // sn e^{i phi}
   return true;
 }
 
@@ -1803,7 +1805,7 @@ void run_jacobi_multi(cudaStream_t st, cplx* Xs, cplx* Vs, const std::vector<Blk
     TDVP_CUDA(cudaGetDevice(&dev));
     TDVP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
     TDVP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_groups, 256, 0));
-    return std::max(1, sms * std::min(2, std::max(1, per_sm)));
+    return std::max(1, sms * std::min(4, std::max(1, per_sm)));
   }();
   // CTAs per block: one per pair of a round, scaled down together when they do not all fit
   std::vector<long long> pairs(nblk);
