@@ -82,6 +82,8 @@ __global__ void k_one(cplx* p) { p[0] = mkc(1.0, 0.0); }
 // Right density environment, last stage:
 // F[w][a][wb][ab] = sum_{(t,v,tb,vb)} Om[(w,wb),(t,v,tb,vb)] T2[v][a][t][vb][ab][tb],
 // Om[(w,wb),(t,v,tb,vb)] = sum_s W[w,s,t,v] conj(W[wb,s,tb,vb]).
+// T2 rows (a, t, v, vb), columns (ab, tb); F out as [a][w][wb][ab] (row index a outermost,
+// the layout the next site's single GEMM reads)
 __global__ void k_omega_stage(const cplx* __restrict__ T2, cplx* __restrict__ F, int ml, int d, int wl, int wr,
                               const int* __restrict__ off, const int* __restrict__ idx,
                               const cplx* __restrict__ val) {
@@ -92,11 +94,21 @@ __global__ void k_omega_stage(const cplx* __restrict__ T2, cplx* __restrict__ F,
   cplx acc = mkc(0.0, 0.0);
   for (int e = off[pr]; e < off[pr + 1]; ++e) {
     const int t = idx[4 * e], v = idx[4 * e + 1], tb = idx[4 * e + 2], vb = idx[4 * e + 3];
-    const long long o = (((((long long)v * ml + a) * d + t) * wr + vb) * ml + ab) * d + tb;
+    const long long o = ((((a * d + t) * wr + v) * wr + vb) * ml + ab) * d + tb;
     cfma(acc, val[e], T2[o]);
   }
   const int w = pr / wl, wb = pr % wl;
-  F[(((long long)w * ml + a) * wl + wb) * ml + ab] = acc;
+  F[((a * wl + w) * wl + wb) * ml + ab] = acc;
+}
+
+// F[v][b][x] from Fp[b][v][x] (x: the wr * m contiguous trailing entries)
+__global__ void k_swap_outer(const cplx* __restrict__ Fp, cplx* __restrict__ F, int m, int wr) {
+  const long long inner = (long long)wr * m;
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)m * wr * inner) return;
+  const long long x = e % inner, vb = e / inner;  // vb = v * m + b (destination order)
+  const long long v = vb / m, b = vb % m;
+  F[e] = Fp[(b * wr + v) * inner + x];
 }
 }  // namespace
 
@@ -563,7 +575,8 @@ void KrylovOp::release() {
 
 // One Krylov vector by the density-matrix approach (Sec. I.B): out = (1 - i tau H) src
 // compressed left to right with cutoff eps_k and cap chi_max, then normalised.
-// R->L: right density environments F_i[v][b][vb][bb] of (W src)(W src)^+ over sites > i.
+// R->L: right density environments F_i of (W src)(W src)^+ over sites > i, held as
+// [b][v][vb][bb] (one GEMM per site reads them) and reordered to [v][b][vb][bb] when read.
 // L->R: X[at][w][a] = <compressed left | exact left>; at site i
 //   G[(at,s),(v,b)] = sum W[w,s,t,v] X[at,w,a] A[a,t,b],  rho = G F_i G^+ (size d m~),
 //   its leading eigenvectors are the new left-orthonormal tensor, X <- U^+ G.
@@ -584,15 +597,11 @@ void Engine::krylov_apply(const KrylovOp& kop, const MpsDev& src, MpsDev& out) {
     const int ml = src.m[i], m = src.m[i + 1], wl = w[i], wr = w[i + 1];
     const cplx* A = src.A[i].data();
     T1.ensure(&pool, (size_t)wr * ml * d * wr * m);
-    // T1[v][(a,t)][(vb,bb)] = sum_b A[(a,t),b] F[v][b][(vb,bb)]
-    if (kp == TDVP_PREC_FP64)
-      zgemm(st, OP_N, OP_N, ml * d, wr * m, m, one, A, m, F[i].data(), (long long)wr * m, zero, T1.data(),
-            (long long)wr * m, wr, 0, (long long)m * wr * m, (long long)ml * d * wr * m, &pool);
-    else
-      for (int v = 0; v < wr; ++v)
-        zgemm_prec(st, scr, kp, OP_N, OP_N, ml * d, wr * m, m, A, m, F[i].data() + (long long)v * m * wr * m,
-                   (long long)wr * m, T1.data() + (long long)v * ml * d * wr * m, (long long)wr * m);
-    // T2[(v,a,t,vb),(ab,tb)] = sum_bb T1[(v,a,t,vb),bb] conj(A[(ab,tb),bb])
+    // F[i] is held as [b][v][vb][bb]: one GEMM over all channels,
+    // T1[(a,t)][(v,vb,bb)] = sum_b A[(a,t),b] F[b][(v,vb,bb)]
+    zgemm_prec(st, scr, kp, OP_N, OP_N, ml * d, wr * wr * m, m, A, m, F[i].data(), (long long)wr * wr * m,
+               T1.data(), (long long)wr * wr * m);
+    // T2[(a,t,v,vb),(ab,tb)] = sum_bb T1[(a,t,v,vb),bb] conj(A[(ab,tb),bb])
     T2.ensure(&pool, (size_t)wr * ml * d * wr * ml * d);
     zgemm_prec(st, scr, kp, OP_N, OP_C, wr * ml * d * wr, ml * d, m, T1.data(), m, A, m, T2.data(), ml * d);
     F[i - 1].reset(&pool, (size_t)wl * ml * wl * ml);
@@ -627,6 +636,14 @@ void Engine::krylov_apply(const KrylovOp& kop, const MpsDev& src, MpsDev& out) {
     }
     const int n = mt * d, K = wr * mr;
     H1.ensure(&pool, (size_t)n * K);
+    {
+      // the right density environment in the row order of G's columns: [v][b][vb][bb]
+      DArr Fv(&pool, (size_t)K * K);
+      const long long ne = (long long)K * K;
+      k_swap_outer<<<ceil_div(ne, 256), 256, 0, st>>>(F[i].data(), Fv.data(), mr, wr);
+      TDVP_CHECK_LAUNCH();
+      F[i] = std::move(Fv);
+    }
     zgemm_prec(st, scr, kp, OP_N, OP_N, n, K, K, G.data(), K, F[i].data(), K, H1.data(), K);
     rho.ensure(&pool, (size_t)n * n);
     zgemm_prec(st, scr, kp, OP_N, OP_C, n, n, K, H1.data(), K, G.data(), K, rho.data(), n);

@@ -927,7 +927,8 @@ __device__ bool jacobi_pair_block(cplx* __restrict__ X, cplx* __restrict__ V, in
   if (threadIdx.x == 0) {
     double A = 0, B = 0;
     cplx Cc = mkc(0, 0);
-    for (int u = 0; u < (int)(blockDim.x >> 5); ++u) {
+    const int active = min((int)(blockDim.x >> 5), (p + 31) >> 5);  // the others hold exact zeros
+    for (int u = 0; u < active; ++u) {
       A += ra[u];
       B += rb[u];
       Cc = cadd(Cc, rc[u]);
