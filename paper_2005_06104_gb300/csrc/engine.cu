@@ -800,11 +800,14 @@ void Engine::expand_basis(int k, const double* weights) {
     for (int l = 0; l < nk; ++l) {
       MpsDev& ph = phis[l];
       const int mlp = ph.m[i], mlp0 = ph.m[i - 1];
+      // the Krylov vectors only feed rho~ of the next bond (the basis they enrich, never
+      // |psi> itself), so their centre moves run in the precision form
       DArr Gl(&pool, (size_t)mlp * mnew);
-      zgemm(st, OP_N, OP_C, mlp, mnew, cols, kOne, ph.A[i].data(), cols, Bp.data(), cols, kZero, Gl.data(), mnew, 1, 0, 0, 0, &pool);
+      zgemm_prec(st, scr, opt.precision, OP_N, OP_C, mlp, mnew, cols, ph.A[i].data(), cols, Bp.data(), cols,
+                 Gl.data(), mnew);
       DArr pp(&pool, (size_t)mlp0 * d * mnew);
-      zgemm(st, OP_N, OP_N, mlp0 * d, mnew, mlp, kOne, ph.A[i - 1].data(), mlp, Gl.data(), mnew, kZero, pp.data(),
-            mnew, 1, 0, 0, 0, &pool);
+      zgemm_prec(st, scr, opt.precision, OP_N, OP_N, mlp0 * d, mnew, mlp, ph.A[i - 1].data(), mlp, Gl.data(), mnew,
+                 pp.data(), mnew);
       ph.A[i - 1] = std::move(pp);
       ph.A[i].release();
       ph.m[i] = mnew;
