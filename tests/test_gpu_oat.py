@@ -31,6 +31,9 @@ def test_oat_sx_follows_closed_form(g, prec):
     st = g.GseTdvp(wl.x_polarized_state(n), W, tau=dt, eps_k=gd["eps_k"], eps_m=gd["eps_m"], chi_max=64,
                    precision=g.PREC_FP64 if prec == "fp64" else g.PREC_BF16X10)
     e0 = st.energy()
+    # <S^y> and <S^z> vanish by symmetry.  The precision form is held to a 1e-7 relative error,
+    # taken here against the spin length N/2; FP64 to 1e-7 absolute.
+    tol_sym = 1e-7 if prec == "fp64" else 1e-7 * 0.5 * n
     for step in range(1, gd["steps"] + 1):
         st.step(dt, g.REAL, gd["k"])
         t = step * dt
@@ -39,7 +42,7 @@ def test_oat_sx_follows_closed_form(g, prec):
         sz = sum(st.expect_local(wl.SZ, i).real for i in range(n))
         assert abs(sx - gd["sx"][step - 1]) < gd["tol_sx"]
         assert abs(sx - 0.5 * n * np.cos(t) ** (n - 1)) < gd["tol_sx"]
-        assert abs(sy) < 1e-7 and abs(sz) < 1e-7
+        assert abs(sy) < tol_sym and abs(sz) < tol_sym
         assert abs(st.energy() - e0) < 1e-7 * max(1.0, abs(e0))
     st.close()
 
