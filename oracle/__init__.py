@@ -5,3 +5,4 @@ baseline leg of the benchmark may import this package; the product path (the
 CUDA library and its binding) never does, and shares no code with it.
 """
 from .gse_tdvp1 import *  # noqa: F401,F403
+from .tdvp2 import heff2_apply, tdvp2_sweep  # noqa: F401
