@@ -47,6 +47,7 @@ def parse():
     ap.add_argument("--dt", type=float, default=0.1)
     ap.add_argument("--heff-chi", type=int, default=1024, help="bond dimension of the H_eff roofline probe")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-tdvp2", action="store_true", help="skip the TDVP2 step of the comparison")
     ap.add_argument("--heff-probe", action="store_true",
                     help="only time the tensor-core H_eff apply at --heff-chi (the profiling target)")
     ap.add_argument("--precision", default="bf16x10", choices=sorted(PRECISIONS),
@@ -363,6 +364,25 @@ def run_gpu(args):
     ms_tc = timed_step(b_)
     e_tc, n_tc = b_.energy(), b_.norm()
     b_.close()
+    # the conventional two-site TDVP from the same state at the same bond-dimension cap
+    # (Sec. I.C compares a GSE-TDVP1 step with a TDVP2 step at equal bond dimension)
+    tdvp2 = None
+    if not args.no_tdvp2:
+        c_ = g.GseTdvp(start_state, W, stream=stream, **opts)
+        c_.trace(True)
+        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        ea.record()
+        c_.sweep2(args.dt, g.REAL)
+        eb.record()
+        eb.synchronize()
+        ms_2 = ea.elapsed_time(eb)
+        tdvp2 = {"step_ms": ms_2, "gse_tdvp1_step_ms": ms_tc, "gse_tdvp1_over_tdvp2": ms_tc / ms_2,
+                 "paper_ratio_cpu": 0.36, "bond_dim_max": max(c_.bond_dims()),
+                 "energy": c_.energy(), "discarded_weight": c_.trunc_stats()["disc_eps"],
+                 "phases_ms": c_.trace_read(),
+                 "what": "one TDVP2 step (tdvp_sweep2, same precision form, cap chi_max, eps = 0) from the "
+                         "state the timed GSE-TDVP1 steps started from"}
+        c_.close()
     # e2e through the public API: host state in, one step, full state out
     e2e_ts = []
     h2d = sum(x.nbytes for x in start_state) + sum(w.nbytes for w in W)
@@ -429,6 +449,7 @@ def run_gpu(args):
                               "step_ms_precision_form": ms_tc, "step_ms_fp64": ms_64,
                               "speedup_over_fp64": ms_64 / ms_tc,
                               "rel_energy_err": abs(e_tc - e_64) / abs(e_64), "norm_drift": abs(n_tc - 1.0)},
+        "tdvp2_comparison": tdvp2,
         "energy_conservation": {"E_initial": e_init, "E_after_timed_steps": e_end, "abs_drift": abs(e_end - e_init)},
         "step_stats": nfo,
         "phases_ms_per_step": phases,

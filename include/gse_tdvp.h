@@ -91,7 +91,8 @@ typedef struct {
                               tau = dt; imaginary time: i tau = 1/lambda (Sec. I.B) */
   double eps_k;            /* cutoff applying 1 - i tau H (Sec. I.B, eps_K)         */
   double eps_m;            /* cutoff of the mixed density matrix, Eq. 6 (eps_M)     */
-  double eps;              /* cutoff inside the TDVP1 sweep, imaginary time (eps)   */
+  double eps;              /* cutoff inside the TDVP1 sweep, imaginary time (eps);
+                              also of the two-site SVDs of tdvp_sweep2, both kinds  */
   int chi_max;             /* cap on every bond dimension (state and Krylov vectors)*/
   double lanczos_tol;      /* local exponential error target                        */
   int lanczos_max;         /* maximum Krylov dimension of the local exponential     */
@@ -127,6 +128,17 @@ TDVP_API tdvp_status tdvp_canonicalize(tdvp_handle* h, int site);
  * all ones.  k = 1 only moves the centre to site 0.  The state is unchanged. */
 TDVP_API tdvp_status tdvp_expand_basis(tdvp_handle* h, int k, const double* weights);
 
+/* Memory of the density-matrix Krylov step (Sec. I.B).  Its right density
+ * environments F_j hold (w_{j+1} m_{j+1})^2 complex entries each (about 3.3 GB per
+ * site at m = 1024, w = 14).  When their sum exceeds max_bytes, only every K-th
+ * (K = ceil(sqrt(N))) stays on the device and the others are rebuilt, segment by
+ * segment, when the left-to-right pass needs them: the same launches on the same
+ * inputs, so the Krylov vectors are bit-identical, for at most one extra pass of
+ * density-environment work.  max_bytes = 0 (the default) uses half of the free
+ * device memory; max_bytes < 0 leaves the setting unchanged.  *last_segment
+ * (optional) receives K of the last Krylov step, 1 when every F_j stayed. */
+TDVP_API tdvp_status tdvp_krylov_memory(tdvp_handle* h, double max_bytes, int* last_segment);
+
 /* One Krylov vector in place (Eq. 10 with l = 1, Sec. I.B): the state becomes
  * (1 - i tau H)|psi>, applied by the density-matrix approach with cutoff eps_k
  * and cap chi_max, normalised, left-canonical with the centre at site N-1.
@@ -139,6 +151,21 @@ TDVP_API tdvp_status tdvp_apply_krylov(tdvp_handle* h);
  * exponential, truncating with eps and chi_max.  Starts by moving the centre to
  * site 0 if needed; ends with the centre at site 0. */
 TDVP_API tdvp_status tdvp_sweep(tdvp_handle* h, double dt, tdvp_time kind);
+
+/* One symmetric two-site TDVP step (TDVP2): the conventional integrator that
+ * GSE-TDVP1 is compared with (Introduction; Sec. I.C, cost at equal bond
+ * dimension; Fig. 1(c)).  Left to right then right to left, each with dt/2.
+ * Per bond (i, i+1): Theta = A_i A_{i+1} is evolved forward under the two-site
+ * H_eff (the one-site contraction with the merged MPO of sites i and i+1,
+ * physical dimension d^2), split by an SVD that keeps s > 1e-10 s_max and
+ * truncates with eps and chi_max in real AND imaginary time, and the new
+ * one-site centre is evolved backward under the one-site H_eff (omitted at the
+ * last bond of each half-sweep).  TDVP_IMAG renormalises after every local
+ * exponential.  Contractions use options.precision; SVDs, Lanczos and gauge
+ * products stay FP64.  Needs N >= 2 (else TDVP_ERR_SHAPE).  Starts by moving
+ * the centre to site 0; ends with the centre at site 0.  No basis extension is
+ * involved; tdvp_trunc_stats reports the discarded weight under "eps". */
+TDVP_API tdvp_status tdvp_sweep2(tdvp_handle* h, double dt, tdvp_time kind);
 
 /* One-site effective Hamiltonian at `site` (the operator whose exponential the
  * TDVP1 sweep applies, Sec. I.C step 3; cost O(m^3 w d)):
@@ -248,8 +275,13 @@ TDVP_API tdvp_status tdvp_profile_read(tdvp_handle* h, double* out3);
  * of the sweep's gauge moves, 3 environment updates, 4 Krylov vectors (step 1),
  * 5 basis extension (step 2), 6 gauge moves of tdvp_canonicalize, 7 right
  * density environments of the Krylov vectors, 8 their eigendecompositions,
- * 9 SVDs of the extension.  Intervals nest (3 runs inside 0..2, 7-8 inside 4,
- * 9 inside 5), so the entries do not add up. */
+ * 9 SVDs of the extension; inside every blocked SVD or eigendecomposition of
+ * 2, 6, 8, 9: 10 block detection (nonzero mask, host union-find, gather),
+ * 11 pivoted Cholesky of density matrices, 12 Jacobi sweeps, 13 selection and
+ * scatter of the kept vectors.  Intervals nest (3 runs inside 0..2, 7-8 inside
+ * 4, 9 inside 5, 10-13 inside the factorisations), so the entries do not add
+ * up.  n may be smaller or larger than 14; missing phases are left out,
+ * entries past the last phase are zero. */
 TDVP_API tdvp_status tdvp_trace(tdvp_handle* h, int enable);
 TDVP_API tdvp_status tdvp_trace_read(tdvp_handle* h, double* out, int n);
 

@@ -11,6 +11,12 @@ namespace {
 template <class F>
 tdvp_status guarded(tdvp_handle* h, F&& f) {
   if (!h) return TDVP_ERR_INVALID_ARG;
+  // the factorisations of this call record their phases on the handle's tracer
+  struct Bind {
+    Tracer* prev;
+    explicit Bind(Tracer* t) : prev(t_tracer) { t_tracer = t; }
+    ~Bind() { t_tracer = prev; }
+  } bind(h->eng.tracer.on ? &h->eng.tracer : nullptr);
   try {
     f();
     h->err.clear();
@@ -131,6 +137,22 @@ tdvp_status tdvp_sweep(tdvp_handle* h, double dt, tdvp_time kind) {
     tdvp_require(std::isfinite(dt), TDVP_ERR_INVALID_ARG, "dt not finite");
     tdvp_require(kind == TDVP_REAL || kind == TDVP_IMAG, TDVP_ERR_INVALID_ARG, "bad time kind");
     h->eng.sweep(dt, kind);
+  });
+}
+
+tdvp_status tdvp_krylov_memory(tdvp_handle* h, double max_bytes, int* last_segment) {
+  return guarded(h, [&] {
+    tdvp_require(std::isfinite(max_bytes), TDVP_ERR_INVALID_ARG, "max_bytes not finite");
+    if (max_bytes >= 0.0) h->eng.krylov_mem_budget = max_bytes;
+    if (last_segment) *last_segment = h->eng.krylov_env_segment;
+  });
+}
+
+tdvp_status tdvp_sweep2(tdvp_handle* h, double dt, tdvp_time kind) {
+  return guarded(h, [&] {
+    tdvp_require(std::isfinite(dt), TDVP_ERR_INVALID_ARG, "dt not finite");
+    tdvp_require(kind == TDVP_REAL || kind == TDVP_IMAG, TDVP_ERR_INVALID_ARG, "bad time kind");
+    h->eng.sweep2(dt, kind);
   });
 }
 

@@ -102,6 +102,12 @@ class DevicePool {
   }
   ~DevicePool() { trim(); }
   size_t live_bytes() const { return live_bytes_; }
+  // bytes held in the free lists (allocated from the device, not in use)
+  size_t cached_bytes() const {
+    size_t b = 0;
+    for (const auto& kv : free_) b += kv.first * kv.second.size();
+    return b;
+  }
   static size_t size_class(size_t bytes) {
     size_t c = 4096;
     while (c < bytes) c <<= 1;

@@ -174,6 +174,7 @@ void Engine::init(const tdvp_mps_desc* mps, const tdvp_mpo_desc* mpo, const tdvp
 
 void Engine::release() {
   for (auto& ws : Wsp) ws.free_device();
+  for (auto& ws : Wsp2) ws.free_device();
   lw.release();
   blas.release();
   for (auto& p : ev_pairs) {
@@ -252,8 +253,55 @@ SiteOp Engine::site_op(int i) {
   return op;
 }
 
-void Engine::heff(int site, const cplx* x, cplx* y, int precision) {
-  const SiteOp op = site_op(site);
+SiteOp Engine::pair_op(int i) {
+  SiteOp op;
+  op.L = L[i].data();
+  op.R = R[i + 1].data();
+  op.W = &Wsp2[i];
+  op.ml = psi.m[i];
+  op.mr = psi.m[i + 2];
+  op.wl = w[i];
+  op.wr = w[i + 2];
+  op.d = d * d;
+  op.env_key = ((long long)(N + i) << 40) ^ env_epoch;  // key space apart from the one-site operators
+  return op;
+}
+
+// W2[w, (s t), (s' t'), u] = sum_v W_i[w, s, s', v] W_{i+1}[v, t, t', u]: the two-site
+// effective Hamiltonian is the one-site one with physical dimension d^2, acting on
+// Theta[a][(s t)][b] = sum_k A_i[a][s][k] A_{i+1}[k][t][b] in the one-site layout.
+void Engine::build_pair_mpo() {
+  if ((int)Wsp2.size() == N - 1) return;
+  Wsp2.resize(std::max(N - 1, 0));
+  const int D = d * d;
+  for (int i = 0; i + 1 < N; ++i) {
+    const int wl = w[i], wm = w[i + 1], wr = w[i + 2];
+    std::vector<cplx> W2((size_t)wl * D * D * wr, kZero);
+    const std::vector<cplx>& A = W_host[i];
+    const std::vector<cplx>& B = W_host[i + 1];
+    for (int a = 0; a < wl; ++a)
+      for (int s = 0; s < d; ++s)
+        for (int sp = 0; sp < d; ++sp)
+          for (int v = 0; v < wm; ++v) {
+            const cplx x = A[((a * d + s) * d + sp) * wm + v];
+            if (x.x == 0.0 && x.y == 0.0) continue;
+            for (int t = 0; t < d; ++t)
+              for (int tp = 0; tp < d; ++tp)
+                for (int u = 0; u < wr; ++u) {
+                  const cplx y = B[((v * d + t) * d + tp) * wr + u];
+                  if (y.x == 0.0 && y.y == 0.0) continue;
+                  cplx& e = W2[((a * D + s * d + t) * D + sp * d + tp) * wr + u];
+                  e = cadd(e, cmul(x, y));
+                }
+          }
+    Wsp2[i].build(W2.data(), wl, wr, D);
+    Wsp2[i].upload();
+  }
+}
+
+void Engine::heff(int site, const cplx* x, cplx* y, int precision) { apply_op(site_op(site), x, y, precision); }
+
+void Engine::apply_op(const SiteOp& op, const cplx* x, cplx* y, int precision) {
   if (!profile) {
     heff_apply_prec(st, scr, op, x, y, precision);
     return;
@@ -495,6 +543,117 @@ void Engine::sweep(double dt, int kind) {
 }
 
 // ============================================================================
+// Two-site TDVP (TDVP2): the conventional integrator GSE-TDVP1 is compared with
+// (Introduction; Sec. I.C).  Per bond, the two-site centre Theta = A_i A_{i+1} is
+// evolved by dt/2 under the two-site H_eff, split by a truncated SVD (cutoff eps and
+// cap chi_max in real and imaginary time), and the new one-site centre is evolved
+// back by dt/2 under the one-site H_eff, except at the last bond of a half-sweep.
+// ============================================================================
+void Engine::sweep2(double dt, int kind) {
+  tdvp_require(N >= 2, TDVP_ERR_SHAPE, "TDVP2 needs at least two sites");
+  build_pair_mpo();
+  canonicalize(0);
+  const double delta = 0.5 * dt;
+  const bool imag = kind == TDVP_IMAG;
+  const int prec = opt.precision;
+  const int want_env = (prec == TDVP_PREC_TF32X3_ENV) ? TDVP_PREC_TF32X3 : prec_is_bf16(prec) ? prec : TDVP_PREC_FP64;
+  if (want_env != TDVP_PREC_FP64)
+    for (int j = 0; j < N; ++j) Lok[j] = Rok[j] = 0;
+  env_prec = want_env;
+  for (int i = 0; i < N; ++i) ensure_R(i);
+  ensure_L(0);
+  lanczos_iters = lanczos_calls = 0;
+  disc_eps = 0.0;
+  SvdRule rule;
+  rule.eps = opt.eps;
+  rule.cap = opt.chi_max;
+  rule.discarded = &disc_eps;
+  DArr theta, y;
+  auto normalize = [&](cplx* v, long long n) {
+    blas.norm2(st, v, n, lw.real + 140);
+    scale_by_inv_sqrt(st, v, v, lw.real + 140, n);
+  };
+  // y <- exp(-i delta H_eff^(2)) A_i A_{i+1}, then its SVD as (m_i d) x (d m_{i+2})
+  auto evolve_split = [&](int i, SvdOut& sv) {
+    const int ml = psi.m[i], m = psi.m[i + 1], mr = psi.m[i + 2];
+    const long long n = (long long)ml * d * d * mr;
+    theta.ensure(&pool, n);
+    y.ensure(&pool, n);
+    zgemm(st, OP_N, OP_N, ml * d, d * mr, m, kOne, psi.A[i].data(), m, psi.A[i + 1].data(), d * mr, kZero,
+          theta.data(), d * mr, 1, 0, 0, 0, &pool);
+    const SiteOp op = pair_op(i);
+    {
+      PhaseScope ps(tracer, PH_LANCZOS_SITE);
+      lanczos([&](const cplx* a, cplx* b) { apply_op(op, a, b, prec); }, theta.data(), y.data(), n, delta, kind);
+    }
+    if (imag) normalize(y.data(), n);
+    PhaseScope ps(tracer, PH_SVD);
+    svd_jacobi(st, &pool, y.data(), ml * d, d * mr, rule, sv, true, true);
+    tdvp_require(sv.rank >= 1, TDVP_ERR_NONFINITE, "sweep2: zero two-site tensor");
+  };
+  // C <- exp(+i delta H_eff^(1)) C on site j (the backward step)
+  auto evolve_back = [&](int j, DArr& C) {
+    const long long n = (long long)psi.m[j] * d * psi.m[j + 1];
+    DArr out(&pool, n);
+    {
+      PhaseScope ps(tracer, PH_LANCZOS_BOND);
+      lanczos([&](const cplx* a, cplx* b) { heff(j, a, b, prec); }, C.data(), out.data(), n, -delta, kind);
+    }
+    if (imag) normalize(out.data(), n);
+    C = std::move(out);
+  };
+  auto upload_s = [&](const SvdOut& sv) {
+    double* d_s = nullptr;
+    TDVP_CUDA(cudaMallocAsync(&d_s, sizeof(double) * sv.rank, st));
+    TDVP_CUDA(cudaMemcpyAsync(d_s, sv.s.data(), sizeof(double) * sv.rank, cudaMemcpyHostToDevice, st));
+    return d_s;
+  };
+  for (int i = 0; i + 1 < N; ++i) {
+    const int mr = psi.m[i + 2];
+    SvdOut sv;
+    evolve_split(i, sv);
+    const int r = sv.rank;
+    DArr C(&pool, (size_t)r * d * mr);  // S Vh: the centre on site i+1
+    double* d_s = upload_s(sv);
+    scale_rows(st, C.data(), sv.Vh.data(), d_s, r, d * mr);
+    TDVP_CUDA(cudaFreeAsync(d_s, st));
+    psi.A[i] = std::move(sv.U);
+    psi.m[i + 1] = r;
+    env_left(i);  // L[i+1]
+    for (int j = 0; j <= i; ++j) Rok[j] = 0;  // R[j] read site i+1
+    if (i + 2 < N) evolve_back(i + 1, C);
+    psi.A[i + 1] = std::move(C);
+    center = i + 1;
+    for (int j = i + 2; j < N; ++j) Lok[j] = 0;
+  }
+  for (int i = N - 2; i >= 0; --i) {
+    const int ml = psi.m[i];
+    SvdOut sv;
+    evolve_split(i, sv);
+    const int r = sv.rank;
+    DArr C(&pool, (size_t)ml * d * r);  // U S: the centre on site i
+    double* d_s = upload_s(sv);
+    scale_cols(st, C.data(), sv.U.data(), d_s, ml * d, r);
+    TDVP_CUDA(cudaFreeAsync(d_s, st));
+    psi.A[i + 1] = std::move(sv.Vh);
+    psi.m[i + 1] = r;
+    env_right(i + 1);  // R[i]
+    if (i > 0) evolve_back(i, C);
+    psi.A[i] = std::move(C);
+    center = i;
+    for (int j = 0; j < i; ++j) Rok[j] = 0;
+    for (int j = i + 1; j < N; ++j) Lok[j] = 0;
+  }
+  center = 0;
+  for (int j = 1; j < N; ++j) Lok[j] = 0;
+  if (env_prec != TDVP_PREC_FP64)
+    for (int j = 0; j < N; ++j) Lok[j] = Rok[j] = 0;
+  env_prec = TDVP_PREC_FP64;
+  ++env_epoch;
+  sync();
+}
+
+// ============================================================================
 // Krylov vectors and basis extension (Sec. I.A-I.C, steps 1-2)
 // ============================================================================
 namespace {
@@ -587,12 +746,29 @@ void Engine::krylov_apply(const KrylovOp& kop, const MpsDev& src, MpsDev& out) {
   // the Krylov vectors only enrich the basis (the state itself is kept exactly by the
   // extension), so the precision form may build them on the tensor cores
   const int kp = opt.precision;
+  // Right density environments F[j] (sites > j), (w_{j+1} m_{j+1})^2 entries each, are built
+  // right to left and read left to right, once each.  When all of them exceed the memory
+  // budget only every K-th (K = ceil(sqrt(N))) stays resident; the others are rebuilt from
+  // the next resident one when the left-to-right pass reaches their segment.  The rebuild
+  // runs the same launches on the same inputs, so the results are identical.
   std::vector<DArr> F(N);
   F[N - 1].reset(&pool, 1);
   k_one<<<1, 1, 0, st>>>(F[N - 1].data());
   TDVP_CHECK_LAUNCH();
+  double f_total = 0.0;
+  for (int j = 0; j + 1 < N; ++j) f_total += (double)sizeof(cplx) * w[j + 1] * src.m[j + 1] * w[j + 1] * src.m[j + 1];
+  double budget = krylov_mem_budget;
+  if (!(budget > 0.0)) {
+    size_t fr = 0, tot = 0;
+    TDVP_CUDA(cudaMemGetInfo(&fr, &tot));
+    budget = 0.5 * ((double)fr + (double)pool.cached_bytes());
+  }
+  const int seg = f_total <= budget ? 1 : std::max(2, (int)std::ceil(std::sqrt((double)N)));
+  krylov_env_segment = seg;
+  auto resident = [&](int j) { return seg == 1 || j == N - 1 || j % seg == 0; };
   DArr T1, T2;
-  for (int i = N - 1; i >= 1; --i) {
+  // F[i-1] from F[i] and site i
+  auto step_F = [&](int i) {
     PhaseScope ps(tracer, PH_KRYLOV_RENV);
     const int ml = src.m[i], m = src.m[i + 1], wl = w[i], wr = w[i + 1];
     const cplx* A = src.A[i].data();
@@ -610,9 +786,22 @@ void Engine::krylov_apply(const KrylovOp& kop, const MpsDev& src, MpsDev& out) {
     k_omega_stage<<<g, 128, 0, st>>>(T2.data(), F[i - 1].data(), ml, d, wl, wr, kop.om_off[i], kop.om_idx[i],
                                       kop.om_val[i]);
     TDVP_CHECK_LAUNCH();
+  };
+  for (int i = N - 1; i >= 1; --i) {
+    step_F(i);
+    if (!resident(i)) F[i].release();
   }
   T1.release();
   T2.release();
+  // makes F[i] resident again: rebuilds the segment below the next resident environment
+  auto need_F = [&](int i) {
+    if (F[i].size() > 0) return;
+    int c = i + 1;
+    while (!resident(c)) ++c;
+    for (int j = c; j > i; --j) step_F(j);
+    T1.release();
+    T2.release();
+  };
   out.N = N;
   out.d = d;
   out.m.assign(N + 1, 1);
@@ -636,6 +825,7 @@ void Engine::krylov_apply(const KrylovOp& kop, const MpsDev& src, MpsDev& out) {
     }
     const int n = mt * d, K = wr * mr;
     H1.ensure(&pool, (size_t)n * K);
+    need_F(i);
     {
       // the right density environment in the row order of G's columns: [v][b][vb][bb]
       DArr Fv(&pool, (size_t)K * K);

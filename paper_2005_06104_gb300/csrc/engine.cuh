@@ -26,74 +26,6 @@ struct KrylovOp {
   void release();
 };
 
-// Phases timed by the tracer (CUDA events on the engine stream).
-enum TracePhase {
-  PH_LANCZOS_SITE = 0, PH_LANCZOS_BOND, PH_SVD, PH_ENV, PH_KRYLOV, PH_EXTEND, PH_CANON,
-  PH_KRYLOV_RENV, PH_KRYLOV_EIG, PH_EXTEND_SVD, PH_COUNT
-};
-
-struct Tracer {
-  bool on = false;
-  cudaStream_t st = nullptr;
-  std::vector<cudaEvent_t> pool;
-  struct Mark {
-    int phase;
-    cudaEvent_t a, b;
-  };
-  std::vector<Mark> marks;
-  cudaEvent_t get() {
-    if (!pool.empty()) {
-      cudaEvent_t e = pool.back();
-      pool.pop_back();
-      return e;
-    }
-    cudaEvent_t e;
-    TDVP_CUDA(cudaEventCreate(&e));
-    return e;
-  }
-  // sums per phase (ms) and recycles the events; the stream must be idle
-  void read(double* out, int n) {
-    for (int p = 0; p < n; ++p) out[p] = 0.0;
-    for (auto& m : marks) {
-      float t = 0.f;
-      TDVP_CUDA(cudaEventElapsedTime(&t, m.a, m.b));
-      if (m.phase < n) out[m.phase] += t;
-      pool.push_back(m.a);
-      pool.push_back(m.b);
-    }
-    marks.clear();
-  }
-  void release() {
-    for (auto& m : marks) {
-      cudaEventDestroy(m.a);
-      cudaEventDestroy(m.b);
-    }
-    for (auto e : pool) cudaEventDestroy(e);
-    marks.clear();
-    pool.clear();
-  }
-};
-
-// Records one interval of `phase` on the stream while it is in scope.
-struct PhaseScope {
-  Tracer& tr;
-  int phase;
-  cudaEvent_t a = nullptr;
-  PhaseScope(Tracer& t, int p) : tr(t), phase(p) {
-    if (tr.on) {
-      a = tr.get();
-      cudaEventRecord(a, tr.st);
-    }
-  }
-  ~PhaseScope() {
-    if (tr.on && a) {
-      cudaEvent_t b = tr.get();
-      cudaEventRecord(b, tr.st);
-      tr.marks.push_back({phase, a, b});
-    }
-  }
-};
-
 struct Engine {
   // declared first so it is destroyed last: every DArr below returns its block here
   DevicePool pool;
@@ -102,6 +34,7 @@ struct Engine {
   std::vector<int> w;                    // MPO bond dims
   std::vector<std::vector<cplx>> W_host; // MPO of H (host copy)
   std::vector<WSparse> Wsp;              // MPO of H (device sparse)
+  std::vector<WSparse> Wsp2;             // merged pair MPO of sites (i, i+1), physical dim d^2 (TDVP2)
   MpsDev psi;
   int center = 0;
   tdvp_options opt{};
@@ -116,6 +49,9 @@ struct Engine {
   LanczosWork lw;
   long long env_epoch = 0;  // bumped whenever an environment is rebuilt or dropped
   int env_prec = TDVP_PREC_FP64;  // arithmetic of environment updates (the sweep's precision while it runs)
+  // device bytes the Krylov step may hold in right density environments (0: half the free memory)
+  double krylov_mem_budget = 0.0;
+  int krylov_env_segment = 1;  // last Krylov step: 1 = all resident, else the checkpoint spacing
   // optional timing of the H_eff applies (CUDA events on the engine stream)
   bool profile = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -137,7 +73,10 @@ struct Engine {
   void invalidate_from_site(int i);  // A[i] changed
   // contractions (FP64 unless precision says otherwise)
   void heff(int site, const cplx* x, cplx* y, int precision);
+  void apply_op(const SiteOp& op, const cplx* x, cplx* y, int precision);  // H_eff of op (timed when profiling)
   SiteOp site_op(int site);
+  SiteOp pair_op(int i);  // two-site H_eff of (i, i+1): L[i], R[i+1], merged MPO, physical dim d^2
+  void build_pair_mpo();
   void env_left(int i);   // L[i+1] from L[i], A[i]
   void env_right(int i);  // R[i-1] from R[i], A[i]
   // gauge moves
@@ -149,6 +88,7 @@ struct Engine {
               long long n, double delta, int kind);
   // algorithm steps
   void sweep(double dt, int kind);
+  void sweep2(double dt, int kind);  // two-site TDVP (the conventional integrator GSE-TDVP1 is compared with)
   void expand_basis(int k, const double* weights);
   void build_krylov_op(KrylovOp& kop);
   void krylov_apply(const KrylovOp& kop, const MpsDev& src, MpsDev& out);

@@ -2,6 +2,8 @@
 // stages, Krylov-vector BLAS-1, the small tridiagonal exponential of the
 // Lanczos exponentiator and a one-sided Jacobi SVD.
 #include <algorithm>
+#include <memory>
+#include <optional>
 #include <numeric>
 
 #include "linalg.cuh"
@@ -1668,6 +1670,7 @@ struct DSU {
 }  // namespace
 
 SvdCounters g_svd_counters;
+thread_local Tracer* t_tracer = nullptr;
 std::atomic<long long> g_kernel_launches{0};
 
 // Barrier of the n CTAs that work on one block (all co-resident: cooperative launch).
@@ -1866,6 +1869,7 @@ void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows
   }
   const int words = (cols + 31) / 32;
   std::vector<unsigned> mask((size_t)rows * words);
+  auto prep = std::make_unique<ActivePhase>(PH_SVD_PREP);
   {
     RawBuf dm;
     dm.ensure(pool, sizeof(unsigned) * mask.size());
@@ -1975,7 +1979,9 @@ void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows
     TDVP_CUDA(cudaMemsetAsync(d_bad, 0, 3 * sizeof(int), st));
     k_gather_batched<<<nsmall, 256, 0, st>>>(M, cols, d_desc, d_ridx, d_cidx, Xs.data(), Vs.data());
     TDVP_CHECK_LAUNCH();
+    prep.reset();
     if (psd) {
+      ActivePhase ph(PH_SVD_PCHOL);
       // eigendecomposition of a Hermitian PSD matrix: Jacobi SVD of its pivoted Cholesky
       // factor per block; eigenvalues below 1e-15 of the block's largest diagonal entry
       // (under every keep floor of the method) end the factorisation
@@ -1984,6 +1990,7 @@ void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows
       k_pchol_batched<<<nsmall, 256, 0, st>>>(Xs.data(), d_desc, d_piv, 1e-15);
       TDVP_CHECK_LAUNCH();
     }
+    std::optional<ActivePhase> jac(std::in_place, PH_SVD_JACOBI);
     if (!multi) {
       static const bool attr = [] {
         TDVP_CUDA(cudaFuncSetAttribute(k_jacobi_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
@@ -1996,6 +2003,7 @@ void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows
     } else {
       run_jacobi_multi(st, Xs.data(), Vs.data(), desc, d_desc, d_s, d_bad);
     }
+    jac.reset();
     std::vector<double> hs(so);
     int hbad[3] = {0, 0, 0};
     TDVP_CUDA(cudaMemcpyAsync(hs.data(), d_s, sizeof(double) * so, cudaMemcpyDeviceToHost, st));
@@ -2015,6 +2023,8 @@ void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows
         }
       }
   }
+  prep.reset();
+  ActivePhase select_phase(PH_SVD_SELECT);
   std::stable_sort(all.begin(), all.end(), [](const Cand& a, const Cand& b) { return a.s > b.s; });
   out.rows = rows;
   out.cols = cols;

@@ -49,6 +49,88 @@ void wstage_right(cudaStream_t st, const WSparse& w, const cplx* in, cplx* out, 
 // out[s][a][b] = in[a][s][b] (and back with the inverse flag)
 void permute_asb_sab(cudaStream_t st, const cplx* in, cplx* out, int A, int S, int B);
 
+// Phases timed by the tracer (CUDA events on the engine stream).
+enum TracePhase {
+  PH_LANCZOS_SITE = 0, PH_LANCZOS_BOND, PH_SVD, PH_ENV, PH_KRYLOV, PH_EXTEND, PH_CANON,
+  PH_KRYLOV_RENV, PH_KRYLOV_EIG, PH_EXTEND_SVD,
+  // inside every blocked SVD / eigendecomposition: block detection (mask, host union-find,
+  // gather), pivoted Cholesky, Jacobi sweeps, selection and scatter of the kept vectors
+  PH_SVD_PREP, PH_SVD_PCHOL, PH_SVD_JACOBI, PH_SVD_SELECT, PH_COUNT
+};
+
+struct Tracer {
+  bool on = false;
+  cudaStream_t st = nullptr;
+  std::vector<cudaEvent_t> pool;
+  struct Mark {
+    int phase;
+    cudaEvent_t a, b;
+  };
+  std::vector<Mark> marks;
+  cudaEvent_t get() {
+    if (!pool.empty()) {
+      cudaEvent_t e = pool.back();
+      pool.pop_back();
+      return e;
+    }
+    cudaEvent_t e;
+    TDVP_CUDA(cudaEventCreate(&e));
+    return e;
+  }
+  // sums per phase (ms) and recycles the events; the stream must be idle
+  void read(double* out, int n) {
+    for (int p = 0; p < n; ++p) out[p] = 0.0;
+    for (auto& m : marks) {
+      float t = 0.f;
+      TDVP_CUDA(cudaEventElapsedTime(&t, m.a, m.b));
+      if (m.phase < n) out[m.phase] += t;
+      pool.push_back(m.a);
+      pool.push_back(m.b);
+    }
+    marks.clear();
+  }
+  void release() {
+    for (auto& m : marks) {
+      cudaEventDestroy(m.a);
+      cudaEventDestroy(m.b);
+    }
+    for (auto e : pool) cudaEventDestroy(e);
+    marks.clear();
+    pool.clear();
+  }
+};
+
+// Records one interval of `phase` on the stream while it is in scope.
+struct PhaseScope {
+  Tracer& tr;
+  int phase;
+  cudaEvent_t a = nullptr;
+  PhaseScope(Tracer& t, int p) : tr(t), phase(p) {
+    if (tr.on) {
+      a = tr.get();
+      cudaEventRecord(a, tr.st);
+    }
+  }
+  ~PhaseScope() {
+    if (tr.on && a) {
+      cudaEvent_t b = tr.get();
+      cudaEventRecord(b, tr.st);
+      tr.marks.push_back({phase, a, b});
+    }
+  }
+};
+
+// The tracer of the handle whose call runs on this thread (null when tracing is off);
+// set by the C-ABI entry points, read by the factorisations.
+extern thread_local Tracer* t_tracer;
+
+// PhaseScope on the active tracer, when there is one.
+struct ActivePhase {
+  Tracer idle;
+  PhaseScope ps;
+  explicit ActivePhase(int p) : ps(t_tracer ? *t_tracer : idle, p) {}
+};
+
 // Reductions (deterministic, two-pass).  Results land in device memory.
 struct Blas1 {
   DevicePool* pool = nullptr;

@@ -55,6 +55,8 @@ _sig = {
     "tdvp_expand_basis": [_h, C.c_int, C.c_void_p],
     "tdvp_apply_krylov": [_h],
     "tdvp_sweep": [_h, C.c_double, C.c_int],
+    "tdvp_sweep2": [_h, C.c_double, C.c_int],
+    "tdvp_krylov_memory": [_h, C.c_double, C.POINTER(C.c_int)],
     "tdvp_heff_apply": [_h, C.c_int, C.c_void_p, C.c_void_p, C.c_int],
     "tdvp_keff_apply": [_h, C.c_int, C.c_void_p, C.c_void_p, C.c_int],
     "tdvp_evolve_site": [_h, C.c_int, C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.c_int,
@@ -355,6 +357,17 @@ class GseTdvp:
         self.expand_basis(k, weights)
         self.sweep(dt, kind)
 
+    def krylov_memory(self, max_bytes=-1.0):
+        """Sets the device-byte budget of the Krylov step's density environments (0: half the
+        free memory; < 0: unchanged) and returns the checkpoint spacing of the last Krylov step."""
+        seg = C.c_int(0)
+        self._chk(_lib.tdvp_krylov_memory(self.h, float(max_bytes), C.byref(seg)))
+        return seg.value
+
+    def sweep2(self, dt, kind=REAL):
+        """One two-site TDVP step (TDVP2), truncating with eps and chi_max in both time kinds."""
+        self._chk(_lib.tdvp_sweep2(self.h, dt, kind))
+
     def heff_apply(self, site, x, y, precision=PREC_FP64):
         self._chk(_lib.tdvp_heff_apply(self.h, site, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
                                        precision))
@@ -412,7 +425,8 @@ class GseTdvp:
         return dict(applies=int(out[0]), ms=out[1], flops=out[2])
 
     PHASES = ("lanczos_site", "lanczos_bond", "svd_sweep", "env", "krylov", "extend", "canonicalize",
-              "krylov_right_envs", "krylov_eig", "extend_svd")
+              "krylov_right_envs", "krylov_eig", "extend_svd", "svd_prep", "svd_pchol", "svd_jacobi",
+              "svd_select")
 
     def trace(self, enable=True):
         self._chk(_lib.tdvp_trace(self.h, 1 if enable else 0))

@@ -235,3 +235,31 @@ def test_save_and_load_resume_the_trajectory(g, tmp_path):
     assert abs(a.energy() - b.energy()) < 1e-10
     a.close()
     b.close()
+
+
+@pytest.mark.parametrize("prec,chi", [("fp64", 8), ("bf16x10", 32)])
+def test_checkpointed_density_environments_are_identical(g, prec, chi):
+    """With a budget below the density environments' size only every K-th stays resident and
+    the rest are rebuilt: the Krylov step and the following sweep are bit-identical."""
+    lat = wl.zigzag_ladder(6, 1.0, 0.6)
+    W = wl.heisenberg_mpo(lat)
+    psi = O.left_canonicalize(wl.random_mps(lat.n, chi, 21))
+    psi[-1] /= np.linalg.norm(psi[-1])
+    kw = dict(tau=0.1, eps_k=1e-10, eps_m=1e-9, chi_max=64,
+              precision=g.PREC_FP64 if prec == "fp64" else g.PREC_BF16X10)
+    a = g.GseTdvp(psi, W, **kw)
+    b = g.GseTdvp(psi, W, **kw)
+    b.krylov_memory(1.0)
+    a.apply_krylov()
+    b.apply_krylov()
+    assert a.krylov_memory() == 1
+    assert b.krylov_memory() == int(np.ceil(np.sqrt(lat.n)))
+    for x, y in zip(a.get_mps(), b.get_mps()):
+        assert np.array_equal(x, y)
+    a.step(0.1, g.REAL, 3)
+    b.step(0.1, g.REAL, 3)
+    assert a.bond_dims() == b.bond_dims()
+    for x, y in zip(a.get_mps(), b.get_mps()):
+        assert np.array_equal(x, y)
+    a.close()
+    b.close()
