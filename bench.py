@@ -4,9 +4,11 @@ One timed step = one full GSE-TDVP1 time step (Sec. I.C: Krylov vectors of
 Eq. 10, basis extension of Eqs. 3-7, symmetric TDVP1 sweep) on the 4 x 16
 Heisenberg cylinder (snake path, MPO bond dimension up to 14) along the real-time
 trajectory from the Neel state with one flipped spin; the state is resident in
-HBM.  Untimed preparation steps grow the bond dimension towards chi_max first.
-The precision form runs H_eff, the sweep's environment updates and the Krylov
-GEMMs on the tcgen05 split-TF32 path; Lanczos, SVDs and observables are FP64.
+HBM.  Untimed preparation and warm-up steps grow the bond dimension to chi_max
+(1024 by default) first.  The precision form (BF16X10 by default) runs H_eff,
+K_eff, the environment updates and the Krylov GEMMs on the tcgen05 tensor cores;
+Lanczos, SVDs and observables are FP64.  The FP64 comparison and the TDVP2
+comparison run on a second trajectory capped at --compare-chi (256).
 
     python bench.py [--gpus N] [--steps K] [--warmup W] [--chi-max X] [--prep-steps P]
     python bench.py --impl reference ...      (the CPU oracle on the host cores)
@@ -37,11 +39,13 @@ UNIT = "sweeps/s"
 def parse():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--steps", type=int, default=1)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--chi-max", type=int, default=256)
-    ap.add_argument("--prep-steps", type=int, default=8,
+    ap.add_argument("--chi-max", type=int, default=1024)
+    ap.add_argument("--compare-chi", type=int, default=256,
+                    help="bond-dimension cap of the trajectory that carries the FP64 and TDVP2 comparisons")
+    ap.add_argument("--prep-steps", type=int, default=9,
                     help="untimed GSE-TDVP1 steps that grow the bond dimension before warm-up")
     ap.add_argument("--k", type=int, default=3)
     ap.add_argument("--dt", type=float, default=0.1)
@@ -91,6 +95,7 @@ def workload(args):
            "krylov_order_k": args.k, "dt": args.dt, "tau": args.dt, "eps_k": 1e-8, "eps_m": 1e-8, "eps": 0.0,
            "time": "real", "precision_form": PRECISION_TEXT[args.precision],
            "start_state": "Neel with the spin at (8,0) flipped", "prep_steps": args.prep_steps,
+           "compare_chi": args.compare_chi,
            "l2": "working set of a step (environments, Krylov vectors, density environments) > L2; no flush"}
     return lat, W, psi, cfg
 
@@ -151,45 +156,58 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def cpu_baseline(args, W, budget_s=20.0):
-    """The oracle (as it stands) on the host cores, on a bounded sample of the same step:
-    TDVP1 site updates (forward Lanczos, SVD, environment update, backward Lanczos) at the
-    centre of a random MPS with the workload's bond dimensions (min(chi_max, 2^i, 2^(N-i))),
-    repeated until ~budget_s, then scaled to the 2N site updates of one sweep by each site's
-    m_l m_r (m_l + m_r) share.  Steps 1-2 are left out, which favours the CPU."""
+def _lanczos_iters_oracle(args, W, chi=32):
+    """Mean Krylov dimension per local exponential of the oracle's TDVP1 sweep on the same
+    lattice and time step at a small bond dimension (the count depends on dt and the
+    spectral width of H, not on chi)."""
+    import oracle as O
+    from paper_2005_06104_gb300 import workloads as wl
+    psi = O.right_canonicalize(wl.random_mps(len(W), chi, seed=11))
+    psi[0] = psi[0] / np.linalg.norm(psi[0])
+    st = {}
+    O.tdvp1_sweep(psi, W, args.dt, "real", stats=st)
+    return float(np.mean(st["lanczos_iters"]))
+
+
+def cpu_baseline(args, W, iters=None):
+    """The oracle (as it stands) on the host cores, on a bounded sample of one sweep: its
+    primitives timed once each at the centre site's shapes (bond dimension
+    min(chi_max, 2^(N/2)), MPO width of the centre), composed into a TDVP1 site update
+    (iters H_eff applies, one SVD of the centre tensor, one environment update, iters K_eff
+    applies) and scaled to the 2N site updates of a sweep by each site's m_l m_r (m_l + m_r)
+    share.  iters: Krylov dimension per local exponential, from _lanczos_iters_oracle.
+    Steps 1-2 (Krylov vectors, extension) are left out, which favours the CPU."""
     import oracle as O
     from paper_2005_06104_gb300 import workloads as wl
     n = len(W)
-    psi = O.right_canonicalize(wl.random_mps(n, args.chi_max, seed=11))
-    psi[0] = psi[0] / np.linalg.norm(psi[0])
     c = n // 2
-    for i in range(c):
-        ml, d, mr = psi[i].shape
-        U, S, Vh, _ = O.svd_truncate(psi[i].reshape(ml * d, mr))
-        psi[i] = U.reshape(ml, d, -1)
-        psi[i + 1] = np.tensordot(S[:, None] * Vh, psi[i + 1], axes=([1], [0]))
-    Ls, Rs = O.build_envs(psi, W, c)
-    delta = 0.5 * args.dt
-    t0 = time.perf_counter()
-    reps = 0
-    while True:
-        A = psi[c]
-        A2, _ = O.lanczos_expm(lambda v: O.heff_apply(Ls[c], W[c], Rs[c], v), A, delta, "real")
-        ml, d, mr = A2.shape
-        U, S, Vh, _ = O.svd_truncate(A2.reshape(ml * d, mr))
-        Q = U.reshape(ml, d, -1)
-        Lnew = O.env_left_step(Ls[c], Q, W[c])
-        Rb = O.env_right_step(Rs[c + 1], psi[c + 1], W[c + 1]) if c + 1 < n else Rs[c]
-        O.lanczos_expm(lambda v: O.keff_apply(Lnew, Rs[c], v), S[:, None] * Vh, -delta, "real")
-        reps += 1
-        if time.perf_counter() - t0 > budget_s or reps >= 50:
-            break
-    t_site = (time.perf_counter() - t0) / reps
     dims = wl.full_bond_dims(n, args.chi_max)
+    m, wc, wr = dims[c], W[c].shape[0], W[c].shape[3]
+    rng = np.random.default_rng(11)
+
+    def rnd(*shape):
+        return (rng.standard_normal(shape) + 1j * rng.standard_normal(shape)) / np.sqrt(np.prod(shape))
+    A, L, R = rnd(m, 2, m), rnd(m, wc, m), rnd(m, wr, m)
+    C, Lb = rnd(m, m), rnd(m, wr, m)
+    if iters is None:
+        iters = _lanczos_iters_oracle(args, W)
+
+    def timed(f):
+        t = time.perf_counter()
+        f()
+        return time.perf_counter() - t
+    t_heff = timed(lambda: O.heff_apply(L, W[c], R, A))
+    t_keff = timed(lambda: O.keff_apply(Lb, R, C))
+    t_svd = timed(lambda: O.svd_truncate(A.reshape(2 * m, m)))
+    t_env = timed(lambda: O.env_left_step(L, A, W[c]))
+    t_site = iters * (t_heff + t_keff) + t_svd + t_env
     cost = [dims[i] * dims[i + 1] * (dims[i] + dims[i + 1]) for i in range(n)]
     t_sweep = 2.0 * t_site * sum(cost) / cost[c]
     return {"value": 1.0 / t_sweep, "unit": UNIT, "cores": _blas_threads(), "kind": "oracle",
-            "sample": f"{reps} TDVP1 centre-site updates (chi={dims[c]}) of the same lattice, scaled to one "
+            "sample": f"oracle primitives at the centre site (chi={m}, w={wc}) timed once each: H_eff apply "
+                      f"{t_heff:.2f} s, K_eff apply {t_keff:.2f} s, SVD {t_svd:.2f} s, environment update "
+                      f"{t_env:.2f} s; a site update = {iters:.1f} Krylov iterations (the oracle's own mean "
+                      f"on this lattice and dt at chi=32) of H_eff and of K_eff + SVD + update; scaled to one "
                       f"sweep by m_l m_r (m_l+m_r); Krylov and extension steps excluded (favours the CPU)",
             "seconds_per_site_update": t_site}
 
@@ -212,10 +230,10 @@ def run_reference(args):
     if rank != 0:
         return
     lat, W, psi, cfg = workload(args)
-    budget = max(2.0, min(20.0, 150.0 / max(1, args.steps + args.warmup)))
+    iters = _lanczos_iters_oracle(args, W)
     for _ in range(args.warmup):
-        cpu_baseline(args, W, budget_s=budget)
-    samples = [cpu_baseline(args, W, budget_s=budget) for _ in range(args.steps)]
+        cpu_baseline(args, W, iters)
+    samples = [cpu_baseline(args, W, iters) for _ in range(args.steps)]
     t_sweep = [1.0 / x["value"] for x in samples]
     v = args.steps / sum(t_sweep)
     cb = dict(samples[-1])
@@ -323,6 +341,7 @@ def run_gpu(args):
         heff_flops += pr["flops"]
         heff_n += pr["applies"]
         nfo = st.trunc_stats()
+        nfo["krylov_env_segment"] = st.krylov_memory()
     torch.cuda.synchronize()
     launches = g.launch_count() - launches0
     if world > 1:
@@ -348,40 +367,42 @@ def run_gpu(args):
         if world > 1:
             dist.destroy_process_group()
         return
-    # precision form vs FP64 GPU form: one step of each from the same state (device time)
-    def timed_step(h):
+    # precision form vs FP64 GPU form, and TDVP2 against GSE-TDVP1 (Sec. I.C): one step of each
+    # from the same state of a second trajectory capped at --compare-chi (an FP64 step at
+    # chi = 1024 takes about 12 minutes)
+    def timed_step(h, fn):
         ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ea.record()
-        step(h)
+        fn(h)
         eb.record()
         eb.synchronize()
         return ea.elapsed_time(eb)
-    a = g.GseTdvp(start_state, W, stream=stream, **dict(opts, precision=g.PREC_FP64))
-    ms_64 = timed_step(a)
+    copts = dict(opts, chi_max=args.compare_chi)
+    cmp_h = g.GseTdvp(psi0, W, stream=stream, **copts)
+    for _ in range(8 + args.warmup):
+        step(cmp_h)
+    cmp_state = cmp_h.get_mps()
+    cmp_dims = cmp_h.bond_dims()
+    cmp_h.close()
+    a = g.GseTdvp(cmp_state, W, stream=stream, **dict(copts, precision=g.PREC_FP64))
+    ms_64 = timed_step(a, step)
     e_64 = a.energy()
     a.close()
-    b_ = g.GseTdvp(start_state, W, stream=stream, **opts)
-    ms_tc = timed_step(b_)
+    b_ = g.GseTdvp(cmp_state, W, stream=stream, **copts)
+    ms_tc = timed_step(b_, step)
     e_tc, n_tc = b_.energy(), b_.norm()
     b_.close()
-    # the conventional two-site TDVP from the same state at the same bond-dimension cap
-    # (Sec. I.C compares a GSE-TDVP1 step with a TDVP2 step at equal bond dimension)
     tdvp2 = None
     if not args.no_tdvp2:
-        c_ = g.GseTdvp(start_state, W, stream=stream, **opts)
+        c_ = g.GseTdvp(cmp_state, W, stream=stream, **copts)
         c_.trace(True)
-        ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        ea.record()
-        c_.sweep2(args.dt, g.REAL)
-        eb.record()
-        eb.synchronize()
-        ms_2 = ea.elapsed_time(eb)
-        tdvp2 = {"step_ms": ms_2, "gse_tdvp1_step_ms": ms_tc, "gse_tdvp1_over_tdvp2": ms_tc / ms_2,
-                 "paper_ratio_cpu": 0.36, "bond_dim_max": max(c_.bond_dims()),
-                 "energy": c_.energy(), "discarded_weight": c_.trunc_stats()["disc_eps"],
-                 "phases_ms": c_.trace_read(),
-                 "what": "one TDVP2 step (tdvp_sweep2, same precision form, cap chi_max, eps = 0) from the "
-                         "state the timed GSE-TDVP1 steps started from"}
+        ms_2 = timed_step(c_, lambda h: h.sweep2(args.dt, g.REAL))
+        tdvp2 = {"chi_max": args.compare_chi, "step_ms": ms_2, "gse_tdvp1_step_ms": ms_tc,
+                 "gse_tdvp1_over_tdvp2": ms_tc / ms_2, "paper_ratio_cpu": 0.36,
+                 "bond_dim_max": max(c_.bond_dims()), "energy": c_.energy(),
+                 "discarded_weight": c_.trunc_stats()["disc_eps"], "phases_ms": c_.trace_read(),
+                 "what": "one TDVP2 step (tdvp_sweep2, same precision form, same cap, eps = 0) and one "
+                         "GSE-TDVP1 step from the same state of the comparison trajectory"}
         c_.close()
     # e2e through the public API: host state in, one step, full state out
     e2e_ts = []
@@ -445,12 +466,15 @@ def run_gpu(args):
                      "timed": "10 applies after 3 warm-up, environment operands cached (as in a Lanczos run)"},
         "heff_in_step": {"applies": heff_n, "ms": heff_ms, "tflops_algorithmic": achieved_step,
                          "share_of_step": heff_ms / sum(ts) if ts else None},
-        "precision_vs_fp64": {"precision": args.precision, "energy_precision_form": e_tc, "energy_fp64": e_64,
+        "precision_vs_fp64": {"chi_max": args.compare_chi, "bond_dims_max": max(cmp_dims),
+                              "precision": args.precision, "energy_precision_form": e_tc, "energy_fp64": e_64,
                               "step_ms_precision_form": ms_tc, "step_ms_fp64": ms_64,
                               "speedup_over_fp64": ms_64 / ms_tc,
                               "rel_energy_err": abs(e_tc - e_64) / abs(e_64), "norm_drift": abs(n_tc - 1.0)},
         "tdvp2_comparison": tdvp2,
-        "energy_conservation": {"E_initial": e_init, "E_after_timed_steps": e_end, "abs_drift": abs(e_end - e_init)},
+        "energy_conservation": {"E_initial": e_init, "E_after_timed_steps": e_end, "abs_drift": abs(e_end - e_init),
+                                "rel_drift": abs(e_end - e_init) / abs(e_init),
+                                "steps": args.prep_steps + args.warmup + args.steps},
         "step_stats": nfo,
         "phases_ms_per_step": phases,
         "cpu_baseline": cpu,

@@ -1,0 +1,38 @@
+"""Host-side pieces of the benchmark that need no GPU: the oracle's CPU baseline sample and
+the reference arm's JSON line."""
+import argparse
+import json
+import subprocess
+import sys
+import os
+
+import pytest
+
+import bench
+from paper_2005_06104_gb300 import workloads as wl
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def test_cpu_baseline_sample_is_bounded_and_scaled():
+    lat = wl.cylinder_snake(16, 4)
+    W = wl.heisenberg_mpo(lat)
+    a = argparse.Namespace(chi_max=32, dt=0.1)
+    iters = bench._lanczos_iters_oracle(a, W, chi=8)
+    assert 2.0 <= iters <= 40.0
+    r = bench.cpu_baseline(a, W, iters)
+    assert r["kind"] == "oracle" and r["unit"] == bench.UNIT and r["value"] > 0
+    # one sweep = 2N site updates weighted by m_l m_r (m_l + m_r); the centre has the largest share
+    assert 1.0 / r["value"] >= 2.0 * r["seconds_per_site_update"]
+    assert "chi=32" in r["sample"]
+
+
+def test_reference_arm_prints_one_line():
+    out = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), "--impl", "reference", "--steps", "1",
+                          "--warmup", "1", "--chi-max", "32"], capture_output=True, text=True, timeout=600,
+                         cwd=ROOT)
+    assert out.returncode == 0, out.stderr[-2000:]
+    line = json.loads(out.stdout.strip().splitlines()[-1])
+    assert line["impl"] == "reference" and line["value"] > 0
+    assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["value"] == line["value"]
+    assert line["config"]["chi_max"] == 32
