@@ -1674,27 +1674,36 @@ thread_local Tracer* t_tracer = nullptr;
 std::atomic<long long> g_kernel_launches{0};
 
 // Barrier of the n CTAs that work on one block (all co-resident: cooperative launch).
-// Bounded like grid_sync; a wait that runs out, or an error raised by any other
-// group (gerr), makes every waiter return false.
-__device__ bool group_sync(GridBar* b, unsigned n, int* gerr) {
+// The arrival counter only grows: the e-th barrier of a group completes when it reaches
+// e * n, so no CTA has to reset it and the waiters need no second signal.  Thread 0
+// arrives with a release add (ordering the block's writes, which bar.sync has ordered
+// before it) and polls with acquire loads (ordering the block's later reads, which the
+// closing bar.sync passes on).  Bounded like grid_sync: every 64 polls the waiter checks
+// the error word of the launch (gerr) and its 2 s limit; either makes it return false.
+// `epoch` counts this CTA's barriers (the same sequence in every CTA of the group).
+__device__ __forceinline__ void red_add_release_gpu(unsigned* p, unsigned v) {
+  asm volatile("red.release.gpu.global.add.u32 [%0], %1;" ::"l"(p), "r"(v) : "memory");
+}
+__device__ __forceinline__ unsigned ld_acquire_gpu(const unsigned* p) {
+  unsigned v;
+  asm volatile("ld.acquire.gpu.global.u32 %0, [%1];" : "=r"(v) : "l"(p) : "memory");
+  return v;
+}
+
+__device__ __forceinline__ bool group_sync(GridBar* b, unsigned n, int* gerr, unsigned& epoch) {
   __shared__ int ok;
   __syncthreads();
+  ++epoch;
   if (threadIdx.x == 0) {
     ok = 1;
     if (n > 1) {
-      volatile unsigned* vgen = &b->gen;
-      volatile int* verr = gerr;
-      const unsigned g = *vgen;
-      __threadfence();
-      const unsigned arrived = atomicAdd(&b->count, 1u);
-      if (arrived == n - 1) {
-        atomicExch(&b->count, 0u);
-        __threadfence();
-        atomicAdd(&b->gen, 1u);
-      } else {
-        const unsigned long long t0 = gtimer();
-        while (*vgen == g) {
-          if (*verr) {
+      const unsigned target = epoch * n;
+      red_add_release_gpu(&b->count, 1u);
+      const unsigned long long t0 = gtimer();
+      unsigned polls = 0;
+      while ((int)(ld_acquire_gpu(&b->count) - target) < 0) {
+        if ((++polls & 63u) == 0u) {
+          if (*(volatile int*)gerr) {
             ok = 0;
             break;
           }
@@ -1705,9 +1714,7 @@ __device__ bool group_sync(GridBar* b, unsigned n, int* gerr) {
           }
         }
       }
-      __threadfence();
     }
-    if (*(volatile int*)gerr) ok = 0;
   }
   __syncthreads();
   return ok != 0;
@@ -1755,7 +1762,8 @@ __global__ void __launch_bounds__(256)
     }
     __syncthreads();
   }
-  if (!group_sync(bar, n_b, gerr)) return;
+  unsigned epoch = 0;
+  if (!group_sync(bar, n_b, gerr, epoch)) return;
   const double floor2 = kJacobiFloor * fro2[b];
   const double tol = fmax(1e-15, sqrt((double)d.p) * 2.2e-16);
   const int qpad = d.q + (d.q & 1);
@@ -1771,7 +1779,7 @@ __global__ void __launch_bounds__(256)
         if (jacobi_pair_block(X + d.x_off, V + d.v_off, d.p, d.q, P, Q, tol, floor2, d.need_v) && threadIdx.x == 0)
           rot[sweep % 3] = 1;
       }
-      if (!group_sync(bar, n_b, gerr)) return;
+      if (!group_sync(bar, n_b, gerr, epoch)) return;
     }
     converged = ((volatile int*)rot)[sweep % 3] == 0;  // every CTA of the group reads it after the barrier
   }
