@@ -52,6 +52,8 @@ def parse():
     ap.add_argument("--heff-chi", type=int, default=1024, help="bond dimension of the H_eff roofline probe")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tdvp2", action="store_true", help="skip the TDVP2 step of the comparison")
+    ap.add_argument("--svd-probe", action="store_true",
+                    help="time only the blocked Jacobi SVDs of tdvp_create on a dense random MPS (bond --heff-chi)")
     ap.add_argument("--heff-probe", action="store_true",
                     help="only time the tensor-core H_eff apply at --heff-chi (the profiling target)")
     ap.add_argument("--precision", default="bf16x10", choices=sorted(PRECISIONS),
@@ -500,6 +502,30 @@ def run_heff_probe(args):
                       "algorithmic_tflops": flops / ms / 1e9}), flush=True)
 
 
+def run_svd_probe(args):
+    """The blocked Jacobi SVD on its own: tdvp_create left-canonicalises a dense random MPS
+    of the cylinder's length at bond dimension --heff-chi (no conserved charge, so every
+    gauge move is one dense (2m) x m block), timed with CUDA events."""
+    import torch
+    from paper_2005_06104_gb300 import gse_tdvp as g
+    from paper_2005_06104_gb300 import workloads as wl
+    lat = wl.cylinder_snake(16, 4)
+    W = wl.heisenberg_mpo(lat)
+    psi = wl.random_mps(lat.n, args.heff_chi, 3)
+    out = []
+    for _ in range(2):  # the first call also warms the allocator
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record()
+        st = g.GseTdvp(psi, W, stream=torch.cuda.current_stream().cuda_stream)
+        b.record()
+        b.synchronize()
+        out.append(a.elapsed_time(b))
+        nfo = st.trunc_stats()
+        st.close()
+    print(json.dumps({"svd_chi": args.heff_chi, "gauge_moves": lat.n - 1, "ms_create": out[-1],
+                      "jacobi_sweeps": nfo["svd_sweeps"], "widest_block": nfo["svd_max_block"]}), flush=True)
+
+
 def run_batch(args):
     """Independent random-field chains stepped as one batch (one stream per chain, host worker
     pool) against the same chains stepped one after another on one stream each, same steps."""
@@ -549,7 +575,9 @@ def main():
     if args.batch_chains > 0:
         run_batch(args)
         return
-    if args.heff_probe:
+    if args.svd_probe:
+        run_svd_probe(args)
+    elif args.heff_probe:
         run_heff_probe(args)
     elif args.impl == "reference":
         run_reference(args)

@@ -336,22 +336,20 @@ void Engine::move_right(int i, double eps, int cap, bool trunc) {
     rule.discarded = &disc_eps;
   }
   SvdOut sv;
-  svd_jacobi(st, &pool, psi.A[i].data(), ml * d, mr, rule, sv, true, true);
+  svd_jacobi(st, &pool, psi.A[i].data(), ml * d, mr, rule, sv, true, false);
   const int r = sv.rank;
   tdvp_require(r >= 1, TDVP_ERR_NONFINITE, "move_right: zero tensor");
-  // C = S Vh (r x mr); A[i+1] <- C A[i+1]
+  // C = U^+ A = S Vh (r x mr), one FP64 GEMM instead of rotating V in every Jacobi round;
+  // A[i+1] <- C A[i+1]
   DArr C(&pool, (size_t)r * mr);
-  double* d_s = nullptr;
-  TDVP_CUDA(cudaMallocAsync(&d_s, sizeof(double) * r, st));
-  TDVP_CUDA(cudaMemcpyAsync(d_s, sv.s.data(), sizeof(double) * r, cudaMemcpyHostToDevice, st));
-  scale_rows(st, C.data(), sv.Vh.data(), d_s, r, mr);
+  zgemm(st, OP_C, OP_N, r, mr, ml * d, kOne, sv.U.data(), r, psi.A[i].data(), mr, kZero, C.data(), mr, 1, 0, 0, 0,
+        &pool);
   DArr nxt(&pool, (size_t)r * d * mr2);
   zgemm(st, OP_N, OP_N, r, d * mr2, mr, kOne, C.data(), mr, psi.A[i + 1].data(), d * mr2, kZero, nxt.data(),
         d * mr2, 1, 0, 0, 0, &pool);
   psi.A[i] = std::move(sv.U);
   psi.A[i + 1] = std::move(nxt);
   psi.m[i + 1] = r;
-  TDVP_CUDA(cudaFreeAsync(d_s, st));
   invalidate_from_site(i);
   invalidate_from_site(i + 1);
 }
@@ -365,20 +363,18 @@ void Engine::move_left(int i, double eps, int cap, bool trunc) {
     rule.discarded = &disc_eps;
   }
   SvdOut sv;
-  svd_jacobi(st, &pool, psi.A[i].data(), ml, d * mr, rule, sv, true, true);
+  svd_jacobi(st, &pool, psi.A[i].data(), ml, d * mr, rule, sv, false, true);
   const int r = sv.rank;
   tdvp_require(r >= 1, TDVP_ERR_NONFINITE, "move_left: zero tensor");
+  // C = A Vh^+ = U S (ml x r), one FP64 GEMM instead of rotating U in every Jacobi round
   DArr C(&pool, (size_t)ml * r);
-  double* d_s = nullptr;
-  TDVP_CUDA(cudaMallocAsync(&d_s, sizeof(double) * r, st));
-  TDVP_CUDA(cudaMemcpyAsync(d_s, sv.s.data(), sizeof(double) * r, cudaMemcpyHostToDevice, st));
-  scale_cols(st, C.data(), sv.U.data(), d_s, ml, r);
+  zgemm(st, OP_N, OP_C, ml, r, d * mr, kOne, psi.A[i].data(), d * mr, sv.Vh.data(), d * mr, kZero, C.data(), r, 1, 0,
+        0, 0, &pool);
   DArr prv(&pool, (size_t)ml0 * d * r);
   zgemm(st, OP_N, OP_N, ml0 * d, r, ml, kOne, psi.A[i - 1].data(), ml, C.data(), r, kZero, prv.data(), r, 1, 0, 0, 0, &pool);
   psi.A[i] = std::move(sv.Vh);
   psi.A[i - 1] = std::move(prv);
   psi.m[i] = r;
-  TDVP_CUDA(cudaFreeAsync(d_s, st));
   invalidate_from_site(i);
   invalidate_from_site(i - 1);
 }
@@ -460,16 +456,13 @@ void Engine::sweep(double dt, int kind) {
     SvdOut sv;
     {
       PhaseScope ps(tracer, PH_SVD);
-      svd_jacobi(st, &pool, psi.A[i].data(), ml * d, mold, rule, sv, true, true);
+      svd_jacobi(st, &pool, psi.A[i].data(), ml * d, mold, rule, sv, true, false);
     }
     const int r = sv.rank;
     tdvp_require(r >= 1, TDVP_ERR_NONFINITE, "sweep: zero site tensor");
-    DArr C(&pool, (size_t)r * mold);
-    double* d_s = nullptr;
-    TDVP_CUDA(cudaMallocAsync(&d_s, sizeof(double) * r, st));
-    TDVP_CUDA(cudaMemcpyAsync(d_s, sv.s.data(), sizeof(double) * r, cudaMemcpyHostToDevice, st));
-    scale_rows(st, C.data(), sv.Vh.data(), d_s, r, mold);
-    TDVP_CUDA(cudaFreeAsync(d_s, st));
+    DArr C(&pool, (size_t)r * mold);  // C = U^+ A = S Vh
+    zgemm(st, OP_C, OP_N, r, mold, ml * d, kOne, sv.U.data(), r, psi.A[i].data(), mold, kZero, C.data(), mold, 1,
+          0, 0, 0, &pool);
     psi.A[i] = std::move(sv.U);
     psi.m[i + 1] = r;  // L[i+1] is r x w x r, R[i] still mold x w x mold
     env_left(i);
@@ -503,16 +496,13 @@ void Engine::sweep(double dt, int kind) {
     SvdOut sv;
     {
       PhaseScope ps(tracer, PH_SVD);
-      svd_jacobi(st, &pool, psi.A[i].data(), mold, d * mr, rule, sv, true, true);
+      svd_jacobi(st, &pool, psi.A[i].data(), mold, d * mr, rule, sv, false, true);
     }
     const int r = sv.rank;
     tdvp_require(r >= 1, TDVP_ERR_NONFINITE, "sweep: zero site tensor");
-    DArr C(&pool, (size_t)mold * r);
-    double* d_s = nullptr;
-    TDVP_CUDA(cudaMallocAsync(&d_s, sizeof(double) * r, st));
-    TDVP_CUDA(cudaMemcpyAsync(d_s, sv.s.data(), sizeof(double) * r, cudaMemcpyHostToDevice, st));
-    scale_cols(st, C.data(), sv.U.data(), d_s, mold, r);
-    TDVP_CUDA(cudaFreeAsync(d_s, st));
+    DArr C(&pool, (size_t)mold * r);  // C = A Vh^+ = U S
+    zgemm(st, OP_N, OP_C, mold, r, d * mr, kOne, psi.A[i].data(), d * mr, sv.Vh.data(), d * mr, kZero, C.data(), r,
+          1, 0, 0, 0, &pool);
     psi.A[i] = std::move(sv.Vh);
     psi.m[i] = r;
     env_right(i);  // R[i-1]: r x w x r
@@ -573,8 +563,10 @@ void Engine::sweep2(double dt, int kind) {
     blas.norm2(st, v, n, lw.real + 140);
     scale_by_inv_sqrt(st, v, v, lw.real + 140, n);
   };
-  // y <- exp(-i delta H_eff^(2)) A_i A_{i+1}, then its SVD as (m_i d) x (d m_{i+2})
-  auto evolve_split = [&](int i, SvdOut& sv) {
+  // y <- exp(-i delta H_eff^(2)) A_i A_{i+1}, then its SVD as (m_i d) x (d m_{i+2}); only the
+  // factor that becomes a site tensor (U left to right, Vh right to left) is formed, the
+  // centre is then a GEMM with y
+  auto evolve_split = [&](int i, SvdOut& sv, bool left_to_right) {
     const int ml = psi.m[i], m = psi.m[i + 1], mr = psi.m[i + 2];
     const long long n = (long long)ml * d * d * mr;
     theta.ensure(&pool, n);
@@ -588,7 +580,7 @@ void Engine::sweep2(double dt, int kind) {
     }
     if (imag) normalize(y.data(), n);
     PhaseScope ps(tracer, PH_SVD);
-    svd_jacobi(st, &pool, y.data(), ml * d, d * mr, rule, sv, true, true);
+    svd_jacobi(st, &pool, y.data(), ml * d, d * mr, rule, sv, left_to_right, !left_to_right);
     tdvp_require(sv.rank >= 1, TDVP_ERR_NONFINITE, "sweep2: zero two-site tensor");
   };
   // C <- exp(+i delta H_eff^(1)) C on site j (the backward step)
@@ -602,21 +594,15 @@ void Engine::sweep2(double dt, int kind) {
     if (imag) normalize(out.data(), n);
     C = std::move(out);
   };
-  auto upload_s = [&](const SvdOut& sv) {
-    double* d_s = nullptr;
-    TDVP_CUDA(cudaMallocAsync(&d_s, sizeof(double) * sv.rank, st));
-    TDVP_CUDA(cudaMemcpyAsync(d_s, sv.s.data(), sizeof(double) * sv.rank, cudaMemcpyHostToDevice, st));
-    return d_s;
-  };
   for (int i = 0; i + 1 < N; ++i) {
     const int mr = psi.m[i + 2];
     SvdOut sv;
-    evolve_split(i, sv);
+    evolve_split(i, sv, true);
     const int r = sv.rank;
-    DArr C(&pool, (size_t)r * d * mr);  // S Vh: the centre on site i+1
-    double* d_s = upload_s(sv);
-    scale_rows(st, C.data(), sv.Vh.data(), d_s, r, d * mr);
-    TDVP_CUDA(cudaFreeAsync(d_s, st));
+    const int ml = psi.m[i];
+    DArr C(&pool, (size_t)r * d * mr);  // U^+ Theta = S Vh: the centre on site i+1
+    zgemm(st, OP_C, OP_N, r, d * mr, ml * d, kOne, sv.U.data(), r, y.data(), d * mr, kZero, C.data(), d * mr, 1, 0,
+          0, 0, &pool);
     psi.A[i] = std::move(sv.U);
     psi.m[i + 1] = r;
     env_left(i);  // L[i+1]
@@ -629,12 +615,12 @@ void Engine::sweep2(double dt, int kind) {
   for (int i = N - 2; i >= 0; --i) {
     const int ml = psi.m[i];
     SvdOut sv;
-    evolve_split(i, sv);
+    evolve_split(i, sv, false);
     const int r = sv.rank;
-    DArr C(&pool, (size_t)ml * d * r);  // U S: the centre on site i
-    double* d_s = upload_s(sv);
-    scale_cols(st, C.data(), sv.U.data(), d_s, ml * d, r);
-    TDVP_CUDA(cudaFreeAsync(d_s, st));
+    const int mr = psi.m[i + 2];
+    DArr C(&pool, (size_t)ml * d * r);  // Theta Vh^+ = U S: the centre on site i
+    zgemm(st, OP_N, OP_C, ml * d, r, d * mr, kOne, y.data(), d * mr, sv.Vh.data(), d * mr, kZero, C.data(), r, 1, 0,
+          0, 0, &pool);
     psi.A[i + 1] = std::move(sv.Vh);
     psi.m[i + 1] = r;
     env_right(i + 1);  // R[i]
