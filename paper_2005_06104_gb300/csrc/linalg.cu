@@ -857,6 +857,12 @@ __device__ __forceinline__ void rr_pair(int round, int k, int qpad, int& P, int&
 // them against each other chases rounding noise for extra sweeps while moving the
 // kept columns by at most 1e-15.
 constexpr double kJacobiFloor = 1e-30;
+// A sweep whose rotations all have |sin theta| <= 1e-8 ends the iteration.  Each rotation
+// annihilates its pair's coupling and only mixes the couplings of its two columns with the
+// others, so after such a sweep every remaining coupling is of second order in the angles
+// (about 1e-16 relative), which a further sweep would only confirm.  Near-degenerate
+// columns with a tiny coupling give large angles and keep the iteration going.
+constexpr double kJacobiSmallAngle2 = 1e-16;
 __device__ __forceinline__ bool jacobi_params(double a, double b, cplx c, double tol, double floor2,
                                               double& cs, cplx& sne) {
   const double big = fmax(a, b), small = fmin(a, b);
@@ -896,7 +902,8 @@ __global__ void k_svd_prepare(const cplx* __restrict__ M, int rows, int cols, in
   }
 }
 
-// One pair (P, Q) rotated by a whole block; returns true when a rotation was applied.
+// One pair (P, Q) rotated by a whole block; returns true when a rotation with
+// |sin theta| above 1e-8 was applied (kJacobiSmallAngle2).
 __device__ bool jacobi_pair_block(cplx* __restrict__ X, cplx* __restrict__ V, int p, int q, int P, int Q,
                                   double tol, double floor2, int want_v) {
   __shared__ double ra[8], rb[8];
@@ -953,6 +960,7 @@ __device__ bool jacobi_pair_block(cplx* __restrict__ X, cplx* __restrict__ V, in
     xp[r] = u;
     xq[r] = v;
   }
+  const bool significant = cabs2(sne) > kJacobiSmallAngle2;
   if (want_v) {
     cplx* vp = V + (long long)P * q;
     cplx* vq = V + (long long)Q * q;
@@ -963,7 +971,7 @@ __device__ bool jacobi_pair_block(cplx* __restrict__ X, cplx* __restrict__ V, in
       vq[r] = v;
     }
   }
-  return true;
+  return significant;
 }
 
 // Grid-wide barrier for the cooperative path (all blocks co-resident by cooperative
@@ -1086,7 +1094,7 @@ __global__ void __launch_bounds__(256)
         double cs;
         cplx sne;
         if (!jacobi_params(a, b, c, tol, floor2, cs, sne)) continue;
-        if (lane == 0) s_rot = 1;
+        if (lane == 0 && cabs2(sne) > kJacobiSmallAngle2) s_rot = 1;
         for (int r = lane; r < p; r += 32) {
           cplx u = xp[r], v = xq[r];
           rotate_pair(u, v, cs, sne);
@@ -1465,7 +1473,7 @@ __global__ void __launch_bounds__(256)
         double cs;
         cplx sne;
         if (!jacobi_params(a, b, c, tol, floor2, cs, sne)) continue;
-        if (lane == 0) s_rot = 1;
+        if (lane == 0 && cabs2(sne) > kJacobiSmallAngle2) s_rot = 1;
         for (int r = lane; r < p; r += 32) {
           cplx u = xp[r], v = xq[r];
           rotate_pair(u, v, cs, sne);
