@@ -1319,18 +1319,6 @@ void svd_jacobi_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows,
 // small helpers
 // ============================================================================
 namespace {
-__global__ void k_scale_rows(cplx* __restrict__ out, const cplx* __restrict__ in,
-                             const double* __restrict__ s, int r, int c) {
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (long long)r * c) return;
-  out[e] = cscale(in[e], s[e / c]);
-}
-__global__ void k_scale_cols(cplx* __restrict__ out, const cplx* __restrict__ in,
-                             const double* __restrict__ s, int rows, int r) {
-  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (e >= (long long)rows * r) return;
-  out[e] = cscale(in[e], s[e % r]);
-}
 __global__ void k_copy_block(cplx* __restrict__ dst, long long ldd, const cplx* __restrict__ src,
                              long long lds, int rows, int cols) {
   const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
@@ -1340,18 +1328,6 @@ __global__ void k_copy_block(cplx* __restrict__ dst, long long ldd, const cplx* 
 }
 }  // namespace
 
-void scale_rows(cudaStream_t st, cplx* out, const cplx* in, const double* s_dev, int r, int c) {
-  const long long n = (long long)r * c;
-  if (!n) return;
-  k_scale_rows<<<ceil_div(n, 256), 256, 0, st>>>(out, in, s_dev, r, c);
-  TDVP_CHECK_LAUNCH();
-}
-void scale_cols(cudaStream_t st, cplx* out, const cplx* in, const double* s_dev, int rows, int r) {
-  const long long n = (long long)rows * r;
-  if (!n) return;
-  k_scale_cols<<<ceil_div(n, 256), 256, 0, st>>>(out, in, s_dev, rows, r);
-  TDVP_CHECK_LAUNCH();
-}
 void copy_block(cudaStream_t st, cplx* dst, long long ldd, const cplx* src, long long lds, int rows,
                 int cols) {
   const long long n = (long long)rows * cols;

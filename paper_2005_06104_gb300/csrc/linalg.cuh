@@ -227,9 +227,6 @@ inline void eig_psd_jacobi(cudaStream_t st, DevicePool* pool, const cplx* M, int
   svd_blocked_keep(st, pool, M, n, n, thunk, &select, out, true, false, true);
 }
 
-// rows-of-Vh scaling helpers: out[r][c] = s[r] * Vh[r][c]; out[i][r] = U[i][r] * s[r]
-void scale_rows(cudaStream_t st, cplx* out, const cplx* in, const double* s_dev, int r, int c);
-void scale_cols(cudaStream_t st, cplx* out, const cplx* in, const double* s_dev, int rows, int r);
 // copy a (rows x cols) block into a (rows x ldo) destination at column offset
 void copy_block(cudaStream_t st, cplx* dst, long long ldd, const cplx* src, long long lds,
                 int rows, int cols);
