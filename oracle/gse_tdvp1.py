@@ -410,16 +410,55 @@ def apply_mpo_exact(W, mps):
     return out
 
 
-def krylov_vectors(psi, W, tau, k, eps_k, chi_max):
+ZIP_RELAX = 0.1  # Z1: the zip pass truncates with ZIP_RELAX * eps and a cap of 2 chi_max
+
+
+def apply_mpo_zipup(W, mps, eps, chi_max=None):
+    """W|mps> by the zip-up algorithm (Stoudenmire and White, NJP 12, 055026), the
+    alternative to the density-matrix application that needs no right density environments
+    (Sec. I.B names applying the MPO variationally or by density matrices).
+
+    The state is brought to left-canonical form (exact, R1).  A right-to-left pass then
+    contracts each site with the MPO and the carry from the right and splits the result
+    by an SVD truncated with the relaxed cutoff ZIP_RELAX * eps and a cap of 2 chi_max
+    (the right block of W|mps> is not orthonormal, so the local weights are only
+    approximate there); the rows become right-orthonormal site tensors and U S moves
+    left.  A left-to-right compression with eps and chi_max follows.
+    Returns a left-canonical MPS with the centre at site N (not normalised)."""
+    psi = left_canonicalize(mps)
+    n = len(psi)
+    cap_zip = None if chi_max is None else 2 * chi_max
+    carry = np.ones((1, 1, 1), dtype=np.complex128)      # [v, b, r]: MPO bond, state bond, new bond
+    out = [None] * n
+    for i in range(n - 1, -1, -1):
+        T = np.tensordot(psi[i], W[i], axes=([1], [2]))  # [a, b, w, s, v]
+        T = np.tensordot(T, carry, axes=([1, 4], [1, 0]))  # [a, w, s, r]
+        ml, wl, d, rt = T.shape
+        M = T.reshape(ml * wl, d * rt)
+        if i == 0:
+            out[0] = M.reshape(1, d, rt)
+            break
+        U, S, Vh, _ = svd_truncate(M, ZIP_RELAX * eps, cap_zip)
+        out[i] = Vh.reshape(-1, d, rt)
+        carry = (U * S[None, :]).reshape(ml, wl, -1).transpose(1, 0, 2)
+    return left_canonicalize(out, eps, chi_max)
+
+
+def krylov_vectors(psi, W, tau, k, eps_k, chi_max, method="exact"):
     """|psi~_l> = (1 - i tau H)^l |psi>, l = 1..k-1 (Eq. 10), each compressed with
-    cutoff eps_k and cap chi_max, normalised, left-canonical with centre at N."""
+    cutoff eps_k and cap chi_max, normalised, left-canonical with centre at N.
+    method "exact": exact application and SVD compression (the result of the density-matrix
+    algorithm up to ties); "zipup": apply_mpo_zipup."""
     Wk = mpo_one_minus_itau_h(W, tau)
     phis = []
     phi = psi
     for _ in range(1, k):
-        phi = apply_mpo_exact(Wk, phi)
-        phi = right_canonicalize(phi)
-        phi = left_canonicalize(phi, eps_k, chi_max)
+        if method == "zipup":
+            phi = apply_mpo_zipup(Wk, phi, eps_k, chi_max)
+        else:
+            phi = apply_mpo_exact(Wk, phi)
+            phi = right_canonicalize(phi)
+            phi = left_canonicalize(phi, eps_k, chi_max)
         phi[-1] = phi[-1] / np.linalg.norm(phi[-1])
         phis.append(phi)
     return phis
@@ -483,12 +522,13 @@ def basis_extension(psi, phis, weights=None, eps_m=1e-8, chi_max=None):
 
 
 # ------------------------------------------------------------ one GSE-TDVP1 step (Sec. I.C)
-def expand_basis(psi, W, tau, k, eps_k, eps_m, chi_max, weights=None):
-    """Steps 1 and 2: psi (any gauge) -> right-canonical, centre at site 1, bases enlarged."""
+def expand_basis(psi, W, tau, k, eps_k, eps_m, chi_max, weights=None, method="exact"):
+    """Steps 1 and 2: psi (any gauge) -> right-canonical, centre at site 1, bases enlarged.
+    method: how the Krylov vectors apply the MPO (krylov_vectors)."""
     psi = left_canonicalize(psi)
     if k <= 1:
         return right_canonicalize(psi)
-    phis = krylov_vectors(psi, W, tau, k, eps_k, chi_max)
+    phis = krylov_vectors(psi, W, tau, k, eps_k, chi_max, method)
     out, _ = basis_extension(psi, phis, weights, eps_m, chi_max)
     return out
 
@@ -496,7 +536,7 @@ def expand_basis(psi, W, tau, k, eps_k, eps_m, chi_max, weights=None):
 def gse_tdvp1_step(psi, W, p, stats=None):
     """Steps 1-3 of GSE-TDVP1 with the parameters dict p (keys as in workloads)."""
     psi = expand_basis(psi, W, p["tau"], p["k"], p["eps_k"], p["eps_m"], p["chi_max"],
-                       p.get("weights"))
+                       p.get("weights"), p.get("krylov", "exact"))
     return tdvp1_sweep(psi, W, p["dt"], p["kind"], p.get("eps", 0.0), p["chi_max"],
                        p.get("tol", 1e-12), p.get("nmax", 40), stats)
 
