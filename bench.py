@@ -48,6 +48,8 @@ def parse():
     ap.add_argument("--prep-steps", type=int, default=9,
                     help="untimed GSE-TDVP1 steps that grow the bond dimension before warm-up")
     ap.add_argument("--k", type=int, default=3)
+    ap.add_argument("--krylov", default="dm", choices=["dm", "zipup"],
+                    help="Krylov vectors by the density-matrix algorithm (default) or by zip-up")
     ap.add_argument("--dt", type=float, default=0.1)
     ap.add_argument("--heff-chi", type=int, default=1024, help="bond dimension of the H_eff roofline probe")
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -97,7 +99,7 @@ def workload(args):
            "krylov_order_k": args.k, "dt": args.dt, "tau": args.dt, "eps_k": 1e-8, "eps_m": 1e-8, "eps": 0.0,
            "time": "real", "precision_form": PRECISION_TEXT[args.precision],
            "start_state": "Neel with the spin at (8,0) flipped", "prep_steps": args.prep_steps,
-           "compare_chi": args.compare_chi,
+           "compare_chi": args.compare_chi, "krylov_method": "density_matrix" if args.krylov == "dm" else "zipup",
            "l2": "working set of a step (environments, Krylov vectors, density environments) > L2; no flush"}
     return lat, W, psi, cfg
 
@@ -301,10 +303,16 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     from paper_2005_06104_gb300 import gse_tdvp as g
     lat, W, psi0, cfg = workload(args)
+
+    def new_handle(*a, **kw):
+        h = g.GseTdvp(*a, **kw)
+        if args.krylov == "zipup":
+            h.krylov_method(g.KRYLOV_ZIPUP)
+        return h
     opts = dict(tau=args.dt, eps_k=1e-8, eps_m=1e-8, eps=0.0, chi_max=args.chi_max,
                 precision=prec_code(g, args.precision))
     stream = torch.cuda.current_stream().cuda_stream
-    st = g.GseTdvp(psi0, W, stream=stream, **opts)
+    st = new_handle(psi0, W, stream=stream, **opts)
     e_init = st.energy()
 
     def step(h):
@@ -380,23 +388,23 @@ def run_gpu(args):
         eb.synchronize()
         return ea.elapsed_time(eb)
     copts = dict(opts, chi_max=args.compare_chi)
-    cmp_h = g.GseTdvp(psi0, W, stream=stream, **copts)
+    cmp_h = new_handle(psi0, W, stream=stream, **copts)
     for _ in range(8 + args.warmup):
         step(cmp_h)
     cmp_state = cmp_h.get_mps()
     cmp_dims = cmp_h.bond_dims()
     cmp_h.close()
-    a = g.GseTdvp(cmp_state, W, stream=stream, **dict(copts, precision=g.PREC_FP64))
+    a = new_handle(cmp_state, W, stream=stream, **dict(copts, precision=g.PREC_FP64))
     ms_64 = timed_step(a, step)
     e_64 = a.energy()
     a.close()
-    b_ = g.GseTdvp(cmp_state, W, stream=stream, **copts)
+    b_ = new_handle(cmp_state, W, stream=stream, **copts)
     ms_tc = timed_step(b_, step)
     e_tc, n_tc = b_.energy(), b_.norm()
     b_.close()
     tdvp2 = None
     if not args.no_tdvp2:
-        c_ = g.GseTdvp(cmp_state, W, stream=stream, **copts)
+        c_ = new_handle(cmp_state, W, stream=stream, **copts)
         c_.trace(True)
         ms_2 = timed_step(c_, lambda h: h.sweep2(args.dt, g.REAL))
         tdvp2 = {"chi_max": args.compare_chi, "step_ms": ms_2, "gse_tdvp1_step_ms": ms_tc,
@@ -413,7 +421,7 @@ def run_gpu(args):
     for _ in range(max(1, min(args.steps, 2))):
         torch.cuda.synchronize()
         t = time.perf_counter()
-        s2 = g.GseTdvp(start_state, W, stream=stream, **opts)
+        s2 = new_handle(start_state, W, stream=stream, **opts)
         step(s2)
         out = s2.get_mps()
         s2.close()

@@ -139,6 +139,20 @@ TDVP_API tdvp_status tdvp_expand_basis(tdvp_handle* h, int k, const double* weig
  * (optional) receives K of the last Krylov step, 1 when every F_j stayed. */
 TDVP_API tdvp_status tdvp_krylov_memory(tdvp_handle* h, double max_bytes, int* last_segment);
 
+/* How tdvp_expand_basis and tdvp_apply_krylov apply 1 - i tau H (Sec. I.B names
+ * the density-matrix approach and applying the MPO variationally).
+ *  TDVP_KRYLOV_DENSITY_MATRIX (default): right density environments, then one
+ *    left-to-right pass of density-matrix eigendecompositions (optimal truncation;
+ *    F_j memory, see tdvp_krylov_memory).
+ *  TDVP_KRYLOV_ZIPUP: the zip-up algorithm, no density environments.  Right to left
+ *    over the left-canonical source, each site contracted with the MPO and the carry
+ *    is split by the eigendecomposition of its Gram matrix with the relaxed cutoff
+ *    0.1 eps_k and the cap chi_max; then one left-to-right SVD compression with eps_k
+ *    and chi_max.  The result is normalised, left-canonical, centre at N-1.
+ * Other values give TDVP_ERR_INVALID_ARG. */
+typedef enum { TDVP_KRYLOV_DENSITY_MATRIX = 0, TDVP_KRYLOV_ZIPUP = 1 } tdvp_krylov_method;
+TDVP_API tdvp_status tdvp_set_krylov_method(tdvp_handle* h, int method);
+
 /* One Krylov vector in place (Eq. 10 with l = 1, Sec. I.B): the state becomes
  * (1 - i tau H)|psi>, applied by the density-matrix approach with cutoff eps_k
  * and cap chi_max, normalised, left-canonical with the centre at site N-1.

@@ -410,7 +410,7 @@ def apply_mpo_exact(W, mps):
     return out
 
 
-ZIP_RELAX = 0.1  # Z1: the zip pass truncates with ZIP_RELAX * eps and a cap of 2 chi_max
+ZIP_RELAX = 0.1  # Z1: the zip pass truncates with ZIP_RELAX * eps and the cap chi_max
 
 
 def apply_mpo_zipup(W, mps, eps, chi_max=None):
@@ -420,14 +420,13 @@ def apply_mpo_zipup(W, mps, eps, chi_max=None):
 
     The state is brought to left-canonical form (exact, R1).  A right-to-left pass then
     contracts each site with the MPO and the carry from the right and splits the result
-    by an SVD truncated with the relaxed cutoff ZIP_RELAX * eps and a cap of 2 chi_max
+    by an SVD truncated with the relaxed cutoff ZIP_RELAX * eps and the cap chi_max
     (the right block of W|mps> is not orthonormal, so the local weights are only
     approximate there); the rows become right-orthonormal site tensors and U S moves
     left.  A left-to-right compression with eps and chi_max follows.
     Returns a left-canonical MPS with the centre at site N (not normalised)."""
     psi = left_canonicalize(mps)
     n = len(psi)
-    cap_zip = None if chi_max is None else 2 * chi_max
     carry = np.ones((1, 1, 1), dtype=np.complex128)      # [v, b, r]: MPO bond, state bond, new bond
     out = [None] * n
     for i in range(n - 1, -1, -1):
@@ -438,7 +437,7 @@ def apply_mpo_zipup(W, mps, eps, chi_max=None):
         if i == 0:
             out[0] = M.reshape(1, d, rt)
             break
-        U, S, Vh, _ = svd_truncate(M, ZIP_RELAX * eps, cap_zip)
+        U, S, Vh, _ = svd_truncate(M, ZIP_RELAX * eps, chi_max)
         out[i] = Vh.reshape(-1, d, rt)
         carry = (U * S[None, :]).reshape(ml, wl, -1).transpose(1, 0, 2)
     return left_canonicalize(out, eps, chi_max)

@@ -148,6 +148,14 @@ tdvp_status tdvp_krylov_memory(tdvp_handle* h, double max_bytes, int* last_segme
   });
 }
 
+tdvp_status tdvp_set_krylov_method(tdvp_handle* h, int method) {
+  return guarded(h, [&] {
+    tdvp_require(method == TDVP_KRYLOV_DENSITY_MATRIX || method == TDVP_KRYLOV_ZIPUP, TDVP_ERR_INVALID_ARG,
+                 "unknown Krylov method");
+    h->eng.krylov_method = method;
+  });
+}
+
 tdvp_status tdvp_sweep2(tdvp_handle* h, double dt, tdvp_time kind) {
   return guarded(h, [&] {
     tdvp_require(std::isfinite(dt), TDVP_ERR_INVALID_ARG, "dt not finite");

@@ -101,6 +101,32 @@ __global__ void k_omega_stage(const cplx* __restrict__ T2, cplx* __restrict__ F,
   F[((a * wl + w) * wl + wb) * ml + ab] = acc;
 }
 
+// Zip-up MPO stage: out[a][w][s][c] = sum_{(v,t)} W[w,s,t,v] in[a][t][v][c]
+// (the right grouping of the sparse MPO lists: row s * wl + w holds the (v, t) entries).
+__global__ void k_wstage_zip(const cplx* __restrict__ in, cplx* __restrict__ out, int wl, int wr, int d, int C,
+                             const int* __restrict__ off, const int* __restrict__ idx,
+                             const cplx* __restrict__ val) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  const int sw = blockIdx.y;
+  const long long a = blockIdx.z;
+  if (c >= C) return;
+  const int s = sw / wl, w = sw % wl;
+  cplx acc = mkc(0.0, 0.0);
+  for (int e = off[sw]; e < off[sw + 1]; ++e) {
+    const int v = idx[2 * e], t = idx[2 * e + 1];
+    cfma(acc, val[e], in[((a * d + t) * wr + v) * (long long)C + c]);
+  }
+  out[((a * wl + w) * d + s) * (long long)C + c] = acc;
+}
+
+// out[k][j] = conj(in[j][k]), in: rows x cols
+__global__ void k_adjoint(const cplx* __restrict__ in, cplx* __restrict__ out, int rows, int cols) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e >= (long long)rows * cols) return;
+  const long long k = e / rows, j = e % rows;  // e indexes out[k][j]
+  out[e] = cconj(in[j * cols + k]);
+}
+
 // F[v][b][x] from Fp[b][v][x] (x: the wr * m contiguous trailing entries)
 __global__ void k_swap_outer(const cplx* __restrict__ Fp, cplx* __restrict__ F, int m, int wr) {
   const long long inner = (long long)wr * m;
@@ -728,6 +754,10 @@ void KrylovOp::release() {
 // This reaches, up to ties, the state of exact application followed by a
 // right-canonical sweep and left-to-right SVD truncation.
 void Engine::krylov_apply(const KrylovOp& kop, const MpsDev& src, MpsDev& out) {
+  if (krylov_method == 1) {
+    krylov_zipup(kop, src, out);
+    return;
+  }
   const cplx one = mkc(1.0, 0.0), zero = mkc(0.0, 0.0);
   // the Krylov vectors only enrich the basis (the state itself is kept exactly by the
   // extension), so the precision form may build them on the tensor cores
@@ -858,6 +888,106 @@ void Engine::krylov_apply(const KrylovOp& kop, const MpsDev& src, MpsDev& out) {
   const long long n = (long long)out.m[N - 1] * d;
   blas.norm2(st, out.A[N - 1].data(), n, lw.real + 150);
   scale_by_inv_sqrt(st, out.A[N - 1].data(), out.A[N - 1].data(), lw.real + 150, n);
+}
+
+// Zip-up application of 1 - i tau H (the alternative to the density-matrix algorithm that
+// needs no right density environments).  The source is left-canonical with its centre at
+// N-1.  Right to left, each site is contracted with the MPO and the carry from the right,
+// M[(a,w)][(s,r)]; its Gram matrix M^+ M gives the right singular vectors V (Hermitian PSD
+// eigendecomposition) under the relaxed cutoff 0.1 eps_k and the cap chi_max.  The rows of
+// V^+ become right-orthonormal site tensors and M V = U S is the next carry.  One
+// left-to-right compression with eps_k and chi_max follows; the result is normalised,
+// left-canonical with its centre at N-1.
+void Engine::krylov_zipup(const KrylovOp& kop, const MpsDev& src, MpsDev& out) {
+  const int kp = opt.precision;
+  const double eps_k = opt.eps_k;
+  const int cap = opt.chi_max;
+  MpsDev t;
+  t.N = N;
+  t.d = d;
+  t.m.assign(N + 1, 1);
+  t.A.resize(N);
+  DArr X(&pool, 1), T1, M, rho;
+  k_one<<<1, 1, 0, st>>>(X.data());
+  TDVP_CHECK_LAUNCH();
+  int rt = 1;  // carry X[b][v][r]: src.m[i+1] x w[i+1] x rt
+  for (int i = N - 1; i >= 0; --i) {
+    const int ml = src.m[i], mr = src.m[i + 1], wl = w[i], wr = w[i + 1];
+    // T1[(a,t)][(v,r)] = sum_b A[(a,t), b] X[b][(v,r)]
+    T1.ensure(&pool, (size_t)ml * d * wr * rt);
+    zgemm_prec(st, scr, kp, OP_N, OP_N, ml * d, wr * rt, mr, src.A[i].data(), mr, X.data(), (long long)wr * rt,
+               T1.data(), (long long)wr * rt);
+    // M[(a,w)][(s,r)] = sum_{(v,t)} W[w,s,t,v] T1[a][t][v][r]
+    M.ensure(&pool, (size_t)ml * wl * d * rt);
+    {
+      const WSparse& ws = kop.Wsp[i];
+      tdvp_require(ml <= 65535, TDVP_ERR_INVALID_ARG, "zip-up: bond too large");
+      dim3 g(ceil_div(rt, 128), d * wl, ml);
+      k_wstage_zip<<<g, 128, 0, st>>>(T1.data(), M.data(), wl, wr, d, rt, ws.d_r_off, ws.d_r_idx, ws.d_r_val);
+      TDVP_CHECK_LAUNCH();
+    }
+    const int n = d * rt, K = ml * wl;
+    if (i == 0) {  // K = 1: M is the centre tensor (1, d, rt)
+      t.A[0].reset(&pool, (size_t)n);
+      TDVP_CUDA(cudaMemcpyAsync(t.A[0].data(), M.data(), sizeof(cplx) * n, cudaMemcpyDeviceToDevice, st));
+      t.m[1] = rt;
+      break;
+    }
+    rho.ensure(&pool, (size_t)n * n);
+    zgemm_prec(st, scr, kp, OP_C, OP_N, n, n, K, M.data(), n, M.data(), n, rho.data(), n);
+    auto rule = [eps_k, cap](const std::vector<double>& ev) -> int {
+      double tot = 0.0;
+      for (double v : ev) tot += v;
+      if (!(tot > 0.0)) return 0;
+      return keep_count(ev, tot, 0.1 * eps_k, cap, 1e-14 * ev[0]);
+    };
+    SvdOut sv;
+    {
+      PhaseScope ps(tracer, PH_KRYLOV_EIG);
+      eig_psd_jacobi(st, &pool, rho.data(), n, rule, sv);
+    }
+    const int keep = sv.rank;
+    tdvp_require(keep >= 1, TDVP_ERR_NONFINITE, "zip-up: zero site");
+    // site tensor V^+ (keep x (s, r)); next carry M V ((a, w) x keep) = [b][v][r] of site i-1
+    t.A[i].reset(&pool, (size_t)keep * n);
+    k_adjoint<<<ceil_div((long long)keep * n, 256), 256, 0, st>>>(sv.U.data(), t.A[i].data(), n, keep);
+    TDVP_CHECK_LAUNCH();
+    DArr Xn(&pool, (size_t)K * keep);
+    zgemm_prec(st, scr, kp, OP_N, OP_N, K, keep, n, M.data(), n, sv.U.data(), keep, Xn.data(), keep);
+    X = std::move(Xn);
+    t.m[i] = keep;
+    t.m[i + 1] = rt;
+    rt = keep;
+  }
+  T1.release();
+  M.release();
+  rho.release();
+  X.release();
+  // left-to-right compression with eps_k and chi_max (the centre moves by U^+ A)
+  SvdRule crule;
+  crule.eps = eps_k;
+  crule.cap = cap;
+  crule.discarded = &disc_k;
+  for (int i = 0; i + 1 < N; ++i) {
+    const int ml = t.m[i], mr = t.m[i + 1], mr2 = t.m[i + 2];
+    SvdOut sv;
+    svd_jacobi(st, &pool, t.A[i].data(), ml * d, mr, crule, sv, true, false);
+    const int r = sv.rank;
+    tdvp_require(r >= 1, TDVP_ERR_NONFINITE, "zip-up: zero tensor in the compression");
+    DArr C(&pool, (size_t)r * mr);
+    zgemm(st, OP_C, OP_N, r, mr, ml * d, kOne, sv.U.data(), r, t.A[i].data(), mr, kZero, C.data(), mr, 1, 0, 0, 0,
+          &pool);
+    DArr nxt(&pool, (size_t)r * d * mr2);
+    zgemm(st, OP_N, OP_N, r, d * mr2, mr, kOne, C.data(), mr, t.A[i + 1].data(), d * mr2, kZero, nxt.data(),
+          d * mr2, 1, 0, 0, 0, &pool);
+    t.A[i] = std::move(sv.U);
+    t.A[i + 1] = std::move(nxt);
+    t.m[i + 1] = r;
+  }
+  const long long n_last = (long long)t.m[N - 1] * d;
+  blas.norm2(st, t.A[N - 1].data(), n_last, lw.real + 150);
+  scale_by_inv_sqrt(st, t.A[N - 1].data(), t.A[N - 1].data(), lw.real + 150, n_last);
+  out = std::move(t);
 }
 
 void Engine::expand_basis(int k, const double* weights) {

@@ -52,6 +52,7 @@ struct Engine {
   // device bytes the Krylov step may hold in right density environments (0: half the free memory)
   double krylov_mem_budget = 0.0;
   int krylov_env_segment = 1;  // last Krylov step: 1 = all resident, else the checkpoint spacing
+  int krylov_method = 0;       // 0: density-matrix application, 1: zip-up
   // optional timing of the H_eff applies (CUDA events on the engine stream)
   bool profile = false;
   std::vector<cudaEvent_t> ev_pool;
@@ -92,6 +93,8 @@ struct Engine {
   void expand_basis(int k, const double* weights);
   void build_krylov_op(KrylovOp& kop);
   void krylov_apply(const KrylovOp& kop, const MpsDev& src, MpsDev& out);
+  // the zip-up application of the same operator (no right density environments)
+  void krylov_zipup(const KrylovOp& kop, const MpsDev& src, MpsDev& out);
   void apply_krylov();  // state <- normalised, compressed (1 - i tau H) state
   // observables
   double energy();

@@ -23,6 +23,7 @@ _lib = C.CDLL(LIB_PATH)
 
 REAL, IMAG = 0, 1
 PREC_FP64, PREC_TF32X3, PREC_TF32X3_ENV, PREC_BF16X10, PREC_BF16X6 = 0, 1, 2, 3, 4
+KRYLOV_DENSITY_MATRIX, KRYLOV_ZIPUP = 0, 1
 STATUS = {0: "ok", 1: "invalid argument", 2: "shape mismatch", 3: "out of memory",
           4: "Lanczos not converged", 5: "non-finite value", 6: "device wait timed out",
           7: "CUDA error", 8: "SVD not converged"}
@@ -57,6 +58,7 @@ _sig = {
     "tdvp_sweep": [_h, C.c_double, C.c_int],
     "tdvp_sweep2": [_h, C.c_double, C.c_int],
     "tdvp_krylov_memory": [_h, C.c_double, C.POINTER(C.c_int)],
+    "tdvp_set_krylov_method": [_h, C.c_int],
     "tdvp_heff_apply": [_h, C.c_int, C.c_void_p, C.c_void_p, C.c_int],
     "tdvp_keff_apply": [_h, C.c_int, C.c_void_p, C.c_void_p, C.c_int],
     "tdvp_evolve_site": [_h, C.c_int, C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.c_int,
@@ -363,6 +365,10 @@ class GseTdvp:
         seg = C.c_int(0)
         self._chk(_lib.tdvp_krylov_memory(self.h, float(max_bytes), C.byref(seg)))
         return seg.value
+
+    def krylov_method(self, method):
+        """KRYLOV_DENSITY_MATRIX (default) or KRYLOV_ZIPUP for the Krylov vectors of Eq. 10."""
+        self._chk(_lib.tdvp_set_krylov_method(self.h, int(method)))
 
     def sweep2(self, dt, kind=REAL):
         """One two-site TDVP step (TDVP2), truncating with eps and chi_max in both time kinds."""
