@@ -1790,9 +1790,215 @@ __global__ void __launch_bounds__(256)
   }
 }
 
+// Pivoted Cholesky of Hermitian PSD blocks with one group of CTAs per block (cooperative
+// launch), for blocks too wide for one SM's FP64 pipe.  The block is column-major
+// (entry (r, c) at c n + r); CTA lc of a group of G owns the columns c = lc (mod G).  Pivot
+// step j: every CTA posts the largest diagonal entry of its own columns from row j on
+// (ties to the smaller index); after a group barrier all read the same pivot k.  CTA 0
+// swaps columns j and k whole, then rows j and k inside them, and forms column j of the
+// factor; the other CTAs swap rows j and k in their own columns.  After a second barrier
+// every CTA updates its own trailing columns with column j.  Each entry sees the
+// arithmetic of k_pchol_batched, so the factor and the pivots are the same.
+__global__ void __launch_bounds__(256)
+    k_pchol_groups(cplx* __restrict__ X, BlkDesc* __restrict__ desc, int* __restrict__ piv,
+                   const int* __restrict__ cta_off, int nblk, double rel_floor, double* __restrict__ pval,
+                   int* __restrict__ pidx, GridBar* __restrict__ bars, int* __restrict__ gerr) {
+  __shared__ double s_val[8];
+  __shared__ int s_idx[8];
+  int lo = 0, hi = nblk - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (cta_off[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+  }
+  const int b = lo;
+  const int c0 = cta_off[b];
+  const int lc = blockIdx.x - c0;
+  const int G = cta_off[b + 1] - c0;
+  GridBar* bar = bars + b;
+  const int n = desc[b].p;
+  cplx* A = X + desc[b].x_off;
+  int* pv = piv + desc[b].r_off;
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5, nw = blockDim.x >> 5;
+  unsigned epoch = 0;
+  if (lc == 0)
+    for (int i = tid; i < n; i += blockDim.x) pv[i] = i;
+  // first index >= from owned by this CTA
+  auto first_own = [&](int from) { return from + ((lc - from % G) % G + G) % G; };
+  // posts (largest diagonal entry of the own columns i >= from, its index); n = none
+  auto post_argmax = [&](int from) {
+    double v = -1.0;
+    int k = n;
+    for (int i = first_own(from) + tid * G; i < n; i += blockDim.x * G) {
+      const double t = A[(long long)i * n + i].x;
+      if (t > v || (t == v && i < k)) {
+        v = t;
+        k = i;
+      }
+    }
+    for (int o = 16; o > 0; o >>= 1) {
+      const double ov = __shfl_xor_sync(0xffffffffu, v, o);
+      const int ok = __shfl_xor_sync(0xffffffffu, k, o);
+      if (ov > v || (ov == v && ok < k)) {
+        v = ov;
+        k = ok;
+      }
+    }
+    if (lane == 0) {
+      s_val[warp] = v;
+      s_idx[warp] = k;
+    }
+    __syncthreads();
+    if (tid == 0) {
+      double bv = s_val[0];
+      int bk = s_idx[0];
+      for (int u = 1; u < nw; ++u)
+        if (s_val[u] > bv || (s_val[u] == bv && s_idx[u] < bk)) {
+          bv = s_val[u];
+          bk = s_idx[u];
+        }
+      pval[blockIdx.x] = bv;
+      pidx[blockIdx.x] = bk;
+    }
+  };
+  // the group's pivot from the posted partials (every thread, same order, same result)
+  auto read_argmax = [&](double& val, int& idx) {
+    double bv = -1.0;
+    int bk = n;
+    for (int u = 0; u < G; ++u) {
+      const double t = ((volatile double*)pval)[c0 + u];
+      const int kk = ((volatile int*)pidx)[c0 + u];
+      if (t > bv || (t == bv && kk < bk)) {
+        bv = t;
+        bk = kk;
+      }
+    }
+    val = bv;
+    idx = bk;
+  };
+  post_argmax(0);
+  if (!group_sync(bar, (unsigned)G, gerr, epoch)) return;
+  double dmax;
+  int k0;
+  read_argmax(dmax, k0);
+  const double thr = rel_floor * dmax;
+  int rank = 0;
+  for (int j = 0; j < n; ++j) {
+    double val = dmax;
+    int k = k0;
+    if (j > 0) {
+      __syncthreads();  // the own trailing columns are complete
+      post_argmax(j);
+      if (!group_sync(bar, (unsigned)G, gerr, epoch)) return;
+      read_argmax(val, k);
+    }
+    if (!(val > thr)) break;  // uniform over the group: every CTA read the same partials
+    if (k != j)
+      for (int c = lc + tid * G; c < n; c += blockDim.x * G) {  // rows j and k, own columns
+        if (c == j || c == k) continue;
+        const cplx t = A[(long long)c * n + j];
+        A[(long long)c * n + j] = A[(long long)c * n + k];
+        A[(long long)c * n + k] = t;
+      }
+    if (lc == 0) {
+      if (k != j) {
+        for (int r = tid; r < n; r += blockDim.x) {  // columns j and k, every row
+          const cplx t = A[(long long)j * n + r];
+          A[(long long)j * n + r] = A[(long long)k * n + r];
+          A[(long long)k * n + r] = t;
+        }
+        __syncthreads();
+        if (tid == 0) {  // rows j and k inside columns j and k
+          cplx t = A[(long long)j * n + j];
+          A[(long long)j * n + j] = A[(long long)j * n + k];
+          A[(long long)j * n + k] = t;
+          t = A[(long long)k * n + j];
+          A[(long long)k * n + j] = A[(long long)k * n + k];
+          A[(long long)k * n + k] = t;
+          const int tp = pv[j];
+          pv[j] = pv[k];
+          pv[k] = tp;
+        }
+        __syncthreads();
+      }
+      const double ljj = sqrt(A[(long long)j * n + j].x);
+      const double inv = 1.0 / ljj;
+      __syncthreads();
+      for (int i = tid; i < n; i += blockDim.x) {
+        cplx& a = A[(long long)j * n + i];
+        if (i > j)
+          a = cscale(a, inv);
+        else if (i < j)
+          a = mkc(0.0, 0.0);
+        else
+          a = mkc(ljj, 0.0);
+      }
+    }
+    if (!group_sync(bar, (unsigned)G, gerr, epoch)) return;  // column j is complete
+    const int m = n - j - 1;
+    const int l0 = first_own(j + 1);
+    const int nc = l0 < n ? (n - 1 - l0) / G + 1 : 0;
+    for (long long e = tid; e < (long long)m * nc; e += blockDim.x) {
+      const int i = j + 1 + (int)(e % m), l = l0 + (int)(e / m) * G;
+      const cplx li = A[(long long)j * n + i], ll = A[(long long)j * n + l];
+      cplx& a = A[(long long)l * n + i];
+      a = csub(a, cmul(li, cconj(ll)));
+    }
+    rank = j + 1;
+  }
+  if (lc == 0 && tid == 0) desc[b].q = rank;
+}
+
 namespace {
 // Host side of k_jacobi_groups: CTA groups per block, one cooperative launch, bounded-wait check.
 // d_stat receives {bad, max sweeps, total sweeps} like the batched kernel.
+// Host side of k_pchol_groups: gsz[b] CTAs for block b (scaled down together when the
+// groups do not all fit on the device at once), one cooperative launch, bounded-wait check.
+void run_pchol_groups(cudaStream_t st, cplx* Xs, BlkDesc* d_desc, int* d_piv, std::vector<int> gsz) {
+  const int nblk = (int)gsz.size();
+  static const int max_ctas = [] {
+    int dev = 0, sms = 0, per_sm = 0;
+    TDVP_CUDA(cudaGetDevice(&dev));
+    TDVP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+    TDVP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_pchol_groups, 256, 0));
+    return std::max(1, sms * std::min(4, std::max(1, per_sm)));
+  }();
+  long long total = 0;
+  for (int g : gsz) total += g;
+  const int budget = std::max(max_ctas, nblk);
+  if (total > budget)
+    for (int& g : gsz) g = std::max<long long>(1, (long long)g * budget / total);
+  std::vector<int> cta_off(nblk + 1, 0);
+  for (int b = 0; b < nblk; ++b) cta_off[b + 1] = cta_off[b] + gsz[b];
+  const int nctas = cta_off[nblk];
+  tdvp_require(nctas <= budget, TDVP_ERR_INVALID_ARG, "Cholesky groups exceed the co-resident CTAs");
+  int* d_off = nullptr;
+  int* d_idx = nullptr;
+  double* d_val = nullptr;
+  GridBar* bars = nullptr;
+  TDVP_CUDA(cudaMallocAsync(&d_off, sizeof(int) * (nblk + 1), st));
+  TDVP_CUDA(cudaMallocAsync(&d_idx, sizeof(int) * (nctas + 1), st));  // + the error word
+  TDVP_CUDA(cudaMallocAsync(&d_val, sizeof(double) * nctas, st));
+  TDVP_CUDA(cudaMallocAsync(&bars, sizeof(GridBar) * nblk, st));
+  int* d_gerr = d_idx + nctas;
+  TDVP_CUDA(cudaMemsetAsync(bars, 0, sizeof(GridBar) * nblk, st));
+  TDVP_CUDA(cudaMemsetAsync(d_gerr, 0, sizeof(int), st));
+  TDVP_CUDA(cudaMemcpyAsync(d_off, cta_off.data(), sizeof(int) * (nblk + 1), cudaMemcpyHostToDevice, st));
+  int nb = nblk;
+  double rel = 1e-15;
+  const int* po = d_off;
+  void* args[] = {&Xs, &d_desc, &d_piv, &po, &nb, &rel, &d_val, &d_idx, &bars, &d_gerr};
+  TDVP_CUDA(cudaLaunchCooperativeKernel((void*)k_pchol_groups, dim3(nctas), dim3(256), args, 0, st));
+  g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+  int herr = 0;
+  TDVP_CUDA(cudaMemcpyAsync(&herr, d_gerr, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TDVP_CUDA(cudaStreamSynchronize(st));
+  TDVP_CUDA(cudaFreeAsync(d_off, st));
+  TDVP_CUDA(cudaFreeAsync(d_idx, st));
+  TDVP_CUDA(cudaFreeAsync(d_val, st));
+  TDVP_CUDA(cudaFreeAsync(bars, st));
+  if (herr) throw TdvpError(TDVP_ERR_TIMEOUT, "pivoted Cholesky: a group barrier wait ran out");
+}
+
 void run_jacobi_multi(cudaStream_t st, cplx* Xs, cplx* Vs, const std::vector<BlkDesc>& desc, const BlkDesc* d_desc,
                       double* d_s, int* d_stat) {
   const int nblk = (int)desc.size();
@@ -1979,8 +2185,19 @@ void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows
       // (under every keep floor of the method) end the factorisation
       TDVP_CUDA(cudaMallocAsync(&d_piv, sizeof(int) * std::max<size_t>(1, ridx.size()), st));
       TDVP_CUDA(cudaMemsetAsync(d_s, 0, sizeof(double) * std::max(1, so), st));
-      k_pchol_batched<<<nsmall, 256, 0, st>>>(Xs.data(), d_desc, d_piv, 1e-15);
-      TDVP_CHECK_LAUNCH();
+      // blocks wider than one SM's FP64 pipe handles quickly get a group of CTAs each
+      std::vector<int> gsz(nsmall);
+      bool grouped = false;
+      for (int b = 0; b < nsmall; ++b) {
+        gsz[b] = std::min(16, std::max(1, desc[b].p / 48));
+        grouped = grouped || gsz[b] > 1;
+      }
+      if (grouped) {
+        run_pchol_groups(st, Xs.data(), d_desc, d_piv, gsz);
+      } else {
+        k_pchol_batched<<<nsmall, 256, 0, st>>>(Xs.data(), d_desc, d_piv, 1e-15);
+        TDVP_CHECK_LAUNCH();
+      }
     }
     std::optional<ActivePhase> jac(std::in_place, PH_SVD_JACOBI);
     if (!multi) {
