@@ -54,6 +54,10 @@ def parse():
     ap.add_argument("--heff-chi", type=int, default=1024, help="bond dimension of the H_eff roofline probe")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tdvp2", action="store_true", help="skip the TDVP2 step of the comparison")
+    ap.add_argument("--fig3", action="store_true",
+                    help="imaginary time on the rung-decoupled ladder (Fig. 3): GSE-TDVP1 at d tau 0.1 and 0.4, TDVP2")
+    ap.add_argument("--fig3-leg", type=int, default=20, help="leg length of the --fig3 ladder")
+    ap.add_argument("--fig3-tau", type=float, default=4.0, help="imaginary time of the --fig3 runs")
     ap.add_argument("--svd-probe", action="store_true",
                     help="time only the blocked Jacobi SVDs of tdvp_create on a dense random MPS (bond --heff-chi)")
     ap.add_argument("--heff-probe", action="store_true",
@@ -534,6 +538,71 @@ def run_svd_probe(args):
                       "jacobi_sweeps": nfo["svd_sweeps"], "widest_block": nfo["svd_max_block"]}), flush=True)
 
 
+def _chain_ground_energy(n):
+    """Lowest eigenvalue of the open Heisenberg chain (J = 1, S = sigma/2) in the S^z = 0
+    sector, by a sparse Lanczos solver on the basis of bit strings with n/2 up spins."""
+    import itertools
+    import scipy.sparse as sp
+    import scipy.sparse.linalg as spla
+    states = [sum(1 << b for b in c) for c in itertools.combinations(range(n), n // 2)]
+    index = {s: i for i, s in enumerate(states)}
+    rows, cols, vals = [], [], []
+    for i, s in enumerate(states):
+        diag = 0.0
+        for b in range(n - 1):
+            u, v = (s >> b) & 1, (s >> (b + 1)) & 1
+            if u == v:
+                diag += 0.25
+            else:
+                diag -= 0.25
+                rows.append(index[s ^ (3 << b)])  # S+S- + S-S+ flips the pair, amplitude 1/2
+                cols.append(i)
+                vals.append(0.5)
+        rows.append(i)
+        cols.append(i)
+        vals.append(diag)
+    H = sp.csr_matrix((vals, (rows, cols)), shape=(len(states), len(states)))
+    return float(spla.eigsh(H, k=1, which="SA", tol=1e-12)[0][0])
+
+
+def run_fig3(args):
+    """Imaginary time on the rung-decoupled zigzag ladder from Neel (Sec. II.A, Fig. 3 at leg
+    length --fig3-leg): GSE-TDVP1 at d tau = 0.1 and 0.4 (i tau = 1/lambda, k = 3,
+    eps_K = 1e-12, eps_M = 1e-8, eps = 1e-10, chi_max 128) against twice the exact ground
+    energy of one leg, and TDVP2 from the same product state."""
+    import torch
+    from paper_2005_06104_gb300 import gse_tdvp as g
+    from paper_2005_06104_gb300 import workloads as wl
+    lx = args.fig3_leg
+    lat = wl.zigzag_ladder(lx, 1.0, 0.0)
+    W = wl.heisenberg_mpo(lat)
+    lam = wl.lambda_top(lat)
+    e_ref = 2.0 * _chain_ground_energy(lx)
+    kw = dict(tau=-1j / lam, eps_k=1e-12, eps_m=1e-8, eps=1e-10, chi_max=128,
+              stream=torch.cuda.current_stream().cuda_stream)
+    out = {"leg": lx, "n_sites": lat.n, "E_ref": e_ref, "tau_max": args.fig3_tau, "runs": {}}
+    for dt in (0.1, 0.4):
+        st = g.GseTdvp(wl.neel_state(lat), W, **kw)
+        trace = []
+        for step in range(1, int(round(args.fig3_tau / dt)) + 1):
+            st.step(dt, g.IMAG, 3)
+            e = st.energy()
+            trace.append([round(step * dt, 6), e, (e - e_ref) / abs(e_ref), max(st.bond_dims())])
+        st.close()
+        out["runs"][f"gse_tdvp1_dt{dt}"] = trace
+    st = g.GseTdvp(wl.neel_state(lat), W, **kw)
+    e0 = st.energy()
+    trace = []
+    for step in range(1, 6):
+        st.sweep2(0.1, g.IMAG)
+        e = st.energy()
+        trace.append([round(step * 0.1, 6), e, (e - e_ref) / abs(e_ref), max(st.bond_dims())])
+    st.close()
+    out["runs"]["tdvp2_dt0.1"] = trace
+    out["E_neel"] = e0
+    print(json.dumps(out), flush=True)
+
+
 def run_batch(args):
     """Independent random-field chains stepped as one batch (one stream per chain, host worker
     pool) against the same chains stepped one after another on one stream each, same steps."""
@@ -583,7 +652,9 @@ def main():
     if args.batch_chains > 0:
         run_batch(args)
         return
-    if args.svd_probe:
+    if args.fig3:
+        run_fig3(args)
+    elif args.svd_probe:
         run_svd_probe(args)
     elif args.heff_probe:
         run_heff_probe(args)
