@@ -1,4 +1,5 @@
-"""CPU FP64 oracle for GSE-TDVP1 (Yang & White, arXiv:2005.06104).
+"""CPU FP64 oracle for GSE-TDVP1 (Yang & White, arXiv:2005.06104), with the two-site TDVP
+it is compared with (tdvp2.py) and the zip-up MPO application (apply_mpo_zipup).
 
 TEST INFRASTRUCTURE ONLY.  Only the test suite, the smoke check and the CPU
 baseline leg of the benchmark may import this package; the product path (the

@@ -39,6 +39,10 @@ by specification only, never by code):
       singular vectors of near-degenerate values from different blocks and leak
       weight out of the conserved sector (1.6e-6 by step 5 on the 10-site chain).
 
+  Z1  the zip-up application of an MPO truncates its right-to-left pass with 0.1 eps and
+      the cap chi_max (the right block is not orthonormal there), then compresses left to
+      right with eps and chi_max (R1-R3).
+
 Functions whose parity is pinned by tests only through properties (not by a
 closed form): none; every public routine here has a pin in tests/.
 """

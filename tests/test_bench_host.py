@@ -36,3 +36,12 @@ def test_reference_arm_prints_one_line():
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["value"] == line["value"]
     assert line["config"]["chi_max"] == 32
+
+
+@pytest.mark.parametrize("n", [6, 8, 10])
+def test_fig3_reference_energy_matches_dense_ed(n):
+    """The --fig3 reference (sparse S^z = 0 Lanczos written from the bond terms) equals the
+    Kronecker-product Hamiltonian's ground energy in that sector."""
+    from exact import ground_energy_sz0
+    ref = ground_energy_sz0(n, [(i, i + 1, 1.0) for i in range(n - 1)])
+    assert abs(bench._chain_ground_energy(n) - ref) < 1e-12
