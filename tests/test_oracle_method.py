@@ -112,6 +112,31 @@ def test_extension_spans_krylov_vectors():
             assert np.linalg.norm(M - proj) < 1e-10
 
 
+@pytest.mark.parametrize("eps_m", [1e-3, 1e-5])
+def test_extension_weights(eps_m):
+    """Eq. 5's weights: rho~ = sum_l w_l C~_l^+ C~_l and eps_M is relative to tr rho~, so a
+    common factor on the weights changes nothing, a zero weight removes that vector, and an
+    unequal weighting changes the enlarged bases."""
+    lat = wl.zigzag_ladder(4, 1.0, 1.0)
+    W = wl.heisenberg_mpo(lat)
+    psi = O.left_canonicalize(wl.random_mps(8, 2, 4))
+    psi[-1] /= np.linalg.norm(psi[-1])
+    phis = O.krylov_vectors(psi, W, 0.1, 3, 0.0, None)
+
+    def projectors(out):
+        return [right_basis(out, i) @ right_basis(out, i).conj().T for i in range(1, len(out))]
+
+    base, n_base = O.basis_extension(psi, phis, None, eps_m, None)
+    scaled, n_scaled = O.basis_extension(psi, phis, [4.0, 4.0], eps_m, None)
+    assert n_scaled == n_base
+    assert all(np.allclose(a, b, atol=1e-12) for a, b in zip(projectors(base), projectors(scaled)))
+    zero, n_zero = O.basis_extension(psi, phis, [1.0, 0.0], eps_m, None)
+    one, n_one = O.basis_extension(psi, phis[:1], None, eps_m, None)
+    assert n_zero == n_one
+    assert all(np.allclose(a, b, atol=1e-12) for a, b in zip(projectors(zero), projectors(one)))
+    assert n_zero != n_base
+
+
 def test_extension_bbar_orthogonal_to_b_and_svd_equivalence():
     """B_bar B^+ = 0 and eig(P rho~ P) = SVD of the direct sum of the P-projected C~_l (Eq. 6)."""
     lat = wl.chain(6)
