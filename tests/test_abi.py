@@ -59,3 +59,18 @@ def test_launch_counter_reads_without_a_gpu(lib):
     n0 = g.launch_count()
     assert isinstance(n0, int) and n0 >= 0
     assert g.launch_count() == n0  # nothing launched in between
+
+
+def test_binding_constants_match_the_header():
+    """The binding's enum values are the header's (time kind, precision form, Krylov method,
+    status codes)."""
+    from paper_2005_06104_gb300 import gse_tdvp as g
+    txt = open(HEADER).read()
+    enum = {k: int(v) for k, v in re.findall(r"\b(TDVP_[A-Z0-9_]+)\s*=\s*(\d+)", txt)}
+    assert (g.REAL, g.IMAG) == (enum["TDVP_REAL"], enum["TDVP_IMAG"])
+    for name in ("FP64", "TF32X3", "TF32X3_ENV", "BF16X10", "BF16X6"):
+        assert getattr(g, "PREC_" + name) == enum["TDVP_PREC_" + name]
+    assert g.KRYLOV_DENSITY_MATRIX == enum["TDVP_KRYLOV_DENSITY_MATRIX"]
+    assert g.KRYLOV_ZIPUP == enum["TDVP_KRYLOV_ZIPUP"]
+    codes = sorted(v for k, v in enum.items() if k == "TDVP_OK" or k.startswith("TDVP_ERR_"))
+    assert codes == sorted(g.STATUS)
