@@ -198,6 +198,27 @@ def test_tdvp1_reversible_and_conserving():
     assert abs(abs(O.mps_overlap(back, psi)) - 1) < 1e-10
 
 
+def test_tdvp1_is_second_order_in_dt():
+    """The symmetric splitting (dt/2 left to right, dt/2 right to left; reading R4) is of
+    second order: against its own small-dt limit on a fixed-rank manifold the global error
+    falls by 4 when dt halves (a first-order splitting would give 2)."""
+    lat = wl.chain(8)
+    W = wl.heisenberg_mpo(lat)
+    psi0 = O.right_canonicalize(wl.random_mps(8, 3, 5))
+    psi0[0] /= np.linalg.norm(psi0[0])
+    T = 0.4
+
+    def run(nsteps):
+        psi = psi0
+        for _ in range(nsteps):
+            psi = O.tdvp1_sweep(psi, W, T / nsteps, "real")
+        return mps_to_dense(psi)
+    ref = run(128)
+    errs = [np.linalg.norm(run(n) - ref) for n in (2, 4, 8)]
+    for a, b in zip(errs, errs[1:]):
+        assert 3.5 < a / b < 4.6
+
+
 def test_tdvp1_product_state_stays_product():
     """Plain TDVP1 from a product state never grows the bond dimension (Introduction)."""
     lat = wl.zigzag_ladder(5, 1.0, 0.0)
