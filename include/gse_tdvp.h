@@ -154,9 +154,10 @@ typedef enum { TDVP_KRYLOV_DENSITY_MATRIX = 0, TDVP_KRYLOV_ZIPUP = 1 } tdvp_kryl
 TDVP_API tdvp_status tdvp_set_krylov_method(tdvp_handle* h, int method);
 
 /* One Krylov vector in place (Eq. 10 with l = 1, Sec. I.B): the state becomes
- * (1 - i tau H)|psi>, applied by the density-matrix approach with cutoff eps_k
- * and cap chi_max, normalised, left-canonical with the centre at site N-1.
- * (tdvp_expand_basis builds its Krylov vectors with the same routine.) */
+ * (1 - i tau H)|psi>, applied by the method tdvp_set_krylov_method selects (the
+ * density-matrix approach by default) with cutoff eps_k and cap chi_max,
+ * normalised, left-canonical with the centre at site N-1.  (tdvp_expand_basis
+ * builds its Krylov vectors with the same routine.) */
 TDVP_API tdvp_status tdvp_apply_krylov(tdvp_handle* h);
 
 /* GSE step 3 (Sec. I.C): one symmetric one-site TDVP sweep, left to right then
