@@ -16,11 +16,15 @@ Tensors are numpy complex128 arrays:
 Readings of places where the paper is silent (all shared with the CUDA path
 by specification only, never by code):
 
-  R1  every factorisation is an SVD; "without truncation" keeps singular values
-      s > 1e-10 * s_max (numerical rank).  The threshold sits two decades above the
-      Lanczos tolerance (1e-12), the size of the differences between two correct
-      implementations, so they classify the same values; energy conservation is
-      unaffected (|E - E0| stays ~1e-14 on the 10-site chain);
+  R1  a gauge move that truncates nothing (the real-time sweep, where eps = 0 keeps the
+      evolution exactly unitary, Sec. II.B; every canonicalisation) is a thin QR
+      (LQ right to left) taken block by block (R8): it keeps min(rows, cols) directions
+      of each block and drops none.  Every factorisation that selects (the SVD of the
+      centre in the extension, Eq. 3; truncated moves in imaginary time; Krylov
+      compression) is an SVD whose numerical rank keeps s > 1e-10 * s_max.  That
+      threshold sits two decades above the Lanczos tolerance (1e-12), the size of the
+      differences between two correct implementations, so both classify the same
+      values; a pin shows that at 1e-14 the gauge-invariant results do not move;
   R2  truncation cutoffs are relative discarded weights: sum of dropped s^2
       (or eigenvalues) <= eps * total;
   R3  a cut never splits a cluster of values within relative 1e-8: the count
@@ -158,6 +162,33 @@ def eigh_blocks(H):
     return np.array(vals)[order], np.array(vecs).T[:, order]
 
 
+def qr_blocks(M):
+    """Thin QR of M block by block (R1, R8): M = Q R with Q^+ Q = 1.
+
+    Each connected block (rows ri, cols ci) gets numpy's Householder QR, keeping
+    min(len(ri), len(ci)) columns of Q; the new index runs over the blocks in turn.
+    Rows and columns outside every block (all zero) get no direction."""
+    rows, cols = M.shape
+    comps = _components(M != 0)
+    k = sum(min(len(ri), len(ci)) for ri, ci in comps)
+    Q = np.zeros((rows, k), dtype=M.dtype)
+    R = np.zeros((k, cols), dtype=M.dtype)
+    off = 0
+    for ri, ci in comps:
+        q, r = np.linalg.qr(M[np.ix_(ri, ci)], mode="reduced")
+        n = q.shape[1]
+        Q[np.ix_(ri, np.arange(off, off + n))] = q
+        R[np.ix_(np.arange(off, off + n), ci)] = r
+        off += n
+    return Q, R
+
+
+def lq_blocks(M):
+    """M = L Q with Q Q^+ = 1, block by block: the conjugate of qr_blocks(M^+)."""
+    Qh, Rh = qr_blocks(M.conj().T)
+    return Rh.conj().T, Qh.conj().T
+
+
 def svd_truncate(M, eps=0.0, cap=None):
     """M = U S Vh, keeping columns by R1 + R2 + R3.  Returns U, S, Vh, discarded weight."""
     U, S, Vh = svd_blocks(M)
@@ -173,24 +204,38 @@ def svd_truncate(M, eps=0.0, cap=None):
 
 # ------------------------------------------------------------ MPS gauge moves
 def left_canonicalize(mps, eps=0.0, cap=None):
-    """Left-orthonormal A_1..A_{N-1}, centre at site N (Eq. 1), by SVDs left to right."""
+    """Left-orthonormal A_1..A_{N-1}, centre at site N (Eq. 1), left to right: by block
+    QRs when nothing is cut (R1), by truncated SVDs when eps or cap is given."""
     out = [a.copy() for a in mps]
+    exact = eps == 0.0 and cap is None
     for i in range(len(out) - 1):
         ml, d, mr = out[i].shape
-        U, S, Vh, _ = svd_truncate(out[i].reshape(ml * d, mr), eps, cap)
-        out[i] = U.reshape(ml, d, -1)
-        out[i + 1] = np.tensordot(S[:, None] * Vh, out[i + 1], axes=([1], [0]))
+        M = out[i].reshape(ml * d, mr)
+        if exact:
+            Q, C = qr_blocks(M)
+        else:
+            Q, S, Vh, _ = svd_truncate(M, eps, cap)
+            C = S[:, None] * Vh
+        out[i] = Q.reshape(ml, d, -1)
+        out[i + 1] = np.tensordot(C, out[i + 1], axes=([1], [0]))
     return out
 
 
 def right_canonicalize(mps, eps=0.0, cap=None):
-    """Right-orthonormal B_2..B_N, centre at site 1 (Eq. 4), by SVDs right to left."""
+    """Right-orthonormal B_2..B_N, centre at site 1 (Eq. 4), right to left: by block
+    LQs when nothing is cut (R1), by truncated SVDs when eps or cap is given."""
     out = [a.copy() for a in mps]
+    exact = eps == 0.0 and cap is None
     for i in range(len(out) - 1, 0, -1):
         ml, d, mr = out[i].shape
-        U, S, Vh, _ = svd_truncate(out[i].reshape(ml, d * mr), eps, cap)
-        out[i] = Vh.reshape(-1, d, mr)
-        out[i - 1] = np.tensordot(out[i - 1], U * S[None, :], axes=([2], [0]))
+        M = out[i].reshape(ml, d * mr)
+        if exact:
+            C, Q = lq_blocks(M)
+        else:
+            U, S, Q, _ = svd_truncate(M, eps, cap)
+            C = U * S[None, :]
+        out[i] = Q.reshape(-1, d, mr)
+        out[i - 1] = np.tensordot(out[i - 1], C, axes=([2], [0]))
     return out
 
 
@@ -331,16 +376,17 @@ def tdvp1_sweep(mps, W, dt, kind, eps=0.0, chi_max=None, tol=1e-12, nmax=40, sta
     each with time step dt/2 (R4).  Input: right-canonical, centre at site 1.
     Output: right-canonical, centre at site 1.
 
-    Per site (L->R): A <- exp(-i delta H_eff) A; split A = U S Vh (R1, plus
-    cutoff eps and cap in imaginary time); L_{i+1} from U; C = S Vh <-
-    exp(+i delta K_eff) C; A_{i+1} <- C A_{i+1}.  Mirrored for R->L.
+    Per site (L->R): A <- exp(-i delta H_eff) A; split A = Q C, by a block QR in real
+    time (nothing is cut, eps = 0 keeps the step unitary: R1) and by an SVD with cutoff
+    eps and cap in imaginary time (Q = U, C = S Vh); L_{i+1} from Q; C <- exp(+i delta
+    K_eff) C; A_{i+1} <- C A_{i+1}.  Mirrored for R->L with LQ.
     """
     n = len(mps)
     psi = [a.copy() for a in mps]
     delta = 0.5 * dt
     imag = kind == "imag"
-    cut_eps = eps if imag else 0.0
-    cap = chi_max if imag else None
+    cut_eps = eps
+    cap = chi_max
     Ls, Rs = build_envs(psi, W, 0)
     iters = []
 
@@ -359,20 +405,30 @@ def tdvp1_sweep(mps, W, dt, kind, eps=0.0, chi_max=None, tol=1e-12, nmax=40, sta
         if i == n - 1:
             break
         ml, d, mr = psi[i].shape
-        U, S, Vh, _ = svd_truncate(psi[i].reshape(ml * d, mr), cut_eps, cap)
-        psi[i] = U.reshape(ml, d, -1)
+        M = psi[i].reshape(ml * d, mr)
+        if imag:
+            Q, S, Vh, _ = svd_truncate(M, cut_eps, cap)
+            C = S[:, None] * Vh
+        else:
+            Q, C = qr_blocks(M)
+        psi[i] = Q.reshape(ml, d, -1)
         Ls[i + 1] = env_left_step(Ls[i], psi[i], W[i])
-        C = bwd(Ls[i + 1], Rs[i], S[:, None] * Vh)
+        C = bwd(Ls[i + 1], Rs[i], C)
         psi[i + 1] = np.tensordot(C, psi[i + 1], axes=([1], [0]))
     for i in range(n - 1, -1, -1):
         psi[i] = fwd(i, psi[i])
         if i == 0:
             break
         ml, d, mr = psi[i].shape
-        U, S, Vh, _ = svd_truncate(psi[i].reshape(ml, d * mr), cut_eps, cap)
-        psi[i] = Vh.reshape(-1, d, mr)
+        M = psi[i].reshape(ml, d * mr)
+        if imag:
+            U, S, Q, _ = svd_truncate(M, cut_eps, cap)
+            C = U * S[None, :]
+        else:
+            C, Q = lq_blocks(M)
+        psi[i] = Q.reshape(-1, d, mr)
         Rs[i - 1] = env_right_step(Rs[i], psi[i], W[i])
-        C = bwd(Ls[i], Rs[i - 1], U * S[None, :])
+        C = bwd(Ls[i], Rs[i - 1], C)
         psi[i - 1] = np.tensordot(psi[i - 1], C, axes=([2], [0]))
     if stats is not None:
         stats["lanczos_iters"] = iters
