@@ -286,17 +286,19 @@ TDVP_API tdvp_status tdvp_profile_read(tdvp_handle* h, double* out3);
 /* Per-phase timing (CUDA events on the handle's stream).  tdvp_trace(h, 1)
  * starts recording; tdvp_trace_read writes the milliseconds spent since the
  * last read into out[0..n) and resets.  Phases: 0 local exponentials of the
- * sweep (H_eff Lanczos), 1 backward bond exponentials (K_eff Lanczos), 2 SVDs
- * of the sweep's gauge moves, 3 environment updates, 4 Krylov vectors (step 1),
- * 5 basis extension (step 2), 6 gauge moves of tdvp_canonicalize, 7 right
- * density environments of the Krylov vectors, 8 their eigendecompositions,
- * 9 SVDs of the extension; inside every blocked SVD or eigendecomposition of
- * 2, 6, 8, 9: 10 block detection (nonzero mask, host union-find, gather),
- * 11 pivoted Cholesky of density matrices, 12 Jacobi sweeps, 13 selection and
- * scatter of the kept vectors.  Intervals nest (3 runs inside 0..2, 7-8 inside
- * 4, 9 inside 5, 10-13 inside the factorisations), so the entries do not add
- * up.  n may be smaller or larger than 14; missing phases are left out,
- * entries past the last phase are zero. */
+ * sweep (H_eff Lanczos), 1 backward bond exponentials (K_eff Lanczos), 2 gauge
+ * moves of the sweep (block QR in real time, truncated SVD in imaginary time),
+ * 3 environment updates, 4 Krylov vectors (step 1), 5 basis extension (step 2),
+ * 6 gauge moves of tdvp_canonicalize, 7 right density environments of the
+ * Krylov vectors, 8 their eigendecompositions, 9 SVDs of the extension; inside
+ * every blocked SVD or eigendecomposition of 2, 6, 8, 9: 10 block detection
+ * (nonzero mask, host union-find, gather), 11 pivoted Cholesky of density
+ * matrices, 12 Jacobi sweeps, 13 selection and scatter of the kept vectors;
+ * 14 every block QR / LQ (gauge moves that cut nothing, inside 2 and 6).
+ * Intervals nest (3 runs inside 0..2, 7-8 inside 4, 9 inside 5, 10-14 inside
+ * the factorisations), so the entries do not add up.  n may be smaller or
+ * larger than 15; missing phases are left out, entries past the last phase
+ * are zero. */
 TDVP_API tdvp_status tdvp_trace(tdvp_handle* h, int enable);
 TDVP_API tdvp_status tdvp_trace_read(tdvp_handle* h, double* out, int n);
 

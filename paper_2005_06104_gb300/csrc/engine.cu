@@ -351,10 +351,26 @@ void Engine::apply_op(const SiteOp& op, const cplx* x, cplx* y, int precision) {
 }
 
 // ============================================================================
-// gauge moves (SVD; real time keeps s > 1e-14 s_max, imaginary time also cuts)
+// gauge moves: a block QR / LQ when nothing is cut (R1), else a truncated SVD
+// (numerical rank 1e-10 s_max, cutoff eps, cap)
 // ============================================================================
 void Engine::move_right(int i, double eps, int cap, bool trunc) {
   const int ml = psi.m[i], mr = psi.m[i + 1], mr2 = psi.m[i + 2];
+  if (!trunc) {
+    QrOut qo;
+    qr_blocked(st, &pool, psi.A[i].data(), ml * d, mr, 0, qo);
+    const int r = qo.k;
+    tdvp_require(r >= 1, TDVP_ERR_NONFINITE, "move_right: zero tensor");
+    DArr nxt(&pool, (size_t)r * d * mr2);
+    zgemm(st, OP_N, OP_N, r, d * mr2, mr, kOne, qo.C.data(), mr, psi.A[i + 1].data(), d * mr2, kZero, nxt.data(),
+          d * mr2, 1, 0, 0, 0, &pool);
+    psi.A[i] = std::move(qo.Q);
+    psi.A[i + 1] = std::move(nxt);
+    psi.m[i + 1] = r;
+    invalidate_from_site(i);
+    invalidate_from_site(i + 1);
+    return;
+  }
   SvdRule rule;
   if (trunc) {
     rule.eps = eps;
@@ -382,6 +398,21 @@ void Engine::move_right(int i, double eps, int cap, bool trunc) {
 
 void Engine::move_left(int i, double eps, int cap, bool trunc) {
   const int ml = psi.m[i], mr = psi.m[i + 1], ml0 = psi.m[i - 1];
+  if (!trunc) {
+    QrOut qo;
+    qr_blocked(st, &pool, psi.A[i].data(), ml, d * mr, 1, qo);
+    const int r = qo.k;
+    tdvp_require(r >= 1, TDVP_ERR_NONFINITE, "move_left: zero tensor");
+    DArr prv(&pool, (size_t)ml0 * d * r);
+    zgemm(st, OP_N, OP_N, ml0 * d, r, ml, kOne, psi.A[i - 1].data(), ml, qo.C.data(), r, kZero, prv.data(), r, 1, 0,
+          0, 0, &pool);
+    psi.A[i] = std::move(qo.Q);
+    psi.A[i - 1] = std::move(prv);
+    psi.m[i] = r;
+    invalidate_from_site(i);
+    invalidate_from_site(i - 1);
+    return;
+  }
   SvdRule rule;
   if (trunc) {
     rule.eps = eps;
@@ -473,23 +504,32 @@ void Engine::sweep(double dt, int kind) {
     evolve_site(i);
     if (i == N - 1) break;
     const int ml = psi.m[i], mold = psi.m[i + 1], mr2 = psi.m[i + 2];
-    SvdRule rule;
-    if (imag) {
-      rule.eps = opt.eps;
-      rule.cap = opt.chi_max;
-      rule.discarded = &disc_eps;
-    }
-    SvdOut sv;
+    DArr C;  // A = Q C
+    int r = 0;
     {
       PhaseScope ps(tracer, PH_SVD);
-      svd_jacobi(st, &pool, psi.A[i].data(), ml * d, mold, rule, sv, true, false);
+      if (imag) {  // truncated SVD: Q = U, C = U^+ A = S Vh
+        SvdRule rule;
+        rule.eps = opt.eps;
+        rule.cap = opt.chi_max;
+        rule.discarded = &disc_eps;
+        SvdOut sv;
+        svd_jacobi(st, &pool, psi.A[i].data(), ml * d, mold, rule, sv, true, false);
+        r = sv.rank;
+        tdvp_require(r >= 1, TDVP_ERR_NONFINITE, "sweep: zero site tensor");
+        C.reset(&pool, (size_t)r * mold);
+        zgemm(st, OP_C, OP_N, r, mold, ml * d, kOne, sv.U.data(), r, psi.A[i].data(), mold, kZero, C.data(), mold,
+              1, 0, 0, 0, &pool);
+        psi.A[i] = std::move(sv.U);
+      } else {  // real time cuts nothing: block QR (R1)
+        QrOut qo;
+        qr_blocked(st, &pool, psi.A[i].data(), ml * d, mold, 0, qo);
+        r = qo.k;
+        tdvp_require(r >= 1, TDVP_ERR_NONFINITE, "sweep: zero site tensor");
+        C = std::move(qo.C);
+        psi.A[i] = std::move(qo.Q);
+      }
     }
-    const int r = sv.rank;
-    tdvp_require(r >= 1, TDVP_ERR_NONFINITE, "sweep: zero site tensor");
-    DArr C(&pool, (size_t)r * mold);  // C = U^+ A = S Vh
-    zgemm(st, OP_C, OP_N, r, mold, ml * d, kOne, sv.U.data(), r, psi.A[i].data(), mold, kZero, C.data(), mold, 1,
-          0, 0, 0, &pool);
-    psi.A[i] = std::move(sv.U);
     psi.m[i + 1] = r;  // L[i+1] is r x w x r, R[i] still mold x w x mold
     env_left(i);
     DArr C2(&pool, (size_t)r * mold);
@@ -513,23 +553,32 @@ void Engine::sweep(double dt, int kind) {
     evolve_site(i);
     if (i == 0) break;
     const int mold = psi.m[i], mr = psi.m[i + 1], ml0 = psi.m[i - 1];
-    SvdRule rule;
-    if (imag) {
-      rule.eps = opt.eps;
-      rule.cap = opt.chi_max;
-      rule.discarded = &disc_eps;
-    }
-    SvdOut sv;
+    DArr C;  // A = C Q
+    int r = 0;
     {
       PhaseScope ps(tracer, PH_SVD);
-      svd_jacobi(st, &pool, psi.A[i].data(), mold, d * mr, rule, sv, false, true);
+      if (imag) {  // truncated SVD: Q = Vh, C = A Vh^+ = U S
+        SvdRule rule;
+        rule.eps = opt.eps;
+        rule.cap = opt.chi_max;
+        rule.discarded = &disc_eps;
+        SvdOut sv;
+        svd_jacobi(st, &pool, psi.A[i].data(), mold, d * mr, rule, sv, false, true);
+        r = sv.rank;
+        tdvp_require(r >= 1, TDVP_ERR_NONFINITE, "sweep: zero site tensor");
+        C.reset(&pool, (size_t)mold * r);
+        zgemm(st, OP_N, OP_C, mold, r, d * mr, kOne, psi.A[i].data(), d * mr, sv.Vh.data(), d * mr, kZero, C.data(),
+              r, 1, 0, 0, 0, &pool);
+        psi.A[i] = std::move(sv.Vh);
+      } else {  // real time cuts nothing: block LQ (R1)
+        QrOut qo;
+        qr_blocked(st, &pool, psi.A[i].data(), mold, d * mr, 1, qo);
+        r = qo.k;
+        tdvp_require(r >= 1, TDVP_ERR_NONFINITE, "sweep: zero site tensor");
+        C = std::move(qo.C);
+        psi.A[i] = std::move(qo.Q);
+      }
     }
-    const int r = sv.rank;
-    tdvp_require(r >= 1, TDVP_ERR_NONFINITE, "sweep: zero site tensor");
-    DArr C(&pool, (size_t)mold * r);  // C = A Vh^+ = U S
-    zgemm(st, OP_N, OP_C, mold, r, d * mr, kOne, psi.A[i].data(), d * mr, sv.Vh.data(), d * mr, kZero, C.data(), r,
-          1, 0, 0, 0, &pool);
-    psi.A[i] = std::move(sv.Vh);
     psi.m[i] = r;
     env_right(i);  // R[i-1]: r x w x r
     DArr C2(&pool, (size_t)mold * r);
@@ -1029,7 +1078,9 @@ void Engine::expand_basis(int k, const double* weights) {
     tdvp_require(r >= 1, TDVP_ERR_NONFINITE, "extension: zero centre tensor");
     int nb = 0;
     DArr Bbar;
-    if (r < cols) {
+    // at most min(chi_max, d m') - rank B states can be added (R12); a saturated bond adds none
+    const int cap = std::min(cols, opt.chi_max) - r;
+    if (cap > 0) {
       // Y = [sqrt(w_1) C~_1; ...]  (sum m~ x cols); tr rho~ = |Y|_F^2
       int rows = 0;
       for (int l = 0; l < nk; ++l) rows += phis[l].m[i];
@@ -1051,9 +1102,7 @@ void Engine::expand_basis(int k, const double* weights) {
         zgemm(st, OP_N, OP_C, rows, r, cols, kOne, Y.data(), cols, sv.Vh.data(), cols, kZero, G.data(), r, 1, 0, 0, 0, &pool);
         zgemm(st, OP_N, OP_N, rows, cols, r, kMinusOne, G.data(), r, sv.Vh.data(), cols, kOne, Y.data(), cols, 1, 0, 0, 0, &pool);
       }
-      int cap = cols - r;
-      cap = std::min(cap, opt.chi_max - r);
-      if (cap > 0 && tr > 0.0) {
+      if (tr > 0.0) {
         const double eps_m = opt.eps_m;
         double* disc = &disc_m;
         auto rule = [tr, eps_m, cap, disc](const std::vector<double>& s) -> int {

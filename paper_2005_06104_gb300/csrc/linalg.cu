@@ -2056,18 +2056,14 @@ void run_jacobi_multi(cudaStream_t st, cplx* Xs, cplx* Vs, const std::vector<Blk
 }
 }  // namespace
 
-void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows, int cols,
-                      int (*select)(const std::vector<double>& s, void* ctx), void* ctx, SvdOut& out, bool want_u,
-                      bool want_v, bool psd) {
-  g_svd_counters.calls++;
-  const long long n = (long long)rows * cols;
-  if (rows <= 1 || cols <= 1 || n > (1LL << 27)) {
-    svd_jacobi_keep(st, pool, M, rows, cols, select, ctx, out, want_u, want_v);
-    return;
-  }
+namespace {
+// Connected blocks of the nonzero pattern of M (rows x cols, row-major): a device mask, then
+// a host union-find over rows and columns.  Keyed by the smallest row of each block; rows and
+// columns without a nonzero entry belong to no block.
+std::map<int, std::pair<std::vector<int>, std::vector<int>>> block_components(cudaStream_t st, DevicePool* pool,
+                                                                              const cplx* M, int rows, int cols) {
   const int words = (cols + 31) / 32;
   std::vector<unsigned> mask((size_t)rows * words);
-  auto prep = std::make_unique<ActivePhase>(PH_SVD_PREP);
   {
     RawBuf dm;
     dm.ensure(pool, sizeof(unsigned) * mask.size());
@@ -2096,6 +2092,21 @@ void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows
     if (row_nz[r]) comp[dsu.find(r)].first.push_back(r);
   for (int c = 0; c < cols; ++c)
     if (col_nz[c]) comp[dsu.find(rows + c)].second.push_back(c);
+  return comp;
+}
+}  // namespace
+
+void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows, int cols,
+                      int (*select)(const std::vector<double>& s, void* ctx), void* ctx, SvdOut& out, bool want_u,
+                      bool want_v, bool psd) {
+  g_svd_counters.calls++;
+  const long long n = (long long)rows * cols;
+  if (rows <= 1 || cols <= 1 || n > (1LL << 27)) {
+    svd_jacobi_keep(st, pool, M, rows, cols, select, ctx, out, want_u, want_v);
+    return;
+  }
+  auto prep = std::make_unique<ActivePhase>(PH_SVD_PREP);
+  auto comp = block_components(st, pool, M, rows, cols);
   if (comp.empty()) {
     svd_jacobi_keep(st, pool, M, rows, cols, select, ctx, out, want_u, want_v);
     return;
@@ -2274,4 +2285,326 @@ void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows
     TDVP_CUDA(cudaFreeAsync(d_s, st));
     if (d_piv) TDVP_CUDA(cudaFreeAsync(d_piv, st));
   }
+}
+
+// ============================================================================
+// Block-structured thin QR / LQ: the gauge moves that cut nothing (real-time sweeps,
+// canonicalisation).  Blocks come from the exact-zero pattern as for the SVD.  Block b
+// is gathered as the column-major working matrix X_b (p x q): the block itself (orient 0,
+// M = Q C) or its conjugate transpose (orient 1, M = C Q, an LQ).  Householder QR of X_b
+// with kq = min(p, q) reflectors H_j = 1 - tau_j v_j v_j^H, v_j[j] = 1:
+//   x = X_b[j:, j],  beta = -e^{i arg x_j} |x|,  v = (x - beta e_j) / (x_j - beta),
+//   tau = 1 + |x_j| / |x|,  H_j x = beta e_j
+// (tau = 0 for a zero column).  v_j's tail overwrites X_b below the diagonal, beta the
+// diagonal; R is the upper trapezoid.  Q_b[:, c] = H_0 H_1 ... H_c e_c.
+// ============================================================================
+namespace {
+struct QrDesc {
+  int orient, p, q, kq;
+  long long x_off, q_off;   // X_b (p x q) and Q_b (p x kq), column-major
+  int r_off, c_off, k_off;  // the block's rows and columns in the index lists; its first new index
+  int t_off;                // tau_b
+};
+
+__global__ void k_qr_gather(const cplx* __restrict__ M, int cols, const QrDesc* __restrict__ desc,
+                            const int* __restrict__ ridx, const int* __restrict__ cidx, cplx* __restrict__ X) {
+  const QrDesc d = desc[blockIdx.x];
+  cplx* Xb = X + d.x_off;
+  for (long long e = threadIdx.x; e < (long long)d.p * d.q; e += blockDim.x) {
+    const int i = (int)(e % d.p), j = (int)(e / d.p);
+    Xb[e] = d.orient == 0 ? M[(long long)ridx[d.r_off + i] * cols + cidx[d.c_off + j]]
+                          : cconj(M[(long long)ridx[d.r_off + j] * cols + cidx[d.c_off + i]]);
+  }
+}
+
+constexpr int kQrChunk = 8;  // columns whose dot products one block reduction serves
+
+// Block-wide sums of n <= kQrChunk complex partials; the totals land in out[0..n).
+__device__ __forceinline__ void qr_block_sums(cplx* acc, int n, cplx (*red)[kQrChunk], cplx* out) {
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  for (int t = 0; t < n; ++t) {
+    const cplx v = warp_sum(acc[t]);
+    if (lane == 0) red[warp][t] = v;
+  }
+  __syncthreads();
+  if (threadIdx.x < n) {
+    cplx s = mkc(0.0, 0.0);
+    for (int w = 0; w < (int)(blockDim.x >> 5); ++w) s = cadd(s, red[w][threadIdx.x]);
+    out[threadIdx.x] = s;
+  }
+  __syncthreads();
+}
+
+// Reflector j from column j of X_b (rows j..p-1), by the whole block.
+__device__ void qr_make_reflector(cplx* __restrict__ Xb, int p, int j, double* __restrict__ tau,
+                                  cplx (*red)[kQrChunk], cplx* tot) {
+  __shared__ cplx s_inv;
+  __shared__ int s_zero;
+  cplx* x = Xb + (long long)j * p;
+  cplx acc[1] = {mkc(0.0, 0.0)};
+  for (int r = j + threadIdx.x; r < p; r += blockDim.x) acc[0].x += cabs2(x[r]);
+  qr_block_sums(acc, 1, red, tot);
+  if (threadIdx.x == 0) {
+    const double nrm = sqrt(tot[0].x);
+    const cplx a = x[j];
+    s_zero = !(nrm > 0.0);
+    if (s_zero) {
+      tau[j] = 0.0;
+    } else {
+      const double aa = sqrt(cabs2(a));
+      const cplx ph = aa > 0.0 ? cscale(a, 1.0 / aa) : mkc(1.0, 0.0);
+      const double den = aa + nrm;
+      s_inv = cscale(cconj(ph), 1.0 / den);  // 1 / (x_j - beta) = e^{-i arg x_j} / (|x_j| + |x|)
+      tau[j] = den / nrm;
+      x[j] = cscale(ph, -nrm);  // beta
+    }
+  }
+  __syncthreads();
+  if (!s_zero) {
+    const cplx inv = s_inv;
+    for (int r = j + 1 + threadIdx.x; r < p; r += blockDim.x) x[r] = cmul(x[r], inv);
+  }
+  __syncthreads();
+}
+
+// Applies H_j (v staged in sv[0..p-j), sv[0] = 1) to the columns cols[0..n) of Y (rows j..p-1).
+__device__ __forceinline__ void qr_apply(cplx* __restrict__ Y, int p, int j, const cplx* __restrict__ sv,
+                                         double tj, const int* cols, int n, cplx (*red)[kQrChunk], cplx* tot) {
+  cplx acc[kQrChunk];
+#pragma unroll
+  for (int t = 0; t < kQrChunk; ++t) acc[t] = mkc(0.0, 0.0);
+  for (int r = j + threadIdx.x; r < p; r += blockDim.x) {
+    const cplx v = sv[r - j];
+#pragma unroll
+    for (int t = 0; t < kQrChunk; ++t)
+      if (t < n) cfma_conj(acc[t], v, Y[(long long)cols[t] * p + r]);
+  }
+  qr_block_sums(acc, n, red, tot);
+  cplx w[kQrChunk];
+#pragma unroll
+  for (int t = 0; t < kQrChunk; ++t) w[t] = t < n ? cscale(tot[t], tj) : mkc(0.0, 0.0);
+  for (int r = j + threadIdx.x; r < p; r += blockDim.x) {
+    const cplx v = sv[r - j];
+#pragma unroll
+    for (int t = 0; t < kQrChunk; ++t)
+      if (t < n) {
+        cplx& y = Y[(long long)cols[t] * p + r];
+        y = csub(y, cmul(w[t], v));
+      }
+  }
+  __syncthreads();
+}
+
+// One cooperative launch: the CTAs [cta_off[b], cta_off[b+1]) factorise block b.  CTA lc of a
+// group of G owns the columns c = lc (mod G).  Step j: every CTA stages v_j in shared memory
+// and applies H_j to its own columns right of j; the owner of column j+1 then forms reflector
+// j+1 from it; one bounded group barrier ends the step.  Q_b is then accumulated column by
+// column (each CTA its own columns, H_j for j = c down to 0), with no further barrier.
+__global__ void __launch_bounds__(256)
+    k_qr_groups(cplx* __restrict__ X, cplx* __restrict__ Qb, double* __restrict__ tau,
+                const QrDesc* __restrict__ desc, const int* __restrict__ cta_off, int nblk, GridBar* __restrict__ bars,
+                int* __restrict__ gerr) {
+  extern __shared__ cplx sv[];
+  __shared__ cplx red[8][kQrChunk];
+  __shared__ cplx tot[kQrChunk];
+  int lo = 0, hi = nblk - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (cta_off[mid] <= (int)blockIdx.x) lo = mid; else hi = mid - 1;
+  }
+  const int b = lo;
+  const int lc = blockIdx.x - cta_off[b];
+  const int G = cta_off[b + 1] - cta_off[b];
+  const QrDesc d = desc[b];
+  cplx* Xb = X + d.x_off;
+  double* tb = tau + d.t_off;
+  GridBar* bar = bars + b;
+  unsigned epoch = 0;
+  const int p = d.p, q = d.q, kq = d.kq;
+  int cols[kQrChunk];
+  if (kq > 0 && lc == 0) qr_make_reflector(Xb, p, 0, tb, red, tot);
+  if (!group_sync(bar, (unsigned)G, gerr, epoch)) return;
+  for (int j = 0; j < kq; ++j) {
+    for (int r = j + threadIdx.x; r < p; r += blockDim.x) sv[r - j] = r == j ? mkc(1.0, 0.0) : Xb[(long long)j * p + r];
+    __syncthreads();
+    const double tj = tb[j];
+    // own columns right of j (the smallest one first)
+    int c0 = j + 1 + ((lc - (j + 1)) % G + G) % G;
+    if (tj != 0.0)
+      for (int c = c0; c < q;) {
+        int n = 0;
+        for (; n < kQrChunk && c < q; ++n, c += G) cols[n] = c;
+        qr_apply(Xb, p, j, sv, tj, cols, n, red, tot);
+      }
+    if (j + 1 < kq) {
+      if ((j + 1) % G == lc) qr_make_reflector(Xb, p, j + 1, tb, red, tot);
+      if (!group_sync(bar, (unsigned)G, gerr, epoch)) return;
+    }
+  }
+  // Q_b: own columns c < kq start as e_c; H_j applies to the columns c >= j
+  cplx* Qc = Qb + d.q_off;
+  for (int c = lc; c < kq; c += G)
+    for (int r = threadIdx.x; r < p; r += blockDim.x) Qc[(long long)c * p + r] = mkc(r == c ? 1.0 : 0.0, 0.0);
+  __syncthreads();
+  const int last = lc < kq ? lc + ((kq - 1 - lc) / G) * G : -1;  // largest own column
+  for (int j = last; j >= 0; --j) {
+    const double tj = tb[j];
+    if (tj == 0.0) continue;
+    for (int r = j + threadIdx.x; r < p; r += blockDim.x) sv[r - j] = r == j ? mkc(1.0, 0.0) : Xb[(long long)j * p + r];
+    __syncthreads();
+    int c0 = j + ((lc - j) % G + G) % G;
+    for (int c = c0; c < kq;) {
+      int n = 0;
+      for (; n < kQrChunk && c < kq; ++n, c += G) cols[n] = c;
+      qr_apply(Qc, p, j, sv, tj, cols, n, red, tot);
+    }
+  }
+}
+
+// Entry (blk, j): column j of Q_b and row j of R_b into the outputs.
+//   orient 0: Qout rows x K  (Qout[row, k_off + j] = Q_b[i, j]),
+//             Cout K x cols  (Cout[k_off + j, col] = R_b[j, c], c >= j)
+//   orient 1: Qout K x cols  (Qout[k_off + j, col] = conj Q_b[i, j]),
+//             Cout rows x K  (Cout[row, k_off + j] = conj R_b[j, r], r >= j)
+__global__ void k_qr_scatter(const cplx* __restrict__ X, const cplx* __restrict__ Qb, const QrDesc* __restrict__ desc,
+                             const int2* __restrict__ ent, const int* __restrict__ ridx, const int* __restrict__ cidx,
+                             cplx* __restrict__ Qout, cplx* __restrict__ Cout, int cols, int K) {
+  const int2 e = ent[blockIdx.x];
+  const QrDesc d = desc[e.x];
+  const int j = e.y;
+  const long long k = d.k_off + j;
+  const cplx* qcol = Qb + d.q_off + (long long)j * d.p;
+  const cplx* Xb = X + d.x_off;
+  if (d.orient == 0) {
+    for (int i = threadIdx.x; i < d.p; i += blockDim.x) Qout[(long long)ridx[d.r_off + i] * K + k] = qcol[i];
+    for (int c = j + threadIdx.x; c < d.q; c += blockDim.x)
+      Cout[k * cols + cidx[d.c_off + c]] = Xb[(long long)c * d.p + j];
+  } else {
+    for (int i = threadIdx.x; i < d.p; i += blockDim.x) Qout[k * cols + cidx[d.c_off + i]] = cconj(qcol[i]);
+    for (int r = j + threadIdx.x; r < d.q; r += blockDim.x)
+      Cout[(long long)ridx[d.r_off + r] * K + k] = cconj(Xb[(long long)r * d.p + j]);
+  }
+}
+}  // namespace
+
+void qr_blocked(cudaStream_t st, DevicePool* pool, const cplx* M, int rows, int cols, int orient, QrOut& out) {
+  ActivePhase phase(PH_QR);
+  out.k = 0;
+  out.Q.release();
+  out.C.release();
+  auto comp = block_components(st, pool, M, rows, cols);
+  std::vector<QrDesc> desc;
+  std::vector<int> ridx, cidx;
+  long long xo = 0, qo = 0;
+  int to = 0, K = 0, pmax = 1;
+  for (auto& kv : comp) {
+    auto& rr = kv.second.first;
+    auto& cc = kv.second.second;
+    const int nr = (int)rr.size(), nc = (int)cc.size();
+    QrDesc d;
+    d.orient = orient;
+    d.p = orient == 0 ? nr : nc;
+    d.q = orient == 0 ? nc : nr;
+    d.kq = std::min(d.p, d.q);
+    d.x_off = xo;
+    d.q_off = qo;
+    d.r_off = (int)ridx.size();
+    d.c_off = (int)cidx.size();
+    d.k_off = K;
+    d.t_off = to;
+    ridx.insert(ridx.end(), rr.begin(), rr.end());
+    cidx.insert(cidx.end(), cc.begin(), cc.end());
+    xo += (long long)d.p * d.q;
+    qo += (long long)d.p * d.kq;
+    to += d.kq;
+    K += d.kq;
+    pmax = std::max(pmax, d.p);
+    desc.push_back(d);
+  }
+  if (K == 0) return;
+  const int nblk = (int)desc.size();
+  const size_t smem = (size_t)pmax * sizeof(cplx);
+  tdvp_require(smem <= 200 * 1024, TDVP_ERR_INVALID_ARG, "QR: block too tall for the staged reflector");
+  static const bool attr = [] {
+    TDVP_CUDA(cudaFuncSetAttribute(k_qr_groups, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024));
+    return true;
+  }();
+  (void)attr;
+  int dev = 0, sms = 0, per_sm = 0;
+  TDVP_CUDA(cudaGetDevice(&dev));
+  TDVP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
+  TDVP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_qr_groups, 256, smem));
+  tdvp_require(per_sm >= 1, TDVP_ERR_INVALID_ARG, "QR: kernel does not fit on an SM");
+  const int budget = std::max(nblk, sms * std::min(4, per_sm));
+  // CTAs per block in proportion to its work (p q kq), at most one per two columns; a group of
+  // one needs no barrier
+  std::vector<double> work(nblk);
+  double wsum = 0.0;
+  for (int b = 0; b < nblk; ++b) {
+    work[b] = (double)desc[b].p * desc[b].q * std::max(1, desc[b].kq);
+    wsum += work[b];
+  }
+  std::vector<int> cta_off(nblk + 1, 0);
+  for (int b = 0; b < nblk; ++b) {
+    const int cap = std::max(1, (desc[b].q + 1) / 2);
+    long long g = (long long)std::floor((double)(budget - nblk) * work[b] / wsum);
+    g = std::max<long long>(1, std::min<long long>(cap, g));
+    cta_off[b + 1] = cta_off[b] + (int)g;
+  }
+  const int nctas = cta_off[nblk];
+  tdvp_require(nctas <= budget, TDVP_ERR_INVALID_ARG, "QR groups exceed the co-resident CTAs");
+  DArr X(pool, (size_t)xo), Qb(pool, (size_t)std::max<long long>(1, qo));
+  RawBuf meta;
+  const size_t b_desc = sizeof(QrDesc) * nblk, b_r = sizeof(int) * ridx.size(), b_c = sizeof(int) * cidx.size();
+  const size_t b_off = sizeof(int) * (nblk + 1), b_tau = sizeof(double) * to, b_bar = sizeof(GridBar) * nblk;
+  std::vector<int2> ent;
+  for (int b = 0; b < nblk; ++b)
+    for (int j = 0; j < desc[b].kq; ++j) ent.push_back(make_int2(b, j));
+  const size_t b_ent = sizeof(int2) * ent.size();
+  auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
+  const size_t o_desc = 0, o_r = al(b_desc), o_c = o_r + al(b_r), o_off = o_c + al(b_c), o_tau = o_off + al(b_off),
+               o_bar = o_tau + al(b_tau), o_ent = o_bar + al(b_bar), o_err = o_ent + al(b_ent);
+  meta.ensure(pool, o_err + 256);
+  char* base = meta.as<char>();
+  auto* d_desc = reinterpret_cast<QrDesc*>(base + o_desc);
+  auto* d_r = reinterpret_cast<int*>(base + o_r);
+  auto* d_c = reinterpret_cast<int*>(base + o_c);
+  auto* d_off = reinterpret_cast<int*>(base + o_off);
+  auto* d_tau = reinterpret_cast<double*>(base + o_tau);
+  auto* d_bar = reinterpret_cast<GridBar*>(base + o_bar);
+  auto* d_ent = reinterpret_cast<int2*>(base + o_ent);
+  auto* d_err = reinterpret_cast<int*>(base + o_err);
+  TDVP_CUDA(cudaMemcpyAsync(d_desc, desc.data(), b_desc, cudaMemcpyHostToDevice, st));
+  TDVP_CUDA(cudaMemcpyAsync(d_r, ridx.data(), b_r, cudaMemcpyHostToDevice, st));
+  TDVP_CUDA(cudaMemcpyAsync(d_c, cidx.data(), b_c, cudaMemcpyHostToDevice, st));
+  TDVP_CUDA(cudaMemcpyAsync(d_off, cta_off.data(), b_off, cudaMemcpyHostToDevice, st));
+  TDVP_CUDA(cudaMemcpyAsync(d_ent, ent.data(), b_ent, cudaMemcpyHostToDevice, st));
+  TDVP_CUDA(cudaMemsetAsync(d_bar, 0, b_bar, st));
+  TDVP_CUDA(cudaMemsetAsync(d_err, 0, sizeof(int), st));
+  k_qr_gather<<<nblk, 256, 0, st>>>(M, cols, d_desc, d_r, d_c, X.data());
+  TDVP_CHECK_LAUNCH();
+  {
+    cplx* xp = X.data();
+    cplx* qp = Qb.data();
+    const QrDesc* dd = d_desc;
+    const int* po = d_off;
+    int nb = nblk;
+    void* args[] = {&xp, &qp, &d_tau, &dd, &po, &nb, &d_bar, &d_err};
+    TDVP_CUDA(cudaLaunchCooperativeKernel((void*)k_qr_groups, dim3(nctas), dim3(256), args, smem, st));
+    g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
+  }
+  const size_t nq = orient == 0 ? (size_t)rows * K : (size_t)K * cols;
+  const size_t nc = orient == 0 ? (size_t)K * cols : (size_t)rows * K;
+  out.Q.reset(pool, nq);
+  out.C.reset(pool, nc);
+  fill_zero(st, out.Q.data(), (long long)nq);
+  fill_zero(st, out.C.data(), (long long)nc);
+  k_qr_scatter<<<(int)ent.size(), 128, 0, st>>>(X.data(), Qb.data(), d_desc, d_ent, d_r, d_c, out.Q.data(),
+                                                  out.C.data(), cols, K);
+  TDVP_CHECK_LAUNCH();
+  int herr = 0;
+  TDVP_CUDA(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TDVP_CUDA(cudaStreamSynchronize(st));
+  if (herr) throw TdvpError(TDVP_ERR_TIMEOUT, "QR: a group barrier wait ran out");
+  out.k = K;
 }

@@ -55,7 +55,9 @@ enum TracePhase {
   PH_KRYLOV_RENV, PH_KRYLOV_EIG, PH_EXTEND_SVD,
   // inside every blocked SVD / eigendecomposition: block detection (mask, host union-find,
   // gather), pivoted Cholesky, Jacobi sweeps, selection and scatter of the kept vectors
-  PH_SVD_PREP, PH_SVD_PCHOL, PH_SVD_JACOBI, PH_SVD_SELECT, PH_COUNT
+  PH_SVD_PREP, PH_SVD_PCHOL, PH_SVD_JACOBI, PH_SVD_SELECT,
+  // every block QR / LQ of a gauge move that cuts nothing
+  PH_QR, PH_COUNT
 };
 
 struct Tracer {
@@ -230,3 +232,15 @@ inline void eig_psd_jacobi(cudaStream_t st, DevicePool* pool, const cplx* M, int
 // copy a (rows x cols) block into a (rows x ldo) destination at column offset
 void copy_block(cudaStream_t st, cplx* dst, long long ldd, const cplx* src, long long lds,
                 int rows, int cols);
+
+// Thin QR (orient 0) or LQ (orient 1) of a row-major complex FP64 matrix, block by block
+// (the exact-zero blocks of svd_blocked_keep), by Householder reflections in FP64.
+// orient 0: M = Q C, Q rows x k with orthonormal columns, C k x cols.
+// orient 1: M = C Q, Q k x cols with orthonormal rows, C rows x k.
+// k = sum over blocks of min(block rows, block cols): no direction is dropped.  k = 0 (and
+// no buffers) for a zero matrix.  Waits in the kernel are bounded (TDVP_ERR_TIMEOUT).
+struct QrOut {
+  int k = 0;
+  DArr Q, C;
+};
+void qr_blocked(cudaStream_t st, DevicePool* pool, const cplx* M, int rows, int cols, int orient, QrOut& out);

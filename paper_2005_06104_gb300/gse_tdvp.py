@@ -430,9 +430,9 @@ class GseTdvp:
         self._chk(_lib.tdvp_profile_read(self.h, out))
         return dict(applies=int(out[0]), ms=out[1], flops=out[2])
 
-    PHASES = ("lanczos_site", "lanczos_bond", "svd_sweep", "env", "krylov", "extend", "canonicalize",
+    PHASES = ("lanczos_site", "lanczos_bond", "gauge_sweep", "env", "krylov", "extend", "canonicalize",
               "krylov_right_envs", "krylov_eig", "extend_svd", "svd_prep", "svd_pchol", "svd_jacobi",
-              "svd_select")
+              "svd_select", "qr")
 
     def trace(self, enable=True):
         self._chk(_lib.tdvp_trace(self.h, 1 if enable else 0))
