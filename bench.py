@@ -32,6 +32,7 @@ import numpy as np
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
+T_START = time.time()
 METRIC = "GSE-TDVP1 sweeps/s and H_eff TFLOP/s at chi=1024, precision vs FP64 GPU, at <=1e-7 energy err"
 UNIT = "sweeps/s"
 
@@ -47,6 +48,11 @@ def parse():
                     help="bond-dimension cap of the trajectory that carries the FP64 and TDVP2 comparisons")
     ap.add_argument("--prep-steps", type=int, default=9,
                     help="untimed GSE-TDVP1 steps that grow the bond dimension before warm-up")
+    ap.add_argument("--compare-prep", type=int, default=10,
+                    help="steps of the comparison trajectory before its FP64 / precision-form / TDVP2 steps")
+    ap.add_argument("--time-budget", type=float, default=1650.0,
+                    help="wall-clock seconds the whole run may take: the timed loop stops early (and says so) "
+                         "when the steps left and the e2e step would not fit")
     ap.add_argument("--k", type=int, default=3)
     ap.add_argument("--krylov", default="dm", choices=["dm", "zipup"],
                     help="Krylov vectors by the density-matrix algorithm (default) or by zip-up")
@@ -178,13 +184,14 @@ def _lanczos_iters_oracle(args, W, chi=32):
 
 
 def cpu_baseline(args, W, iters=None):
-    """The oracle (as it stands) on the host cores, on a bounded sample of one sweep: its
-    primitives timed once each at the centre site's shapes (bond dimension
-    min(chi_max, 2^(N/2)), MPO width of the centre), composed into a TDVP1 site update
-    (iters H_eff applies, one SVD of the centre tensor, one environment update, iters K_eff
-    applies) and scaled to the 2N site updates of a sweep by each site's m_l m_r (m_l + m_r)
-    share.  iters: Krylov dimension per local exponential, from _lanczos_iters_oracle.
-    Steps 1-2 (Krylov vectors, extension) are left out, which favours the CPU."""
+    """The oracle (as it stands) on the host cores, on a bounded sample of one sweep at the
+    bench's bond dimension: its primitives timed once each at the centre site's shapes (bond
+    dimension min(chi_max, 2^(N/2)), MPO width of the centre): one H_eff apply, one K_eff
+    apply, one block QR (the real-time gauge move) and one environment update.  The sweep is
+    extrapolated from that sample: a site update = iters H_eff applies + iters K_eff applies +
+    QR + update, scaled to the 2N site updates by each site's m_l m_r (m_l + m_r) share.
+    iters: Krylov dimension per local exponential, from _lanczos_iters_oracle.  Steps 1-2
+    (Krylov vectors, extension) are left out, which favours the CPU."""
     import oracle as O
     from paper_2005_06104_gb300 import workloads as wl
     n = len(W)
@@ -204,20 +211,23 @@ def cpu_baseline(args, W, iters=None):
         t = time.perf_counter()
         f()
         return time.perf_counter() - t
+    t0 = time.perf_counter()
     t_heff = timed(lambda: O.heff_apply(L, W[c], R, A))
     t_keff = timed(lambda: O.keff_apply(Lb, R, C))
-    t_svd = timed(lambda: O.svd_truncate(A.reshape(2 * m, m)))
+    t_qr = timed(lambda: O.qr_blocks(A.reshape(2 * m, m)))
     t_env = timed(lambda: O.env_left_step(L, A, W[c]))
-    t_site = iters * (t_heff + t_keff) + t_svd + t_env
+    sample_s = time.perf_counter() - t0
+    t_site = iters * (t_heff + t_keff) + t_qr + t_env
     cost = [dims[i] * dims[i + 1] * (dims[i] + dims[i + 1]) for i in range(n)]
     t_sweep = 2.0 * t_site * sum(cost) / cost[c]
-    return {"value": 1.0 / t_sweep, "unit": UNIT, "cores": _blas_threads(), "kind": "oracle",
+    return {"value": 1.0 / t_sweep, "unit": UNIT, "cores": _blas_threads(),
+            "kind": "oracle: timed sample at chi_max, extrapolated to one sweep (Krylov and extension excluded)",
             "sample": f"oracle primitives at the centre site (chi={m}, w={wc}) timed once each: H_eff apply "
-                      f"{t_heff:.2f} s, K_eff apply {t_keff:.2f} s, SVD {t_svd:.2f} s, environment update "
-                      f"{t_env:.2f} s; a site update = {iters:.1f} Krylov iterations (the oracle's own mean "
-                      f"on this lattice and dt at chi=32) of H_eff and of K_eff + SVD + update; scaled to one "
-                      f"sweep by m_l m_r (m_l+m_r); Krylov and extension steps excluded (favours the CPU)",
-            "seconds_per_site_update": t_site}
+                      f"{t_heff:.2f} s, K_eff apply {t_keff:.2f} s, block QR {t_qr:.2f} s, environment update "
+                      f"{t_env:.2f} s; a site update = {iters:.1f} Krylov iterations (the oracle's own mean on "
+                      f"this lattice and dt at chi=32) of H_eff and of K_eff + QR + update; scaled to one sweep "
+                      f"by m_l m_r (m_l+m_r); Krylov and extension steps excluded (favours the CPU)",
+            "sample_s": sample_s, "seconds_per_site_update": t_site, "extrapolated_s_per_sweep": t_sweep}
 
 
 def _blas_threads():
@@ -232,8 +242,10 @@ def _blas_threads():
 
 
 def run_reference(args):
-    """The oracle on the host cores, on the same workload's bounded sample per step (see
-    cpu_baseline): rank 0 only; other ranks exit without work."""
+    """The oracle on the host cores (rank 0 only; other ranks exit without work).  Each step
+    is one bounded sample of the chi_max workload (cpu_baseline: the oracle's primitives at the
+    centre site, timed); ms_per_step is the measured wall time of a sample, and value is the
+    sweep rate extrapolated from the samples (labelled as such in cpu_baseline.kind)."""
     rank = int(os.environ.get("RANK", "0"))
     if rank != 0:
         return
@@ -242,12 +254,15 @@ def run_reference(args):
     for _ in range(args.warmup):
         cpu_baseline(args, W, iters)
     samples = [cpu_baseline(args, W, iters) for _ in range(args.steps)]
-    t_sweep = [1.0 / x["value"] for x in samples]
+    t_sweep = [x["extrapolated_s_per_sweep"] for x in samples]
     v = args.steps / sum(t_sweep)
     cb = dict(samples[-1])
     cb["value"] = v
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus,
-            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * sum(t_sweep) / args.steps,
+            "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": 1e3 * sum(x["sample_s"] for x in samples) / args.steps,
+            "ms_per_step_is": "measured wall time of one timed sample (the value is extrapolated from it)",
+            "extrapolated_ms_per_sweep": 1e3 * sum(t_sweep) / args.steps,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "c128",
             "data": "synthetic", "config": cfg, "cpu_baseline": cb,
             "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
@@ -296,94 +311,18 @@ def job_throughput(world, steps, t_max):
     return world * steps / t_max
 
 
-def run_gpu(args):
-    import torch
-    import torch.distributed as dist
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    if world > 1:
-        dist.init_process_group("nccl")
-    torch.cuda.set_device(local)
-    from paper_2005_06104_gb300 import gse_tdvp as g
-    lat, W, psi0, cfg = workload(args)
+def _pinned_alloc(torch):
+    """Page-locked host arrays (numpy views of pinned torch tensors) for the e2e leg."""
+    def alloc(shape):
+        t = torch.empty(int(np.prod(shape)) * 2, dtype=torch.float64, pin_memory=True)
+        return t.numpy().view(np.complex128).reshape(shape)
+    return alloc
 
-    def new_handle(*a, **kw):
-        h = g.GseTdvp(*a, **kw)
-        if args.krylov == "zipup":
-            h.krylov_method(g.KRYLOV_ZIPUP)
-        return h
-    opts = dict(tau=args.dt, eps_k=1e-8, eps_m=1e-8, eps=0.0, chi_max=args.chi_max,
-                precision=prec_code(g, args.precision))
-    stream = torch.cuda.current_stream().cuda_stream
-    st = new_handle(psi0, W, stream=stream, **opts)
-    e_init = st.energy()
 
-    def step(h):
-        h.expand_basis(args.k)
-        h.sweep(args.dt, g.REAL)
-
-    for _ in range(args.prep_steps + args.warmup):
-        step(st)
-    start_state = st.get_mps()
-    dims_start = st.bond_dims()
-    clocks = Clocks(local)
-    ts, phases = [], {}
-    heff_ms = heff_flops = 0.0
-    heff_n = 0
-    nfo = {}
-    if world > 1:
-        dist.barrier()
-    torch.cuda.synchronize()
-    clocks.start()
-    launches0 = g.launch_count()
-    for _ in range(args.steps):
-        st.profile(True)
-        st.trace(True)
-        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        torch.cuda.nvtx.range_push("gse_step")  # lets a profiler select exactly the timed steps
-        a.record()
-        step(st)
-        b.record()
-        torch.cuda.nvtx.range_pop()
-        b.synchronize()
-        ts.append(a.elapsed_time(b))
-        pr = st.profile_read()
-        for kk, vv in st.trace_read().items():
-            phases[kk] = phases.get(kk, 0.0) + vv / args.steps
-        heff_ms += pr["ms"]
-        heff_flops += pr["flops"]
-        heff_n += pr["applies"]
-        nfo = st.trunc_stats()
-        nfo["krylov_env_segment"] = st.krylov_memory()
-    torch.cuda.synchronize()
-    launches = g.launch_count() - launches0
-    if world > 1:
-        dist.barrier()
-    ck = clocks.stop()
-    t_rank = sum(ts) / 1e3
-    if world > 1:
-        t_rank = max_over_ranks(t_rank, dist, "cuda")
-    value = job_throughput(world, args.steps, t_rank)
-    nfo["bond_dim_max"] = max(st.bond_dims())
-    nfo["bond_dims_start"] = dims_start
-    e_end = st.energy()
-    st.close()
-    if rank != 0:
-        if world > 1:
-            dist.destroy_process_group()
-        return
-    if args.step_only:
-        print(json.dumps({"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-                          "warmup": args.warmup, "ms_per_step": sum(ts) / len(ts), "step_only": True,
-                          "config": dict(cfg, parallelism=f"replicas{world}"), "gpu_launches": launches,
-                          "phases_ms_per_step": phases, "step_stats": nfo}), flush=True)
-        if world > 1:
-            dist.destroy_process_group()
-        return
-    # precision form vs FP64 GPU form, and TDVP2 against GSE-TDVP1 (Sec. I.C): one step of each
-    # from the same state of a second trajectory capped at --compare-chi (an FP64 step at
-    # chi = 1024 takes about 12 minutes)
+def comparison_legs(args, g, torch, W, psi0, opts, stream, new_handle, step):
+    """Precision form vs FP64 GPU form, and TDVP2 against GSE-TDVP1 (Sec. I.C): one step of
+    each from the same state of a second trajectory capped at --compare-chi (an FP64 step at
+    chi = 1024 takes tens of minutes)."""
     def timed_step(h, fn):
         ea, eb = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         ea.record()
@@ -393,19 +332,25 @@ def run_gpu(args):
         return ea.elapsed_time(eb)
     copts = dict(opts, chi_max=args.compare_chi)
     cmp_h = new_handle(psi0, W, stream=stream, **copts)
-    for _ in range(8 + args.warmup):
+    for _ in range(args.compare_prep):
         step(cmp_h)
     cmp_state = cmp_h.get_mps()
     cmp_dims = cmp_h.bond_dims()
     cmp_h.close()
     a = new_handle(cmp_state, W, stream=stream, **dict(copts, precision=g.PREC_FP64))
     ms_64 = timed_step(a, step)
-    e_64 = a.energy()
+    e_64, n_64 = a.energy(), a.norm()
     a.close()
     b_ = new_handle(cmp_state, W, stream=stream, **copts)
     ms_tc = timed_step(b_, step)
     e_tc, n_tc = b_.energy(), b_.norm()
     b_.close()
+    prec = {"chi_max": args.compare_chi, "bond_dims_max": max(cmp_dims), "steps_before": args.compare_prep,
+            "precision": args.precision, "energy_precision_form": e_tc, "energy_fp64": e_64,
+            "step_ms_precision_form": ms_tc, "step_ms_fp64": ms_64, "speedup_over_fp64": ms_64 / ms_tc,
+            "rel_energy_err": abs(e_tc - e_64) / abs(e_64), "norm_drift": abs(n_tc - 1.0),
+            "norm_drift_fp64": abs(n_64 - 1.0),
+            "what": "one GSE-TDVP1 step in each form from the same state of the comparison trajectory"}
     tdvp2 = None
     if not args.no_tdvp2:
         c_ = new_handle(cmp_state, W, stream=stream, **copts)
@@ -418,19 +363,10 @@ def run_gpu(args):
                  "what": "one TDVP2 step (tdvp_sweep2, same precision form, same cap, eps = 0) and one "
                          "GSE-TDVP1 step from the same state of the comparison trajectory"}
         c_.close()
-    # e2e through the public API: host state in, one step, full state out
-    e2e_ts = []
-    h2d = sum(x.nbytes for x in start_state) + sum(w.nbytes for w in W)
-    d2h = 0
-    for _ in range(max(1, min(args.steps, 2))):
-        torch.cuda.synchronize()
-        t = time.perf_counter()
-        s2 = new_handle(start_state, W, stream=stream, **opts)
-        step(s2)
-        out = s2.get_mps()
-        s2.close()
-        e2e_ts.append(time.perf_counter() - t)
-        d2h = sum(x.nbytes for x in out)
+    return prec, tdvp2
+
+
+def roofline_line(args, g, torch, W):
     Wmax = max(W, key=lambda w: w.shape[0] * w.shape[3])
     pflops, pms, pms_unc = heff_roofline(g, torch, args.heff_chi, Wmax, prec_code(g, args.precision))
     peaks_path = os.path.join(ROOT, "MEASURED_PEAKS.json")
@@ -457,47 +393,168 @@ def run_gpu(args):
         traffic = 5.11e9
         traffic_src = ("ncu dram__bytes_read.sum + dram__bytes_write.sum over the 5 launches of one cached "
                        "apply (slice x, GEMM 1, MPO stage, GEMM 3 split 4 ways, split-K sum) of these kernels")
-    cpu = None
-    if not args.no_cpu_baseline:
-        try:
-            cpu = cpu_baseline(args, W)
-        except Exception as ex:  # reported, never silently replaced
-            cpu = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle", "sample": f"failed: {ex}"}
-    achieved_step = heff_flops / (heff_ms / 1e3) / 1e12 if heff_ms > 0 else None
     achieved = pflops / (pms / 1e3) / 1e12
-    line = {
-        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": sum(ts) / len(ts), "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": f"c128 state / {args.precision} contractions",
-        "data": "synthetic", "config": dict(cfg, parallelism=f"replicas{world}"),
-        "roofline": {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
-                     "frac": achieved / peak, "traffic": traffic, "kernel": kern, "peak_source": peak_src,
-                     "traffic_source": traffic_src,
-                     "tensor_flops_per_algorithmic_flop": products,
-                     "tensor_frac_executed": achieved * products / peak,
-                     "ms_per_apply": pms, "algorithmic_flops_per_apply": pflops,
-                     "ms_per_apply_rebuilding_env_operands": pms_unc,
-                     "timed": "10 applies after 3 warm-up, environment operands cached (as in a Lanczos run)"},
-        "heff_in_step": {"applies": heff_n, "ms": heff_ms, "tflops_algorithmic": achieved_step,
+    return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
+            "frac": achieved / peak, "traffic": traffic, "kernel": kern, "peak_source": peak_src,
+            "traffic_source": traffic_src, "tensor_flops_per_algorithmic_flop": products,
+            "tensor_frac_executed": achieved * products / peak, "ms_per_apply": pms,
+            "algorithmic_flops_per_apply": pflops, "ms_per_apply_rebuilding_env_operands": pms_unc,
+            "timed": "10 applies after 3 warm-up, environment operands cached (as in a Lanczos run)"}
+
+
+def run_gpu(args):
+    import torch
+    import torch.distributed as dist
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if world > 1:
+        dist.init_process_group("nccl")
+    torch.cuda.set_device(local)
+    from paper_2005_06104_gb300 import gse_tdvp as g
+    lat, W, psi0, cfg = workload(args)
+
+    def new_handle(*a, **kw):
+        h = g.GseTdvp(*a, **kw)
+        if args.krylov == "zipup":
+            h.krylov_method(g.KRYLOV_ZIPUP)
+        return h
+    opts = dict(tau=args.dt, eps_k=1e-8, eps_m=1e-8, eps=0.0, chi_max=args.chi_max,
+                precision=prec_code(g, args.precision))
+    stream = torch.cuda.current_stream().cuda_stream
+
+    def step(h):
+        h.expand_basis(args.k)
+        h.sweep(args.dt, g.REAL)
+
+    # bounded legs first (rank 0): the H_eff roofline probe, the CPU oracle sample, the
+    # precision-vs-FP64 and TDVP2 comparisons on a trajectory capped at --compare-chi
+    legs = {}
+    if rank == 0 and not args.step_only:
+        legs["roofline"] = roofline_line(args, g, torch, W)
+        legs["precision_vs_fp64"], legs["tdvp2_comparison"] = comparison_legs(
+            args, g, torch, W, psi0, opts, stream, new_handle, step)
+        if not args.no_cpu_baseline:
+            try:
+                legs["cpu_baseline"] = cpu_baseline(args, W)
+            except Exception as ex:  # reported, never silently replaced
+                legs["cpu_baseline"] = {"value": None, "unit": UNIT, "cores": os.cpu_count(), "kind": "oracle",
+                                        "sample": f"failed: {ex}"}
+    # the chi_max trajectory: growth steps, warm-up steps, timed steps
+    st = new_handle(psi0, W, stream=stream, **opts)
+    e_init = st.energy()
+    for _ in range(args.prep_steps + args.warmup):
+        step(st)
+    start_state = st.get_mps()
+    dims_start = st.bond_dims()
+    clocks = Clocks(local)
+    ts, phases = [], {}
+    heff_ms = heff_flops = 0.0
+    heff_n = 0
+    nfo = {}
+    if world > 1:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    launches0 = g.launch_count()
+    stopped_early = False
+    for i in range(args.steps):
+        # time guard: the timed steps left plus the e2e step must fit the wall-clock budget;
+        # every rank takes the same decision
+        if ts:
+            mean_s = sum(ts) / len(ts) / 1e3
+            over = (time.time() - T_START) + (args.steps - i + 1) * mean_s > args.time_budget
+            if world > 1:
+                over = max_over_ranks(1.0 if over else 0.0, dist, "cuda") > 0.0
+            if over:
+                stopped_early = True
+                break
+        st.profile(True)
+        st.trace(True)
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        torch.cuda.nvtx.range_push("gse_step")  # lets a profiler select exactly the timed steps
+        a.record()
+        step(st)
+        b.record()
+        torch.cuda.nvtx.range_pop()
+        b.synchronize()
+        ts.append(a.elapsed_time(b))
+        pr = st.profile_read()
+        for kk, vv in st.trace_read().items():
+            phases[kk] = phases.get(kk, 0.0) + vv
+        heff_ms += pr["ms"]
+        heff_flops += pr["flops"]
+        heff_n += pr["applies"]
+        nfo = st.trunc_stats()
+        nfo["krylov_env_segment"] = st.krylov_memory()
+    torch.cuda.synchronize()
+    launches = g.launch_count() - launches0
+    if world > 1:
+        dist.barrier()
+    ck = clocks.stop()
+    n_timed = len(ts)
+    phases = {kk: vv / n_timed for kk, vv in phases.items()}
+    t_rank = sum(ts) / 1e3
+    if world > 1:
+        t_rank = max_over_ranks(t_rank, dist, "cuda")
+    value = job_throughput(world, n_timed, t_rank)
+    nfo["bond_dim_max"] = max(st.bond_dims())
+    nfo["bond_dims_start"] = dims_start
+    e_end = st.energy()
+    st.close()
+    if rank != 0:
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    base = {"metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": n_timed,
+            "warmup": args.warmup, "ms_per_step": sum(ts) / n_timed, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": f"c128 state / {args.precision} contractions",
+            "data": "synthetic", "config": dict(cfg, parallelism=f"replicas{world}", untimed_steps_before=
+                                                args.prep_steps + args.warmup),
+            "gpu_launches": launches, "clocks": ck, "phases_ms_per_step": phases, "step_stats": nfo}
+    if stopped_early:
+        base["steps_requested"] = args.steps
+        base["stopped_by_time_budget"] = args.time_budget
+    if args.step_only:
+        print(json.dumps(dict(base, step_only=True)), flush=True)
+        if world > 1:
+            dist.destroy_process_group()
+        return
+    # e2e through the public API: the state in page-locked host memory, tdvp_create (copy to the
+    # device, canonical form), one step, tdvp_get_mps back into page-locked memory
+    alloc = _pinned_alloc(torch)
+    host_in = []
+    for x in start_state:
+        y = alloc(x.shape)
+        y[...] = x
+        host_in.append(y)
+    h2d = sum(x.nbytes for x in host_in) + sum(w.nbytes for w in W)
+    torch.cuda.synchronize()
+    t = time.perf_counter()
+    s2 = new_handle(host_in, W, stream=stream, **opts)
+    step(s2)
+    out = s2.get_mps(alloc)
+    s2.close()
+    e2e_s = time.perf_counter() - t
+    d2h = sum(x.nbytes for x in out)
+    roof = legs.get("roofline")
+    achieved_step = heff_flops / (heff_ms / 1e3) / 1e12 if heff_ms > 0 else None
+    line = dict(base)
+    line.update({
+        "roofline": roof,
+        "heff_in_step": {"applies": heff_n / n_timed, "ms": heff_ms / n_timed, "tflops_algorithmic": achieved_step,
                          "share_of_step": heff_ms / sum(ts) if ts else None},
-        "precision_vs_fp64": {"chi_max": args.compare_chi, "bond_dims_max": max(cmp_dims),
-                              "precision": args.precision, "energy_precision_form": e_tc, "energy_fp64": e_64,
-                              "step_ms_precision_form": ms_tc, "step_ms_fp64": ms_64,
-                              "speedup_over_fp64": ms_64 / ms_tc,
-                              "rel_energy_err": abs(e_tc - e_64) / abs(e_64), "norm_drift": abs(n_tc - 1.0)},
-        "tdvp2_comparison": tdvp2,
+        "precision_vs_fp64": legs.get("precision_vs_fp64"),
+        "tdvp2_comparison": legs.get("tdvp2_comparison"),
         "energy_conservation": {"E_initial": e_init, "E_after_timed_steps": e_end, "abs_drift": abs(e_end - e_init),
                                 "rel_drift": abs(e_end - e_init) / abs(e_init),
-                                "steps": args.prep_steps + args.warmup + args.steps},
-        "step_stats": nfo,
-        "phases_ms_per_step": phases,
-        "cpu_baseline": cpu,
-        "e2e": {"value": len(e2e_ts) / sum(e2e_ts), "unit": UNIT, "h2d_bytes_per_step": h2d,
-                "d2h_bytes_per_step": d2h,
-                "what": "tdvp_create from host MPS + expand + sweep + tdvp_get_mps + destroy"},
-        "gpu_launches": launches,
-        "clocks": ck,
-    }
+                                "steps": args.prep_steps + args.warmup + n_timed},
+        "cpu_baseline": legs.get("cpu_baseline"),
+        "e2e": {"value": 1.0 / e2e_s, "unit": UNIT, "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
+                "steps": 1, "what": "page-locked host MPS -> tdvp_create (copy, canonical form) + expand + sweep "
+                                    "+ tdvp_get_mps into page-locked memory + destroy, host wall clock"},
+        "wall_s": time.time() - T_START,
+    })
     print(json.dumps(line), flush=True)
     if world > 1:
         dist.destroy_process_group()

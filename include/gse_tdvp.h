@@ -134,8 +134,10 @@ TDVP_API tdvp_status tdvp_expand_basis(tdvp_handle* h, int k, const double* weig
  * (K = ceil(sqrt(N))) stays on the device and the others are rebuilt, segment by
  * segment, when the left-to-right pass needs them: the same launches on the same
  * inputs, so the Krylov vectors are bit-identical, for at most one extra pass of
- * density-environment work.  max_bytes = 0 (the default) uses half of the free
- * device memory; max_bytes < 0 leaves the setting unchanged.  *last_segment
+ * density-environment work.  max_bytes = 0 (the default) uses the free device
+ * memory (plus the blocks this handle has cached) less the step's GEMM
+ * intermediates, three times the largest F_j and 16 GiB; max_bytes < 0 leaves the
+ * setting unchanged.  *last_segment
  * (optional) receives K of the last Krylov step, 1 when every F_j stayed. */
 TDVP_API tdvp_status tdvp_krylov_memory(tdvp_handle* h, double max_bytes, int* last_segment);
 

@@ -108,9 +108,16 @@ class DevicePool {
     for (const auto& kv : free_) b += kv.first * kv.second.size();
     return b;
   }
+  // powers of two up to 256 MiB; above, multiples of 1/16 of the next power of two (at most
+  // 6.25 % unused), so that the large environments of a high bond dimension do not waste
+  // up to half of their block
   static size_t size_class(size_t bytes) {
     size_t c = 4096;
     while (c < bytes) c <<= 1;
+    if (c > (size_t(256) << 20)) {
+      const size_t step = c >> 4;
+      c = (bytes + step - 1) / step * step;
+    }
     return c;
   }
 

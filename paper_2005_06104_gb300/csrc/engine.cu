@@ -820,13 +820,26 @@ void Engine::krylov_apply(const KrylovOp& kop, const MpsDev& src, MpsDev& out) {
   F[N - 1].reset(&pool, 1);
   k_one<<<1, 1, 0, st>>>(F[N - 1].data());
   TDVP_CHECK_LAUNCH();
-  double f_total = 0.0;
-  for (int j = 0; j + 1 < N; ++j) f_total += (double)sizeof(cplx) * w[j + 1] * src.m[j + 1] * w[j + 1] * src.m[j + 1];
+  double f_total = 0.0, f_max = 0.0, t_max = 0.0;
+  for (int j = 0; j + 1 < N; ++j) {
+    const double f = (double)DevicePool::size_class(sizeof(cplx) * (size_t)w[j + 1] * src.m[j + 1] * w[j + 1] *
+                                                    src.m[j + 1]);
+    f_total += f;
+    f_max = std::max(f_max, f);
+  }
+  for (int i = 1; i < N; ++i) {  // the two GEMM intermediates of step_F
+    const size_t t1 = sizeof(cplx) * (size_t)w[i + 1] * src.m[i] * d * w[i + 1] * src.m[i + 1];
+    const size_t t2 = sizeof(cplx) * (size_t)w[i + 1] * src.m[i] * d * w[i + 1] * src.m[i] * d;
+    t_max = std::max(t_max, (double)DevicePool::size_class(t1) + (double)DevicePool::size_class(t2));
+  }
   double budget = krylov_mem_budget;
   if (!(budget > 0.0)) {
+    // what the device has left (free plus this engine's cached blocks), less the GEMM
+    // intermediates, the operand slices and the reordered copy of the largest environment, and
+    // 16 GiB for everything else the pass allocates
     size_t fr = 0, tot = 0;
     TDVP_CUDA(cudaMemGetInfo(&fr, &tot));
-    budget = 0.5 * ((double)fr + (double)pool.cached_bytes());
+    budget = (double)fr + (double)pool.cached_bytes() - t_max - 3.0 * f_max - 16.0 * (1ull << 30);
   }
   const int seg = f_total <= budget ? 1 : std::max(2, (int)std::ceil(std::sqrt((double)N)));
   krylov_env_segment = seg;

@@ -442,9 +442,15 @@ class GseTdvp:
         self._chk(_lib.tdvp_trace_read(self.h, out, len(self.PHASES)))
         return dict(zip(self.PHASES, list(out)))
 
-    def get_mps(self):
+    def get_mps(self, alloc=None):
+        """The state as host arrays [m_l, d, m_r].  alloc(shape) may supply the destination
+        arrays (complex128, C-contiguous; e.g. views of page-locked memory)."""
         m = self.bond_dims()
-        arrs = [np.empty((m[i], self.d, m[i + 1]), dtype=np.complex128) for i in range(self.n)]
+        shapes = [(m[i], self.d, m[i + 1]) for i in range(self.n)]
+        arrs = [np.empty(s, dtype=np.complex128) if alloc is None else alloc(s) for s in shapes]
+        for a, s in zip(arrs, shapes):
+            if a.shape != s or a.dtype != np.complex128 or not a.flags.c_contiguous:
+                raise ValueError("get_mps: destination arrays must be C-contiguous complex128 of the bond shapes")
         ptrs = (C.c_void_p * self.n)(*[a.ctypes.data for a in arrs])
         self._chk(_lib.tdvp_get_mps(self.h, ptrs))
         return arrs

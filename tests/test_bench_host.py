@@ -21,7 +21,8 @@ def test_cpu_baseline_sample_is_bounded_and_scaled():
     iters = bench._lanczos_iters_oracle(a, W, chi=8)
     assert 2.0 <= iters <= 40.0
     r = bench.cpu_baseline(a, W, iters)
-    assert r["kind"] == "oracle" and r["unit"] == bench.UNIT and r["value"] > 0
+    assert r["kind"].startswith("oracle") and "extrapolated" in r["kind"]
+    assert r["unit"] == bench.UNIT and r["value"] > 0 and r["sample_s"] > 0
     # one sweep = 2N site updates weighted by m_l m_r (m_l + m_r); the centre has the largest share
     assert 1.0 / r["value"] >= 2.0 * r["seconds_per_site_update"]
     assert "chi=32" in r["sample"]
@@ -36,6 +37,9 @@ def test_reference_arm_prints_one_line():
     assert line["impl"] == "reference" and line["value"] > 0
     assert line["e2e"]["h2d_bytes_per_step"] == 0 and line["cpu_baseline"]["value"] == line["value"]
     assert line["config"]["chi_max"] == 32
+    # ms_per_step is the measured sample time; the extrapolated sweep time is reported beside it
+    assert line["ms_per_step"] == pytest.approx(1e3 * line["cpu_baseline"]["sample_s"], rel=1e-9)
+    assert line["extrapolated_ms_per_sweep"] == pytest.approx(1e3 / line["value"], rel=1e-9)
 
 
 @pytest.mark.parametrize("n", [6, 8, 10])
