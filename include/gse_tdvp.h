@@ -270,10 +270,17 @@ TDVP_API tdvp_status tdvp_save(tdvp_handle* h, const char* path);
 TDVP_API tdvp_status tdvp_load(const char* path, const tdvp_mpo_desc* mpo, const tdvp_options* opt, void* stream,
                                tdvp_handle** out);
 TDVP_API tdvp_status tdvp_checkpoint_write(const char* path, const tdvp_mps_desc* mps);
-/* N and d, and bond_dims (N + 1 ints) when non-null. */
-TDVP_API tdvp_status tdvp_checkpoint_read_header(const char* path, int* n_sites, int* d, int* bond_dims);
-/* Site tensors into caller buffers sized from the header (2 m_i d m_{i+1} doubles). */
-TDVP_API tdvp_status tdvp_checkpoint_read(const char* path, double* const* sites_out);
+/* N and d; and bond_dims (N + 1 ints) when bond_dims is non-null and capacity >= N + 1
+ * (else TDVP_ERR_SHAPE, nothing written). */
+TDVP_API tdvp_status tdvp_checkpoint_read_header(const char* path, int* n_sites, int* d, int* bond_dims,
+                                                 int capacity);
+/* Site tensors into caller buffers of the shapes the caller states (n_sites, d, bond_dims:
+ * site i holds 2 m_i d m_{i+1} doubles).  The file is read once, checked against the size its
+ * header implies and against its hash into memory of the library's own; the caller's buffers
+ * are written only after that, and only when the file's N, d and bond dimensions equal the
+ * stated ones (else TDVP_ERR_SHAPE).  tdvp_load reads the same way. */
+TDVP_API tdvp_status tdvp_checkpoint_read(const char* path, int n_sites, int d, const int* bond_dims,
+                                          double* const* sites_out);
 TDVP_API const char* tdvp_checkpoint_last_error(void);
 
 /* ---------------------------------------------------------------------------
@@ -346,10 +353,14 @@ TDVP_API tdvp_status tdvp_expm_contract(const tdvp_site_dims* dims, const void* 
                                         const void* R_dev, const void* x_dev, void* y_dev, double delta,
                                         tdvp_time kind, int precision, double tol, int nmax, int* iters,
                                         void* stream);
+/* The handle-free calls above share one library-wide context (device pool, operand
+ * caches, Lanczos work space), set up on the device current at the first of them;
+ * a later call with another device current returns TDVP_ERR_INVALID_ARG. */
 TDVP_API const char* tdvp_contract_last_error(void);
 
-/* y = H_eff x exactly as tdvp_heff_contract(..., TDVP_PREC_FP64, ...), but
- * without allocating device memory.  The paper has no counterpart: this entry
+/* y = H_eff x by the same FP64 contraction as tdvp_heff_contract(...,
+ * TDVP_PREC_FP64, ...) (the summation order may differ: the results agree to
+ * about 1e-12 relative), but without allocating device memory.  The paper has no counterpart: this entry
  * exists for callers that cannot call cudaMalloc (a host framework that owns
  * every device allocation, or a loop that must never block on the allocator).
  * Its intermediates live in a fixed 32 MiB file-scope device array that every

@@ -339,6 +339,7 @@ struct RawCtx {
   Blas1 blas;
   LanczosWork lw;
   bool ready = false;
+  int device = -1;  // the device the pool, scratch and work space were set up on
   std::string err;
   long long key = 0;
 };
@@ -352,15 +353,22 @@ tdvp_status raw_guarded(F&& f) {
   RawCtx& c = raw();
   std::lock_guard<std::mutex> lk(c.mu);
   try {
+    int dev = 0;
+    TDVP_CUDA(cudaGetDevice(&dev));
     if (!c.ready) {
-      int dev = 0, sms = 148;
-      TDVP_CUDA(cudaGetDevice(&dev));
+      int sms = 148;
       TDVP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
       c.scr.pool = &c.pool;
       c.blas.init(&c.pool, sms);
       c.lw.init(&c.pool);
+      c.device = dev;
       c.ready = true;
     }
+    // the context's device memory belongs to the device of the first call: another
+    // current device would hand that device's kernels foreign pointers
+    tdvp_require(dev == c.device, TDVP_ERR_INVALID_ARG,
+                 "handle-free contractions run on the device current at their first call (" +
+                     std::to_string(c.device) + "), not on device " + std::to_string(dev));
     f(c);
     c.err.clear();
     return TDVP_OK;

@@ -75,29 +75,43 @@ Header read_header(FILE* f, Fnv& h, const std::string& path) {
   return r;
 }
 
-// The whole file: header, sites (into caller buffers when `sites` is non-null), hash.
-Header read_file(const std::string& path, double* const* sites) {
+// Bytes of a file with header r: magic, 4 ints, bond dims, sites, hash.
+long double file_bytes(const Header& r) {
+  long double b = 8.0L + 16.0L + 4.0L * (r.n + 1) + 8.0L;
+  for (int i = 0; i < r.n; ++i) b += 16.0L * r.m[i] * r.d * r.m[i + 1];
+  return b;
+}
+
+// A whole checkpoint read through one open file: the header, a check that the file has exactly
+// the size the header implies (before anything large is allocated), every site into memory of
+// its own, and the hash.  Nothing reaches a caller before the hash has been verified.
+struct Loaded {
+  Header hdr;
+  std::vector<std::vector<double>> sites;
+};
+
+Loaded load_file(const std::string& path) {
   File fl(fopen(path.c_str(), "rb"));
   tdvp_require(fl.f != nullptr, TDVP_ERR_INVALID_ARG, "checkpoint: cannot open " + path);
+  tdvp_require(std::fseek(fl.f, 0, SEEK_END) == 0, TDVP_ERR_INVALID_ARG, "checkpoint: cannot seek " + path);
+  const long size = std::ftell(fl.f);
+  tdvp_require(size >= 0 && std::fseek(fl.f, 0, SEEK_SET) == 0, TDVP_ERR_INVALID_ARG,
+               "checkpoint: cannot seek " + path);
   Fnv h;
-  Header r = read_header(fl.f, h, path);
-  std::vector<double> tmp;
-  for (int i = 0; i < r.n; ++i) {
-    const size_t cnt = 2 * (size_t)r.m[i] * r.d * r.m[i + 1];
-    double* dst = nullptr;
-    if (sites) {
-      tdvp_require(sites[i] != nullptr, TDVP_ERR_INVALID_ARG, "checkpoint: null site buffer");
-      dst = sites[i];
-    } else {
-      tmp.resize(cnt);
-      dst = tmp.data();
-    }
-    get(fl.f, &h, dst, sizeof(double) * cnt, path);
+  Loaded out;
+  out.hdr = read_header(fl.f, h, path);
+  const long double want = file_bytes(out.hdr);
+  tdvp_require(want == (long double)size, TDVP_ERR_INVALID_ARG,
+               "checkpoint: file size does not match its header (truncated or corrupt): " + path);
+  out.sites.resize(out.hdr.n);
+  for (int i = 0; i < out.hdr.n; ++i) {
+    out.sites[i].resize(2 * (size_t)out.hdr.m[i] * out.hdr.d * out.hdr.m[i + 1]);
+    get(fl.f, &h, out.sites[i].data(), sizeof(double) * out.sites[i].size(), path);
   }
-  uint64_t want = 0;
-  get(fl.f, nullptr, &want, sizeof(want), path);
-  tdvp_require(want == h.h, TDVP_ERR_INVALID_ARG, "checkpoint: hash mismatch (corrupt file): " + path);
-  return r;
+  uint64_t sum = 0;
+  get(fl.f, nullptr, &sum, sizeof(sum), path);
+  tdvp_require(sum == h.h, TDVP_ERR_INVALID_ARG, "checkpoint: hash mismatch (corrupt file): " + path);
+  return out;
 }
 
 void write_file(const std::string& path, int n, int d, const int* m, const double* const* sites) {
@@ -151,23 +165,33 @@ tdvp_status tdvp_checkpoint_write(const char* path, const tdvp_mps_desc* mps) {
   });
 }
 
-tdvp_status tdvp_checkpoint_read_header(const char* path, int* n_sites, int* d, int* bond_dims) {
+tdvp_status tdvp_checkpoint_read_header(const char* path, int* n_sites, int* d, int* bond_dims, int capacity) {
   return ckpt_guarded([&] {
     tdvp_require(path && n_sites && d, TDVP_ERR_INVALID_ARG, "null argument");
     File fl(fopen(path, "rb"));
     tdvp_require(fl.f != nullptr, TDVP_ERR_INVALID_ARG, std::string("checkpoint: cannot open ") + path);
     Fnv h;
     const Header r = read_header(fl.f, h, path);
+    if (bond_dims)
+      tdvp_require(capacity >= r.n + 1, TDVP_ERR_SHAPE, "checkpoint: bond_dims buffer holds fewer than N + 1 ints");
     *n_sites = r.n;
     *d = r.d;
     if (bond_dims) std::memcpy(bond_dims, r.m.data(), sizeof(int) * (r.n + 1));
   });
 }
 
-tdvp_status tdvp_checkpoint_read(const char* path, double* const* sites_out) {
+tdvp_status tdvp_checkpoint_read(const char* path, int n_sites, int d, const int* bond_dims,
+                                 double* const* sites_out) {
   return ckpt_guarded([&] {
-    tdvp_require(path && sites_out, TDVP_ERR_INVALID_ARG, "null argument");
-    read_file(path, sites_out);
+    tdvp_require(path && bond_dims && sites_out, TDVP_ERR_INVALID_ARG, "null argument");
+    const Loaded f = load_file(path);
+    tdvp_require(f.hdr.n == n_sites && f.hdr.d == d, TDVP_ERR_SHAPE, "checkpoint: N or d differ from the buffers'");
+    for (int i = 0; i <= n_sites; ++i)
+      tdvp_require(f.hdr.m[i] == bond_dims[i], TDVP_ERR_SHAPE, "checkpoint: bond dimensions differ from the buffers'");
+    for (int i = 0; i < n_sites; ++i) {
+      tdvp_require(sites_out[i] != nullptr, TDVP_ERR_INVALID_ARG, "checkpoint: null site buffer");
+      std::memcpy(sites_out[i], f.sites[i].data(), sizeof(double) * f.sites[i].size());
+    }
   });
 }
 
@@ -175,47 +199,38 @@ const char* tdvp_checkpoint_last_error(void) { return g_ckpt_err.c_str(); }
 
 tdvp_status tdvp_save(tdvp_handle* h, const char* path) {
   if (!h) return TDVP_ERR_INVALID_ARG;
-  const int n = h->eng.N, d = h->eng.d;
-  std::vector<int> m(h->eng.psi.m.begin(), h->eng.psi.m.end());
-  std::vector<std::vector<double>> host(n);
-  std::vector<double*> ptr(n);
-  for (int i = 0; i < n; ++i) {
-    host[i].resize(2 * (size_t)m[i] * d * m[i + 1]);
-    ptr[i] = host[i].data();
-  }
-  tdvp_status s = tdvp_get_mps(h, ptr.data());
-  if (s != TDVP_OK) return s;
-  tdvp_mps_desc desc;
-  desc.n_sites = n;
-  desc.d = d;
-  desc.bond_dims = m.data();
-  desc.sites = ptr.data();
-  s = tdvp_checkpoint_write(path, &desc);
-  if (s != TDVP_OK) h->err = g_ckpt_err;
-  return s;
+  tdvp_status s = TDVP_OK;
+  const tdvp_status g = ckpt_guarded([&] {
+    tdvp_require(path != nullptr, TDVP_ERR_INVALID_ARG, "null path");
+    const int n = h->eng.N, d = h->eng.d;
+    std::vector<int> m(h->eng.psi.m.begin(), h->eng.psi.m.end());
+    std::vector<std::vector<double>> host(n);
+    std::vector<double*> ptr(n);
+    for (int i = 0; i < n; ++i) {
+      host[i].resize(2 * (size_t)m[i] * d * m[i + 1]);
+      ptr[i] = host[i].data();
+    }
+    s = tdvp_get_mps(h, ptr.data());
+    if (s != TDVP_OK) return;
+    write_file(path, n, d, m.data(), ptr.data());
+  });
+  if (s != TDVP_OK) return s;  // tdvp_get_mps left its reason on the handle
+  if (g != TDVP_OK) h->err = g_ckpt_err;
+  return g;
 }
 
 tdvp_status tdvp_load(const char* path, const tdvp_mpo_desc* mpo, const tdvp_options* opt, void* stream,
                       tdvp_handle** out) {
   if (!path || !mpo || !out) return TDVP_ERR_INVALID_ARG;
-  int n = 0, d = 0;
-  tdvp_status s = tdvp_checkpoint_read_header(path, &n, &d, nullptr);
+  Loaded f;
+  const tdvp_status s = ckpt_guarded([&] { f = load_file(path); });
   if (s != TDVP_OK) return s;
-  std::vector<int> m(n + 1);
-  s = tdvp_checkpoint_read_header(path, &n, &d, m.data());
-  if (s != TDVP_OK) return s;
-  std::vector<std::vector<double>> host(n);
-  std::vector<double*> ptr(n);
-  for (int i = 0; i < n; ++i) {
-    host[i].resize(2 * (size_t)m[i] * d * m[i + 1]);
-    ptr[i] = host[i].data();
-  }
-  s = tdvp_checkpoint_read(path, ptr.data());
-  if (s != TDVP_OK) return s;
+  std::vector<double*> ptr(f.hdr.n);
+  for (int i = 0; i < f.hdr.n; ++i) ptr[i] = f.sites[i].data();
   tdvp_mps_desc desc;
-  desc.n_sites = n;
-  desc.d = d;
-  desc.bond_dims = m.data();
+  desc.n_sites = f.hdr.n;
+  desc.d = f.hdr.d;
+  desc.bond_dims = f.hdr.m.data();
   desc.sites = ptr.data();
   return tdvp_create(&desc, mpo, opt, stream, out);
 }

@@ -137,13 +137,29 @@ def _stream(stream):
     return C.c_void_p(stream or 0)
 
 
+def _check_site_args(L, W, R, x, y):
+    """Shapes, dtype and placement of the operands of one H_eff contraction; returns
+    (ml, mr, wl, wr, d).  L [ml, wl, ml], R [mr, wr, mr], x and y [ml, d, mr]: contiguous CUDA
+    complex128 tensors; W host [wl, d, d, wr]."""
+    ml, wl, ml2 = L.shape
+    mr, wr, mr2 = R.shape
+    d = W.shape[1]
+    if ml2 != ml or mr2 != mr or W.shape != (wl, d, d, wr):
+        raise ValueError(f"H_eff operands: L {tuple(L.shape)}, W {W.shape}, R {tuple(R.shape)} do not fit")
+    for name, t in (("x", x), ("y", y)):
+        if tuple(t.shape) != (ml, d, mr):
+            raise ValueError(f"H_eff operands: {name} has shape {tuple(t.shape)}, expected {(ml, d, mr)}")
+    for name, t in (("L", L), ("R", R), ("x", x), ("y", y)):
+        if not (t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.complex128"):
+            raise ValueError(f"H_eff operands: {name} must be a contiguous CUDA complex128 tensor")
+    return ml, mr, wl, wr, d
+
+
 def heff_contract(L, W, R, x, y, precision=PREC_FP64, stream=None, env_tag=None):
     """y = H_eff x on caller tensors: L, R, x, y torch CUDA complex128; W numpy [wl, d, d, wr].
     env_tag (int >= 0): reuse the tensor-core operand forms of L and R across calls with
     the same tag (the caller guarantees L, R, W unchanged)."""
-    ml, wl, _ = L.shape
-    mr, wr, _ = R.shape
-    d = W.shape[1]
+    ml, mr, wl, wr, d = _check_site_args(L, W, R, x, y)
     Wc, wp = _host(W)
     dims = C.byref(SiteDims(ml, mr, wl, wr, d))
     if env_tag is None:
@@ -186,9 +202,7 @@ _lib.tdvp_heff_contract_noalloc.restype = C.c_int
 
 def heff_contract_noalloc(L, W, R, x, y, stream=None):
     """y = H_eff x (FP64) with no device allocation (scratch in a fixed device array)."""
-    ml, wl, _ = L.shape
-    mr, wr, _ = R.shape
-    d = W.shape[1]
+    ml, mr, wl, wr, d = _check_site_args(L, W, R, x, y)
     Wc, wp = _host(W)
     buf = C.create_string_buffer(512)
     s = _lib.tdvp_heff_contract_noalloc(C.byref(SiteDims(ml, mr, wl, wr, d)), _ptr(L), wp, _ptr(R), _ptr(x),
@@ -199,9 +213,10 @@ def heff_contract_noalloc(L, W, R, x, y, stream=None):
 
 _lib.tdvp_checkpoint_write.argtypes = [C.c_char_p, C.c_void_p]
 _lib.tdvp_checkpoint_write.restype = C.c_int
-_lib.tdvp_checkpoint_read_header.argtypes = [C.c_char_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_void_p]
+_lib.tdvp_checkpoint_read_header.argtypes = [C.c_char_p, C.POINTER(C.c_int), C.POINTER(C.c_int), C.c_void_p,
+                                              C.c_int]
 _lib.tdvp_checkpoint_read_header.restype = C.c_int
-_lib.tdvp_checkpoint_read.argtypes = [C.c_char_p, C.POINTER(C.c_void_p)]
+_lib.tdvp_checkpoint_read.argtypes = [C.c_char_p, C.c_int, C.c_int, C.c_void_p, C.POINTER(C.c_void_p)]
 _lib.tdvp_checkpoint_read.restype = C.c_int
 _lib.tdvp_checkpoint_last_error.argtypes = []
 _lib.tdvp_checkpoint_last_error.restype = C.c_char_p
@@ -226,9 +241,10 @@ def write_checkpoint(path, mps):
 
 def checkpoint_header(path):
     n, d = C.c_int(0), C.c_int(0)
-    _ckpt_chk(_lib.tdvp_checkpoint_read_header(os.fsencode(path), C.byref(n), C.byref(d), None))
+    _ckpt_chk(_lib.tdvp_checkpoint_read_header(os.fsencode(path), C.byref(n), C.byref(d), None, 0))
     dims = (C.c_int * (n.value + 1))()
-    _ckpt_chk(_lib.tdvp_checkpoint_read_header(os.fsencode(path), C.byref(n), C.byref(d), C.cast(dims, C.c_void_p)))
+    _ckpt_chk(_lib.tdvp_checkpoint_read_header(os.fsencode(path), C.byref(n), C.byref(d), C.cast(dims, C.c_void_p),
+                                               n.value + 1))
     return n.value, d.value, list(dims)
 
 
@@ -237,7 +253,8 @@ def read_checkpoint(path):
     n, d, m = checkpoint_header(path)
     arrs = [np.empty((m[i], d, m[i + 1]), dtype=np.complex128) for i in range(n)]
     ptrs = (C.c_void_p * n)(*[a.ctypes.data for a in arrs])
-    _ckpt_chk(_lib.tdvp_checkpoint_read(os.fsencode(path), ptrs))
+    dims = (C.c_int * (n + 1))(*m)
+    _ckpt_chk(_lib.tdvp_checkpoint_read(os.fsencode(path), n, d, C.cast(dims, C.c_void_p), ptrs))
     return arrs
 
 

@@ -74,3 +74,25 @@ def test_binding_constants_match_the_header():
     assert g.KRYLOV_ZIPUP == enum["TDVP_KRYLOV_ZIPUP"]
     codes = sorted(v for k, v in enum.items() if k == "TDVP_OK" or k.startswith("TDVP_ERR_"))
     assert codes == sorted(g.STATUS)
+
+
+def test_contract_wrappers_check_operands_before_the_call():
+    """The H_eff wrappers refuse operands that do not fit (shapes, dtype, placement) before any
+    pointer reaches the library (a wrong W or x shape would make the C loops read past them)."""
+    import numpy as np
+    import torch
+    from paper_2005_06104_gb300 import gse_tdvp as g
+    from paper_2005_06104_gb300 import workloads as wl
+    W = wl.heisenberg_mpo(wl.zigzag_ladder(4, 1.0, 1.0))[3]
+    wl_, d, _, wr = W.shape
+    L = torch.zeros((5, wl_, 5), dtype=torch.complex128)
+    R = torch.zeros((6, wr, 6), dtype=torch.complex128)
+    x = torch.zeros((5, d, 6), dtype=torch.complex128)
+    y = torch.zeros_like(x)
+    for fn in (g.heff_contract, g.heff_contract_noalloc):
+        with pytest.raises(ValueError, match="CUDA"):
+            fn(L, W, R, x, y)                          # host tensors
+        with pytest.raises(ValueError, match="do not fit"):
+            fn(L, np.zeros((wl_ + 1, d, d, wr), complex), R, x, y)
+        with pytest.raises(ValueError, match="expected"):
+            fn(L, W, R, torch.zeros((5, d, 7), dtype=torch.complex128), y)

@@ -61,3 +61,69 @@ def test_inconsistent_dimensions_are_refused(g, tmp_path):
     assert e.value.status == 2
     with pytest.raises(g.TDVPError):
         g.read_checkpoint(tmp_path / "missing.gse")
+
+
+def _rewrite_header(raw, n=None, dims=None):
+    """Returns raw with its N field and/or bond dimensions replaced (hash left stale)."""
+    import struct
+    raw = bytearray(raw)
+    if n is not None:
+        raw[12:16] = struct.pack("<i", n)
+    if dims is not None:
+        for i, m in enumerate(dims):
+            raw[24 + 4 * i:28 + 4 * i] = struct.pack("<i", m)
+    return bytes(raw)
+
+
+def test_oversized_header_is_refused_before_allocating(g, tmp_path):
+    """A header that claims huge bond dimensions (about 2^40 doubles) in a small file: refused
+    by the size check, before any buffer of that size exists."""
+    psi = wl.random_mps(4, 3, 5)
+    p = tmp_path / "big.gse"
+    g.write_checkpoint(p, psi)
+    m = wl.mps_bond_dims(psi)
+    big = [1, 1 << 20, 1 << 20, 1 << 20, 1]
+    p.write_bytes(_rewrite_header(p.read_bytes(), dims=big))
+    assert g.checkpoint_header(p)[2] == big            # the header alone is well-formed
+    arrs = [np.empty((m[i], 2, m[i + 1]), complex) for i in range(4)]
+    import ctypes as C
+    ptrs = (C.c_void_p * 4)(*[a.ctypes.data for a in arrs])
+    dims = (C.c_int * 5)(*big)
+    st = g._lib.tdvp_checkpoint_read(str(p).encode(), 4, 2, C.cast(dims, C.c_void_p), ptrs)
+    assert st == 1 and b"size" in g._lib.tdvp_checkpoint_last_error()
+    with pytest.raises(g.TDVPError) as e:
+        g.GseTdvp.load(p, wl.heisenberg_mpo(wl.chain(4)))
+    assert e.value.status == 1
+
+
+def test_buffers_of_other_shapes_are_never_written(g, tmp_path):
+    """The caller states its buffers' shapes; a file whose dimensions changed since the header
+    was read (here: another state saved under the same name) is refused, buffers untouched."""
+    p = tmp_path / "state.gse"
+    g.write_checkpoint(p, wl.random_mps(5, 3, 1))
+    n, d, m = g.checkpoint_header(p)
+    arrs = [np.full((m[i], d, m[i + 1]), 7.0 + 0j) for i in range(n)]
+    g.write_checkpoint(p, wl.random_mps(5, 4, 2))      # replaced between header and read
+    import ctypes as C
+    ptrs = (C.c_void_p * n)(*[a.ctypes.data for a in arrs])
+    dims = (C.c_int * (n + 1))(*m)
+    st = g._lib.tdvp_checkpoint_read(str(p).encode(), n, d, C.cast(dims, C.c_void_p), ptrs)
+    assert st == 2
+    assert all(np.all(a == 7.0) for a in arrs)
+    # too small a bond_dims buffer for the header
+    small = (C.c_int * 2)()
+    nn, dd = C.c_int(0), C.c_int(0)
+    st = g._lib.tdvp_checkpoint_read_header(str(p).encode(), C.byref(nn), C.byref(dd), C.cast(small, C.c_void_p), 2)
+    assert st == 2 and list(small) == [0, 0]
+
+
+@pytest.mark.parametrize("cut", [1, 20, 200])
+def test_load_refuses_truncated_files(g, tmp_path, cut):
+    """tdvp_load reads and verifies the whole file before it creates anything on the device."""
+    p = tmp_path / "state.gse"
+    g.write_checkpoint(p, wl.random_mps(6, 4, 3))
+    raw = p.read_bytes()
+    p.write_bytes(raw[:-cut])
+    with pytest.raises(g.TDVPError) as e:
+        g.GseTdvp.load(p, wl.heisenberg_mpo(wl.chain(6)))
+    assert e.value.status == 1
