@@ -60,6 +60,10 @@ def parse():
     ap.add_argument("--heff-chi", type=int, default=1024, help="bond dimension of the H_eff roofline probe")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-tdvp2", action="store_true", help="skip the TDVP2 step of the comparison")
+    ap.add_argument("--config2", action="store_true",
+                    help="imaginary time on the rung-decoupled 2 x 20 ladder, 50 steps, FP64 / TF32X3 / BF16X10")
+    ap.add_argument("--config3", action="store_true",
+                    help="real time on the 2 x 50 ladder, chi <= 512, 40 BF16X10 steps with per-step FP64 checks")
     ap.add_argument("--fig3", action="store_true",
                     help="imaginary time on the rung-decoupled ladder (Fig. 3): GSE-TDVP1 at d tau 0.1 and 0.4, TDVP2")
     ap.add_argument("--fig3-leg", type=int, default=20, help="leg length of the --fig3 ladder")
@@ -70,6 +74,9 @@ def parse():
                     help="only time the tensor-core H_eff apply at --heff-chi (the profiling target)")
     ap.add_argument("--precision", default="bf16x10", choices=sorted(PRECISIONS),
                     help="arithmetic of the dense contractions (Lanczos, SVDs, observables stay FP64)")
+    ap.add_argument("--krylov-precision", default="bf16x6", choices=sorted(PRECISIONS) + ["same"],
+                    help="arithmetic of the Krylov vectors' contractions in the precision form ('same': "
+                         "--precision); FP64 handles always run FP64")
     ap.add_argument("--batch-chains", type=int, default=0,
                     help="time the batch workload instead: this many random-field chains (lengths 20-60, "
                          "chi_max 32-128, dt 0.05, k 2) stepped together, against the same chains one at a time")
@@ -108,6 +115,7 @@ def workload(args):
            "mpo_bond_dim_max": int(max(wl.mpo_bond_dims(W))), "chi_max": args.chi_max,
            "krylov_order_k": args.k, "dt": args.dt, "tau": args.dt, "eps_k": 1e-8, "eps_m": 1e-8, "eps": 0.0,
            "time": "real", "precision_form": PRECISION_TEXT[args.precision],
+           "krylov_precision": args.precision if args.krylov_precision == "same" else args.krylov_precision,
            "start_state": "Neel with the spin at (8,0) flipped", "prep_steps": args.prep_steps,
            "compare_chi": args.compare_chi, "krylov_method": "density_matrix" if args.krylov == "dm" else "zipup",
            "l2": "working set of a step (environments, Krylov vectors, density environments) > L2; no flush"}
@@ -418,6 +426,8 @@ def run_gpu(args):
         h = g.GseTdvp(*a, **kw)
         if args.krylov == "zipup":
             h.krylov_method(g.KRYLOV_ZIPUP)
+        if args.krylov_precision != "same" and kw.get("precision", g.PREC_FP64) != g.PREC_FP64:
+            h.krylov_precision(prec_code(g, args.krylov_precision))
         return h
     opts = dict(tau=args.dt, eps_k=1e-8, eps_m=1e-8, eps=0.0, chi_max=args.chi_max,
                 precision=prec_code(g, args.precision))
@@ -660,6 +670,84 @@ def run_fig3(args):
     print(json.dumps(out), flush=True)
 
 
+def run_config2(args):
+    """Rung-decoupled 2 x 20 zigzag ladder from a random product state (seed 1), imaginary time
+    d tau = 0.1, k = 3, i tau = 1/lambda, eps_K = 1e-12, eps_M = 1e-8, eps = 1e-10, chi <= 128,
+    50 steps (Sec. II.A setting at leg 20), in FP64, TF32X3 and BF16X10: energies per step
+    against twice the exact ground energy of one 20-site leg (sparse Lanczos in S^z = 0)."""
+    import torch
+    from paper_2005_06104_gb300 import gse_tdvp as g
+    from paper_2005_06104_gb300 import workloads as wl
+    p = wl.workload("ladder2x20_rd")
+    lat, W, psi = p["lattice"], p["mpo"], p["psi"]
+    e_ref = 2.0 * _chain_ground_energy(20)
+    stream = torch.cuda.current_stream().cuda_stream
+    kw = dict(tau=p["tau"], eps_k=p["eps_k"], eps_m=p["eps_m"], eps=p["eps"], chi_max=p["chi_max"], stream=stream)
+    runs = {}
+    for name in ("fp64", "tf32x3", "bf16x10"):
+        st = g.GseTdvp(psi, W, precision=prec_code(g, name), **kw)
+        es, dims = [], []
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        for _ in range(p["steps"]):
+            st.step(p["dt"], g.IMAG, p["k"])
+            es.append(st.energy())
+            dims.append(max(st.bond_dims()))
+        el = time.perf_counter() - t
+        st.close()
+        runs[name] = {"energies": es, "bond_dim_max": dims, "s_per_step": el / p["steps"]}
+    e64 = runs["fp64"]["energies"]
+    out = {"config": "ladder2x20_rd", "steps": p["steps"], "E_ref_2E0_L20": e_ref,
+           "final_rel_err_vs_2E0": {k: (v["energies"][-1] - e_ref) / abs(e_ref) for k, v in runs.items()},
+           "monotone_non_increasing": {k: all(b <= a + 1e-12 for a, b in zip(v["energies"], v["energies"][1:]))
+                                       for k, v in runs.items()},
+           "max_rel_diff_vs_fp64": {k: max(abs(a - b) / abs(b) for a, b in zip(v["energies"], e64))
+                                    for k, v in runs.items() if k != "fp64"},
+           "bond_dim_max_final": {k: v["bond_dim_max"][-1] for k, v in runs.items()},
+           "s_per_step": {k: v["s_per_step"] for k, v in runs.items()},
+           "energies_fp64": e64}
+    print(json.dumps(out), flush=True)
+
+
+def run_config3(args):
+    """Rung-coupled 2 x 50 zigzag ladder, Neel with the spin at (25, 0) flipped, real time dt = 0.1,
+    k = 3, chi <= 512, 40 steps in BF16X10.  At steps 1, 10, 20, 30, 40 the state is copied
+    and one FP64 step and one precision-form step run from it: per-step relative energy error
+    and norm drift of the precision form against FP64."""
+    import torch
+    from paper_2005_06104_gb300 import gse_tdvp as g
+    from paper_2005_06104_gb300 import workloads as wl
+    p = wl.workload("ladder2x50")
+    W, psi = p["mpo"], p["psi"]
+    stream = torch.cuda.current_stream().cuda_stream
+    kw = dict(tau=p["tau"], eps_k=p["eps_k"], eps_m=p["eps_m"], eps=p["eps"], chi_max=p["chi_max"], stream=stream)
+    st = g.GseTdvp(psi, W, precision=g.PREC_BF16X10, **kw)
+    e0 = st.energy()
+    checks, es, dims, ts = [], [], [], []
+    for step in range(1, p["steps"] + 1):
+        torch.cuda.synchronize()
+        t = time.perf_counter()
+        st.step(p["dt"], g.REAL, p["k"])
+        ts.append(time.perf_counter() - t)
+        es.append(st.energy())
+        dims.append(max(st.bond_dims()))
+        if step in (1, 10, 20, 30, 40):
+            state = st.get_mps()
+            a = g.GseTdvp(state, W, precision=g.PREC_FP64, **kw)
+            b = g.GseTdvp(state, W, precision=g.PREC_BF16X10, **kw)
+            a.step(p["dt"], g.REAL, p["k"])
+            b.step(p["dt"], g.REAL, p["k"])
+            ea, eb = a.energy(), b.energy()
+            checks.append({"after_step": step, "bond_dim_max": dims[-1], "rel_energy_err": abs(eb - ea) / abs(ea),
+                           "norm_drift": abs(b.norm() - 1.0), "norm_drift_fp64": abs(a.norm() - 1.0)})
+            a.close()
+            b.close()
+    st.close()
+    print(json.dumps({"config": "ladder2x50", "steps": p["steps"], "chi_max": p["chi_max"], "E0": e0,
+                      "energy_drift_abs": abs(es[-1] - e0), "energy_drift_rel": abs(es[-1] - e0) / abs(e0),
+                      "per_step_checks": checks, "bond_dim_max": dims, "s_per_step": ts}), flush=True)
+
+
 def run_batch(args):
     """Independent random-field chains stepped as one batch (one stream per chain, host worker
     pool) against the same chains stepped one after another on one stream each, same steps."""
@@ -709,7 +797,11 @@ def main():
     if args.batch_chains > 0:
         run_batch(args)
         return
-    if args.fig3:
+    if args.config2:
+        run_config2(args)
+    elif args.config3:
+        run_config3(args)
+    elif args.fig3:
         run_fig3(args)
     elif args.svd_probe:
         run_svd_probe(args)

@@ -155,6 +155,16 @@ TDVP_API tdvp_status tdvp_krylov_memory(tdvp_handle* h, double max_bytes, int* l
 typedef enum { TDVP_KRYLOV_DENSITY_MATRIX = 0, TDVP_KRYLOV_ZIPUP = 1 } tdvp_krylov_method;
 TDVP_API tdvp_status tdvp_set_krylov_method(tdvp_handle* h, int method);
 
+/* Arithmetic of the Krylov vectors' contractions (Sec. I.B: the Krylov vectors of
+ * Eq. 10 need less accuracy than |psi> itself, because they only enrich the basis
+ * and the extension keeps |psi> exactly).  precision = -1 (the default) uses the
+ * handle's tdvp_options.precision; a tdvp_precision value sets the form of the
+ * density environments, the density matrices, the zip-up products and the
+ * Krylov vectors' centre moves in the extension.  |psi>'s own contractions, the
+ * sweep and every factorisation are not affected.  Other values give
+ * TDVP_ERR_INVALID_ARG. */
+TDVP_API tdvp_status tdvp_set_krylov_precision(tdvp_handle* h, int precision);
+
 /* One Krylov vector in place (Eq. 10 with l = 1, Sec. I.B): the state becomes
  * (1 - i tau H)|psi>, applied by the method tdvp_set_krylov_method selects (the
  * density-matrix approach by default) with cutoff eps_k and cap chi_max,

@@ -156,6 +156,14 @@ tdvp_status tdvp_set_krylov_method(tdvp_handle* h, int method) {
   });
 }
 
+tdvp_status tdvp_set_krylov_precision(tdvp_handle* h, int precision) {
+  return guarded(h, [&] {
+    tdvp_require(precision == -1 || (precision >= TDVP_PREC_FP64 && precision <= TDVP_PREC_BF16X6),
+                 TDVP_ERR_INVALID_ARG, "unknown precision");
+    h->eng.krylov_prec = precision;
+  });
+}
+
 tdvp_status tdvp_sweep2(tdvp_handle* h, double dt, tdvp_time kind) {
   return guarded(h, [&] {
     tdvp_require(std::isfinite(dt), TDVP_ERR_INVALID_ARG, "dt not finite");

@@ -810,7 +810,7 @@ void Engine::krylov_apply(const KrylovOp& kop, const MpsDev& src, MpsDev& out) {
   const cplx one = mkc(1.0, 0.0), zero = mkc(0.0, 0.0);
   // the Krylov vectors only enrich the basis (the state itself is kept exactly by the
   // extension), so the precision form may build them on the tensor cores
-  const int kp = opt.precision;
+  const int kp = kprec();
   // Right density environments F[j] (sites > j), (w_{j+1} m_{j+1})^2 entries each, are built
   // right to left and read left to right, once each.  When all of them exceed the memory
   // budget only every K-th (K = ceil(sqrt(N))) stays resident; the others are rebuilt from
@@ -961,7 +961,7 @@ void Engine::krylov_apply(const KrylovOp& kop, const MpsDev& src, MpsDev& out) {
 // left-to-right compression with eps_k and chi_max follows; the result is normalised,
 // left-canonical with its centre at N-1.
 void Engine::krylov_zipup(const KrylovOp& kop, const MpsDev& src, MpsDev& out) {
-  const int kp = opt.precision;
+  const int kp = kprec();
   const double eps_k = opt.eps_k;
   const int cap = opt.chi_max;
   MpsDev t;
@@ -1171,10 +1171,10 @@ void Engine::expand_basis(int k, const double* weights) {
       // the Krylov vectors only feed rho~ of the next bond (the basis they enrich, never
       // |psi> itself), so their centre moves run in the precision form
       DArr Gl(&pool, (size_t)mlp * mnew);
-      zgemm_prec(st, scr, opt.precision, OP_N, OP_C, mlp, mnew, cols, ph.A[i].data(), cols, Bp.data(), cols,
+      zgemm_prec(st, scr, kprec(), OP_N, OP_C, mlp, mnew, cols, ph.A[i].data(), cols, Bp.data(), cols,
                  Gl.data(), mnew);
       DArr pp(&pool, (size_t)mlp0 * d * mnew);
-      zgemm_prec(st, scr, opt.precision, OP_N, OP_N, mlp0 * d, mnew, mlp, ph.A[i - 1].data(), mlp, Gl.data(), mnew,
+      zgemm_prec(st, scr, kprec(), OP_N, OP_N, mlp0 * d, mnew, mlp, ph.A[i - 1].data(), mlp, Gl.data(), mnew,
                  pp.data(), mnew);
       ph.A[i - 1] = std::move(pp);
       ph.A[i].release();

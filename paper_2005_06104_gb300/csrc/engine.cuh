@@ -53,6 +53,8 @@ struct Engine {
   double krylov_mem_budget = 0.0;
   int krylov_env_segment = 1;  // last Krylov step: 1 = all resident, else the checkpoint spacing
   int krylov_method = 0;       // 0: density-matrix application, 1: zip-up
+  int krylov_prec = -1;        // arithmetic of the Krylov vectors' contractions (-1: opt.precision)
+  int kprec() const { return krylov_prec < 0 ? opt.precision : krylov_prec; }
   // optional timing of the H_eff applies (CUDA events on the engine stream)
   bool profile = false;
   std::vector<cudaEvent_t> ev_pool;

@@ -59,6 +59,7 @@ _sig = {
     "tdvp_sweep2": [_h, C.c_double, C.c_int],
     "tdvp_krylov_memory": [_h, C.c_double, C.POINTER(C.c_int)],
     "tdvp_set_krylov_method": [_h, C.c_int],
+    "tdvp_set_krylov_precision": [_h, C.c_int],
     "tdvp_heff_apply": [_h, C.c_int, C.c_void_p, C.c_void_p, C.c_int],
     "tdvp_keff_apply": [_h, C.c_int, C.c_void_p, C.c_void_p, C.c_int],
     "tdvp_evolve_site": [_h, C.c_int, C.c_void_p, C.c_void_p, C.c_double, C.c_int, C.c_int,
@@ -382,6 +383,10 @@ class GseTdvp:
         seg = C.c_int(0)
         self._chk(_lib.tdvp_krylov_memory(self.h, float(max_bytes), C.byref(seg)))
         return seg.value
+
+    def krylov_precision(self, precision):
+        """Arithmetic of the Krylov vectors' contractions (-1: the handle's precision)."""
+        self._chk(_lib.tdvp_set_krylov_precision(self.h, int(precision)))
 
     def krylov_method(self, method):
         """KRYLOV_DENSITY_MATRIX (default) or KRYLOV_ZIPUP for the Krylov vectors of Eq. 10."""

@@ -197,6 +197,28 @@ def test_precision_form_energy_and_norm(g, prec):
     b.close()
 
 
+def test_krylov_precision_bf16x6_keeps_the_energy_bar(g):
+    """Krylov vectors in BF16X6 (3 slices) under a BF16X10 sweep: the state itself still holds
+    relative energy error <= 1e-7 and norm drift <= 1e-10 per step against FP64 (the Krylov
+    vectors only enrich the basis, Sec. I.B)."""
+    lat = wl.zigzag_ladder(8, 1.0, 1.0)
+    W = wl.heisenberg_mpo(lat)
+    psi = wl.neel_state(lat, flip=(4, 0))
+    kw = dict(tau=0.1, eps_k=1e-8, eps_m=1e-8, chi_max=48)
+    a = g.GseTdvp(psi, W, precision=g.PREC_FP64, **kw)
+    b = g.GseTdvp(psi, W, precision=g.PREC_BF16X10, **kw)
+    b.krylov_precision(g.PREC_BF16X6)
+    for _ in range(4):
+        a.step(0.1, g.REAL, 3)
+        b.step(0.1, g.REAL, 3)
+        assert abs(b.norm() - 1) < 1e-10
+        assert abs(b.energy() - a.energy()) <= 1e-7 * abs(a.energy())
+    with pytest.raises(g.TDVPError):
+        b.krylov_precision(9)
+    a.close()
+    b.close()
+
+
 def test_errors_are_status_codes(g):
     lat = wl.chain(4)
     W = wl.heisenberg_mpo(lat)
