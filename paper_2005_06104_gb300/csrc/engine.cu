@@ -933,7 +933,7 @@ void Engine::krylov_apply(const KrylovOp& kop, const MpsDev& src, MpsDev& out) {
     SvdOut sv;
     {
       PhaseScope ps(tracer, PH_KRYLOV_EIG);
-      eig_psd_jacobi(st, &pool, rho.data(), n, rule, sv);
+      eig_psd_jacobi(st, &pool, rho.data(), n, rule, sv, kp != TDVP_PREC_FP64);
     }
     const int keep = std::max(1, sv.rank);
     tdvp_require(sv.rank >= 1, TDVP_ERR_NONFINITE, "krylov: zero density matrix");
@@ -1006,7 +1006,7 @@ void Engine::krylov_zipup(const KrylovOp& kop, const MpsDev& src, MpsDev& out) {
     SvdOut sv;
     {
       PhaseScope ps(tracer, PH_KRYLOV_EIG);
-      eig_psd_jacobi(st, &pool, rho.data(), n, rule, sv);
+      eig_psd_jacobi(st, &pool, rho.data(), n, rule, sv, kp != TDVP_PREC_FP64);
     }
     const int keep = sv.rank;
     tdvp_require(keep >= 1, TDVP_ERR_NONFINITE, "zip-up: zero site");

@@ -856,6 +856,52 @@ __device__ __forceinline__ void rr_pair(int round, int k, int qpad, int& P, int&
 // of the method (rank 1e-10 s_max, eigenvalue floor 1e-14 lambda_max), and rotating
 // them against each other chases rounding noise for extra sweeps while moving the
 // kept columns by at most 1e-15.
+// Complex arithmetic and limits for the precision a Jacobi runs in: FP64 (double2) in general,
+// FP32 (float2) for the eigendecompositions that the precision form allows in FP32.
+__host__ __device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__host__ __device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__host__ __device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__host__ __device__ __forceinline__ float2 cconj(float2 a) { return make_float2(a.x, -a.y); }
+__host__ __device__ __forceinline__ float2 cscale(float2 a, float s) { return make_float2(a.x * s, a.y * s); }
+__host__ __device__ __forceinline__ float cabs2(float2 a) { return a.x * a.x + a.y * a.y; }
+__host__ __device__ __forceinline__ void cfma_conj(float2& a, float2 b, float2 c) {
+  a.x = fmaf(b.x, c.x, fmaf(b.y, c.y, a.x));
+  a.y = fmaf(b.x, c.y, fmaf(-b.y, c.x, a.y));
+}
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ float2 warp_sum(float2 v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) {
+    v.x += __shfl_down_sync(0xffffffffu, v.x, o);
+    v.y += __shfl_down_sync(0xffffffffu, v.y, o);
+  }
+  return v;
+}
+template <class T>
+struct Jac;
+template <>
+struct Jac<double> {
+  typedef double2 C;
+  static __device__ __forceinline__ C make(double r, double i) { return make_double2(r, i); }
+  static constexpr double eps = 2.2e-16, tol_min = 1e-15;
+  // A sweep whose rotations all have |sin theta| <= 1e-8 ends the iteration (see below).
+  static constexpr double small_angle2 = 1e-16;
+};
+template <>
+struct Jac<float> {
+  typedef float2 C;
+  static __device__ __forceinline__ C make(float r, float i) { return make_float2(r, i); }
+  static constexpr float eps = 1.2e-7f, tol_min = 1e-7f;
+  // FP32 resolves couplings to about 1e-7: a sweep with |sin theta| <= 1e-6 ends it
+  static constexpr float small_angle2 = 1e-12f;
+};
+
 constexpr double kJacobiFloor = 1e-30;
 // A sweep whose rotations all have |sin theta| <= 1e-8 ends the iteration.  Each rotation
 // annihilates its pair's coupling and only mixes the couplings of its two columns with the
@@ -863,26 +909,27 @@ constexpr double kJacobiFloor = 1e-30;
 // (about 1e-16 relative), which a further sweep would only confirm.  Near-degenerate
 // columns with a tiny coupling give large angles and keep the iteration going.
 constexpr double kJacobiSmallAngle2 = 1e-16;
-__device__ __forceinline__ bool jacobi_params(double a, double b, cplx c, double tol, double floor2,
-                                              double& cs, cplx& sne) {
-  const double big = fmax(a, b), small = fmin(a, b);
-  if (big <= floor2 || small <= kJacobiFloor * big) return false;
-  const double ac2 = cabs2(c);
+template <class T, class C>
+__device__ __forceinline__ bool jacobi_params(T a, T b, C c, T tol, T floor2, T& cs, C& sne) {
+  const T big = fmax(a, b), small = fmin(a, b);
+  if (big <= floor2 || small <= (T)kJacobiFloor * big) return false;
+  const T ac2 = cabs2(c);
   // |c| > tol sqrt(a b), squared (no square root on the common no-rotation path)
   if (!(ac2 > tol * tol * a * b)) return false;
-  const double inv_ac = rsqrt(ac2);
-  const double zeta = 0.5 * (b - a) * inv_ac;
-  const double t = (zeta >= 0.0 ? 1.0 : -1.0) / (fabs(zeta) + sqrt(1.0 + zeta * zeta));
-  cs = rsqrt(1.0 + t * t);
-  const double sn_ac = cs * t * inv_ac;
-  sne = mkc(sn_ac * c.x, sn_ac * c.y);  // sn e^{i phi}
+  const T inv_ac = rsqrt(ac2);
+  const T zeta = (T)0.5 * (b - a) * inv_ac;
+  const T t = (zeta >= (T)0 ? (T)1 : (T)-1) / (fabs(zeta) + sqrt((T)1 + zeta * zeta));
+  cs = rsqrt((T)1 + t * t);
+  const T sn_ac = cs * t * inv_ac;
+  sne = Jac<T>::make(sn_ac * c.x, sn_ac * c.y);  // sn e^{i phi}
   return true;
 }
 
-__device__ __forceinline__ void rotate_pair(cplx& xp, cplx& xq, double cs, cplx sne) {
+template <class T, class C>
+__device__ __forceinline__ void rotate_pair(C& xp, C& xq, T cs, C sne) {
   // xp' = cs xp - conj(sne) xq ; xq' = sne xp + cs xq
-  const cplx np = csub(cscale(xp, cs), cmul(cconj(sne), xq));
-  const cplx nq = cadd(cmul(sne, xp), cscale(xq, cs));
+  const C np = csub(cscale(xp, cs), cmul(cconj(sne), xq));
+  const C nq = cadd(cmul(sne, xp), cscale(xq, cs));
   xp = np;
   xq = nq;
 }
@@ -904,19 +951,21 @@ __global__ void k_svd_prepare(const cplx* __restrict__ M, int rows, int cols, in
 
 // One pair (P, Q) rotated by a whole block; returns true when a rotation with
 // |sin theta| above 1e-8 was applied (kJacobiSmallAngle2).
-__device__ bool jacobi_pair_block(cplx* __restrict__ X, cplx* __restrict__ V, int p, int q, int P, int Q,
-                                  double tol, double floor2, int want_v) {
-  __shared__ double ra[8], rb[8];
-  __shared__ cplx rc[8];
-  __shared__ double s_cs;
-  __shared__ cplx s_sne;
+template <class T>
+__device__ bool jacobi_pair_block(typename Jac<T>::C* __restrict__ X, typename Jac<T>::C* __restrict__ V, int p, int q,
+                                  int P, int Q, T tol, T floor2, int want_v) {
+  typedef typename Jac<T>::C C;
+  __shared__ T ra[8], rb[8];
+  __shared__ C rc[8];
+  __shared__ T s_cs;
+  __shared__ C s_sne;
   __shared__ int s_do;
-  cplx* xp = X + (long long)P * p;
-  cplx* xq = X + (long long)Q * p;
-  double a = 0.0, b = 0.0;
-  cplx c = mkc(0.0, 0.0);
+  C* xp = X + (long long)P * p;
+  C* xq = X + (long long)Q * p;
+  T a = 0, b = 0;
+  C c = Jac<T>::make(0, 0);
   for (int r = threadIdx.x; r < p; r += blockDim.x) {
-    const cplx u = xp[r], v = xq[r];
+    const C u = xp[r], v = xq[r];
     a += cabs2(u);
     b += cabs2(v);
     cfma_conj(c, u, v);
@@ -934,38 +983,38 @@ __device__ bool jacobi_pair_block(cplx* __restrict__ X, cplx* __restrict__ V, in
   }
   __syncthreads();
   if (threadIdx.x == 0) {
-    double A = 0, B = 0;
-    cplx Cc = mkc(0, 0);
+    T A = 0, B = 0;
+    C Cc = Jac<T>::make(0, 0);
     const int active = min((int)(blockDim.x >> 5), (p + 31) >> 5);  // the others hold exact zeros
     for (int u = 0; u < active; ++u) {
       A += ra[u];
       B += rb[u];
       Cc = cadd(Cc, rc[u]);
     }
-    double cs;
-    cplx sne;
+    T cs;
+    C sne;
     s_do = jacobi_params(A, B, Cc, tol, floor2, cs, sne) ? 1 : 0;
     s_cs = cs;
     s_sne = sne;
   }
   __syncthreads();
   const int doit = s_do;
-  const double cs = s_cs;
-  const cplx sne = s_sne;
+  const T cs = s_cs;
+  const C sne = s_sne;
   __syncthreads();  // the shared slots are reused by the next pair
   if (!doit) return false;
   for (int r = threadIdx.x; r < p; r += blockDim.x) {
-    cplx u = xp[r], v = xq[r];
+    C u = xp[r], v = xq[r];
     rotate_pair(u, v, cs, sne);
     xp[r] = u;
     xq[r] = v;
   }
-  const bool significant = cabs2(sne) > kJacobiSmallAngle2;
+  const bool significant = cabs2(sne) > Jac<T>::small_angle2;
   if (want_v) {
-    cplx* vp = V + (long long)P * q;
-    cplx* vq = V + (long long)Q * q;
+    C* vp = V + (long long)P * q;
+    C* vq = V + (long long)Q * q;
     for (int r = threadIdx.x; r < q; r += blockDim.x) {
-      cplx u = vp[r], v = vq[r];
+      C u = vp[r], v = vq[r];
       rotate_pair(u, v, cs, sne);
       vp[r] = u;
       vq[r] = v;
@@ -1394,19 +1443,23 @@ __global__ void k_gather_batched(const cplx* __restrict__ M, int cols, const Blk
   for (int e = threadIdx.x; e < d.q * d.q; e += blockDim.x) Vb[e] = mkc((e % d.q) == (e / d.q) ? 1.0 : 0.0, 0.0);
 }
 
+template <class T>
 __global__ void __launch_bounds__(256)
-    k_jacobi_batched(cplx* __restrict__ X, cplx* __restrict__ V, const BlkDesc* __restrict__ desc, int max_sweeps,
-                     double* __restrict__ s_out, int* __restrict__ bad) {
-  extern __shared__ cplx sm[];
+    k_jacobi_batched(typename Jac<T>::C* __restrict__ X, typename Jac<T>::C* __restrict__ V,
+                     const BlkDesc* __restrict__ desc, int max_sweeps, double* __restrict__ s_out,
+                     int* __restrict__ bad) {
+  typedef typename Jac<T>::C C;
+  extern __shared__ __align__(16) unsigned char sm_raw[];
+  C* sm = reinterpret_cast<C*>(sm_raw);
   __shared__ int s_rot;
-  __shared__ double s_fro[8];
+  __shared__ T s_fro[8];
   const BlkDesc d = desc[blockIdx.x];
   const int p = d.p, q = d.q, qpad = q + (q & 1);
-  cplx* Xs = sm;
-  cplx* Vs = sm + (long long)p * q;
-  cplx* Xg = X + d.x_off;
-  cplx* Vg = V + d.v_off;
-  double f = 0.0;
+  C* Xs = sm;
+  C* Vs = sm + (long long)p * q;
+  C* Xg = X + d.x_off;
+  C* Vg = V + d.v_off;
+  T f = 0;
   for (int e = threadIdx.x; e < p * q; e += blockDim.x) {
     Xs[e] = Xg[e];
     f += cabs2(Xs[e]);
@@ -1416,10 +1469,10 @@ __global__ void __launch_bounds__(256)
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   if (lane == 0) s_fro[warp] = f;
   __syncthreads();
-  double fro2 = 0.0;
+  T fro2 = 0;
   for (int u = 0; u < nw; ++u) fro2 += s_fro[u];
-  const double floor2 = kJacobiFloor * fro2;
-  const double tol = fmax(1e-15, sqrt((double)p) * 2.2e-16);
+  const T floor2 = (T)kJacobiFloor * fro2;
+  const T tol = fmax(Jac<T>::tol_min, sqrt((T)p) * Jac<T>::eps);
   int sweep = 0;
   for (; sweep < max_sweeps && q > 1; ++sweep) {
     if (threadIdx.x == 0) s_rot = 0;
@@ -1429,12 +1482,12 @@ __global__ void __launch_bounds__(256)
         int P, Q;
         rr_pair(round, k, qpad, P, Q);
         if (Q >= q) continue;
-        cplx* xp = Xs + P * p;
-        cplx* xq = Xs + Q * p;
-        double a = 0.0, b = 0.0;
-        cplx c = mkc(0.0, 0.0);
+        C* xp = Xs + P * p;
+        C* xq = Xs + Q * p;
+        T a = 0, b = 0;
+        C c = Jac<T>::make(0, 0);
         for (int r = lane; r < p; r += 32) {
-          const cplx u = xp[r], v = xq[r];
+          const C u = xp[r], v = xq[r];
           a += cabs2(u);
           b += cabs2(v);
           cfma_conj(c, u, v);
@@ -1446,21 +1499,21 @@ __global__ void __launch_bounds__(256)
           c.x += __shfl_xor_sync(0xffffffffu, c.x, o);
           c.y += __shfl_xor_sync(0xffffffffu, c.y, o);
         }
-        double cs;
-        cplx sne;
+        T cs;
+        C sne;
         if (!jacobi_params(a, b, c, tol, floor2, cs, sne)) continue;
-        if (lane == 0 && cabs2(sne) > kJacobiSmallAngle2) s_rot = 1;
+        if (lane == 0 && cabs2(sne) > Jac<T>::small_angle2) s_rot = 1;
         for (int r = lane; r < p; r += 32) {
-          cplx u = xp[r], v = xq[r];
+          C u = xp[r], v = xq[r];
           rotate_pair(u, v, cs, sne);
           xp[r] = u;
           xq[r] = v;
         }
         if (d.need_v) {
-          cplx* vp = Vs + P * q;
-          cplx* vq = Vs + Q * q;
+          C* vp = Vs + P * q;
+          C* vq = Vs + Q * q;
           for (int r = lane; r < q; r += 32) {
-            cplx u = vp[r], v = vq[r];
+            C u = vp[r], v = vq[r];
             rotate_pair(u, v, cs, sne);
             vp[r] = u;
             vq[r] = v;
@@ -1482,10 +1535,10 @@ __global__ void __launch_bounds__(256)
   for (int e = threadIdx.x; e < q * q; e += blockDim.x) Vg[e] = Vs[e];
   __syncthreads();
   for (int j = warp; j < q; j += nw) {
-    double t = 0.0;
+    T t = 0;
     for (int r = lane; r < p; r += 32) t += cabs2(Xs[j * p + r]);
     t = warp_sum(t);
-    if (lane == 0) s_out[d.s_off + j] = sqrt(t);
+    if (lane == 0) s_out[d.s_off + j] = sqrt((double)t);
   }
 }
 
@@ -1713,12 +1766,14 @@ __device__ __forceinline__ bool group_sync(GridBar* b, unsigned n, int* gerr, un
 // b holds CTAs [cta_off[b], cta_off[b+1]); its CTA lc takes the pairs lc, lc + n_b, ...
 // of every round.  flags per block: rot[3] | sweeps; bars: one barrier per block;
 // stat: bad, max sweeps, total sweeps (atomics); gerr: any barrier that ran out.
+template <class T>
 __global__ void __launch_bounds__(256)
-    k_jacobi_groups(cplx* __restrict__ X, cplx* __restrict__ V, const BlkDesc* __restrict__ desc,
-                    const int* __restrict__ cta_off, int nblk, int max_sweeps, double* __restrict__ fro2,
-                    int* __restrict__ flags, GridBar* __restrict__ bars, int* __restrict__ gerr,
-                    double* __restrict__ s_out, int* __restrict__ stat) {
-  __shared__ double red[8];
+    k_jacobi_groups(typename Jac<T>::C* __restrict__ X, typename Jac<T>::C* __restrict__ V,
+                    const BlkDesc* __restrict__ desc, const int* __restrict__ cta_off, int nblk, int max_sweeps,
+                    double* __restrict__ fro2, int* __restrict__ flags, GridBar* __restrict__ bars,
+                    int* __restrict__ gerr, double* __restrict__ s_out, int* __restrict__ stat) {
+  typedef typename Jac<T>::C C;
+  __shared__ T red[8];
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
   int lo = 0, hi = nblk - 1;  // the block whose group holds this CTA
   while (lo < hi) {
@@ -1732,8 +1787,8 @@ __global__ void __launch_bounds__(256)
   int* rot = flags + 4 * b;
   GridBar* bar = bars + b;
   if (lc == 0) {
-    const cplx* Xb = X + d.x_off;
-    double f = 0.0;
+    const C* Xb = X + d.x_off;
+    T f = 0;
     for (long long e = threadIdx.x; e < (long long)d.p * d.q; e += blockDim.x) f += cabs2(Xb[e]);
     f = warp_sum(f);
     if (lane == 0) red[warp] = f;
@@ -1748,8 +1803,8 @@ __global__ void __launch_bounds__(256)
   }
   unsigned epoch = 0;
   if (!group_sync(bar, n_b, gerr, epoch)) return;
-  const double floor2 = kJacobiFloor * fro2[b];
-  const double tol = fmax(1e-15, sqrt((double)d.p) * 2.2e-16);
+  const T floor2 = (T)(kJacobiFloor * fro2[b]);
+  const T tol = fmax(Jac<T>::tol_min, sqrt((T)d.p) * Jac<T>::eps);
   const int qpad = d.q + (d.q & 1);
   int sweep = 0;
   bool converged = d.q <= 1;
@@ -1769,8 +1824,8 @@ __global__ void __launch_bounds__(256)
   }
   // singular values: column norms, spread over the group
   for (int j = lc; j < d.q; j += n_b) {
-    const cplx* col = X + d.x_off + (long long)j * d.p;
-    double t = 0.0;
+    const C* col = X + d.x_off + (long long)j * d.p;
+    T t = 0;
     for (int r = threadIdx.x; r < d.p; r += blockDim.x) t += cabs2(col[r]);
     t = warp_sum(t);
     if (lane == 0) red[warp] = t;
@@ -1953,6 +2008,15 @@ namespace {
 // d_stat receives {bad, max sweeps, total sweeps} like the batched kernel.
 // Host side of k_pchol_groups: gsz[b] CTAs for block b (scaled down together when the
 // groups do not all fit on the device at once), one cooperative launch, bounded-wait check.
+__global__ void k_to_c64(const cplx* __restrict__ in, float2* __restrict__ out, long long n) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) out[e] = make_float2((float)in[e].x, (float)in[e].y);
+}
+__global__ void k_to_c128(const float2* __restrict__ in, cplx* __restrict__ out, long long n) {
+  const long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (e < n) out[e] = mkc((double)in[e].x, (double)in[e].y);
+}
+
 void run_pchol_groups(cudaStream_t st, cplx* Xs, BlkDesc* d_desc, int* d_piv, std::vector<int> gsz) {
   const int nblk = (int)gsz.size();
   static const int max_ctas = [] {
@@ -1999,14 +2063,15 @@ void run_pchol_groups(cudaStream_t st, cplx* Xs, BlkDesc* d_desc, int* d_piv, st
   if (herr) throw TdvpError(TDVP_ERR_TIMEOUT, "pivoted Cholesky: a group barrier wait ran out");
 }
 
-void run_jacobi_multi(cudaStream_t st, cplx* Xs, cplx* Vs, const std::vector<BlkDesc>& desc, const BlkDesc* d_desc,
-                      double* d_s, int* d_stat) {
+template <class T>
+void run_jacobi_multi(cudaStream_t st, typename Jac<T>::C* Xs, typename Jac<T>::C* Vs,
+                      const std::vector<BlkDesc>& desc, const BlkDesc* d_desc, double* d_s, int* d_stat) {
   const int nblk = (int)desc.size();
   static const int max_ctas = [] {
     int dev = 0, sms = 0, per_sm = 0;
     TDVP_CUDA(cudaGetDevice(&dev));
     TDVP_CUDA(cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev));
-    TDVP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_groups, 256, 0));
+    TDVP_CUDA(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_jacobi_groups<T>, 256, 0));
     return std::max(1, sms * std::min(4, std::max(1, per_sm)));
   }();
   // CTAs per block: one per pair of a round, scaled down together when they do not all fit
@@ -2043,7 +2108,7 @@ void run_jacobi_multi(cudaStream_t st, cplx* Xs, cplx* Vs, const std::vector<Blk
   const BlkDesc* dd = d_desc;
   const int* po = d_off;
   void* args[] = {&Xs, &Vs, &dd, &po, &nb, &ms, &d_fro2, &d_flags, &bars, &d_gerr, &d_s, &d_stat};
-  TDVP_CUDA(cudaLaunchCooperativeKernel((void*)k_jacobi_groups, dim3(nctas), dim3(256), args, 0, st));
+  TDVP_CUDA(cudaLaunchCooperativeKernel((void*)k_jacobi_groups<T>, dim3(nctas), dim3(256), args, 0, st));
   g_kernel_launches.fetch_add(1, std::memory_order_relaxed);
   int herr = 0;
   TDVP_CUDA(cudaMemcpyAsync(&herr, d_gerr, sizeof(int), cudaMemcpyDeviceToHost, st));
@@ -2098,7 +2163,7 @@ std::map<int, std::pair<std::vector<int>, std::vector<int>>> block_components(cu
 
 void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows, int cols,
                       int (*select)(const std::vector<double>& s, void* ctx), void* ctx, SvdOut& out, bool want_u,
-                      bool want_v, bool psd) {
+                      bool want_v, bool psd, bool jacobi_fp32) {
   g_svd_counters.calls++;
   const long long n = (long long)rows * cols;
   if (rows <= 1 || cols <= 1 || n > (1LL << 27)) {
@@ -2211,17 +2276,38 @@ void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows
       }
     }
     std::optional<ActivePhase> jac(std::in_place, PH_SVD_JACOBI);
-    if (!multi) {
-      static const bool attr = [] {
-        TDVP_CUDA(cudaFuncSetAttribute(k_jacobi_batched, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       (int)kSmemCap));
-        return true;
-      }();
-      (void)attr;
-      k_jacobi_batched<<<nsmall, 256, smem_need, st>>>(Xs.data(), Vs.data(), d_desc, 60, d_s, d_bad);
+    static const bool attr = [] {
+      TDVP_CUDA(cudaFuncSetAttribute(k_jacobi_batched<double>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kSmemCap));
+      TDVP_CUDA(cudaFuncSetAttribute(k_jacobi_batched<float>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                     (int)kSmemCap));
+      return true;
+    }();
+    (void)attr;
+    if (psd && jacobi_fp32) {
+      // the factor (FP64 pivoted Cholesky) is rotated in FP32: its columns are graded, so the
+      // one-sided Jacobi keeps about 1e-7 relative accuracy in every eigenvalue (s^2)
+      RawBuf x32, v32;
+      x32.ensure(pool, sizeof(float2) * (size_t)std::max<long long>(1, xo));
+      v32.ensure(pool, sizeof(float2) * (size_t)std::max<long long>(1, vo));
+      k_to_c64<<<ceil_div(std::max<long long>(1, xo), 256), 256, 0, st>>>(Xs.data(), x32.as<float2>(), xo);
+      TDVP_CHECK_LAUNCH();
+      k_to_c64<<<ceil_div(std::max<long long>(1, vo), 256), 256, 0, st>>>(Vs.data(), v32.as<float2>(), vo);
+      TDVP_CHECK_LAUNCH();
+      if (!multi) {
+        k_jacobi_batched<float><<<nsmall, 256, smem_need / 2, st>>>(x32.as<float2>(), v32.as<float2>(), d_desc, 60,
+                                                                   d_s, d_bad);
+        TDVP_CHECK_LAUNCH();
+      } else {
+        run_jacobi_multi<float>(st, x32.as<float2>(), v32.as<float2>(), desc, d_desc, d_s, d_bad);
+      }
+      k_to_c128<<<ceil_div(std::max<long long>(1, xo), 256), 256, 0, st>>>(x32.as<float2>(), Xs.data(), xo);
+      TDVP_CHECK_LAUNCH();
+    } else if (!multi) {
+      k_jacobi_batched<double><<<nsmall, 256, smem_need, st>>>(Xs.data(), Vs.data(), d_desc, 60, d_s, d_bad);
       TDVP_CHECK_LAUNCH();
     } else {
-      run_jacobi_multi(st, Xs.data(), Vs.data(), desc, d_desc, d_s, d_bad);
+      run_jacobi_multi<double>(st, Xs.data(), Vs.data(), desc, d_desc, d_s, d_bad);
     }
     jac.reset();
     std::vector<double> hs(so);

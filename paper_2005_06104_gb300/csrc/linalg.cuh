@@ -208,9 +208,13 @@ extern SvdCounters g_svd_counters;
 // psd: M is Hermitian positive semidefinite and only U is wanted; the blocks are then
 // factorised by pivoted Cholesky and the Jacobi SVD runs on the factor (fewer sweeps);
 // out.s holds eigenvalues.
+// jacobi_fp32 (psd only): the Jacobi rotations of the FP64 Cholesky factor run in FP32
+// (eigenvalues to about 1e-7 relative, eigenvectors to about 1e-7 / relative gap); for the
+// Krylov vectors of the precision forms, whose density matrices are formed to about that
+// accuracy by the tensor-core GEMMs.
 void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows, int cols,
                       int (*select)(const std::vector<double>& s, void* ctx), void* ctx,
-                      SvdOut& out, bool want_u, bool want_v, bool psd = false);
+                      SvdOut& out, bool want_u, bool want_v, bool psd = false, bool jacobi_fp32 = false);
 template <class Select>
 inline void svd_jacobi(cudaStream_t st, DevicePool* pool, const cplx* M, int rows, int cols,
                        Select select, SvdOut& out, bool want_u, bool want_v) {
@@ -222,11 +226,12 @@ inline void svd_jacobi(cudaStream_t st, DevicePool* pool, const cplx* M, int row
 // Eigendecomposition of a Hermitian positive semidefinite n x n matrix: out.s the
 // eigenvalues (descending), out.U the kept eigenvectors (n x keep).
 template <class Select>
-inline void eig_psd_jacobi(cudaStream_t st, DevicePool* pool, const cplx* M, int n, Select select, SvdOut& out) {
+inline void eig_psd_jacobi(cudaStream_t st, DevicePool* pool, const cplx* M, int n, Select select, SvdOut& out,
+                           bool jacobi_fp32 = false) {
   auto thunk = [](const std::vector<double>& s, void* ctx) -> int {
     return (*static_cast<Select*>(ctx))(s);
   };
-  svd_blocked_keep(st, pool, M, n, n, thunk, &select, out, true, false, true);
+  svd_blocked_keep(st, pool, M, n, n, thunk, &select, out, true, false, true, jacobi_fp32);
 }
 
 // copy a (rows x cols) block into a (rows x ldo) destination at column offset
