@@ -64,6 +64,9 @@ def parse():
                     help="imaginary time on the rung-decoupled 2 x 20 ladder, 50 steps, FP64 / TF32X3 / BF16X10")
     ap.add_argument("--config3", action="store_true",
                     help="real time on the 2 x 50 ladder, chi <= 512, 40 BF16X10 steps with per-step FP64 checks")
+    ap.add_argument("--oat", action="store_true",
+                    help="one-axis twisting at N = 100 (Fig. 4 setting) against the exact Dicke-subspace solution")
+    ap.add_argument("--oat-chi", type=int, default=256, help="bond-dimension cap of the --oat runs")
     ap.add_argument("--fig3", action="store_true",
                     help="imaginary time on the rung-decoupled ladder (Fig. 3): GSE-TDVP1 at d tau 0.1 and 0.4, TDVP2")
     ap.add_argument("--fig3-leg", type=int, default=20, help="leg length of the --fig3 ladder")
@@ -748,6 +751,48 @@ def run_config3(args):
                       "per_step_checks": checks, "bond_dim_max": dims, "s_per_step": ts}), flush=True)
 
 
+def run_oat(args):
+    """One-axis twisting at the paper's size (Sec. II.B, Fig. 4 setting): N = 100, H = (S^z)^2
+    (w = 3), all spins along +x, real time to t = 0.25, eps = 0; GSE-TDVP1 at dt = 0.025 (k = 3,
+    eps_K = eps_M = 1e-4) and dt = 0.05 (k = 5, eps_K = 1e-4, eps_M = 1e-8), TDVP2 at dt = 0.025
+    (eps = 1e-7), all capped at --oat-chi, FP64.  <S^x> and xi^2 (Eqs. 13-15, from MPO
+    expectations of total-spin products) against the exact Dicke-subspace solution; relative
+    energy error; bond dimensions."""
+    import torch
+    from oracle import oat_exact as X
+    from paper_2005_06104_gb300 import gse_tdvp as g
+    from paper_2005_06104_gb300 import workloads as wl
+    n = 100
+    W = wl.oat_mpo(n)
+    Mx, My, Mz = (wl.total_op_mpo(n, op) for op in (wl.SX, wl.SY, wl.SZ))
+    ops = {"x": Mx, "yy": wl.mpo_product(My, My), "zz": wl.mpo_product(Mz, Mz), "yz": wl.mpo_product(My, Mz),
+           "zy": wl.mpo_product(Mz, My)}
+    stream = torch.cuda.current_stream().cuda_stream
+    runs = {}
+    settings = [("gse_tdvp1_dt0.025_k3", 0.025, 3, 1e-4, 1e-4, 0.0, False),
+                ("gse_tdvp1_dt0.05_k5", 0.05, 5, 1e-4, 1e-8, 0.0, False),
+                ("tdvp2_dt0.025_eps1e-7", 0.025, 1, 1e-4, 1e-4, 1e-7, True)]
+    for name, dt, k, ek, em, eps, two in settings:
+        st = g.GseTdvp(wl.x_polarized_state(n), W, tau=dt, eps_k=ek, eps_m=em, eps=eps, chi_max=args.oat_chi,
+                       lanczos_max=63, stream=stream)
+        e0 = st.energy()
+        rows = []
+        t0 = time.perf_counter()
+        for step in range(1, int(round(0.25 / dt)) + 1):
+            if two:
+                st.sweep2(dt, g.REAL)
+            else:
+                st.step(dt, g.REAL, k)
+            mom = {kk: st.expect_mpo(v) for kk, v in ops.items()}
+            ex = X.oat_moments(n, step * dt)
+            rows.append({"t": round(step * dt, 6), "sx": mom["x"].real, "sx_exact": ex["x"].real,
+                         "xi2": X.squeezing_xi2(mom, n), "xi2_exact": X.squeezing_xi2(ex, n),
+                         "rel_energy_err": abs(st.energy() - e0) / abs(e0), "bond_dim_max": max(st.bond_dims())})
+        runs[name] = {"s_total": time.perf_counter() - t0, "trajectory": rows}
+        st.close()
+    print(json.dumps({"workload": "oat_n100_x_polarized", "chi_max": args.oat_chi, "runs": runs}), flush=True)
+
+
 def run_batch(args):
     """Independent random-field chains stepped as one batch (one stream per chain, host worker
     pool) against the same chains stepped one after another on one stream each, same steps."""
@@ -797,7 +842,9 @@ def main():
     if args.batch_chains > 0:
         run_batch(args)
         return
-    if args.config2:
+    if args.oat:
+        run_oat(args)
+    elif args.config2:
         run_config2(args)
     elif args.config3:
         run_config3(args)

@@ -95,7 +95,9 @@ typedef struct {
                               also of the two-site SVDs of tdvp_sweep2, both kinds  */
   int chi_max;             /* cap on every bond dimension (state and Krylov vectors)*/
   double lanczos_tol;      /* local exponential error target                        */
-  int lanczos_max;         /* maximum Krylov dimension of the local exponential     */
+  int lanczos_max;         /* maximum Krylov dimension of one Lanczos run; a local
+                              exponential that does not converge within it is split
+                              into 2, 4, ... 64 equal sub-steps                     */
   int precision;           /* tdvp_precision used inside tdvp_sweep                 */
 } tdvp_options;
 
@@ -160,9 +162,11 @@ TDVP_API tdvp_status tdvp_set_krylov_method(tdvp_handle* h, int method);
  * and the extension keeps |psi> exactly).  precision = -1 (the default) uses the
  * handle's tdvp_options.precision; a tdvp_precision value sets the form of the
  * density environments, the density matrices, the zip-up products and the
- * Krylov vectors' centre moves in the extension.  |psi>'s own contractions, the
- * sweep and every factorisation are not affected.  Other values give
- * TDVP_ERR_INVALID_ARG. */
+ * Krylov vectors' centre moves in the extension.  With a form of about FP32
+ * accuracy (BF16X6, TF32X3), the eigendecompositions of the Krylov density
+ * matrices also rotate their FP64 Cholesky factors in FP32.  |psi>'s own
+ * contractions, the sweep and its factorisations are not affected.  Other values
+ * give TDVP_ERR_INVALID_ARG. */
 TDVP_API tdvp_status tdvp_set_krylov_precision(tdvp_handle* h, int precision);
 
 /* One Krylov vector in place (Eq. 10 with l = 1, Sec. I.B): the state becomes
@@ -214,8 +218,9 @@ TDVP_API tdvp_status tdvp_keff_apply(tdvp_handle* h, int bond, const void* x_dev
 /* Local exponential by Lanczos (FP64 vectors, full re-orthogonalisation
  * twice): y = exp(-i delta H_eff) x (REAL) or exp(-delta H_eff) x (IMAG) at
  * `site` with the current environments.  iters (host, may be NULL) receives the
- * Krylov dimension used.  Error LANCZOS_NOT_CONVERGED when lanczos_max steps do
- * not reach lanczos_tol. */
+ * Krylov dimension used (summed over sub-steps).  A run that does not reach
+ * lanczos_tol within lanczos_max vectors is repeated as 2, 4, ... 64 equal
+ * sub-steps of delta; LANCZOS_NOT_CONVERGED when 64 sub-steps do not converge. */
 TDVP_API tdvp_status tdvp_evolve_site(tdvp_handle* h, int site, const void* x_dev, void* y_dev,
                              double delta, tdvp_time kind, int precision, int* iters);
 
@@ -224,6 +229,12 @@ TDVP_API tdvp_status tdvp_energy(tdvp_handle* h, double* e);   /* <C|H_eff C>/<C
 TDVP_API tdvp_status tdvp_norm(tdvp_handle* h, double* n);     /* |C| at the centre               */
 /* <psi|op_site|psi>/<psi|psi>; op: host d*d complex128 row-major <s|op|s'>. */
 TDVP_API tdvp_status tdvp_expect_local(tdvp_handle* h, const double* op, int site, double* re_im);
+/* <psi|O|psi>/<psi|psi> for an operator given as an MPO (host descriptor in the layout of
+ * tdvp_create's: N sites, the handle's d, boundary bond dimensions 1), by a left-to-right
+ * FP64 environment contraction in any gauge (Sec. II.B uses two-point functions of the total
+ * spin, Eqs. 14-15).  The state and its environments are left as they are.  re_im receives the
+ * complex value; TDVP_ERR_SHAPE for an MPO of another length or d. */
+TDVP_API tdvp_status tdvp_expect_mpo(tdvp_handle* h, const tdvp_mpo_desc* op, double* re_im);
 TDVP_API tdvp_status tdvp_bond_dims(tdvp_handle* h, int* out);  /* N + 1 ints                   */
 TDVP_API tdvp_status tdvp_center(tdvp_handle* h, int* site);
 /* out[0..3]: discarded weight sums of the last call for eps_k, eps_m, eps, and the

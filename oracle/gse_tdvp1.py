@@ -36,6 +36,9 @@ by specification only, never by code):
   R6  in imaginary time every local exponential is followed by renormalisation;
   R7  the added rows B_bar are projected off range(B) twice and re-orthonormalised
       (by an SVD, keeping every row) so that B_bar B^+ = 0 holds to rounding;
+  R13 a local exponential whose Lanczos space reaches n_max without meeting the tolerance is
+      split into 2, 4, ... 64 equal sub-steps (long-range Hamiltonians such as Eq. 12 have a
+      spectral range of order N^2 / 4, so one step of delta may need more than n_max vectors);
   R8  a matrix that is block diagonal up to a permutation (its rows and columns
       linked only through nonzero entries; conserved quantum numbers such as S^z
       make the forbidden entries exactly zero) is factorised block by block, and
@@ -370,6 +373,24 @@ def lanczos_expm(matvec, x, delta, kind, tol=1e-12, nmax=40):
     return out.reshape(shape), len(y)
 
 
+def local_expm(matvec, x, delta, kind, tol=1e-12, nmax=40):
+    """exp(-i delta H) x or exp(-delta H) x to the Lanczos tolerance (R11) with the sub-step rule
+    R13: when nmax Krylov vectors do not reach tol, the step is split into s = 2, 4, ... 64 equal
+    sub-steps, each a Lanczos exponential of delta / s.  Returns (y, total Krylov dimension)."""
+    s = 1
+    while True:
+        try:
+            y, total = x, 0
+            for _ in range(s):
+                y, it = lanczos_expm(matvec, y, delta / s, kind, tol, nmax)
+                total += it
+            return y, total
+        except LanczosNotConverged:
+            if 2 * s > 64:
+                raise
+            s *= 2
+
+
 # ------------------------------------------------------------ TDVP1 sweep
 def tdvp1_sweep(mps, W, dt, kind, eps=0.0, chi_max=None, tol=1e-12, nmax=40, stats=None):
     """One symmetric TDVP1 step (Sec. I.C step 3): left-to-right then right-to-left,
@@ -391,12 +412,12 @@ def tdvp1_sweep(mps, W, dt, kind, eps=0.0, chi_max=None, tol=1e-12, nmax=40, sta
     iters = []
 
     def fwd(i, A):
-        y, it = lanczos_expm(lambda v: heff_apply(Ls[i], W[i], Rs[i], v), A, delta, kind, tol, nmax)
+        y, it = local_expm(lambda v: heff_apply(Ls[i], W[i], Rs[i], v), A, delta, kind, tol, nmax)
         iters.append(it)
         return y / np.linalg.norm(y) if imag else y
 
     def bwd(Lb, Rb, C):
-        y, it = lanczos_expm(lambda v: keff_apply(Lb, Rb, v), C, -delta, kind, tol, nmax)
+        y, it = local_expm(lambda v: keff_apply(Lb, Rb, v), C, -delta, kind, tol, nmax)
         iters.append(it)
         return y / np.linalg.norm(y) if imag else y
 

@@ -30,7 +30,7 @@ from __future__ import annotations
 
 import numpy as np
 
-from .gse_tdvp1 import build_envs, env_left_step, env_right_step, heff_apply, lanczos_expm, svd_truncate
+from .gse_tdvp1 import build_envs, env_left_step, env_right_step, heff_apply, local_expm, svd_truncate
 
 
 def heff2_apply(L, W1, W2, R, X):
@@ -56,7 +56,7 @@ def tdvp2_sweep(mps, W, dt, kind, eps=0.0, chi_max=None, tol=1e-12, nmax=40, sta
     iters, disc = [], []
 
     def evolve(matvec, x, dl):
-        y, it = lanczos_expm(matvec, x, dl, kind, tol, nmax)
+        y, it = local_expm(matvec, x, dl, kind, tol, nmax)
         iters.append(it)
         return y / np.linalg.norm(y) if imag else y
 

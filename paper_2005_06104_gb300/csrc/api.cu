@@ -243,6 +243,15 @@ tdvp_status tdvp_expect_local(tdvp_handle* h, const double* op, int site, double
   });
 }
 
+tdvp_status tdvp_expect_mpo(tdvp_handle* h, const tdvp_mpo_desc* op, double* re_im) {
+  return guarded(h, [&] {
+    tdvp_require(op && re_im && op->bond_dims && op->sites, TDVP_ERR_INVALID_ARG, "null pointer");
+    cplx v = h->eng.expect_mpo(op);
+    re_im[0] = v.x;
+    re_im[1] = v.y;
+  });
+}
+
 tdvp_status tdvp_bond_dims(tdvp_handle* h, int* out) {
   return guarded(h, [&] {
     tdvp_require(out != nullptr, TDVP_ERR_INVALID_ARG, "null output");

@@ -17,6 +17,14 @@ const cplx kZero = {0.0, 0.0};
 const cplx kMinusOne = {-1.0, 0.0};
 }  // namespace
 
+// The Krylov density matrices of a precision form whose operands keep about FP32 accuracy
+// (BF16X6: 2^-25; TF32X3: about 1e-6) are themselves formed to that accuracy, so their
+// eigendecomposition rotates the FP64 Cholesky factor in FP32 (the Krylov vectors only enrich
+// the basis, Sec. I.B).  FP64 and BF16X10 (about 1e-8) keep the FP64 rotations.
+bool krylov_eig_fp32(int kp) {
+  return kp == TDVP_PREC_BF16X6 || kp == TDVP_PREC_TF32X3 || kp == TDVP_PREC_TF32X3_ENV;
+}
+
 int keep_count(const std::vector<double>& w, double total, double eps, int cap, double floor_) {
   int n_cand = 0;
   while (n_cand < (int)w.size() && w[n_cand] > floor_) ++n_cand;
@@ -454,11 +462,25 @@ void Engine::canonicalize(int c) {
 // ============================================================================
 // Lanczos exponential (full re-orthogonalisation, applied twice)
 // ============================================================================
+// A step whose Lanczos space reaches lanczos_max without meeting the tolerance is split into
+// s = 2, 4, ... 64 equal sub-steps (long-range Hamiltonians have a spectral range of order N^2,
+// so one step may need more Krylov vectors than lanczos_max); lanczos_expm reads x before it
+// writes out, so the sub-steps run in place.
 int Engine::lanczos(const std::function<void(const cplx*, cplx*)>& op, const cplx* x, cplx* out,
                     long long n, double delta, int kind) {
   int used = 0;
   try {
-    used = lanczos_expm(st, &pool, blas, lw, op, x, out, n, delta, kind, opt.lanczos_tol, opt.lanczos_max);
+    for (int s = 1;; s *= 2) {
+      try {
+        used = 0;
+        for (int k = 0; k < s; ++k)
+          used += lanczos_expm(st, &pool, blas, lw, op, k == 0 ? x : out, out, n, delta / s, kind, opt.lanczos_tol,
+                               opt.lanczos_max);
+        break;
+      } catch (const TdvpError& e) {
+        if (e.status != TDVP_ERR_LANCZOS_NOT_CONVERGED || 2 * s > 64) throw;
+      }
+    }
   } catch (...) {
     tc_check(st, scr);  // a device timeout explains a failure better than what followed it
     throw;
@@ -933,7 +955,7 @@ void Engine::krylov_apply(const KrylovOp& kop, const MpsDev& src, MpsDev& out) {
     SvdOut sv;
     {
       PhaseScope ps(tracer, PH_KRYLOV_EIG);
-      eig_psd_jacobi(st, &pool, rho.data(), n, rule, sv, kp != TDVP_PREC_FP64);
+      eig_psd_jacobi(st, &pool, rho.data(), n, rule, sv, krylov_eig_fp32(kp));
     }
     const int keep = std::max(1, sv.rank);
     tdvp_require(sv.rank >= 1, TDVP_ERR_NONFINITE, "krylov: zero density matrix");
@@ -1006,7 +1028,7 @@ void Engine::krylov_zipup(const KrylovOp& kop, const MpsDev& src, MpsDev& out) {
     SvdOut sv;
     {
       PhaseScope ps(tracer, PH_KRYLOV_EIG);
-      eig_psd_jacobi(st, &pool, rho.data(), n, rule, sv, kp != TDVP_PREC_FP64);
+      eig_psd_jacobi(st, &pool, rho.data(), n, rule, sv, krylov_eig_fp32(kp));
     }
     const int keep = sv.rank;
     tdvp_require(keep >= 1, TDVP_ERR_NONFINITE, "zip-up: zero site");
@@ -1251,4 +1273,35 @@ cplx Engine::expect_local(const double* op, int site) {
   TDVP_CUDA(cudaMemcpyAsync(&nn, lw.real + 154, sizeof(double), cudaMemcpyDeviceToHost, st));
   sync();
   return mkc(e.x / nn, e.y / nn);
+}
+
+// <psi|O|psi> / <psi|psi> for an MPO O: E_{i+1} = sum conj(A_i) E_i W_i A_i from E_0 = 1 over all
+// sites (FP64, any gauge); <psi|psi> = |C|^2 at the orthogonality centre.
+cplx Engine::expect_mpo(const tdvp_mpo_desc* op) {
+  tdvp_require(op->n_sites == N && op->d == d, TDVP_ERR_SHAPE, "expect_mpo: MPO length or d differ from the state's");
+  std::vector<int> wo(op->bond_dims, op->bond_dims + N + 1);
+  tdvp_require(wo[0] == 1 && wo[N] == 1, TDVP_ERR_SHAPE, "expect_mpo: MPO boundary bond dims must be 1");
+  for (int i = 0; i <= N; ++i) tdvp_require(wo[i] >= 1, TDVP_ERR_SHAPE, "expect_mpo: bond dims must be >= 1");
+  DArr E(&pool, 1), En;
+  k_one<<<1, 1, 0, st>>>(E.data());
+  TDVP_CHECK_LAUNCH();
+  for (int i = 0; i < N; ++i) {
+    tdvp_require(op->sites[i] != nullptr, TDVP_ERR_INVALID_ARG, "expect_mpo: null MPO site");
+    const cplx* Wi = reinterpret_cast<const cplx*>(op->sites[i]);
+    for (size_t e = 0; e < (size_t)wo[i] * d * d * wo[i + 1]; ++e)
+      tdvp_require(std::isfinite(Wi[e].x) && std::isfinite(Wi[e].y), TDVP_ERR_NONFINITE, "non-finite MPO entry");
+    WSparse ws;
+    ws.build(Wi, wo[i], wo[i + 1], d);
+    ws.upload();
+    const int ml = psi.m[i], mr = psi.m[i + 1];
+    En.reset(&pool, (size_t)mr * wo[i + 1] * mr);
+    env_left_fp64(st, scr, E.data(), ws, psi.A[i].data(), ml, mr, d, En.data(), TDVP_PREC_FP64);
+    sync();
+    ws.free_device();
+    E = std::move(En);
+  }
+  cplx v;
+  TDVP_CUDA(cudaMemcpyAsync(&v, E.data(), sizeof(cplx), cudaMemcpyDeviceToHost, st));
+  const double n = norm();
+  return mkc(v.x / (n * n), v.y / (n * n));
 }

@@ -102,6 +102,7 @@ struct Engine {
   double energy();
   double norm();
   cplx expect_local(const double* op, int site);
+  cplx expect_mpo(const tdvp_mpo_desc* op);  // <psi|O|psi>/<psi|psi>, O an MPO of N sites
   void sync() { TDVP_CUDA(cudaStreamSynchronize(st)); }
 };
 

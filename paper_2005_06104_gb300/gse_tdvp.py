@@ -67,6 +67,7 @@ _sig = {
     "tdvp_energy": [_h, C.POINTER(C.c_double)],
     "tdvp_norm": [_h, C.POINTER(C.c_double)],
     "tdvp_expect_local": [_h, C.c_void_p, C.c_int, C.POINTER(C.c_double)],
+    "tdvp_expect_mpo": [_h, C.POINTER(_Desc), C.POINTER(C.c_double)],
     "tdvp_bond_dims": [_h, C.POINTER(C.c_int)],
     "tdvp_center": [_h, C.POINTER(C.c_int)],
     "tdvp_trunc_stats": [_h, C.POINTER(C.c_double)],
@@ -424,6 +425,14 @@ class GseTdvp:
         op = np.ascontiguousarray(op, dtype=np.complex128)
         out = (C.c_double * 2)()
         self._chk(_lib.tdvp_expect_local(self.h, C.c_void_p(op.ctypes.data), site, out))
+        return complex(out[0], out[1])
+
+    def expect_mpo(self, mpo):
+        """<psi|O|psi>/<psi|psi> for an operator O given as an MPO (list of [wl, d, d, wr])."""
+        dims = [mpo[0].shape[0]] + [w.shape[3] for w in mpo]
+        pw = _Pinned(mpo, dims)
+        out = (C.c_double * 2)()
+        self._chk(_lib.tdvp_expect_mpo(self.h, C.byref(pw.desc(self.d)), out))
         return complex(out[0], out[1])
 
     def bond_dims(self):

@@ -179,6 +179,35 @@ def oat_mpo(n, chi=1.0):
     return W
 
 
+def total_op_mpo(n, op):
+    """MPO of sum_i op_i (one-site operator on every site), w = 2: channels "before" and
+    "after" the site that carries op."""
+    W = []
+    for i in range(n):
+        wl = 1 if i == 0 else 2
+        wr = 1 if i == n - 1 else 2
+        w = np.zeros((wl, D, D, wr), dtype=np.complex128)
+        last = wr - 1
+        if i < n - 1:
+            w[0, :, :, 0] = ID2
+        w[0, :, :, last] += op
+        if i > 0:
+            w[wl - 1, :, :, last] += ID2
+        W.append(w)
+    return W
+
+
+def mpo_product(A, B):
+    """MPO of the operator product A B (A applied after B), bond dimensions multiplied:
+    P[(w, u), s, s', (v, x)] = sum_t A[w, s, t, v] B[u, t, s', x]."""
+    out = []
+    for a, b in zip(A, B):
+        p = np.einsum("wstv,utrx->wusrvx", a, b)
+        wl, ul, d, _, vr, xr = p.shape
+        out.append(p.reshape(wl * ul, d, d, vr * xr))
+    return out
+
+
 def mpo_bond_dims(W):
     return [W[0].shape[0]] + [w.shape[3] for w in W]
 

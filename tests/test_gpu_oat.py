@@ -62,3 +62,59 @@ def test_oat_matches_oracle_trajectory(g):
     assert st.bond_dims() == wl.mps_bond_dims(ref)
     assert abs(abs(O.mps_overlap(st.get_mps(), ref)) - 1) < 1e-9
     st.close()
+
+
+def _squeezing(st, n, ops):
+    """<S^x> and xi^2 (Eq. 15) of a device state from MPO expectations of total-spin products."""
+    from oracle import oat_exact as X
+    mom = {k: st.expect_mpo(v) for k, v in ops.items()}
+    return mom["x"].real, X.squeezing_xi2(mom, n)
+
+
+def _spin_ops(n):
+    Mx, My, Mz = (wl.total_op_mpo(n, op) for op in (wl.SX, wl.SY, wl.SZ))
+    return {"x": Mx, "yy": wl.mpo_product(My, My), "zz": wl.mpo_product(Mz, Mz),
+            "yz": wl.mpo_product(My, Mz), "zy": wl.mpo_product(Mz, My)}
+
+
+def test_expect_mpo_matches_oracle(g):
+    n = 10
+    psi = wl.random_mps(n, 8, 31)
+    st = g.GseTdvp(psi, wl.heisenberg_mpo(wl.chain(n)))
+    for W in list(_spin_ops(n).values()) + [wl.oat_mpo(n), wl.heisenberg_mpo(wl.chain(n))]:
+        assert abs(st.expect_mpo(W) - O.mpo_expectation(psi, W)) < 1e-12 * max(1.0, abs(O.mpo_expectation(psi, W)))
+    with pytest.raises(g.TDVPError):
+        st.expect_mpo(wl.oat_mpo(n + 1))
+    st.close()
+
+
+@pytest.mark.parametrize("dt,k,eps_m,steps", [(0.025, 3, 1e-4, 4), (0.05, 5, 1e-8, 2)])
+def test_oat_n100_paper_settings(g, dt, k, eps_m, steps):
+    """N = 100 (Sec. II.B) in the paper's two settings (tau = dt, eps_K = 1e-4, eps = 0), capped
+    at chi 64, to t = 0.1: the device follows the oracle (which sub-steps its local
+    exponentials, R13: the spectral range is about N^2 / 4) in <S^x>, xi^2 and the energy, holds
+    the energy to 1e-10 relative (the paper's bound for GSE-TDVP1), and stays within 1 % of the
+    spin length of Eq. 13 and within a factor 1.6 of the exact xi^2 (Dicke subspace)."""
+    from oracle import oat_exact as X
+    n = 100
+    W = wl.oat_mpo(n)
+    psi = wl.x_polarized_state(n)
+    ops = _spin_ops(n)
+    p = dict(tau=dt, k=k, eps_k=1e-4, eps_m=eps_m, chi_max=64, dt=dt, kind="real", eps=0.0)
+    st = g.GseTdvp(psi, W, tau=dt, eps_k=1e-4, eps_m=eps_m, chi_max=64)
+    e0 = st.energy()
+    ref = psi
+    for step in range(1, steps + 1):
+        st.step(dt, g.REAL, k)
+        ref = O.gse_tdvp1_step(ref, W, p)
+        sx, xi2 = _squeezing(st, n, ops)
+        mom_ref = {kk: O.mpo_expectation(ref, v) for kk, v in ops.items()}
+        assert st.bond_dims() == wl.mps_bond_dims(ref)
+        assert abs(sx - mom_ref["x"].real) < 1e-8 * n
+        assert abs(xi2 - X.squeezing_xi2(mom_ref, n)) < 1e-7 * xi2
+        assert abs(st.energy() - e0) < 1e-10 * abs(e0)
+        ex = X.oat_moments(n, step * dt)
+        assert abs(sx - ex["x"].real) < 0.01 * 0.5 * n
+        xi_ex = X.squeezing_xi2(ex, n)
+        assert xi_ex / 1.6 < xi2 < 1.6 * xi_ex
+    st.close()

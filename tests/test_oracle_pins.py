@@ -206,3 +206,21 @@ def test_expect_local_and_overlap_dense():
     for i in (0, 3, 5):
         ref = np.vdot(v, site_op(SZ, i, 6) @ v) / np.vdot(v, v)
         assert abs(O.expect_local(psi, SZ, i) - ref) < 1e-13
+
+
+def test_local_expm_substeps_reach_expm():
+    """R13: a step whose Lanczos space would need more than n_max vectors (spectral range 500,
+    delta 0.1: phase range 50) is split into sub-steps and still matches expm to 1e-10; the
+    single-run Lanczos with the same n_max refuses it."""
+    rng = np.random.default_rng(12)
+    n = 80
+    A = rng.standard_normal((n, n)) + 1j * rng.standard_normal((n, n))
+    H = 0.5 * (A + A.conj().T)
+    H *= 250.0 / np.max(np.abs(np.linalg.eigvalsh(H)))
+    x = rng.standard_normal(n) + 1j * rng.standard_normal(n)
+    with pytest.raises(O.LanczosNotConverged):
+        O.lanczos_expm(lambda v: H @ v, x, 0.1, "real", 1e-12, 20)
+    y, it = O.local_expm(lambda v: H @ v, x, 0.1, "real", 1e-12, 20)
+    ref = sla.expm(-0.1j * H) @ x
+    assert np.linalg.norm(y - ref) < 1e-10 * np.linalg.norm(x)
+    assert it > 20
