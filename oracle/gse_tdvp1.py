@@ -17,9 +17,13 @@ Readings of places where the paper is silent (all shared with the CUDA path
 by specification only, never by code):
 
   R1  a gauge move that truncates nothing (the real-time sweep, where eps = 0 keeps the
-      evolution exactly unitary, Sec. II.B; every canonicalisation) is a thin QR
-      (LQ right to left) taken block by block (R8): it keeps min(rows, cols) directions
-      of each block and drops none.  Every factorisation that selects (the SVD of the
+      evolution exactly unitary, Sec. II.B; every canonicalisation) keeps the numerical
+      rank: a thin QR (LQ right to left) taken block by block (R8) when every |R_jj|
+      exceeds 1e-10 times the largest (full numerical rank: min(rows, cols) directions of
+      each block), else the SVD with the numerical rank below.  A plain QR of a
+      rank-deficient block (states with extra symmetry, such as the OAT state of Sec. II.B,
+      have them) would keep directions set by rounding, which the next local updates then
+      evolve into.  Every factorisation that selects (the SVD of the
       centre in the extension, Eq. 3; truncated moves in imaginary time; Krylov
       compression) is an SVD whose numerical rank keeps s > 1e-10 * s_max.  That
       threshold sits two decades above the Lanczos tolerance (1e-12), the size of the
@@ -192,6 +196,37 @@ def lq_blocks(M):
     return Rh.conj().T, Qh.conj().T
 
 
+def _qr_full_rank(M, R):
+    """True when every block of the QR shows full numerical rank: all |R_jj| > RANK_RTOL times
+    the largest |R_jj| of the matrix (a rank-deficient block has a column in the span of the
+    ones before it, whose remainder R_jj vanishes)."""
+    diag = []
+    off = 0
+    for ri, ci in _components(M != 0):
+        n = min(len(ri), len(ci))
+        diag.extend(abs(R[off + j, ci[j]]) for j in range(n))
+        off += n
+    if not diag:
+        return False
+    return min(diag) > RANK_RTOL * max(diag)
+
+
+def gauge_split_right(M):
+    """M = Q C with orthonormal columns Q, nothing cut (R1): the block QR when it shows full
+    numerical rank, else the SVD with the numerical rank (Q = U, C = S Vh)."""
+    Q, R = qr_blocks(M)
+    if _qr_full_rank(M, R):
+        return Q, R
+    U, S, Vh, _ = svd_truncate(M)
+    return U, S[:, None] * Vh
+
+
+def gauge_split_left(M):
+    """M = C Q with orthonormal rows Q, nothing cut: the mirror image of gauge_split_right."""
+    Qh, Ch = gauge_split_right(M.conj().T)
+    return Ch.conj().T, Qh.conj().T
+
+
 def svd_truncate(M, eps=0.0, cap=None):
     """M = U S Vh, keeping columns by R1 + R2 + R3.  Returns U, S, Vh, discarded weight."""
     U, S, Vh = svd_blocks(M)
@@ -215,7 +250,7 @@ def left_canonicalize(mps, eps=0.0, cap=None):
         ml, d, mr = out[i].shape
         M = out[i].reshape(ml * d, mr)
         if exact:
-            Q, C = qr_blocks(M)
+            Q, C = gauge_split_right(M)
         else:
             Q, S, Vh, _ = svd_truncate(M, eps, cap)
             C = S[:, None] * Vh
@@ -233,7 +268,7 @@ def right_canonicalize(mps, eps=0.0, cap=None):
         ml, d, mr = out[i].shape
         M = out[i].reshape(ml, d * mr)
         if exact:
-            C, Q = lq_blocks(M)
+            C, Q = gauge_split_left(M)
         else:
             U, S, Q, _ = svd_truncate(M, eps, cap)
             C = U * S[None, :]
@@ -431,7 +466,7 @@ def tdvp1_sweep(mps, W, dt, kind, eps=0.0, chi_max=None, tol=1e-12, nmax=40, sta
             Q, S, Vh, _ = svd_truncate(M, cut_eps, cap)
             C = S[:, None] * Vh
         else:
-            Q, C = qr_blocks(M)
+            Q, C = gauge_split_right(M)
         psi[i] = Q.reshape(ml, d, -1)
         Ls[i + 1] = env_left_step(Ls[i], psi[i], W[i])
         C = bwd(Ls[i + 1], Rs[i], C)
@@ -446,7 +481,7 @@ def tdvp1_sweep(mps, W, dt, kind, eps=0.0, chi_max=None, tol=1e-12, nmax=40, sta
             U, S, Q, _ = svd_truncate(M, cut_eps, cap)
             C = U * S[None, :]
         else:
-            C, Q = lq_blocks(M)
+            C, Q = gauge_split_left(M)
         psi[i] = Q.reshape(-1, d, mr)
         Rs[i - 1] = env_right_step(Rs[i], psi[i], W[i])
         C = bwd(Ls[i], Rs[i - 1], C)

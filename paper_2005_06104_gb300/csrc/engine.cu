@@ -364,11 +364,10 @@ void Engine::apply_op(const SiteOp& op, const cplx* x, cplx* y, int precision) {
 // ============================================================================
 void Engine::move_right(int i, double eps, int cap, bool trunc) {
   const int ml = psi.m[i], mr = psi.m[i + 1], mr2 = psi.m[i + 2];
-  if (!trunc) {
-    QrOut qo;
-    qr_blocked(st, &pool, psi.A[i].data(), ml * d, mr, 0, qo);
+  QrOut qo;
+  if (!trunc) qr_blocked(st, &pool, psi.A[i].data(), ml * d, mr, 0, qo);
+  if (!trunc && qo.full_rank(kRankRtol)) {  // R1: the QR keeps the numerical rank
     const int r = qo.k;
-    tdvp_require(r >= 1, TDVP_ERR_NONFINITE, "move_right: zero tensor");
     DArr nxt(&pool, (size_t)r * d * mr2);
     zgemm(st, OP_N, OP_N, r, d * mr2, mr, kOne, qo.C.data(), mr, psi.A[i + 1].data(), d * mr2, kZero, nxt.data(),
           d * mr2, 1, 0, 0, 0, &pool);
@@ -406,11 +405,10 @@ void Engine::move_right(int i, double eps, int cap, bool trunc) {
 
 void Engine::move_left(int i, double eps, int cap, bool trunc) {
   const int ml = psi.m[i], mr = psi.m[i + 1], ml0 = psi.m[i - 1];
-  if (!trunc) {
-    QrOut qo;
-    qr_blocked(st, &pool, psi.A[i].data(), ml, d * mr, 1, qo);
+  QrOut qo;
+  if (!trunc) qr_blocked(st, &pool, psi.A[i].data(), ml, d * mr, 1, qo);
+  if (!trunc && qo.full_rank(kRankRtol)) {  // R1: the LQ keeps the numerical rank
     const int r = qo.k;
-    tdvp_require(r >= 1, TDVP_ERR_NONFINITE, "move_left: zero tensor");
     DArr prv(&pool, (size_t)ml0 * d * r);
     zgemm(st, OP_N, OP_N, ml0 * d, r, ml, kOne, psi.A[i - 1].data(), ml, qo.C.data(), r, kZero, prv.data(), r, 1, 0,
           0, 0, &pool);
@@ -530,11 +528,15 @@ void Engine::sweep(double dt, int kind) {
     int r = 0;
     {
       PhaseScope ps(tracer, PH_SVD);
-      if (imag) {  // truncated SVD: Q = U, C = U^+ A = S Vh
+      QrOut qo;
+      if (!imag) qr_blocked(st, &pool, psi.A[i].data(), ml * d, mold, 0, qo);
+      if (imag || !qo.full_rank(kRankRtol)) {  // SVD: Q = U, C = U^+ A = S Vh
         SvdRule rule;
-        rule.eps = opt.eps;
-        rule.cap = opt.chi_max;
-        rule.discarded = &disc_eps;
+        if (imag) {
+          rule.eps = opt.eps;
+          rule.cap = opt.chi_max;
+          rule.discarded = &disc_eps;
+        }
         SvdOut sv;
         svd_jacobi(st, &pool, psi.A[i].data(), ml * d, mold, rule, sv, true, false);
         r = sv.rank;
@@ -543,11 +545,8 @@ void Engine::sweep(double dt, int kind) {
         zgemm(st, OP_C, OP_N, r, mold, ml * d, kOne, sv.U.data(), r, psi.A[i].data(), mold, kZero, C.data(), mold,
               1, 0, 0, 0, &pool);
         psi.A[i] = std::move(sv.U);
-      } else {  // real time cuts nothing: block QR (R1)
-        QrOut qo;
-        qr_blocked(st, &pool, psi.A[i].data(), ml * d, mold, 0, qo);
+      } else {  // real time cuts nothing: block QR of full numerical rank (R1)
         r = qo.k;
-        tdvp_require(r >= 1, TDVP_ERR_NONFINITE, "sweep: zero site tensor");
         C = std::move(qo.C);
         psi.A[i] = std::move(qo.Q);
       }
@@ -579,11 +578,15 @@ void Engine::sweep(double dt, int kind) {
     int r = 0;
     {
       PhaseScope ps(tracer, PH_SVD);
-      if (imag) {  // truncated SVD: Q = Vh, C = A Vh^+ = U S
+      QrOut qo;
+      if (!imag) qr_blocked(st, &pool, psi.A[i].data(), mold, d * mr, 1, qo);
+      if (imag || !qo.full_rank(kRankRtol)) {  // SVD: Q = Vh, C = A Vh^+ = U S
         SvdRule rule;
-        rule.eps = opt.eps;
-        rule.cap = opt.chi_max;
-        rule.discarded = &disc_eps;
+        if (imag) {
+          rule.eps = opt.eps;
+          rule.cap = opt.chi_max;
+          rule.discarded = &disc_eps;
+        }
         SvdOut sv;
         svd_jacobi(st, &pool, psi.A[i].data(), mold, d * mr, rule, sv, false, true);
         r = sv.rank;
@@ -592,11 +595,8 @@ void Engine::sweep(double dt, int kind) {
         zgemm(st, OP_N, OP_C, mold, r, d * mr, kOne, psi.A[i].data(), d * mr, sv.Vh.data(), d * mr, kZero, C.data(),
               r, 1, 0, 0, 0, &pool);
         psi.A[i] = std::move(sv.Vh);
-      } else {  // real time cuts nothing: block LQ (R1)
-        QrOut qo;
-        qr_blocked(st, &pool, psi.A[i].data(), mold, d * mr, 1, qo);
+      } else {  // real time cuts nothing: block LQ of full numerical rank (R1)
         r = qo.k;
-        tdvp_require(r >= 1, TDVP_ERR_NONFINITE, "sweep: zero site tensor");
         C = std::move(qo.C);
         psi.A[i] = std::move(qo.Q);
       }

@@ -2,9 +2,11 @@
 // stages, Krylov-vector BLAS-1, the small tridiagonal exponential of the
 // Lanczos exponentiator and a one-sided Jacobi SVD.
 #include <algorithm>
+#include <cstring>
 #include <memory>
-#include <optional>
 #include <numeric>
+#include <optional>
+#include <unordered_map>
 
 #include "linalg.cuh"
 
@@ -2141,17 +2143,43 @@ std::map<int, std::pair<std::vector<int>, std::vector<int>>> block_components(cu
   }
   DSU dsu(rows + cols);
   std::vector<char> row_nz(rows, 0), col_nz(cols, 0);
-  for (int r = 0; r < rows; ++r)
+  // Rows of one conserved-charge block usually share one nonzero pattern: a row whose pattern
+  // equals an earlier row's is united with that row only, so the bit-by-bit unions run once
+  // per distinct pattern.
+  std::unordered_map<uint64_t, std::vector<int>> seen;
+  for (int r = 0; r < rows; ++r) {
+    const unsigned* rw = mask.data() + (size_t)r * words;
+    uint64_t h = 1469598103934665603ull;
+    bool any = false;
     for (int w = 0; w < words; ++w) {
-      unsigned bits = mask[(size_t)r * words + w];
+      h = (h ^ rw[w]) * 1099511628211ull;
+      any = any || rw[w] != 0u;
+    }
+    if (!any) continue;
+    row_nz[r] = 1;
+    auto& reps = seen[h];
+    int twin = -1;
+    for (int q : reps)
+      if (std::memcmp(mask.data() + (size_t)q * words, rw, sizeof(unsigned) * words) == 0) {
+        twin = q;
+        break;
+      }
+    if (twin >= 0) {
+      dsu.unite(r, twin);
+      continue;
+    }
+    reps.push_back(r);
+    for (int w = 0; w < words; ++w) {
+      unsigned bits = rw[w];
       while (bits) {
         const int b = __builtin_ctz(bits);
         bits &= bits - 1;
         const int c = w * 32 + b;
         dsu.unite(r, rows + c);
-        row_nz[r] = col_nz[c] = 1;
+        col_nz[c] = 1;
       }
     }
+  }
   std::map<int, std::pair<std::vector<int>, std::vector<int>>> comp;
   for (int r = 0; r < rows; ++r)
     if (row_nz[r]) comp[dsu.find(r)].first.push_back(r);
@@ -2554,13 +2582,15 @@ __global__ void __launch_bounds__(256)
 //             Cout rows x K  (Cout[row, k_off + j] = conj R_b[j, r], r >= j)
 __global__ void k_qr_scatter(const cplx* __restrict__ X, const cplx* __restrict__ Qb, const QrDesc* __restrict__ desc,
                              const int2* __restrict__ ent, const int* __restrict__ ridx, const int* __restrict__ cidx,
-                             cplx* __restrict__ Qout, cplx* __restrict__ Cout, int cols, int K) {
+                             cplx* __restrict__ Qout, cplx* __restrict__ Cout, int cols, int K,
+                             double* __restrict__ diag) {
   const int2 e = ent[blockIdx.x];
   const QrDesc d = desc[e.x];
   const int j = e.y;
   const long long k = d.k_off + j;
   const cplx* qcol = Qb + d.q_off + (long long)j * d.p;
   const cplx* Xb = X + d.x_off;
+  if (threadIdx.x == 0) diag[k] = sqrt(cabs2(Xb[(long long)j * d.p + j]));  // |R_jj| = |beta_j|
   if (d.orient == 0) {
     for (int i = threadIdx.x; i < d.p; i += blockDim.x) Qout[(long long)ridx[d.r_off + i] * K + k] = qcol[i];
     for (int c = j + threadIdx.x; c < d.q; c += blockDim.x)
@@ -2649,7 +2679,8 @@ void qr_blocked(cudaStream_t st, DevicePool* pool, const cplx* M, int rows, int 
   const size_t b_ent = sizeof(int2) * ent.size();
   auto al = [](size_t x) { return (x + 255) & ~size_t(255); };
   const size_t o_desc = 0, o_r = al(b_desc), o_c = o_r + al(b_r), o_off = o_c + al(b_c), o_tau = o_off + al(b_off),
-               o_bar = o_tau + al(b_tau), o_ent = o_bar + al(b_bar), o_err = o_ent + al(b_ent);
+               o_bar = o_tau + al(b_tau), o_ent = o_bar + al(b_bar), o_diag = o_ent + al(b_ent),
+               o_err = o_diag + al(sizeof(double) * K);
   meta.ensure(pool, o_err + 256);
   char* base = meta.as<char>();
   auto* d_desc = reinterpret_cast<QrDesc*>(base + o_desc);
@@ -2660,6 +2691,7 @@ void qr_blocked(cudaStream_t st, DevicePool* pool, const cplx* M, int rows, int 
   auto* d_bar = reinterpret_cast<GridBar*>(base + o_bar);
   auto* d_ent = reinterpret_cast<int2*>(base + o_ent);
   auto* d_err = reinterpret_cast<int*>(base + o_err);
+  auto* d_diag = reinterpret_cast<double*>(base + o_diag);
   TDVP_CUDA(cudaMemcpyAsync(d_desc, desc.data(), b_desc, cudaMemcpyHostToDevice, st));
   TDVP_CUDA(cudaMemcpyAsync(d_r, ridx.data(), b_r, cudaMemcpyHostToDevice, st));
   TDVP_CUDA(cudaMemcpyAsync(d_c, cidx.data(), b_c, cudaMemcpyHostToDevice, st));
@@ -2686,11 +2718,16 @@ void qr_blocked(cudaStream_t st, DevicePool* pool, const cplx* M, int rows, int 
   fill_zero(st, out.Q.data(), (long long)nq);
   fill_zero(st, out.C.data(), (long long)nc);
   k_qr_scatter<<<(int)ent.size(), 128, 0, st>>>(X.data(), Qb.data(), d_desc, d_ent, d_r, d_c, out.Q.data(),
-                                                  out.C.data(), cols, K);
+                                                  out.C.data(), cols, K, d_diag);
   TDVP_CHECK_LAUNCH();
   int herr = 0;
+  std::vector<double> diag(K);
   TDVP_CUDA(cudaMemcpyAsync(&herr, d_err, sizeof(int), cudaMemcpyDeviceToHost, st));
+  TDVP_CUDA(cudaMemcpyAsync(diag.data(), d_diag, sizeof(double) * K, cudaMemcpyDeviceToHost, st));
   TDVP_CUDA(cudaStreamSynchronize(st));
   if (herr) throw TdvpError(TDVP_ERR_TIMEOUT, "QR: a group barrier wait ran out");
   out.k = K;
+  out.diag_min = *std::min_element(diag.begin(), diag.end());
+  out.diag_max = *std::max_element(diag.begin(), diag.end());
+  for (double v : diag) tdvp_require(std::isfinite(v), TDVP_ERR_NONFINITE, "QR: non-finite factor");
 }

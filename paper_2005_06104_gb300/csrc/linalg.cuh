@@ -247,5 +247,9 @@ void copy_block(cudaStream_t st, cplx* dst, long long ldd, const cplx* src, long
 struct QrOut {
   int k = 0;
   DArr Q, C;
+  double diag_min = 0.0, diag_max = 0.0;  // smallest and largest |R_jj| over all blocks
+  // every block has full numerical rank: all |R_jj| > rtol max |R_jj| (a rank-deficient block
+  // has a column in the span of the ones before it, whose remainder R_jj vanishes)
+  bool full_rank(double rtol) const { return k > 0 && diag_min > rtol * diag_max; }
 };
 void qr_blocked(cudaStream_t st, DevicePool* pool, const cplx* M, int rows, int cols, int orient, QrOut& out);

@@ -240,3 +240,65 @@ def test_total_sz_stays_exact_along_gse_steps():
                 if vals:
                     qn[r] = vals.pop()
             q = qn
+
+
+def _householder_qr_blocks(M):
+    """Another unpivoted QR of each block, written out (beta = -e^{i arg x_0} |x|, reflectors
+    applied column by column, Q accumulated backward): the same |R_jj| as numpy's up to rounding,
+    other rounding everywhere."""
+    rows, cols = M.shape
+    comps = G._components(M != 0)
+    k = sum(min(len(ri), len(ci)) for ri, ci in comps)
+    Q = np.zeros((rows, k), dtype=np.complex128)
+    R = np.zeros((k, cols), dtype=np.complex128)
+    off = 0
+    for ri, ci in comps:
+        X = M[np.ix_(ri, ci)].copy()
+        p_, q_ = X.shape
+        kq = min(p_, q_)
+        vs, taus = [], []
+        for j in range(kq):
+            x = X[j:, j].copy()
+            nrm = np.linalg.norm(x)
+            ph = x[0] / abs(x[0]) if abs(x[0]) > 0 else 1.0
+            v = x.copy()
+            v[0] = x[0] + ph * nrm
+            vn = np.linalg.norm(v)
+            if vn == 0:
+                vs.append(None)
+                continue
+            v = v / vn
+            X[j:, j:] -= 2.0 * np.outer(v, v.conj() @ X[j:, j:])
+            vs.append(v)
+        Qb = np.eye(p_, kq, dtype=np.complex128)
+        for j in range(kq - 1, -1, -1):
+            if vs[j] is not None:
+                Qb[j:, :] -= 2.0 * np.outer(vs[j], vs[j].conj() @ Qb[j:, :])
+        Q[np.ix_(ri, np.arange(off, off + kq))] = Qb
+        R[np.ix_(np.arange(off, off + kq), ci)] = np.triu(X[:kq])
+        off += kq
+    return Q, R
+
+
+def test_rank_deficient_moves_fall_back_to_the_rank_revealing_svd(monkeypatch):
+    """R1 on a state with extra symmetry: one OAT step at N = 100 (Sec. II.B, dt = 0.05, k = 5)
+    meets tall blocks of numerical rank below their width (s_min / s_max ~ 1e-17).  With the
+    SVD fallback the step does not depend on the unpivoted QR used (1e-9 in <S^x>); a plain QR
+    of those blocks keeps rounding-set directions, and two QRs then disagree by more than 1e-7."""
+    n = 100
+    W = wl.oat_mpo(n)
+    Mx = wl.total_op_mpo(n, wl.SX)
+    p = dict(tau=0.05, k=5, eps_k=1e-4, eps_m=1e-8, chi_max=64, dt=0.05, kind="real", eps=0.0)
+
+    def sx(qr, fallback):
+        monkeypatch.setattr(G, "qr_blocks", qr)
+        if not fallback:
+            monkeypatch.setattr(G, "_qr_full_rank", lambda M, R: True)
+        out = O.gse_tdvp1_step(wl.x_polarized_state(n), W, p)
+        monkeypatch.undo()
+        return O.mpo_expectation(out, Mx).real
+    qr0 = G.qr_blocks
+    Q, R = _householder_qr_blocks(np.arange(12.0).reshape(4, 3) + 1j)
+    assert np.allclose(Q @ R, np.arange(12.0).reshape(4, 3) + 1j) and np.allclose(Q.conj().T @ Q, np.eye(3))
+    assert abs(sx(qr0, True) - sx(_householder_qr_blocks, True)) < 1e-9
+    assert abs(sx(qr0, False) - sx(_householder_qr_blocks, False)) > 1e-7
