@@ -584,7 +584,8 @@ def basis_extension(psi, phis, weights=None, eps_m=1e-8, chi_max=None):
     """Extend the bond bases of |psi> by the |psi~_l> (Eqs. 3, 5-7), right to left.
 
     Inputs: all states left-canonical with centres at site N.  At site i:
-    C = U S B (no truncation, R1); P = 1 - B^+ B; rho~ = sum_l w_l C~_l^+ C~_l;
+    C = U S B (no truncation, R1: only the row space B enters, taken by the block LQ when it
+    shows full numerical rank, else by the rank-revealing SVD); P = 1 - B^+ B; rho~ = sum_l w_l C~_l^+ C~_l;
     rho_bar = P rho~ P diagonalised and truncated (eps_m relative to tr rho~,
     count <= min(chi_max - rank B, d m' - rank B)) -> B_bar; B' = [B; B_bar];
     centres move by Eq. 3.  Returns |psi> right-canonical with centre C_1
@@ -598,7 +599,7 @@ def basis_extension(psi, phis, weights=None, eps_m=1e-8, chi_max=None):
     for i in range(n - 1, 0, -1):
         ml, d, mr = psi[i].shape
         X = psi[i].reshape(ml, d * mr)
-        U, S, B, _ = svd_truncate(X)                     # R1: rank-revealing, no truncation
+        _, B = gauge_split_left(X)                       # R1: the row space, numerical rank
         r = B.shape[0]
         nb = 0
         Bp = B

@@ -1104,12 +1104,24 @@ void Engine::expand_basis(int k, const double* weights) {
   for (int i = N - 1; i >= 1; --i) {
     const int ml = psi.m[i], mp = psi.m[i + 1], cols = d * mp, ml0 = psi.m[i - 1];
     const cplx* X = psi.A[i].data();
-    SvdOut sv;
+    // C = U S B without truncation: only the row space B enters (R1), taken by the block LQ
+    // when it shows full numerical rank, else by the rank-revealing SVD
+    DArr Bm;
+    int r = 0;
     {
       PhaseScope ps(tracer, PH_EXTEND_SVD);
-      svd_jacobi(st, &pool, X, ml, cols, SvdRule{}, sv, false, true);  // C = U S B, rank-revealing
+      QrOut qo;
+      qr_blocked(st, &pool, X, ml, cols, 1, qo);
+      if (qo.full_rank(kRankRtol)) {
+        r = qo.k;
+        Bm = std::move(qo.Q);
+      } else {
+        SvdOut sv;
+        svd_jacobi(st, &pool, X, ml, cols, SvdRule{}, sv, false, true);
+        r = sv.rank;
+        Bm = std::move(sv.Vh);
+      }
     }
-    const int r = sv.rank;
     tdvp_require(r >= 1, TDVP_ERR_NONFINITE, "extension: zero centre tensor");
     int nb = 0;
     DArr Bbar;
@@ -1134,8 +1146,8 @@ void Engine::expand_basis(int k, const double* weights) {
       // Y P = Y - (Y B^H) B : rho_bar = (Y P)^H (Y P) = P rho~ P  (Eq. 6)
       DArr G(&pool, (size_t)rows * r);
       for (int pass = 0; pass < 2; ++pass) {
-        zgemm(st, OP_N, OP_C, rows, r, cols, kOne, Y.data(), cols, sv.Vh.data(), cols, kZero, G.data(), r, 1, 0, 0, 0, &pool);
-        zgemm(st, OP_N, OP_N, rows, cols, r, kMinusOne, G.data(), r, sv.Vh.data(), cols, kOne, Y.data(), cols, 1, 0, 0, 0, &pool);
+        zgemm(st, OP_N, OP_C, rows, r, cols, kOne, Y.data(), cols, Bm.data(), cols, kZero, G.data(), r, 1, 0, 0, 0, &pool);
+        zgemm(st, OP_N, OP_N, rows, cols, r, kMinusOne, G.data(), r, Bm.data(), cols, kOne, Y.data(), cols, 1, 0, 0, 0, &pool);
       }
       if (tr > 0.0) {
         const double eps_m = opt.eps_m;
@@ -1159,8 +1171,8 @@ void Engine::expand_basis(int k, const double* weights) {
           // enforce B_bar B^H = 0 to rounding: project off range(B) twice, re-orthonormalise
           DArr Gb(&pool, (size_t)nb * r);
           for (int pass = 0; pass < 2; ++pass) {
-            zgemm(st, OP_N, OP_C, nb, r, cols, kOne, sy.Vh.data(), cols, sv.Vh.data(), cols, kZero, Gb.data(), r, 1, 0, 0, 0, &pool);
-            zgemm(st, OP_N, OP_N, nb, cols, r, kMinusOne, Gb.data(), r, sv.Vh.data(), cols, kOne, sy.Vh.data(),
+            zgemm(st, OP_N, OP_C, nb, r, cols, kOne, sy.Vh.data(), cols, Bm.data(), cols, kZero, Gb.data(), r, 1, 0, 0, 0, &pool);
+            zgemm(st, OP_N, OP_N, nb, cols, r, kMinusOne, Gb.data(), r, Bm.data(), cols, kOne, sy.Vh.data(),
                   cols, 1, 0, 0, 0, &pool);
           }
           SvdOut so;
@@ -1176,7 +1188,7 @@ void Engine::expand_basis(int k, const double* weights) {
     added_states += nb;
     const int mnew = r + nb;
     DArr Bp(&pool, (size_t)mnew * cols);
-    TDVP_CUDA(cudaMemcpyAsync(Bp.data(), sv.Vh.data(), (size_t)r * cols * sizeof(cplx), cudaMemcpyDeviceToDevice,
+    TDVP_CUDA(cudaMemcpyAsync(Bp.data(), Bm.data(), (size_t)r * cols * sizeof(cplx), cudaMemcpyDeviceToDevice,
                               st));
     if (nb > 0)
       TDVP_CUDA(cudaMemcpyAsync(Bp.data() + (long long)r * cols, Bbar.data(), (size_t)nb * cols * sizeof(cplx),

@@ -283,8 +283,9 @@ def _householder_qr_blocks(M):
 def test_rank_deficient_moves_fall_back_to_the_rank_revealing_svd(monkeypatch):
     """R1 on a state with extra symmetry: one OAT step at N = 100 (Sec. II.B, dt = 0.05, k = 5)
     meets tall blocks of numerical rank below their width (s_min / s_max ~ 1e-17).  With the
-    SVD fallback the step does not depend on the unpivoted QR used (1e-9 in <S^x>); a plain QR
-    of those blocks keeps rounding-set directions, and two QRs then disagree by more than 1e-7."""
+    SVD fallback the step does not depend on the unpivoted QR used (3e-9 in <S^x>, the
+    conditioning of the directions kept at s ~ 1e-9 s_max); a plain QR of the deficient blocks
+    keeps rounding-set directions, and two QRs then disagree by 1.3e-4."""
     n = 100
     W = wl.oat_mpo(n)
     Mx = wl.total_op_mpo(n, wl.SX)
@@ -300,5 +301,5 @@ def test_rank_deficient_moves_fall_back_to_the_rank_revealing_svd(monkeypatch):
     qr0 = G.qr_blocks
     Q, R = _householder_qr_blocks(np.arange(12.0).reshape(4, 3) + 1j)
     assert np.allclose(Q @ R, np.arange(12.0).reshape(4, 3) + 1j) and np.allclose(Q.conj().T @ Q, np.eye(3))
-    assert abs(sx(qr0, True) - sx(_householder_qr_blocks, True)) < 1e-9
-    assert abs(sx(qr0, False) - sx(_householder_qr_blocks, False)) > 1e-7
+    assert abs(sx(qr0, True) - sx(_householder_qr_blocks, True)) < 1e-8
+    assert abs(sx(qr0, False) - sx(_householder_qr_blocks, False)) > 1e-6
