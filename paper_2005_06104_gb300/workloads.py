@@ -269,6 +269,25 @@ def random_mps(n, chi, seed, bond_dims=None):
     return out
 
 
+def random_isometric_mps(n, chi, seed):
+    """Right-canonical random MPS, bond dims min(chi, 2^i, 2^(n-i)): every site but the first
+    is the conjugate transpose of the orthonormal factor of a Gaussian complex matrix, the first
+    a normalised Gaussian tensor.  Its Schmidt spectra are those of random isometries (spread
+    over a few decades), unlike the products of Gaussian tensors of random_mps, whose spectra
+    span many more."""
+    rng = np.random.default_rng(seed)
+    m = full_bond_dims(n, chi)
+    out = [None] * n
+    for i in range(n - 1, 0, -1):
+        rows, cols = m[i], D * m[i + 1]
+        g = rng.standard_normal((cols, rows)) + 1j * rng.standard_normal((cols, rows))
+        q, _ = np.linalg.qr(g)                              # cols x rows, orthonormal columns
+        out[i] = q.conj().T.reshape(rows, D, m[i + 1])
+    a = rng.standard_normal((1, D, m[1])) + 1j * rng.standard_normal((1, D, m[1]))
+    out[0] = (a / np.linalg.norm(a)).astype(np.complex128)
+    return out
+
+
 def mps_bond_dims(mps):
     return [mps[0].shape[0]] + [a.shape[2] for a in mps]
 
