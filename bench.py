@@ -75,9 +75,9 @@ def parse():
                     help="time only the blocked Jacobi SVDs of tdvp_create on a dense random MPS (bond --heff-chi)")
     ap.add_argument("--heff-probe", action="store_true",
                     help="only time the tensor-core H_eff apply at --heff-chi (the profiling target)")
-    ap.add_argument("--precision", default="bf16x10", choices=sorted(PRECISIONS),
+    ap.add_argument("--precision", default="bf16x6", choices=sorted(PRECISIONS),
                     help="arithmetic of the dense contractions (Lanczos, SVDs, observables stay FP64)")
-    ap.add_argument("--krylov-precision", default="bf16x6", choices=sorted(PRECISIONS) + ["same"],
+    ap.add_argument("--krylov-precision", default="same", choices=sorted(PRECISIONS) + ["same"],
                     help="arithmetic of the Krylov vectors' contractions in the precision form ('same': "
                          "--precision); FP64 handles always run FP64")
     ap.add_argument("--batch-chains", type=int, default=0,
@@ -96,8 +96,10 @@ PRECISION_TEXT = {
     "fp64": "FP64 on CUDA cores throughout",
     "tf32x3": "tcgen05 split TF32 x3 (H_eff, K_eff, Krylov GEMMs); FP64 environments, Lanczos, SVD",
     "tf32x3_env": "tcgen05 split TF32 x3 (H_eff, K_eff, environments, Krylov GEMMs); FP64 Lanczos, SVD",
-    "bf16x10": "tcgen05 BF16 exact slices x10 (H_eff, K_eff, environments, Krylov GEMMs); FP64 Lanczos, SVD",
-    "bf16x6": "tcgen05 BF16 exact slices x6 (H_eff, K_eff, environments, Krylov GEMMs); FP64 Lanczos, SVD",
+    "bf16x10": "tcgen05 BF16 exact slices x10 (H_eff, K_eff, environments, Krylov GEMMs); FP64 Lanczos, QR, SVD, "
+               "eigendecompositions",
+    "bf16x6": "tcgen05 BF16 exact slices x6 (H_eff, K_eff, environments, Krylov GEMMs); FP64 Lanczos, QR, SVD; "
+              "Krylov density matrices: FP64 pivoted Cholesky, FP32 Jacobi rotations",
 }
 
 
