@@ -406,6 +406,11 @@ def roofline_line(args, g, torch, W):
         traffic = 5.11e9
         traffic_src = ("ncu dram__bytes_read.sum + dram__bytes_write.sum over the 5 launches of one cached "
                        "apply (slice x, GEMM 1, MPO stage, GEMM 3 split 4 ways, split-K sum) of these kernels")
+    elif args.precision == "bf16x6" and args.heff_chi == 1024:
+        traffic = 2.599e9
+        traffic_src = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the two k_gemm_bf16s<3> launches of one "
+                       "cached apply (1.264 GB GEMM 1, 1.335 GB GEMM 3; 78 % of the apply's device time in the "
+                       "launch list); the slicing, MPO-stage and split-K launches are not in this figure")
     achieved = pflops / (pms / 1e3) / 1e12
     return {"bound": "tensor", "achieved": achieved, "peak": peak, "unit": "TFLOP/s",
             "frac": achieved / peak, "traffic": traffic, "kernel": kern, "peak_source": peak_src,
