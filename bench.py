@@ -64,6 +64,8 @@ def parse():
                     help="imaginary time on the rung-decoupled 2 x 20 ladder, 50 steps, FP64 / TF32X3 / BF16X10")
     ap.add_argument("--config3", action="store_true",
                     help="real time on the 2 x 50 ladder, chi <= 512, 40 BF16X10 steps with per-step FP64 checks")
+    ap.add_argument("--peaks", action="store_true",
+                    help="measure the FP64 / FP32 / TF32 / complex128 library matmul rates (roofline denominators)")
     ap.add_argument("--oat", action="store_true",
                     help="one-axis twisting at N = 100 (Fig. 4 setting) against the exact Dicke-subspace solution")
     ap.add_argument("--oat-chi", type=int, default=256, help="bond-dimension cap of the --oat runs")
@@ -73,11 +75,13 @@ def parse():
     ap.add_argument("--fig3-tau", type=float, default=4.0, help="imaginary time of the --fig3 runs")
     ap.add_argument("--svd-probe", action="store_true",
                     help="time only the blocked Jacobi SVDs of tdvp_create on a dense random MPS (bond --heff-chi)")
+    ap.add_argument("--u1", action="store_true",
+                    help="with --heff-probe: operands with the zero pattern of U(1) charges")
     ap.add_argument("--heff-probe", action="store_true",
                     help="only time the tensor-core H_eff apply at --heff-chi (the profiling target)")
-    ap.add_argument("--precision", default="bf16x6", choices=sorted(PRECISIONS),
+    ap.add_argument("--precision", default="bf16x10", choices=sorted(PRECISIONS),
                     help="arithmetic of the dense contractions (Lanczos, SVDs, observables stay FP64)")
-    ap.add_argument("--krylov-precision", default="same", choices=sorted(PRECISIONS) + ["same"],
+    ap.add_argument("--krylov-precision", default="bf16x6", choices=sorted(PRECISIONS) + ["same"],
                     help="arithmetic of the Krylov vectors' contractions in the precision form ('same': "
                          "--precision); FP64 handles always run FP64")
     ap.add_argument("--batch-chains", type=int, default=0,
@@ -311,6 +315,53 @@ def heff_roofline(g, torch, chi, W, prec):
     return flops, timed(7), timed(None)
 
 
+def heff_u1_probe(args, g, torch, st, W, mps=None):
+    """H_eff applies on the live chi_max state at its centre site (the trajectory's own
+    environments and sector structure), CUDA events on the launching stream, environment
+    operands cached as in a Lanczos run.  The algorithmic flops are counted over the nonzero
+    U(1) blocks (charges read off the state's nonzero pattern) and, for comparison, densely."""
+    from paper_2005_06104_gb300 import workloads as wl
+    n = len(W)
+    dims = st.bond_dims()
+    c = max(range(n), key=lambda i: dims[i] * dims[i + 1])
+    st.canonicalize(c)
+    if mps is None:
+        mps = st.get_mps()
+    qs = wl.bond_charges(mps[:c + 1])
+    cs = wl.mpo_channel_charges(W)
+    if any(q is None for q in qs[c]) or any(q is None for q in qs[c + 1]):
+        return None
+    blocks = wl.heff_flops_u1(qs[c], qs[c + 1], W[c], cs[c], cs[c + 1])
+    ml, mr = dims[c], dims[c + 1]
+    dense = 8.0 * (ml * 2 * mr * (ml * W[c].shape[0] + mr * W[c].shape[3]) + ml * mr * int(np.count_nonzero(W[c])))
+    x = torch.from_numpy(np.ascontiguousarray(mps[c])).cuda()
+    y = torch.empty_like(x)
+    prec = prec_code(g, args.precision)
+    cur = torch.cuda.current_stream()
+    for _ in range(3):
+        st.heff_apply(c, x, y, prec)
+    torch.cuda.synchronize()
+    v0, m0 = g.gemm_chunk_stats()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    reps = 10
+    a.record(cur)
+    for _ in range(reps):
+        st.heff_apply(c, x, y, prec)
+    b.record(cur)
+    b.synchronize()
+    ms = a.elapsed_time(b) / reps
+    v1, m1 = g.gemm_chunk_stats()
+    tab_l, tab_r = wl.sector_table(qs[c]), wl.sector_table(qs[c + 1])
+    return {"site": c, "ml": ml, "mr": mr, "w": [int(W[c].shape[0]), int(W[c].shape[3])],
+            "sectors_left": len(set(qs[c])), "sectors_right": len(set(qs[c + 1])),
+            "largest_sector": max(max(d for _, d, _ in tab_l), max(d for _, d, _ in tab_r))
+            if tab_l and tab_r else None, "contiguous": tab_l is not None and tab_r is not None,
+            "ms_per_apply": ms, "flops_blocks": blocks, "flops_dense": dense, "block_fraction": blocks / dense,
+            "tflops_blocks": blocks / ms / 1e9, "tflops_dense_equivalent": dense / ms / 1e9,
+            "gemm_chunk_pairs_multiplied": (m1 - m0) / max(1, v1 - v0),
+            "timed": f"{reps} applies after 3 warm-up at the centre site of the state after the timed steps"}
+
+
 def max_over_ranks(x, dist, device):
     """The largest of every rank's x (all ranks receive it)."""
     import torch
@@ -420,6 +471,25 @@ def roofline_line(args, g, torch, W):
             "timed": "10 applies after 3 warm-up, environment operands cached (as in a Lanczos run)"}
 
 
+def u1_roofline(dense_roof, u1):
+    """The roofline line of the H_eff apply on the U(1) state: achieved = flops over the nonzero
+    blocks / measured time; the random dense-operand probe stays as context."""
+    achieved = u1["tflops_blocks"]
+    products = dense_roof["tensor_flops_per_algorithmic_flop"]
+    return {"bound": "tensor", "achieved": achieved, "peak": dense_roof["peak"], "unit": "TFLOP/s",
+            "frac": achieved / dense_roof["peak"], "traffic": None,
+            "kernel": f"H_eff apply on the chi={max(u1['ml'], u1['mr'])} U(1) state (centre site, w={u1['w']}): "
+                      f"slicing, tcgen05 BF16 exact-slice GEMMs ({products} products) skipping all-zero tiles, "
+                      "MPO stage",
+            "peak_source": dense_roof["peak_source"],
+            "traffic_source": "none taken for the tile-skipping GEMMs on this state",
+            "algorithmic_flops": "over the nonzero U(1) blocks (heff_flops_u1)",
+            "algorithmic_flops_per_apply": u1["flops_blocks"], "ms_per_apply": u1["ms_per_apply"],
+            "tensor_flops_per_algorithmic_flop": products,
+            "gemm_chunk_pairs_multiplied": u1["gemm_chunk_pairs_multiplied"],
+            "dense_operand_probe": dense_roof}
+
+
 def run_gpu(args):
     import torch
     import torch.distributed as dist
@@ -521,6 +591,9 @@ def run_gpu(args):
     nfo["bond_dim_max"] = max(st.bond_dims())
     nfo["bond_dims_start"] = dims_start
     e_end = st.energy()
+    u1 = None
+    if rank == 0 and not args.step_only and args.precision != "fp64":
+        u1 = heff_u1_probe(args, g, torch, st, W)
     st.close()
     if rank != 0:
         if world > 1:
@@ -558,12 +631,16 @@ def run_gpu(args):
     e2e_s = time.perf_counter() - t
     d2h = sum(x.nbytes for x in out)
     roof = legs.get("roofline")
+    if roof is not None and u1 is not None:
+        roof = u1_roofline(roof, u1)
     achieved_step = heff_flops / (heff_ms / 1e3) / 1e12 if heff_ms > 0 else None
     line = dict(base)
     line.update({
         "roofline": roof,
-        "heff_in_step": {"applies": heff_n / n_timed, "ms": heff_ms / n_timed, "tflops_algorithmic": achieved_step,
+        "heff_in_step": {"applies": heff_n / n_timed, "ms": heff_ms / n_timed,
+                         "tflops_dense_equivalent": achieved_step,
                          "share_of_step": heff_ms / sum(ts) if ts else None},
+        "heff_u1_probe": u1,
         "precision_vs_fp64": legs.get("precision_vs_fp64"),
         "tdvp2_comparison": legs.get("tdvp2_comparison"),
         "energy_conservation": {"E_initial": e_init, "E_after_timed_steps": e_end, "abs_drift": abs(e_end - e_init),
@@ -584,7 +661,42 @@ def run_heff_probe(args):
     import torch
     from paper_2005_06104_gb300 import gse_tdvp as g
     from paper_2005_06104_gb300 import workloads as wl
-    W = max(wl.heisenberg_mpo(wl.cylinder_snake(16, 4)), key=lambda w: w.shape[0] * w.shape[3])
+    Wall = wl.heisenberg_mpo(wl.cylinder_snake(16, 4))
+    W = max(Wall, key=lambda w: w.shape[0] * w.shape[3])
+    if args.u1:
+        # operands with the zero pattern of U(1) charges: the bond charges of the middle of a
+        # 24-site random charge-conserving state at bond dimension --heff-chi (sectors sorted),
+        # the channel charges of the cylinder MPO's widest site
+        i = max(range(len(Wall)), key=lambda j: Wall[j].shape[0] * Wall[j].shape[3])
+        cs = wl.mpo_channel_charges(Wall)
+        psi = wl.random_u1_mps(24, args.heff_chi, 11, shuffle=False)
+        qs = wl.bond_charges(psi)
+        L, R, x = wl.u1_heff_operands(qs[12], qs[13], cs[i], cs[i + 1], 5)
+        dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+        Ld, Rd, xd = dev(L), dev(R), dev(x)
+        yd = torch.empty_like(xd)
+        prec = prec_code(g, args.precision)
+        cur = torch.cuda.current_stream()
+        for _ in range(3):
+            g.heff_contract(Ld, W, Rd, xd, yd, prec, stream=cur.cuda_stream, env_tag=3)
+        torch.cuda.synchronize()
+        v0, m0 = g.gemm_chunk_stats()
+        a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        a.record(cur)
+        for _ in range(10):
+            g.heff_contract(Ld, W, Rd, xd, yd, prec, stream=cur.cuda_stream, env_tag=3)
+        b.record(cur)
+        b.synchronize()
+        ms = a.elapsed_time(b) / 10
+        v1, m1 = g.gemm_chunk_stats()
+        blocks = wl.heff_flops_u1(qs[12], qs[13], W, cs[i], cs[i + 1])
+        ml, mr = x.shape[0], x.shape[2]
+        dense = 8.0 * (ml * 2 * mr * (ml * W.shape[0] + mr * W.shape[3]) + ml * mr * int(np.count_nonzero(W)))
+        print(json.dumps({"heff_u1_operands": True, "ml": ml, "mr": mr, "w": int(W.shape[0]),
+                          "precision": args.precision, "ms_per_apply": ms, "flops_blocks": blocks,
+                          "flops_dense": dense, "tflops_blocks": blocks / ms / 1e9,
+                          "gemm_chunk_pairs_multiplied": (m1 - m0) / max(1, v1 - v0)}), flush=True)
+        return
     flops, ms, ms_unc = heff_roofline(g, torch, args.heff_chi, W, prec_code(g, args.precision))
     print(json.dumps({"heff_chi": args.heff_chi, "w": int(W.shape[0]), "precision": args.precision,
                       "ms_per_apply": ms, "ms_per_apply_rebuilding_env_operands": ms_unc,
@@ -800,6 +912,37 @@ def run_oat(args):
     print(json.dumps({"workload": "oat_n100_x_polarized", "chi_max": args.oat_chi, "runs": runs}), flush=True)
 
 
+def run_peaks(args):
+    """Library matmul peaks of the arithmetic the FP64 factorisations, the FP32 Jacobi rotations
+    and the TF32 form run in (the measured BF16 peak and the copy bandwidth come with the
+    machine): torch.matmul (cuBLAS) on n x n operands, best of 5 timed with CUDA events after
+    2 warm-ups, 2 n^3 flops per real product."""
+    import torch
+    out = {}
+    for name, dtype, tf32 in [("fp64", torch.float64, False), ("fp32_simt", torch.float32, False),
+                              ("tf32", torch.float32, True), ("c128_zgemm", torch.complex128, False)]:
+        torch.backends.cuda.matmul.allow_tf32 = tf32
+        n = 4096 if dtype in (torch.float64, torch.complex128) else 8192
+        a = torch.randn(n, n, device="cuda", dtype=dtype)
+        b = torch.randn(n, n, device="cuda", dtype=dtype)
+        for _ in range(2):
+            torch.matmul(a, b)
+        best = None
+        for _ in range(5):
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record()
+            torch.matmul(a, b)
+            e1.record()
+            e1.synchronize()
+            ms = e0.elapsed_time(e1)
+            best = ms if best is None else min(best, ms)
+        flops = (8.0 if dtype == torch.complex128 else 2.0) * n ** 3
+        out[name] = {"n": n, "ms": best, "tflops": flops / best / 1e9}
+    torch.backends.cuda.matmul.allow_tf32 = False
+    print(json.dumps({"peaks": out, "how": "torch.matmul best of 5 (CUDA events), 2 n^3 real flops, 8 n^3 complex"}),
+          flush=True)
+
+
 def run_batch(args):
     """Independent random-field chains stepped as one batch (one stream per chain, host worker
     pool) against the same chains stepped one after another on one stream each, same steps."""
@@ -849,7 +992,9 @@ def main():
     if args.batch_chains > 0:
         run_batch(args)
         return
-    if args.oat:
+    if args.peaks:
+        run_peaks(args)
+    elif args.oat:
         run_oat(args)
     elif args.config2:
         run_config2(args)

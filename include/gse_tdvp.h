@@ -338,6 +338,17 @@ TDVP_API tdvp_status tdvp_trace_read(tdvp_handle* h, double* out, int n);
  * Returns TDVP_ERR_INVALID_ARG for a null pointer. */
 TDVP_API tdvp_status tdvp_launch_count(long long* out);
 
+/* Block sparsity the BF16 tensor-core GEMMs exploit (Sec. I.C cost; conserved S^z charges
+ * make most blocks of L, R, W and the site tensors exactly zero).  Each GEMM output tile of
+ * 128 x 128 walks the K dimension in chunks of 128 real entries; the slicing kernels mark every
+ * (128-row operand tile, chunk) that holds a nonzero entry, and a chunk whose A tile or B tile
+ * is all zero adds an exact zero and is not multiplied.  The factorisations order the kept
+ * vectors of every new bond by block, so each charge sector is one contiguous index range.
+ * out2[0]: (output tile, chunk) pairs visited by the BF16 GEMMs on the current device since the
+ * library loaded; out2[1]: the pairs multiplied.  Differences of two reads cover the calls in
+ * between.  Synchronises the device; TDVP_ERR_INVALID_ARG for a null pointer. */
+TDVP_API tdvp_status tdvp_gemm_chunk_stats(long long* out2);
+
 /* ---------------------------------------------------------------------------
  * Handle-free contractions of one site on caller buffers (kernel-level entry
  * points; the same code the handle uses).  Device buffers are caller-owned

@@ -343,6 +343,18 @@ tdvp_status tdvp_launch_count(long long* out) {
   return TDVP_OK;
 }
 
+tdvp_status tdvp_gemm_chunk_stats(long long* out2) {
+  if (!out2) return TDVP_ERR_INVALID_ARG;
+  try {
+    gemm_chunk_pairs(out2);
+    return TDVP_OK;
+  } catch (const TdvpError& e) {
+    return e.status;
+  } catch (...) {
+    return TDVP_ERR_CUDA;
+  }
+}
+
 }  // extern "C"
 
 // ---------------------------------------------------------------------------

@@ -38,6 +38,10 @@ void heff_tf32x3(cudaStream_t st, Scratch& s, const SiteOp& op, const cplx* x, c
 void heff_bf16s(cudaStream_t st, Scratch& s, const SiteOp& op, const cplx* x, cplx* y, int S);
 // Slices per operand of a BF16 precision mode (BF16X6: 3, BF16X10: 4).
 int bf16_slices(int precision);
+// (output tile, 128-entry K chunk) pairs the BF16 tensor-core GEMMs visited on the current
+// device since the library loaded: out[0] all of them, out[1] the ones multiplied (the rest
+// had an all-zero A or B tile and were skipped).  Synchronises the device.
+void gemm_chunk_pairs(long long out[2]);
 bool prec_is_bf16(int precision);
 void heff_apply_prec(cudaStream_t st, Scratch& s, const SiteOp& op, const cplx* x, cplx* y, int precision);
 // C = opA(A) opB(B) (complex, alpha = 1, beta = 0) on the tensor cores (split TF32,

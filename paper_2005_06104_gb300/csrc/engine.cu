@@ -1190,9 +1190,18 @@ void Engine::expand_basis(int k, const double* weights) {
     DArr Bp(&pool, (size_t)mnew * cols);
     TDVP_CUDA(cudaMemcpyAsync(Bp.data(), Bm.data(), (size_t)r * cols * sizeof(cplx), cudaMemcpyDeviceToDevice,
                               st));
-    if (nb > 0)
+    if (nb > 0) {
       TDVP_CUDA(cudaMemcpyAsync(Bp.data() + (long long)r * cols, Bbar.data(), (size_t)nb * cols * sizeof(cplx),
                                 cudaMemcpyDeviceToDevice, st));
+      // B and B_bar each hold every sector of the new index: regroup the rows of B' so each
+      // sector is contiguous (a gauge permutation of the bond; G and the centres below use B')
+      const std::vector<int> perm = sector_row_order(st, &pool, Bp.data(), mnew, cols);
+      if (!perm.empty()) {
+        DArr B2(&pool, (size_t)mnew * cols);
+        gather_rows(st, Bp.data(), mnew, cols, perm, B2.data());
+        Bp = std::move(B2);
+      }
+    }
     // centres move by Eq. 3: C_{i-1} = A_{i-1} (C_i B'^H), likewise for every psi~_l
     DArr G(&pool, (size_t)ml * mnew);
     zgemm(st, OP_N, OP_C, ml, mnew, cols, kOne, X, cols, Bp.data(), cols, kZero, G.data(), mnew, 1, 0, 0, 0, &pool);

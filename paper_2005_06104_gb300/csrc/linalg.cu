@@ -2187,7 +2187,46 @@ std::map<int, std::pair<std::vector<int>, std::vector<int>>> block_components(cu
     if (col_nz[c]) comp[dsu.find(rows + c)].second.push_back(c);
   return comp;
 }
+__global__ void k_gather_rows(const cplx* __restrict__ M, long long cols, const int* __restrict__ perm, int rows,
+                              cplx* __restrict__ out) {
+  const long long n = (long long)rows * cols;
+  for (long long e = (long long)blockIdx.x * blockDim.x + threadIdx.x; e < n; e += (long long)gridDim.x * blockDim.x) {
+    const long long r = e / cols, c = e % cols;
+    out[e] = M[(long long)perm[r] * cols + c];
+  }
+}
 }  // namespace
+
+std::vector<int> sector_row_order(cudaStream_t st, DevicePool* pool, const cplx* M, int rows, int cols) {
+  if (rows <= 1 || cols <= 0) return {};
+  auto comp = block_components(st, pool, M, rows, cols);
+  if (comp.size() <= 1) return {};
+  std::vector<int> perm;
+  perm.reserve(rows);
+  std::vector<char> placed(rows, 0);
+  for (auto& kv : comp)
+    for (int r : kv.second.first) {
+      perm.push_back(r);
+      placed[r] = 1;
+    }
+  for (int r = 0; r < rows; ++r)
+    if (!placed[r]) perm.push_back(r);  // zero rows, at the end
+  bool identity = true;
+  for (int r = 0; r < rows && identity; ++r) identity = perm[r] == r;
+  if (identity) return {};
+  return perm;
+}
+
+void gather_rows(cudaStream_t st, const cplx* M, int rows, int cols, const std::vector<int>& perm, cplx* out) {
+  tdvp_require((int)perm.size() == rows, TDVP_ERR_INVALID_ARG, "gather_rows: permutation length");
+  int* d_perm = nullptr;
+  TDVP_CUDA(cudaMallocAsync(&d_perm, sizeof(int) * rows, st));
+  TDVP_CUDA(cudaMemcpyAsync(d_perm, perm.data(), sizeof(int) * rows, cudaMemcpyHostToDevice, st));
+  const long long n = (long long)rows * cols;
+  k_gather_rows<<<(int)std::min<long long>(ceil_div(n, 256), 152 * 16), 256, 0, st>>>(M, cols, d_perm, rows, out);
+  TDVP_CHECK_LAUNCH();
+  TDVP_CUDA(cudaFreeAsync(d_perm, st));
+}
 
 void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows, int cols,
                       int (*select)(const std::vector<double>& s, void* ctx), void* ctx, SvdOut& out, bool want_u,
@@ -2378,8 +2417,17 @@ void svd_blocked_keep(cudaStream_t st, DevicePool* pool, const cplx* M, int rows
       out.Vh.reset(pool, (size_t)keep * cols);
       fill_zero(st, out.Vh.data(), (long long)keep * cols);
     }
+    // kept vectors grouped by block (a conserved-charge sector), descending s inside each:
+    // every sector of the new index is one contiguous range, so zero tiles of the tensors
+    // built on it stay whole 128-row tiles the tensor-core GEMMs skip
+    std::vector<int> ord(keep);
+    for (int k = 0; k < keep; ++k) ord[k] = k;
+    std::stable_sort(ord.begin(), ord.end(), [&](int a, int b) { return all[a].blk < all[b].blk; });
     std::vector<SelEntry> sel;
-    for (int k = 0; k < keep; ++k) sel.push_back({all[k].blk, all[k].j, k, psd ? std::sqrt(all[k].s) : all[k].s});
+    for (int k = 0; k < keep; ++k) {
+      const Cand& c = all[ord[k]];
+      sel.push_back({c.blk, c.j, k, psd ? std::sqrt(c.s) : c.s});
+    }
     if (!sel.empty()) {
       SelEntry* d_sel = nullptr;
       TDVP_CUDA(cudaMallocAsync(&d_sel, sizeof(SelEntry) * sel.size(), st));

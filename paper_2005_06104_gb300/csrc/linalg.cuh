@@ -177,6 +177,9 @@ void store_beta(cudaStream_t st, const double* nrm2, double* beta_slot);
 struct SvdOut {
   int rows = 0, cols = 0, rank = 0;  // rank = number of computed singular values kept
   std::vector<double> s;             // sorted descending, all min(rows, cols)
+  // U's columns and Vh's rows: the kept vectors grouped by block of the exact-zero pattern
+  // (blocks in order of their smallest row, descending singular value inside a block), so
+  // each conserved-charge sector of the new index is contiguous
   DArr U;                            // rows x keep   (row-major)
   DArr Vh;                           // keep x cols   (row-major)
   int sweeps = 0;
@@ -253,3 +256,10 @@ struct QrOut {
   bool full_rank(double rtol) const { return k > 0 && diag_min > rtol * diag_max; }
 };
 void qr_blocked(cudaStream_t st, DevicePool* pool, const cplx* M, int rows, int cols, int orient, QrOut& out);
+
+// Row order that makes each block of M's exact-zero pattern (rows x cols, row-major) one
+// contiguous range: blocks in order of their smallest row, rows ascending inside a block, zero
+// rows last.  Empty when M is one block or already in that order.
+std::vector<int> sector_row_order(cudaStream_t st, DevicePool* pool, const cplx* M, int rows, int cols);
+// out[r, :] = M[perm[r], :]  (out and M must not overlap)
+void gather_rows(cudaStream_t st, const cplx* M, int rows, int cols, const std::vector<int>& perm, cplx* out);

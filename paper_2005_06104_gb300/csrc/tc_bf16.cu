@@ -44,6 +44,7 @@ using namespace tc;
 
 constexpr int BM = 128, BN = 128, BK = 32, STAGES = 3;
 constexpr int KC = 128;                 // K elements per chunk (exactness bound of P: 128 * 2^16 < 2^24)
+constexpr int kMaxChunks = 1024;        // chunks one CTA can walk (K up to 131072 real entries per split)
 constexpr int KC_KB = KC / BK;          // k-blocks per chunk
 constexpr int EPI_WARPS = 8;
 constexpr int EPI_WARP0 = 4;            // first epilogue warp (second warpgroup)
@@ -82,12 +83,16 @@ __device__ __forceinline__ void two_sum_acc(float& hi, float& lo, float v) {
   lo = __fadd_rn(lo, e);
 }
 
+// (output tile, K chunk) pairs visited by k_gemm_bf16s since load: [0] all, [1] multiplied
+__device__ unsigned long long g_chunk_pairs[2];
+
 template <int S>
 __global__ void __launch_bounds__(THREADS, 1)
     k_gemm_bf16s(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, int M, int N,
                  int nkb_total, int kb_split, const float* __restrict__ sA, long long lsA,
                  const float* __restrict__ sB, void* __restrict__ out, long long ldo, long long split_stride,
-                 int out_df, int* __restrict__ err) {
+                 int out_df, int* __restrict__ err, const unsigned* __restrict__ maskA,
+                 const unsigned* __restrict__ maskB, int mwords) {
   constexpr int STAGE_BYTES = SCfg<S>::STAGE_BYTES;
   extern __shared__ uint8_t smem_raw[];
   uint8_t* smem = reinterpret_cast<uint8_t*>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -106,6 +111,26 @@ __global__ void __launch_bounds__(THREADS, 1)
   const int nkb = min(nkb_total, kb0 + kb_split) - kb0;
   const int c0 = kb0 / KC_KB;
   const int nchunks = (nkb + KC_KB - 1) / KC_KB;
+  // Chunks whose A tile (these BM rows) or B tile (these BN rows) holds only zeros add exact
+  // zeros to this output tile: the list of the others, built once (the slicing kernels set a
+  // bit per 128-row tile and chunk that holds a nonzero entry).  All three roles walk it.
+  __shared__ int act[kMaxChunks];
+  __shared__ int n_act;
+  if (threadIdx.x == 0) {
+    int n = 0;
+    for (int c = 0; c < nchunks; ++c) {
+      const int g = c0 + c;
+      bool on = true;
+      if (maskA) {
+        on = (maskA[(long long)blockIdx.y * mwords + (g >> 5)] >> (g & 31)) & 1u;
+        on = on && ((maskB[(long long)blockIdx.x * mwords + (g >> 5)] >> (g & 31)) & 1u);
+      }
+      if (on && n < kMaxChunks) act[n++] = c;
+    }
+    n_act = n;
+    atomicAdd(&g_chunk_pairs[0], (unsigned long long)nchunks);
+    atomicAdd(&g_chunk_pairs[1], (unsigned long long)n);
+  }
 
   if (threadIdx.x == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -134,30 +159,36 @@ __global__ void __launch_bounds__(THREADS, 1)
     asm volatile("setmaxnreg.dec.sync.aligned.u32 %0;" ::"n"(REGS_LOW));
   if (warp == 0 && lane == 0) {
     // ---------------- TMA producer: all S slices of the A and B tiles of one k-block
-    int issued = 0;
-    for (int kb = 0; kb < nkb; ++kb) {
-      const int s = kb % STAGES, it = kb / STAGES;
-      if (it > 0 && !mbar_wait(smem_u32(&empty[s]), (it - 1) & 1)) {
-        *abort_flag = 1;
-        break;
+    int issued = 0;  // running count of k-blocks loaded (stage = issued % STAGES)
+    for (int ai = 0; ai < n_act && !*abort_flag; ++ai) {
+      const int c = act[ai];
+      const int kb_end = min(nkb, (c + 1) * KC_KB);
+      for (int kb = c * KC_KB; kb < kb_end; ++kb) {
+        const int s = issued % STAGES, it = issued / STAGES;
+        if (it > 0 && !mbar_wait(smem_u32(&empty[s]), (it - 1) & 1)) {
+          *abort_flag = 1;
+          break;
+        }
+        if (*abort_flag) break;
+        uint8_t* st = smem + s * STAGE_BYTES;
+        const uint32_t fb = smem_u32(&full[s]);
+        mbar_expect_tx(fb, STAGE_BYTES);
+        tma_load_3d(smem_u32(st), &tmA, fb, (kb0 + kb) * BK, m0, 0);
+        tma_load_3d(smem_u32(st + S * TILE), &tmB, fb, (kb0 + kb) * BK, n0, 0);
+        ++issued;
       }
-      if (*abort_flag) break;
-      uint8_t* st = smem + s * STAGE_BYTES;
-      const uint32_t fb = smem_u32(&full[s]);
-      mbar_expect_tx(fb, STAGE_BYTES);
-      tma_load_3d(smem_u32(st), &tmA, fb, (kb0 + kb) * BK, m0, 0);
-      tma_load_3d(smem_u32(st + S * TILE), &tmB, fb, (kb0 + kb) * BK, n0, 0);
-      issued = kb + 1;
     }
     if (*abort_flag) {
-      for (int kb = (issued > STAGES ? issued - STAGES : 0); kb < issued; ++kb)
-        (void)mbar_wait(smem_u32(&full[kb % STAGES]), (kb / STAGES) & 1);
+      for (int q = (issued > STAGES ? issued - STAGES : 0); q < issued; ++q)
+        (void)mbar_wait(smem_u32(&full[q % STAGES]), (q / STAGES) & 1);
     }
   } else if (warp == 1 && lane == 0) {
     // ---------------- MMA issuer
     const uint32_t idesc = idesc_bf16(BM, BN);
-    for (int c = 0; c < nchunks && !*abort_flag; ++c) {
-      const int b = c & 1, u = c >> 1;
+    int used = 0;  // running count of k-blocks consumed, in the producer's order
+    for (int ai = 0; ai < n_act && !*abort_flag; ++ai) {
+      const int c = act[ai];
+      const int b = ai & 1, u = ai >> 1;
       if (u > 0 && !mbar_wait(smem_u32(&tempty[b]), (u - 1) & 1)) {
         *abort_flag = 1;
         break;
@@ -167,7 +198,8 @@ __global__ void __launch_bounds__(THREADS, 1)
       const uint32_t accQ = accP + BN;
       const int kb_end = min(nkb, (c + 1) * KC_KB);
       for (int kb = c * KC_KB; kb < kb_end; ++kb) {
-        const int s = kb % STAGES, it = kb / STAGES;
+        const int s = used % STAGES, it = used / STAGES;
+        ++used;
         if (!mbar_wait(smem_u32(&full[s]), it & 1)) {
           *abort_flag = 1;
           break;
@@ -209,8 +241,9 @@ __global__ void __launch_bounds__(THREADS, 1)
 #pragma unroll
     for (int j = 0; j < EC; ++j) hi[j] = lo[j] = 0.f;
     bool ok = true;
-    for (int c = 0; c < nchunks; ++c) {
-      const int b = c & 1, u = c >> 1;
+    for (int ai = 0; ai < n_act; ++ai) {
+      const int c = act[ai];
+      const int b = ai & 1, u = ai >> 1;
       bool got = mbar_wait(smem_u32(&tfull[b]), u & 1);
       if (!got) *abort_flag = 1;
       ok = __all_sync(0xffffffffu, got && !*abort_flag);
@@ -535,6 +568,13 @@ struct Seg {
       hi[i] = lo[i] = 0.f;
     }
   }
+  // any entry not exactly zero (a non-finite one counts)
+  __device__ bool nonzero() const {
+    bool nz = false;
+#pragma unroll
+    for (int i = 0; i < 4; ++i) nz = nz || v[i] != 0.0 || !(v[i] == v[i]) || hi[i] != 0.f || lo[i] != 0.f;
+    return nz;
+  }
   // max key (FP64) or max |hi| (double-float); bad = non-finite seen
   __device__ unsigned long long key() const {
     unsigned long long k = 0;
@@ -586,9 +626,11 @@ __device__ __forceinline__ GroupScale warp_scale(const Seg<Src>& sg) {
 
 // A operands: one warp per (row, chunk of 128 K entries).
 // out: [S][rows_pad][ldk] bf16; scale: [nch][rows_pad] float.
+// mask (when non-null): bit ch of word (row / 128) * mw + ch / 32 is set when the group is not
+// zero (its scale is nonzero or NaN), i.e. when the chunk holds a nonzero entry of the row tile.
 template <int S, class Src>
 __global__ void k_slice_chunks(Src src, int rows_pad, int ldk, int nch, __nv_bfloat16* __restrict__ out,
-                               float* __restrict__ scale) {
+                               float* __restrict__ scale, unsigned* __restrict__ mask, int mw) {
   const long long gw = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (gw >= (long long)rows_pad * nch) return;  // warp-uniform
@@ -600,14 +642,17 @@ __global__ void k_slice_chunks(Src src, int rows_pad, int ldk, int nch, __nv_bfl
   if (k2 < ldk) sg.load(src, row, k2);
   const GroupScale g = warp_scale(sg);
   if (k2 < ldk) sg.template write<S>(g, out + row * ldk + k2, (long long)rows_pad * ldk);
-  if (lane == 0) scale[(long long)ch * rows_pad + row] = g.sc;
+  if (lane == 0) {
+    scale[(long long)ch * rows_pad + row] = g.sc;
+    if (mask && g.sc != 0.f) atomicOr(&mask[(row >> 7) * mw + (ch >> 5)], 1u << (ch & 31));
+  }
 }
 
 // B operands: one 128-thread block per row, one scale per row (two passes over
 // the source: the largest magnitude, then the slices).  scale: [rows_pad] float.
 template <int S, class Src>
 __global__ void __launch_bounds__(128) k_slice_rows(Src src, int rows_pad, int ldk, __nv_bfloat16* __restrict__ out,
-                                                    float* __restrict__ scale) {
+                                                    float* __restrict__ scale, unsigned* __restrict__ mask, int mw) {
   static_assert(!Src::kDF, "row-scaled operands come from FP64 sources");
   __shared__ unsigned long long red[4];
   const long long row = blockIdx.x;
@@ -624,9 +669,17 @@ __global__ void __launch_bounds__(128) k_slice_rows(Src src, int rows_pad, int l
   __syncthreads();
   k = max(max(red[0], red[1]), max(red[2], red[3]));
   const GroupScale g = scale_from_key(k);
-  for (int k2 = 4 * tid; k2 < ldk; k2 += 512) {
-    sg.load(src, row, k2);
-    sg.template write<S>(g, out + row * ldk + k2, (long long)rows_pad * ldk);
+  // warp wid covers the 128 entries [base, base + 128) of one chunk per pass (warp-uniform bound)
+  for (int base = 128 * wid; base < ldk; base += 512) {
+    const int k2 = base + 4 * lane;
+    const bool in = k2 < ldk;
+    if (in) sg.load(src, row, k2); else sg.zero();
+    if (in) sg.template write<S>(g, out + row * ldk + k2, (long long)rows_pad * ldk);
+    const bool nz = __any_sync(0xffffffffu, in && sg.nonzero());
+    if (mask && nz && lane == 0) {
+      const int ch = base >> 7;
+      atomicOr(&mask[(row >> 7) * mw + (ch >> 5)], 1u << (ch & 31));
+    }
   }
   if (tid == 0) scale[row] = g.sc;
 }
@@ -638,8 +691,8 @@ inline int pad128(int k) { return (k + 127) / 128 * 128; }
 // A sliced operand: bf16 slices [S][rows_pad][ldk] and scales, per (chunk, row)
 // ([nch][rows_pad], A operands) or per row ([rows_pad], B operands).
 struct Sliced {
-  RawBuf data, scale;
-  int rows_pad = 0, ldk = 0, nch = 0, S = 0;
+  RawBuf data, scale, mask;
+  int rows_pad = 0, ldk = 0, nch = 0, S = 0, mw = 0;
   bool row_scale = false;
   void shape(DevicePool* pool, int S_, int rows, int K2, bool per_row) {
     S = S_;
@@ -647,8 +700,11 @@ struct Sliced {
     rows_pad = pad128(std::max(rows, 1));
     ldk = pad32(std::max(K2, 1));
     nch = (ldk + KC - 1) / KC;
+    mw = (nch + 31) / 32;
     data.ensure(pool, sizeof(__nv_bfloat16) * (size_t)S * rows_pad * ldk);
     scale.ensure(pool, sizeof(float) * (size_t)(per_row ? 1 : nch) * rows_pad);
+    // one bit per (128-row tile, chunk) holding a nonzero entry (exact zeros of conserved charges)
+    mask.ensure(pool, sizeof(unsigned) * (size_t)(rows_pad / 128) * mw);
   }
 };
 
@@ -656,21 +712,23 @@ template <class Src>
 void slice(cudaStream_t st, const Src& src, Sliced& o) {
   __nv_bfloat16* d = o.data.as<__nv_bfloat16>();
   float* sc = o.scale.as<float>();
+  unsigned* mk = o.mask.as<unsigned>();
+  TDVP_CUDA(cudaMemsetAsync(mk, 0, sizeof(unsigned) * (size_t)(o.rows_pad / 128) * o.mw, st));
   if (o.row_scale) {
     if constexpr (Src::kDF) {
       throw TdvpError(TDVP_ERR_INVALID_ARG, "slice: row-scaled operands come from FP64 sources");
     } else {
       if (o.S == 4)
-        k_slice_rows<4, Src><<<o.rows_pad, 128, 0, st>>>(src, o.rows_pad, o.ldk, d, sc);
+        k_slice_rows<4, Src><<<o.rows_pad, 128, 0, st>>>(src, o.rows_pad, o.ldk, d, sc, mk, o.mw);
       else
-        k_slice_rows<3, Src><<<o.rows_pad, 128, 0, st>>>(src, o.rows_pad, o.ldk, d, sc);
+        k_slice_rows<3, Src><<<o.rows_pad, 128, 0, st>>>(src, o.rows_pad, o.ldk, d, sc, mk, o.mw);
     }
   } else {
     const int blocks = ceil_div((long long)o.rows_pad * o.nch * 32, 256);
     if (o.S == 4)
-      k_slice_chunks<4, Src><<<blocks, 256, 0, st>>>(src, o.rows_pad, o.ldk, o.nch, d, sc);
+      k_slice_chunks<4, Src><<<blocks, 256, 0, st>>>(src, o.rows_pad, o.ldk, o.nch, d, sc, mk, o.mw);
     else
-      k_slice_chunks<3, Src><<<blocks, 256, 0, st>>>(src, o.rows_pad, o.ldk, o.nch, d, sc);
+      k_slice_chunks<3, Src><<<blocks, 256, 0, st>>>(src, o.rows_pad, o.ldk, o.nch, d, sc, mk, o.mw);
   }
   TDVP_CHECK_LAUNCH();
 }
@@ -695,7 +753,8 @@ CUtensorMap make_map3(const Sliced& o, int box_rows) {
 template <int S>
 void launch_bf16s(cudaStream_t st, const CUtensorMap& ma, const CUtensorMap& mb, int M, int N, int nkb,
                   int kb_split, int splits, const float* sA, long long lsA, const float* sB, void* out,
-                  long long ldo, long long split_stride, int out_df, int* d_err) {
+                  long long ldo, long long split_stride, int out_df, int* d_err, const unsigned* maskA,
+                  const unsigned* maskB, int mw) {
   static const bool attr = [] {
     // the register hand-over inside the kernel is sized for exactly this launch allocation
     cudaFuncAttributes fa;
@@ -711,7 +770,7 @@ void launch_bf16s(cudaStream_t st, const CUtensorMap& ma, const CUtensorMap& mb,
   dim3 grid(ceil_div(N, BN), ceil_div(M, BM), splits);
   tdvp_require(grid.y <= 65535 && splits <= 65535, TDVP_ERR_INVALID_ARG, "gemm_bf16s: grid too large");
   k_gemm_bf16s<S><<<grid, THREADS, SCfg<S>::SMEM_BYTES, st>>>(ma, mb, M, N, nkb, kb_split, sA, lsA, sB, out, ldo,
-                                                              split_stride, out_df, d_err);
+                                                              split_stride, out_df, d_err, maskA, maskB, mw);
   TDVP_CHECK_LAUNCH();
 }
 
@@ -784,12 +843,16 @@ void gemm_bf16s(cudaStream_t st, DevicePool* pool, const Sliced& A, const Sliced
     stride = (long long)M * N;
     df = 1;
   }
+  tdvp_require(A.mw == B.mw && (kb_split + KC_KB - 1) / KC_KB <= kMaxChunks, TDVP_ERR_INVALID_ARG,
+               "gemm_bf16s: chunk masks or chunks per split out of range");
+  const unsigned* mA = A.mask.as<unsigned>();
+  const unsigned* mB = B.mask.as<unsigned>();
   if (A.S == 4)
     launch_bf16s<4>(st, ma, mb, M, N, nkb, kb_split, splits, A.scale.as<float>(), A.rows_pad, B.scale.as<float>(),
-                    dst, ld, stride, df, d_err);
+                    dst, ld, stride, df, d_err, mA, mB, A.mw);
   else
     launch_bf16s<3>(st, ma, mb, M, N, nkb, kb_split, splits, A.scale.as<float>(), A.rows_pad, B.scale.as<float>(),
-                    dst, ld, stride, df, d_err);
+                    dst, ld, stride, df, d_err, mA, mB, A.mw);
   if (splits > 1) {
     const long long n = (long long)M * N;
     k_splitk_df<<<ceil_div(n, 256), 256, 0, st>>>(ws.as<float2>(), splits, M, N, out, ldo, out_df ? 1 : 0);
@@ -824,6 +887,13 @@ int* tc_err(cudaStream_t st, Scratch& s) {
 }  // namespace
 
 int bf16_slices(int precision) { return precision == TDVP_PREC_BF16X6 ? 3 : 4; }
+
+void gemm_chunk_pairs(long long out[2]) {
+  unsigned long long h[2] = {0, 0};
+  TDVP_CUDA(cudaMemcpyFromSymbol(h, tcb::g_chunk_pairs, sizeof(h)));
+  out[0] = (long long)h[0];
+  out[1] = (long long)h[1];
+}
 
 void heff_bf16s(cudaStream_t st, Scratch& s, const SiteOp& op, const cplx* x, cplx* y, int S) {
   const int ml = op.ml, mr = op.mr, wl = op.wl, wr = op.wr, d = op.d;

@@ -100,6 +100,20 @@ def launch_count():
     return out.value
 
 
+_lib.tdvp_gemm_chunk_stats.argtypes = [C.POINTER(C.c_longlong)]
+_lib.tdvp_gemm_chunk_stats.restype = C.c_int
+
+
+def gemm_chunk_stats():
+    """(visited, multiplied): (output tile, K chunk) pairs of the BF16 tensor-core GEMMs on the
+    current device since load; the difference is the all-zero block work that was skipped."""
+    out = (C.c_longlong * 2)()
+    s = _lib.tdvp_gemm_chunk_stats(out)
+    if s != 0:
+        raise TDVPError(s, "tdvp_gemm_chunk_stats")
+    return int(out[0]), int(out[1])
+
+
 class SiteDims(C.Structure):
     _fields_ = [("ml", C.c_int), ("mr", C.c_int), ("wl", C.c_int), ("wr", C.c_int), ("d", C.c_int)]
 

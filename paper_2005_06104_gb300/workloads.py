@@ -292,6 +292,192 @@ def mps_bond_dims(mps):
     return [mps[0].shape[0]] + [a.shape[2] for a in mps]
 
 
+# ---------------------------------------------------------------- U(1) S^z sectors
+SZ2 = (1, -1)   # 2 S^z of basis states 0 (up) and 1 (down): the conserved charge per site
+
+
+def random_u1_mps(n, chi, seed, q_total=0, shuffle=True):
+    """Right-canonical random MPS that conserves total 2 S^z = q_total: A_i[l, s, r] is nonzero
+    only where q_r = q_l + SZ2[s] (bond charges from q = 0 at the left end to q_total at the
+    right end).  Sector dimensions are built from the right: a left sector gets the smaller of
+    the columns its block reaches and the left configurations of its charge, scaled down to
+    chi in total; each block (a left sector's rows against the right sectors it reaches) is the
+    conjugate transpose of the orthonormal factor of a Gaussian complex matrix.  shuffle applies
+    a random permutation to every inner bond (both tensors), interleaving the sectors the way a
+    factorisation that orders by singular value would."""
+    from math import comb
+    rng = np.random.default_rng(seed)
+    dims = [None] * (n + 1)           # dims[i]: {charge: dimension} on the bond left of site i
+    dims[n] = {q_total: 1}
+    for i in range(n - 1, -1, -1):
+        cand = {}
+        for q in range(-i, i + 1, 2):
+            reach = sum(dims[i + 1].get(q + dq, 0) for dq in SZ2)
+            left = comb(i, (i + q) // 2)
+            if reach and left:
+                cand[q] = min(reach, left)
+        tot = sum(cand.values())
+        if tot > chi:
+            cand = {q: max(1, (chi * c) // tot) for q, c in cand.items()}
+            while sum(cand.values()) > chi:
+                qmax = max(cand, key=lambda q: cand[q])
+                cand[qmax] -= 1
+        dims[i] = cand
+
+    def offsets(dm):
+        off, o = {}, 0
+        for q in sorted(dm):
+            off[q] = o
+            o += dm[q]
+        return off, o
+
+    out = []
+    for i in range(n):
+        offl, ml = offsets(dims[i])
+        offr, mr = offsets(dims[i + 1])
+        A = np.zeros((ml, D, mr), dtype=np.complex128)
+        for ql, dl in dims[i].items():
+            cols = [(s, qr) for s, dq in enumerate(SZ2) for qr in [ql + dq] if qr in dims[i + 1]]
+            width = sum(dims[i + 1][qr] for _, qr in cols)
+            g = rng.standard_normal((width, dl)) + 1j * rng.standard_normal((width, dl))
+            if i == 0:
+                blk = (g / np.linalg.norm(g)).T
+            else:
+                q, _ = np.linalg.qr(g)                      # width x dl, orthonormal columns
+                blk = q.conj().T                            # dl x width, orthonormal rows
+            c = 0
+            for s, qr in cols:
+                w = dims[i + 1][qr]
+                A[offl[ql]:offl[ql] + dl, s, offr[qr]:offr[qr] + w] = blk[:, c:c + w]
+                c += w
+        out.append(A)
+    if shuffle:
+        for i in range(1, n):
+            p = rng.permutation(out[i].shape[0])
+            out[i - 1] = out[i - 1][:, :, p]
+            out[i] = out[i][p]
+    return out
+
+
+def bond_charges(mps, phys=SZ2, tol=0.0):
+    """Charge of every index of every bond, read off the nonzero pattern: q = 0 on the left end,
+    q_r = q_l + phys[s] for each entry |A[l, s, r]| > tol.  An index with no such entry (or
+    reached only from indices without a charge) gets None.  Raises ValueError when two entries
+    give one index different charges (the state does not conserve the charge)."""
+    ph = np.asarray(phys, dtype=np.int64)
+    qs = [[0] * mps[0].shape[0]]
+    for A in mps:
+        ql = qs[-1]
+        known = np.array([q is not None for q in ql])
+        qlv = np.array([q if q is not None else 0 for q in ql], dtype=np.int64)
+        nz = (np.abs(A) > tol) & known[:, None, None]
+        cand = (qlv[:, None] + ph[None, :])[:, :, None]             # charge each entry implies
+        big = np.iinfo(np.int64).max
+        lo = np.where(nz, cand, big).min(axis=(0, 1))
+        hi = np.where(nz, cand, -big).max(axis=(0, 1))
+        has = nz.any(axis=(0, 1))
+        bad = has & (lo != hi)
+        if bad.any():
+            r = int(np.argmax(bad))
+            raise ValueError(f"bond index {r} carries charges {lo[r]} and {hi[r]}")
+        qs.append([int(lo[r]) if has[r] else None for r in range(A.shape[2])])
+    return qs
+
+
+def mpo_channel_charges(W, phys=SZ2):
+    """Charge carried by every channel of every MPO bond: 0 on the left end, and
+    c_v = c_w + phys[s] - phys[t] for each nonzero W_i[w, s, t, v] (s output, t input spin), so
+    an environment L[a, w, a'] can be nonzero only where q_a - q_a' = c_w.  A channel that no
+    chain of nonzero entries reaches from the left end gets None.  Raises ValueError when the
+    MPO does not conserve the charge."""
+    cs = [[0] * W[0].shape[0]]
+    for Wi in W:
+        cl = cs[-1]
+        cr = [None] * Wi.shape[3]
+        for w, s, t, v in np.argwhere(Wi != 0):
+            if cl[w] is None:        # a channel no term reaches from the left end
+                continue
+            c = cl[w] + phys[s] - phys[t]
+            if cr[v] is None:
+                cr[v] = c
+            elif cr[v] != c:
+                raise ValueError(f"MPO channel {v} carries charges {cr[v]} and {c}")
+        cs.append(cr)
+    return cs
+
+
+def heff_flops_u1(q_l, q_r, Wi, c_l, c_r, phys=SZ2):
+    """Real flops of one H_eff apply counted over the nonzero blocks only (8 per complex
+    multiply-add), for the three stages of the one-site contraction (Sec. I.C step 3):
+      T1[(a,w),(t,b')] = sum_a' L[a,w,a'] x[a',t,b']      L nonzero iff q_a = q_a' + c_w
+                                                          x nonzero iff q_b' = q_a' + phys[t]
+      T2[(a,s),(v,b')] = sum_{w,t} W[w,s,t,v] T1[...]     T1 nonzero iff q_b' - q_a = phys[t] - c_w
+      y[(a,s),b] = sum_{(v,b')} T2[(a,s),(v,b')] R[b,v,b']   R nonzero iff q_b = q_b' + c_v
+    (a channel w no term reaches from the left end, c_w None, holds zero environments).
+    q_l, q_r: charges of the left and right bond indices; c_l, c_r: channel charges of W's
+    bonds.  The dense count of the same stages is 8 [m_l d m_r (m_l w_l + m_r w_r) + m_l m_r nnz W]."""
+    from collections import Counter
+    ql, qr = Counter(q_l), Counter(q_r)
+    cl = Counter(c for c in c_l if c is not None)
+    # stage 1: sum over a' of #(a, w) x #(t, b')
+    f1 = 0
+    for qa1, na1 in ql.items():
+        n_aw = sum(nw * ql.get(qa1 + c, 0) for c, nw in cl.items())
+        n_tb = sum(qr.get(qa1 + p, 0) for p in phys)
+        f1 += na1 * n_aw * n_tb
+    # stage 2: each nonzero W entry couples the (a, b') pairs of its charge difference
+    f2 = 0
+    for w, s, t, v in np.argwhere(Wi != 0):
+        if c_l[w] is None:
+            continue
+        dq = phys[t] - c_l[w]
+        f2 += sum(na * qr.get(qa + dq, 0) for qa, na in ql.items())
+    # stage 3: sum over (v, b') of #(a, s) x #b; T2 has a block (s, v) only where some W entry
+    # of a reachable channel w writes it, and there q_a = q_b' - phys[s] + c_v
+    sv = {(int(s), int(v)) for w, s, t, v in np.argwhere(Wi != 0) if c_l[w] is not None}
+    f3 = 0
+    for s, v in sv:
+        c = c_r[v]
+        for qb1, nb1 in qr.items():
+            f3 += nb1 * ql.get(qb1 - phys[s] + c, 0) * qr.get(qb1 + c, 0)
+    return 8.0 * (f1 + f2 + f3)
+
+
+def u1_heff_operands(q_l, q_r, c_l, c_r, seed, phys=SZ2):
+    """Random operands of one U(1) H_eff apply with the zero pattern the charges fix:
+    L[a, w, a'] where q_a = q_a' + c_w, R[b, v, b'] where q_b = q_b' + c_v and
+    x[a, s, b] where q_b = q_a + phys[s] (Gaussian complex entries there, exact zeros elsewhere;
+    channels with charge None are zero)."""
+    rng = np.random.default_rng(seed)
+    ql, qr = np.asarray(q_l), np.asarray(q_r)
+    cl = np.array([np.nan if c is None else c for c in c_l])
+    cr = np.array([np.nan if c is None else c for c in c_r])
+
+    def rnd(mask):
+        out = np.zeros(mask.shape, dtype=np.complex128)
+        k = int(mask.sum())
+        out[mask] = rng.standard_normal(k) + 1j * rng.standard_normal(k)
+        return out
+    L = rnd(ql[:, None, None] == ql[None, None, :] + cl[None, :, None])
+    R = rnd(qr[:, None, None] == qr[None, None, :] + cr[None, :, None])
+    x = rnd(qr[None, None, :] == ql[:, None, None] + np.asarray(phys)[None, :, None])
+    return L, R, x
+
+
+def sector_table(charges):
+    """[(charge, dim, offset)] of one bond when every charge is one contiguous index range,
+    else None."""
+    table = []
+    for k, q in enumerate(charges):
+        if table and table[-1][0] == q:
+            table[-1][1] += 1
+        else:
+            table.append([q, 1, k])
+    if len({t[0] for t in table}) != len(table):
+        return None
+    return [tuple(t) for t in table]
+
+
 # ---------------------------------------------------------------- workloads
 def lambda_top(lat):
     """Sum_b J_b / 4: the ferromagnetic energy, the top of the Heisenberg spectrum

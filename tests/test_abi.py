@@ -56,6 +56,7 @@ def test_default_options_struct(lib):
 def test_launch_counter_reads_without_a_gpu(lib):
     from paper_2005_06104_gb300 import gse_tdvp as g
     assert lib.tdvp_launch_count(None) == 1
+    assert lib.tdvp_gemm_chunk_stats(None) == 1
     n0 = g.launch_count()
     assert isinstance(n0, int) and n0 >= 0
     assert g.launch_count() == n0  # nothing launched in between
