@@ -211,7 +211,9 @@ TDVP_API tdvp_status tdvp_heff_apply(tdvp_handle* h, int site, const void* x_dev
  *   y[a,b'] = sum L[a,w,a'] x[a',c] R[b',w,c]
  * with L = environment of sites < b and R = environment of sites >= b; needs
  * the centre at site b (tdvp_canonicalize(b)).  x_dev, y_dev: DEVICE buffers of
- * m_b * m_b complex128.  FP64 only. */
+ * m_b * m_b complex128.  precision: tdvp_precision, as the sweep's backward
+ * steps use it (the two GEMMs run on the tensor cores when they are large
+ * enough: M N K >= 2^21, M >= 64, N >= 32; smaller ones stay FP64). */
 TDVP_API tdvp_status tdvp_keff_apply(tdvp_handle* h, int bond, const void* x_dev, void* y_dev,
                             int precision);
 
@@ -237,6 +239,31 @@ TDVP_API tdvp_status tdvp_expect_local(tdvp_handle* h, const double* op, int sit
 TDVP_API tdvp_status tdvp_expect_mpo(tdvp_handle* h, const tdvp_mpo_desc* op, double* re_im);
 TDVP_API tdvp_status tdvp_bond_dims(tdvp_handle* h, int* out);  /* N + 1 ints                   */
 TDVP_API tdvp_status tdvp_center(tdvp_handle* h, int* site);
+
+/* U(1) sector tables of the bond bases.  A Hamiltonian that conserves a U(1) charge
+ * (total S^z of the Heisenberg and OAT models, Secs. II.A-B) keeps a state of
+ * definite charge block sparse: A_i[l][s][r] can be nonzero only where
+ * q_r = q_l + c_s.  The cost statement of Sec. I.C counts its contractions over
+ * these blocks; the library stores tensors densely, orders every new bond index by
+ * block, and lets its tensor-core GEMMs skip the all-zero tiles.
+ *
+ * tdvp_bond_charges reads the charge of every index of every bond (bond 0 to bond
+ * N, N + 1 bonds, bond 0 first) off the exact-zero pattern of the current site
+ * tensors: bond 0 carries charge 0 and index r of bond i+1 gets q_l + c_s from
+ * every nonzero A_i[l][s][r].  phys_charges: d host ints c_s (2 S^z = +1, -1 for
+ * spin 1/2).  charges: host buffer of sum_b m_b ints (tdvp_bond_dims gives m_b).
+ * Errors: INVALID_ARG (null, |c_s| >= 2^20); SHAPE when an index gets two
+ * different charges (the state does not conserve the charge) or none. */
+TDVP_API tdvp_status tdvp_bond_charges(tdvp_handle* h, const int* phys_charges, int* charges);
+
+/* The sector table of bond `bond` (0..N): the runs of equal charge along the bond
+ * index as (charge[k], dim[k], offset[k]), k = 0.. in index order.  *n_sectors
+ * receives the number of runs (at most max_sectors triples are written; host
+ * buffers, may be NULL when max_sectors = 0); *contiguous is 1 when no charge
+ * occurs in two runs (each sector one contiguous index range), else 0.  Errors as
+ * tdvp_bond_charges, and INVALID_ARG for a bond out of range. */
+TDVP_API tdvp_status tdvp_bond_sectors(tdvp_handle* h, const int* phys_charges, int bond, int max_sectors,
+                                       int* charge, int* dim, int* offset, int* n_sectors, int* contiguous);
 /* out[0..3]: discarded weight sums of the last call for eps_k, eps_m, eps, and the
  * number of basis states added by the last extension; out[4]: total Lanczos
  * iterations of the last sweep; out[5]: Lanczos calls of the last sweep;

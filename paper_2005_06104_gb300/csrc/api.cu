@@ -1,6 +1,7 @@
 // C-ABI entry points of libgsetdvp (declared in include/gse_tdvp.h).  Every
 // entry point converts internal errors to a tdvp_status; no exception crosses
 // the boundary.  On error the handle's message is kept for tdvp_last_error().
+#include <algorithm>
 #include <cstring>
 #include <mutex>
 
@@ -192,12 +193,13 @@ tdvp_status tdvp_keff_apply(tdvp_handle* h, int bond, const void* x, void* y, in
     Engine& e = h->eng;
     tdvp_require(x && y && x != y, TDVP_ERR_INVALID_ARG, "x, y must be distinct device buffers");
     tdvp_require(bond >= 1 && bond < e.N, TDVP_ERR_INVALID_ARG, "bond out of range");
-    tdvp_require(precision == TDVP_PREC_FP64, TDVP_ERR_INVALID_ARG, "K_eff runs in FP64 only");
+    tdvp_require(precision >= TDVP_PREC_FP64 && precision <= TDVP_PREC_BF16X6, TDVP_ERR_INVALID_ARG,
+                 "unknown precision");
     e.ensure_L(bond);
     e.ensure_R(bond - 1);
     const int mb = e.psi.m[bond];
     keff_fp64(e.st, e.scr, e.L[bond].data(), mb, e.R[bond - 1].data(), mb, e.w[bond], static_cast<const cplx*>(x),
-              static_cast<cplx*>(y));
+              static_cast<cplx*>(y), precision);
     e.sync();
   });
 }
@@ -256,6 +258,36 @@ tdvp_status tdvp_bond_dims(tdvp_handle* h, int* out) {
   return guarded(h, [&] {
     tdvp_require(out != nullptr, TDVP_ERR_INVALID_ARG, "null output");
     for (int i = 0; i <= h->eng.N; ++i) out[i] = h->eng.psi.m[i];
+  });
+}
+
+tdvp_status tdvp_bond_charges(tdvp_handle* h, const int* phys_charges, int* charges) {
+  return guarded(h, [&] {
+    tdvp_require(phys_charges != nullptr && charges != nullptr, TDVP_ERR_INVALID_ARG, "null argument");
+    const auto q = bond_charges(h->eng, phys_charges);
+    for (const auto& b : q) charges = std::copy(b.begin(), b.end(), charges);
+  });
+}
+
+tdvp_status tdvp_bond_sectors(tdvp_handle* h, const int* phys_charges, int bond, int max_sectors, int* charge,
+                              int* dim, int* offset, int* n_sectors, int* contiguous) {
+  return guarded(h, [&] {
+    tdvp_require(phys_charges != nullptr && n_sectors != nullptr && contiguous != nullptr, TDVP_ERR_INVALID_ARG,
+                 "null argument");
+    tdvp_require(bond >= 0 && bond <= h->eng.N, TDVP_ERR_INVALID_ARG, "bond out of range");
+    tdvp_require(max_sectors >= 0 && (max_sectors == 0 || (charge && dim && offset)), TDVP_ERR_INVALID_ARG,
+                 "null table with max_sectors > 0");
+    const auto q = bond_charges(h->eng, phys_charges);
+    bool cont = true;
+    const std::vector<int> t = sector_runs(q[bond], &cont);
+    const int n = (int)t.size() / 3;
+    for (int k = 0; k < std::min(n, max_sectors); ++k) {
+      charge[k] = t[3 * k];
+      dim[k] = t[3 * k + 1];
+      offset[k] = t[3 * k + 2];
+    }
+    *n_sectors = n;
+    *contiguous = cont ? 1 : 0;
   });
 }
 

@@ -106,6 +106,14 @@ struct Engine {
   void sync() { TDVP_CUDA(cudaStreamSynchronize(st)); }
 };
 
+// U(1) charges of every bond index (N + 1 bonds, bond 0 first), read off the exact-zero pattern
+// of the current site tensors from charge 0 at the left end; phys_host holds the d local
+// charges.  Throws TDVP_ERR_SHAPE when an index gets two charges or none.
+std::vector<std::vector<int>> bond_charges(Engine& e, const int* phys_host);
+// Runs of equal charge along one bond as (charge, dim, offset) triples; *contiguous is false
+// when a charge occurs in more than one run.
+std::vector<int> sector_runs(const std::vector<int>& q, bool* contiguous);
+
 // The opaque handle of the C ABI: one engine and the text of its last error.
 struct tdvp_handle {
   Engine eng;

@@ -70,6 +70,9 @@ _sig = {
     "tdvp_expect_mpo": [_h, C.POINTER(_Desc), C.POINTER(C.c_double)],
     "tdvp_bond_dims": [_h, C.POINTER(C.c_int)],
     "tdvp_center": [_h, C.POINTER(C.c_int)],
+    "tdvp_bond_charges": [_h, C.POINTER(C.c_int), C.POINTER(C.c_int)],
+    "tdvp_bond_sectors": [_h, C.POINTER(C.c_int), C.c_int, C.c_int, C.POINTER(C.c_int), C.POINTER(C.c_int),
+                          C.POINTER(C.c_int), C.POINTER(C.c_int), C.POINTER(C.c_int)],
     "tdvp_trunc_stats": [_h, C.POINTER(C.c_double)],
     "tdvp_get_mps": [_h, C.POINTER(C.c_void_p)],
     "tdvp_profile": [_h, C.c_int],
@@ -453,6 +456,28 @@ class GseTdvp:
         out = (C.c_int * (self.n + 1))()
         self._chk(_lib.tdvp_bond_dims(self.h, out))
         return list(out)
+
+    def bond_charges(self, phys=(1, -1)):
+        """U(1) charge of every index of bonds 0..N (lists), read off the state's zero pattern
+        from charge 0 at the left end; phys: the d local charges (2 S^z for spin 1/2)."""
+        m = self.bond_dims()
+        ph = (C.c_int * self.d)(*phys)
+        out = (C.c_int * sum(m))()
+        self._chk(_lib.tdvp_bond_charges(self.h, ph, out))
+        q, o = [], 0
+        for mb in m:
+            q.append(list(out[o:o + mb]))
+            o += mb
+        return q
+
+    def bond_sectors(self, bond, phys=(1, -1), max_sectors=4096):
+        """([(charge, dim, offset), ...], contiguous) of one bond."""
+        ph = (C.c_int * self.d)(*phys)
+        q, dm, off = (C.c_int * max_sectors)(), (C.c_int * max_sectors)(), (C.c_int * max_sectors)()
+        n, cont = C.c_int(), C.c_int()
+        self._chk(_lib.tdvp_bond_sectors(self.h, ph, bond, max_sectors, q, dm, off, C.byref(n), C.byref(cont)))
+        k = min(n.value, max_sectors)
+        return [(q[i], dm[i], off[i]) for i in range(k)], bool(cont.value)
 
     def center(self):
         v = C.c_int()

@@ -229,3 +229,30 @@ def test_heff_full_size_sampled(g):
     # the whole output: the GPU forms agree norm-wise
     assert (torch.linalg.norm(ytc - y64) / torch.linalg.norm(y64)).item() < TOL_TC
     assert (torch.linalg.norm(ybf - y64) / torch.linalg.norm(y64)).item() < TOL_BF16X10
+
+
+@pytest.mark.parametrize("prec", ["fp64", "tf32x3", "bf16x10", "bf16x6"])
+def test_keff_apply_precision_forms_through_a_handle(g, prec):
+    """tdvp_keff_apply in every precision form (the arithmetic of the sweep's backward bond
+    steps) against the oracle's K_eff on the handle's own state: a 16-site rung-coupled zigzag
+    ladder (w = 8) at bond dimension 144, centre moved to the middle bond, so both K_eff GEMMs
+    (1152 x 144 x 144 and 144 x 144 x 1152) run on the tensor cores in the split forms."""
+    lat = wl.zigzag_ladder(8, 1.0, 1.0)
+    W = wl.heisenberg_mpo(lat)
+    h = g.GseTdvp(wl.random_isometric_mps(16, 144, 4), W, chi_max=256)
+    bond = 8
+    h.canonicalize(bond)
+    mps = h.get_mps()
+    Ls, Rs = O.build_envs(mps, W, bond)
+    R_incl = O.env_right_step(Rs[bond], mps[bond], W[bond])
+    mb = mps[bond].shape[0]
+    assert mb == 144
+    rng = np.random.default_rng(11)
+    x = _rand(rng, mb, mb)
+    xd, = _dev(x)
+    yd = torch.empty_like(xd)
+    code = {"fp64": g.PREC_FP64, "tf32x3": g.PREC_TF32X3, "bf16x10": g.PREC_BF16X10, "bf16x6": g.PREC_BF16X6}[prec]
+    tol = {"fp64": TOL64, "tf32x3": TOL_TC, "bf16x10": TOL_BF16X10, "bf16x6": TOL_BF16X6}[prec]
+    h.keff_apply(bond, xd, yd, code)
+    assert _rel(yd.cpu().numpy(), O.keff_apply(Ls[bond], R_incl, x)) < tol
+    h.close()

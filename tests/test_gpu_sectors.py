@@ -131,3 +131,43 @@ def test_bf16_steps_on_u1_state_skip_block_work_and_keep_the_bar(g):
     assert m1 - m0 < 0.7 * (v1 - v0), (v1 - v0, m1 - m0)
     a.close()
     b.close()
+
+
+def test_bond_charges_and_sector_tables_through_the_abi(g):
+    """tdvp_bond_charges and tdvp_bond_sectors (device read-out of the charges off the zero
+    pattern) equal the host's reading of the state the handle returns, bit for bit, after
+    tdvp_create on a shuffled U(1) state of total charge 2 and after GSE-TDVP1 steps (BF16X10);
+    the right end carries the total charge and every sector is one contiguous range."""
+    n = 16
+    lat = wl.chain(n)
+    W = wl.heisenberg_mpo(lat)
+    psi = wl.random_u1_mps(n, 48, 3, q_total=2)
+    h = g.GseTdvp(psi, W, tau=0.05, eps_k=1e-8, eps_m=1e-8, chi_max=64, precision=g.PREC_BF16X10)
+    for step in range(3):
+        if step:
+            h.step(0.05, g.REAL, 3)
+        q = h.bond_charges()
+        ref = wl.bond_charges(h.get_mps())
+        assert q == ref
+        assert q[0] == [0] and q[n] == [2]
+        for b in range(n + 1):
+            tab, cont = h.bond_sectors(b)
+            host = wl.sector_table(ref[b])
+            assert cont and host is not None
+            assert tab == host
+    # spin flip: local charges (-1, +1) negate every bond charge
+    assert h.bond_charges(phys=(-1, 1)) == [[-c for c in b] for b in ref]
+    h.close()
+
+
+def test_bond_charges_refuse_a_state_that_breaks_the_charge(g):
+    """A dense random MPS conserves no charge: the read-out returns TDVP_ERR_SHAPE."""
+    n = 8
+    W = wl.heisenberg_mpo(wl.chain(n))
+    h = g.GseTdvp(wl.random_mps(n, 6, 1), W, chi_max=16)
+    with pytest.raises(g.TDVPError) as ei:
+        h.bond_charges()
+    assert ei.value.status == 2
+    with pytest.raises(g.TDVPError):
+        h.bond_sectors(3)
+    h.close()
