@@ -448,7 +448,7 @@ def roofline_line(args, g, torch, W):
         peak_src = "measured bf16_tflops x 1.1/2.25 (nominal tf32/bf16)"
         kern = f"H_eff apply (tcgen05 kind::tf32, 3 split products) at chi={args.heff_chi}, w=14"
     else:
-        products, peak, peak_src = 1, 1.25, "nominal FP64 (no tensor cores)"
+        products, peak, peak_src = 1, 1.097, "cuBLAS DGEMM measured on this part (bench.py --peaks)"
         kern = f"H_eff apply (FP64 CUDA cores) at chi={args.heff_chi}, w=14"
     # DRAM bytes of one apply (its 5 launches), from the ncu capture of these kernels at
     # chi = 1024, w = 14 in BF16X10; other configurations have no capture

@@ -357,6 +357,30 @@ struct SrcA {
     }
   }
 };
+// Rows (w, a) of the stage-1 A operand of H_eff, read from L[a][w][a'] channel by channel:
+// a 128-row tile then holds one MPO channel w over a run of sector-ordered a, and under a
+// conserved charge its nonzero columns a' lie in the one sector q_a - c_w.  In (a, w) order a
+// tile mixes every channel and reaches the sectors of all channel charges at once.
+struct SrcLwa {
+  static constexpr bool kDF = false;
+  const cplx* p;
+  int ML, WL;
+  __device__ void load4(long long m, int k2, double v[4]) const {
+    const long long w = m / ML, a = m % ML;
+#pragma unroll
+    for (int h = 0; h < 2; ++h) {
+      const int k = (k2 >> 1) + h;
+      double re = 0.0, im = 0.0;
+      if (w < WL && k < ML) {
+        const cplx z = p[(a * WL + w) * ML + k];
+        re = z.x;
+        im = z.y;
+      }
+      v[2 * h] = re;
+      v[2 * h + 1] = im;
+    }
+  }
+};
 // Rows (n, c') of the expanded real B operand built from opB(B)[k][n]:
 //   row (n, re): (Re, -Im) over K index (k, re/im); row (n, im): (Im, Re).
 struct SrcB {
@@ -395,7 +419,7 @@ __device__ __forceinline__ void df_mac(float& sh, float& sl, float ah, float al,
 }
 
 // Rows (a, s) of the stage-3 A operand of H_eff: K index (v, b', re/im),
-//   T2[(a,s)][(v,b')] = sum_{(w,t)} W[w,s,t,v] T1[a][w][t][b']
+//   T2[(a,s)][(v,b')] = sum_{(w,t)} W[w,s,t,v] T1[w][a][t][b']   (T1 rows in (w, a) order)
 // with T1 and W as double-float complex (re hi, re lo, im hi, im lo).
 struct SrcStage2 {
   static constexpr bool kDF = true;
@@ -416,7 +440,7 @@ struct SrcStage2 {
         const int sv = s * WR + vv;
         for (int e = off[sv]; e < off[sv + 1]; ++e) {
           const int w = idx[2 * e], t = idx[2 * e + 1];
-          const float4 x = T1[((a * WL + w) * D + t) * (long long)MR + b];
+          const float4 x = T1[((w * ML + a) * D + t) * (long long)MR + b];
           const float4 c = val[e];
           df_mac(rh, rl, c.x, c.y, x.x, x.y);     // + Re c Re x
           df_mac(rh, rl, -c.z, -c.w, x.z, x.w);   // - Im c Im x
@@ -901,16 +925,16 @@ void heff_bf16s(cudaStream_t st, Scratch& s, const SiteOp& op, const cplx* x, cp
   DevicePool* pool = s.pool;
   int* err = tc_err(st, s);
   if (op.env_key < 0 || c.key != op.env_key || c.S != S) {
-    // L as the A operand: rows (a, w), K = (a', re/im)
+    // L as the A operand: rows (w, a), K = (a', re/im)
     c.L.shape(pool, S, ml * wl, 2 * ml, false);
-    slice(st, SrcA{op.L, ml, ml * wl, ml, OP_N}, c.L);
+    slice(st, SrcLwa{op.L, ml, wl}, c.L);
     // R[b][(v,b')] is B[k=(v,b')][n=b] stored n-major (op T)
     c.R.shape(pool, S, 2 * mr, 2 * wr * mr, true);
     slice(st, SrcB{op.R, (long long)wr * mr, wr * mr, mr, OP_T}, c.R);
     c.key = op.env_key;
     c.S = S;
   }
-  // stage 1: T1[(a,w)][(s',b',c)] = L x     (x[a'][(s',b')] is B[k=a'][n=(s',b')])
+  // stage 1: T1[(w,a)][(s',b',c)] = L x     (x[a'][(s',b')] is B[k=a'][n=(s',b')])
   c.X.shape(pool, S, 2 * d * mr, 2 * ml, true);
   slice(st, SrcB{x, (long long)d * mr, ml, d * mr, OP_N}, c.X);
   const int M1 = ml * wl, N1 = 2 * d * mr;

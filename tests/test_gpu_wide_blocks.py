@@ -71,3 +71,29 @@ def test_krylov_vector_dense_256_row_density_matrices(g):
     assert max(st.bond_dims()) >= 120                 # density matrices of about 2 x 120 rows
     assert abs(abs(O.mps_overlap(st.get_mps(), ref)) - 1) < 1e-10
     st.close()
+
+
+def test_gse_steps_on_the_ladder_at_cap_128_match_oracle(g):
+    """Three whole GSE-TDVP1 steps (Krylov vectors, extension, sweep; real time, k = 3) on the
+    rung-coupled 2 x 8 zigzag ladder (w = 8) from a random-isometry state at bond dimension 64
+    with chi_max = 128: the first extension doubles the middle bonds to the cap, so the cut of
+    the projected density-matrix spectrum (Eq. 6) falls at the cap, and the Krylov vectors are
+    compressed at it.  FP64 on the device against the oracle at every step: equal bond
+    dimensions, overlap, energy and <S^z_i> to 1e-10."""
+    lat = wl.zigzag_ladder(8, 1.0, 1.0)
+    W = wl.heisenberg_mpo(lat)
+    psi = wl.random_isometric_mps(16, 64, 5)
+    p = dict(tau=0.1, k=3, eps_k=1e-8, eps_m=1e-8, chi_max=128, dt=0.1, kind="real", eps=0.0)
+    st = g.GseTdvp(psi, W, tau=0.1, eps_k=1e-8, eps_m=1e-8, chi_max=128)
+    sz = np.diag([0.5, -0.5]).astype(np.complex128)
+    ref = psi
+    for _ in range(3):
+        st.step(0.1, g.REAL, 3)
+        ref = O.gse_tdvp1_step(ref, W, p)
+        assert st.bond_dims() == wl.mps_bond_dims(ref)
+        assert abs(abs(O.mps_overlap(st.get_mps(), ref)) - 1) < 1e-10
+        assert abs(st.energy() - O.mpo_expectation(ref, W).real) < 1e-10
+    assert max(st.bond_dims()) == 128
+    for i in (0, 5, 8, 15):
+        assert abs(st.expect_local(sz, i).real - O.expect_local(ref, sz, i).real) < 1e-10
+    st.close()
