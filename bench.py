@@ -454,9 +454,10 @@ def roofline_line(args, g, torch, W):
     # chi = 1024, w = 14 in BF16X10; other configurations have no capture
     traffic, traffic_src = None, None
     if args.precision == "bf16x10" and args.heff_chi == 1024:
-        traffic = 5.11e9
+        traffic = 5.121e9
         traffic_src = ("ncu dram__bytes_read.sum + dram__bytes_write.sum over the 5 launches of one cached "
-                       "apply (slice x, GEMM 1, MPO stage, GEMM 3 split 4 ways, split-K sum) of these kernels")
+                       "apply (slice x, GEMM 1 with L channel-major, MPO stage, GEMM 3 split 4 ways, split-K "
+                       "sum) of these kernels on dense random operands")
     elif args.precision == "bf16x6" and args.heff_chi == 1024:
         traffic = 2.599e9
         traffic_src = ("ncu dram__bytes_read.sum + dram__bytes_write.sum of the two k_gemm_bf16s<3> launches of one "
@@ -474,15 +475,20 @@ def roofline_line(args, g, torch, W):
 def u1_roofline(dense_roof, u1):
     """The roofline line of the H_eff apply on the U(1) state: achieved = flops over the nonzero
     blocks / measured time; the random dense-operand probe stays as context."""
+    u1_traffic = 2.147e9  # DRAM bytes of one apply on U(1) operands of this shape (ncu, see source)
     achieved = u1["tflops_blocks"]
     products = dense_roof["tensor_flops_per_algorithmic_flop"]
     return {"bound": "tensor", "achieved": achieved, "peak": dense_roof["peak"], "unit": "TFLOP/s",
-            "frac": achieved / dense_roof["peak"], "traffic": None,
+            "frac": achieved / dense_roof["peak"], "traffic": u1_traffic if products == 10 else None,
             "kernel": f"H_eff apply on the chi={max(u1['ml'], u1['mr'])} U(1) state (centre site, w={u1['w']}): "
                       f"slicing, tcgen05 BF16 exact-slice GEMMs ({products} products) skipping all-zero tiles, "
                       "MPO stage",
             "peak_source": dense_roof["peak_source"],
-            "traffic_source": "none taken for the tile-skipping GEMMs on this state",
+            "traffic_source": ("ncu dram__bytes_read.sum + dram__bytes_write.sum over the 5 launches of one cached "
+                               "BF16X10 apply on U(1) operands of the same shape (charges of the middle bond of a "
+                               "24-site random charge-conserving state at bond dimension 1021, the cylinder MPO's "
+                               "widest site: bench.py --heff-probe --u1), standing in for the live state"
+                               if products == 10 else "no capture for this precision form"),
             "algorithmic_flops": "over the nonzero U(1) blocks (heff_flops_u1)",
             "algorithmic_flops_per_apply": u1["flops_blocks"], "ms_per_apply": u1["ms_per_apply"],
             "tensor_flops_per_algorithmic_flop": products,
