@@ -7,6 +7,8 @@ namespace {
 const cplx kOne = {1.0, 0.0};
 const cplx kZero = {0.0, 0.0};
 constexpr double kBreakdown = 1e-13;  // Lanczos invariant-subspace threshold
+// local dimension up to which a Lanczos run may launch several iterations per host check
+constexpr long long kSpeculateMaxN = 1LL << 18;
 }  // namespace
 
 double heff_flops(const SiteOp& op) {
@@ -101,12 +103,13 @@ void LanczosWork::release() {
 
 int lanczos_expm(cudaStream_t st, DevicePool* pool, Blas1& blas, LanczosWork& lw,
                  const std::function<void(const cplx*, cplx*)>& op, const cplx* x, cplx* out, long long n,
-                 double delta, int kind, double tol, int nmax) {
+                 double delta, int kind, double tol, int nmax, int* hint) {
   nmax = std::min(std::max(1, nmax), 63);
   double* alpha = lw.real;
   double* beta = lw.real + 64;
   double* nrm2 = lw.real + 130;
   double* err = lw.real + 132;
+  double* errs = lw.real + 256;  // 2 per iteration of a speculative batch
   lw.V.ensure(pool, (size_t)(nmax + 1) * n);
   lw.w.ensure(pool, (size_t)n);
   cplx* V = lw.V.data();
@@ -122,32 +125,53 @@ int lanczos_expm(cudaStream_t st, DevicePool* pool, Blas1& blas, LanczosWork& lw
     return 0;
   }
   scale_by_inv_sqrt(st, V, x, nrm2, n);
-  int used = 0;
+  // A small local problem costs a host round trip per iteration more than its arithmetic.  With
+  // a hint, the first hint - 1 iterations go out in one batch (each next vector scaled with a
+  // guard, so an iteration after an invariant subspace only sees zeros) and their stopping
+  // tests are read together.  A run that stops inside the batch recomputes the small
+  // exponential at its stopping point (the same inputs and kernel, so the same result as
+  // stopping there) and ignores the iterations after it.
+  int batch = 1;
+  if (hint && *hint > 2 && n <= kSpeculateMaxN)
+    batch = (int)std::min<long long>({(long long)*hint - 1, (long long)nmax, n});
+  int used = 0, last = -1;
   double last_err = 0.0;
-  for (int j = 0; j < nmax; ++j) {
-    op(V + (long long)j * n, wv);
-    // alpha_j = Re <v_j, w>; w -= V (V^H w), twice (full re-orthogonalisation); beta = |w|
-    blas.lanczos_fused(st, 0, V, n, j + 1, wv, n, nullptr, lw.c.data(), alpha, j, nullptr, nullptr);
-    blas.lanczos_fused(st, 1, V, n, j + 1, wv, n, lw.c.data(), lw.c.data() + 64, nullptr, j, nullptr, nullptr);
-    blas.lanczos_fused(st, 2, V, n, j + 1, wv, n, lw.c.data() + 64, nullptr, nullptr, j, nrm2, beta + j + 1);
-    tridiag_expv(st, alpha, beta, j + 1, delta, kind, nrm2, lw.y.data(), err);
-    double h_err[2];
-    TDVP_CUDA(cudaMemcpyAsync(h_err, err, sizeof(h_err), cudaMemcpyDeviceToHost, st));
-    TDVP_CUDA(cudaStreamSynchronize(st));
-    tdvp_require(std::isfinite(h_err[0]) && std::isfinite(h_err[1]), TDVP_ERR_NONFINITE,
-                 "Lanczos: non-finite coefficient");
-    last_err = h_err[0];
-    if (h_err[0] <= tol || h_err[1] <= kBreakdown || j + 1 == n) {
-      used = j + 1;
-      break;
+  for (int j = 0; j < nmax;) {
+    const int j0 = j;
+    for (int b = 0; b < batch; ++b, ++j) {
+      if (b > 0) scale_by_inv_sqrt_guarded(st, V + (long long)j * n, wv, nrm2, n);
+      op(V + (long long)j * n, wv);
+      // alpha_j = Re <v_j, w>; w -= V (V^H w), twice (full re-orthogonalisation); beta = |w|
+      blas.lanczos_fused(st, 0, V, n, j + 1, wv, n, nullptr, lw.c.data(), alpha, j, nullptr, nullptr);
+      blas.lanczos_fused(st, 1, V, n, j + 1, wv, n, lw.c.data(), lw.c.data() + 64, nullptr, j, nullptr, nullptr);
+      blas.lanczos_fused(st, 2, V, n, j + 1, wv, n, lw.c.data() + 64, nullptr, nullptr, j, nrm2, beta + j + 1);
+      tridiag_expv(st, alpha, beta, j + 1, delta, kind, nrm2, lw.y.data(), batch > 1 ? errs + 2 * b : err);
     }
-    if (j + 1 == nmax) break;
-    scale_by_inv_sqrt(st, V + (long long)(j + 1) * n, wv, nrm2, n);
+    last = j - 1;
+    double h_err[2 * 64];
+    TDVP_CUDA(cudaMemcpyAsync(h_err, batch > 1 ? errs : err, sizeof(double) * 2 * batch, cudaMemcpyDeviceToHost,
+                              st));
+    TDVP_CUDA(cudaStreamSynchronize(st));
+    for (int b = 0; b < batch; ++b) {
+      const int jj = j0 + b;
+      tdvp_require(std::isfinite(h_err[2 * b]) && std::isfinite(h_err[2 * b + 1]), TDVP_ERR_NONFINITE,
+                   "Lanczos: non-finite coefficient");
+      last_err = h_err[2 * b];
+      if (h_err[2 * b] <= tol || h_err[2 * b + 1] <= kBreakdown || jj + 1 == n) {
+        used = jj + 1;
+        break;
+      }
+    }
+    if (used > 0 || j == nmax) break;
+    scale_by_inv_sqrt(st, V + (long long)j * n, wv, nrm2, n);
+    batch = 1;
   }
   if (used == 0)
     throw TdvpError(TDVP_ERR_LANCZOS_NOT_CONVERGED,
                     "Lanczos error estimate " + std::to_string(last_err) + " above tolerance after " +
                         std::to_string(nmax) + " steps");
+  if (used - 1 < last) tridiag_expv(st, alpha, beta, used, delta, kind, nrm2, lw.y.data(), err);
   multi_combine(st, out, V, n, used, lw.y.data(), beta0, n);
+  if (hint) *hint = used;
   return used;
 }

@@ -77,10 +77,14 @@ void env_right_fp64(cudaStream_t st, Scratch& s, const cplx* R, const WSparse& W
 // steps do not bring the error estimate below tol.
 struct LanczosWork {
   DArr V, w, c, y;
-  double* real = nullptr;  // device: alpha[64], beta[65], nrm2, err[2], scratch norms
+  double* real = nullptr;  // device: alpha[64], beta[65], nrm2, err[2], scratch norms; [256, 384):
+                           // the error estimates of each iteration of a speculative run
   void init(DevicePool* pool);
   void release();
 };
+// hint (may be null): the Krylov dimension of the previous run of the same operator kind; read
+// to launch the first iterations of a small local problem without a host round trip each,
+// and updated to this run's dimension.  Results do not depend on it.
 int lanczos_expm(cudaStream_t st, DevicePool* pool, Blas1& blas, LanczosWork& lw,
                  const std::function<void(const cplx*, cplx*)>& op, const cplx* x, cplx* out, long long n,
-                 double delta, int kind, double tol, int nmax);
+                 double delta, int kind, double tol, int nmax, int* hint = nullptr);

@@ -465,7 +465,8 @@ void Engine::canonicalize(int c) {
 // so one step may need more Krylov vectors than lanczos_max); lanczos_expm reads x before it
 // writes out, so the sub-steps run in place.
 int Engine::lanczos(const std::function<void(const cplx*, cplx*)>& op, const cplx* x, cplx* out,
-                    long long n, double delta, int kind) {
+                    long long n, double delta, int kind, int slot) {
+  int* hint = (slot >= 0 && slot < 4) ? &lanczos_hint[slot] : nullptr;
   int used = 0;
   try {
     for (int s = 1;; s *= 2) {
@@ -473,7 +474,7 @@ int Engine::lanczos(const std::function<void(const cplx*, cplx*)>& op, const cpl
         used = 0;
         for (int k = 0; k < s; ++k)
           used += lanczos_expm(st, &pool, blas, lw, op, k == 0 ? x : out, out, n, delta / s, kind, opt.lanczos_tol,
-                               opt.lanczos_max);
+                               opt.lanczos_max, hint);
         break;
       } catch (const TdvpError& e) {
         if (e.status != TDVP_ERR_LANCZOS_NOT_CONVERGED || 2 * s > 64) throw;
@@ -516,7 +517,7 @@ void Engine::sweep(double dt, int kind) {
     y.ensure(&pool, n);
     PhaseScope ps(tracer, PH_LANCZOS_SITE);
     lanczos([&](const cplx* a, cplx* b) { heff(i, a, b, prec); }, psi.A[i].data(), y.data(), n, delta,
-            kind);
+            kind, 0);
     if (imag) normalize(y.data(), n);
     TDVP_CUDA(cudaMemcpyAsync(psi.A[i].data(), y.data(), n * sizeof(cplx), cudaMemcpyDeviceToDevice, st));
   };
@@ -560,7 +561,7 @@ void Engine::sweep(double dt, int kind) {
     {
       PhaseScope ps(tracer, PH_LANCZOS_BOND);
       lanczos([&](const cplx* a, cplx* b) { keff_fp64(st, scr, Lb, r, Rb, mold, wb, a, b, prec); }, C.data(),
-              C2.data(), (long long)r * mold, -delta, kind);
+              C2.data(), (long long)r * mold, -delta, kind, 1);
     }
     if (imag) normalize(C2.data(), (long long)r * mold);
     DArr nxt(&pool, (size_t)r * d * mr2);
@@ -610,7 +611,7 @@ void Engine::sweep(double dt, int kind) {
     {
       PhaseScope ps(tracer, PH_LANCZOS_BOND);
       lanczos([&](const cplx* a, cplx* b) { keff_fp64(st, scr, Lb, mold, Rb, r, wb, a, b, prec); }, C.data(),
-              C2.data(), (long long)mold * r, -delta, kind);
+              C2.data(), (long long)mold * r, -delta, kind, 1);
     }
     if (imag) normalize(C2.data(), (long long)mold * r);
     DArr prv(&pool, (size_t)ml0 * d * r);
@@ -673,7 +674,8 @@ void Engine::sweep2(double dt, int kind) {
     const SiteOp op = pair_op(i);
     {
       PhaseScope ps(tracer, PH_LANCZOS_SITE);
-      lanczos([&](const cplx* a, cplx* b) { apply_op(op, a, b, prec); }, theta.data(), y.data(), n, delta, kind);
+      lanczos([&](const cplx* a, cplx* b) { apply_op(op, a, b, prec); }, theta.data(), y.data(), n, delta, kind,
+              2);
     }
     if (imag) normalize(y.data(), n);
     PhaseScope ps(tracer, PH_SVD);
@@ -686,7 +688,7 @@ void Engine::sweep2(double dt, int kind) {
     DArr out(&pool, n);
     {
       PhaseScope ps(tracer, PH_LANCZOS_BOND);
-      lanczos([&](const cplx* a, cplx* b) { heff(j, a, b, prec); }, C.data(), out.data(), n, -delta, kind);
+      lanczos([&](const cplx* a, cplx* b) { heff(j, a, b, prec); }, C.data(), out.data(), n, -delta, kind, 3);
     }
     if (imag) normalize(out.data(), n);
     C = std::move(out);

@@ -86,9 +86,12 @@ struct Engine {
   void move_right(int i, double eps, int cap, bool imag_trunc);
   void move_left(int i, double eps, int cap, bool imag_trunc);
   void canonicalize(int c);
-  // Lanczos exponential: out = exp(-i delta Op) x (kind 0) or exp(-delta Op) x (kind 1)
+  // Lanczos exponential: out = exp(-i delta Op) x (kind 0) or exp(-delta Op) x (kind 1).  slot
+  // (0..3, or -1 for none) names the operator kind whose previous Krylov dimension lets a small
+  // run launch several iterations per host check (site, bond, two-site, backward site)
   int lanczos(const std::function<void(const cplx*, cplx*)>& op, const cplx* x, cplx* out,
-              long long n, double delta, int kind);
+              long long n, double delta, int kind, int slot = -1);
+  int lanczos_hint[4] = {0, 0, 0, 0};
   // algorithm steps
   void sweep(double dt, int kind);
   void sweep2(double dt, int kind);  // two-site TDVP (the conventional integrator GSE-TDVP1 is compared with)

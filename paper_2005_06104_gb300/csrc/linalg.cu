@@ -472,6 +472,16 @@ __global__ void k_scale_inv_sqrt(cplx* __restrict__ dst, const cplx* __restrict_
   dst[i] = cscale(src[i], s);
 }
 
+// as k_scale_inv_sqrt, but a norm that is not a positive finite number above 1e-200 gives zeros
+__global__ void k_scale_inv_sqrt_guarded(cplx* __restrict__ dst, const cplx* __restrict__ src,
+                                         const double* __restrict__ nrm2, long long n) {
+  const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i >= n) return;
+  const double q = *nrm2;
+  const double s = (q > 1e-200 && q <= 1.7e308) ? 1.0 / sqrt(q) : 0.0;
+  dst[i] = cscale(src[i], s);
+}
+
 __global__ void k_scale_host(cplx* __restrict__ dst, const cplx* __restrict__ src, cplx s, long long n) {
   const long long i = (long long)blockIdx.x * blockDim.x + threadIdx.x;
   if (i >= n) return;
@@ -652,6 +662,12 @@ void multi_combine(cudaStream_t st, cplx* y, const cplx* V, long long ldv, int n
 void scale_by_inv_sqrt(cudaStream_t st, cplx* dst, const cplx* src, const double* nrm2, long long n) {
   if (n == 0) return;
   k_scale_inv_sqrt<<<ceil_div(n, 256), 256, 0, st>>>(dst, src, nrm2, n);
+  TDVP_CHECK_LAUNCH();
+}
+
+void scale_by_inv_sqrt_guarded(cudaStream_t st, cplx* dst, const cplx* src, const double* nrm2, long long n) {
+  if (n == 0) return;
+  k_scale_inv_sqrt_guarded<<<ceil_div(n, 256), 256, 0, st>>>(dst, src, nrm2, n);
   TDVP_CHECK_LAUNCH();
 }
 

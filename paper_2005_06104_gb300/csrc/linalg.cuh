@@ -162,6 +162,8 @@ void multi_combine(cudaStream_t st, cplx* y, const cplx* V, long long ldv, int n
 // dst = src * (1 / sqrt(*nrm2))   (nrm2 in device memory)
 void scale_by_inv_sqrt(cudaStream_t st, cplx* dst, const cplx* src, const double* nrm2,
                        long long n);
+// the same with zeros when *nrm2 is not a positive finite number above 1e-200
+void scale_by_inv_sqrt_guarded(cudaStream_t st, cplx* dst, const cplx* src, const double* nrm2, long long n);
 void scale_host(cudaStream_t st, cplx* dst, const cplx* src, cplx s, long long n);
 void fill_zero(cudaStream_t st, cplx* p, long long n);
 // Lanczos bookkeeping: alpha[j] = Re c[j]
