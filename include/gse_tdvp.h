@@ -117,9 +117,10 @@ TDVP_API tdvp_status tdvp_set_options(tdvp_handle* h, const tdvp_options* opt);
 TDVP_API const char* tdvp_last_error(const tdvp_handle* h);
 TDVP_API const char* tdvp_status_string(tdvp_status s);
 
-/* Moves the orthogonality centre to `site` by exact gauge moves (SVDs that keep
- * every singular value above 1e-10 s_max) and builds the environments L_site and
- * R_site.  The state is unchanged. */
+/* Moves the orthogonality centre to `site` by exact gauge moves (a QR / LQ per
+ * conserved-charge block when every |R_jj| exceeds 1e-10 of the largest, else an
+ * SVD keeping every singular value above 1e-10 s_max) and builds the
+ * environments L_site and R_site.  The state is unchanged. */
 TDVP_API tdvp_status tdvp_canonicalize(tdvp_handle* h, int site);
 
 /* GSE steps 1 and 2 (Sec. I.C): builds |psi~_l> = (1 - i tau H)^l |psi>,
@@ -252,7 +253,7 @@ TDVP_API tdvp_status tdvp_center(tdvp_handle* h, int* site);
  * tensors: bond 0 carries charge 0 and index r of bond i+1 gets q_l + c_s from
  * every nonzero A_i[l][s][r].  phys_charges: d host ints c_s (2 S^z = +1, -1 for
  * spin 1/2).  charges: host buffer of sum_b m_b ints (tdvp_bond_dims gives m_b).
- * Errors: INVALID_ARG (null, |c_s| >= 2^20); SHAPE when an index gets two
+ * Errors: INVALID_ARG (null, |c_s| >= 2^20, N max|c_s| >= 2^30); SHAPE when an index gets two
  * different charges (the state does not conserve the charge) or none. */
 TDVP_API tdvp_status tdvp_bond_charges(tdvp_handle* h, const int* phys_charges, int* charges);
 

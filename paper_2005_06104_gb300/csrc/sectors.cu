@@ -8,6 +8,7 @@
 // block); this file reads the charges back off that pattern, bond by bond from the left end
 // (charge 0), so that a caller can see the sector table (charge, dim, offset) of every bond.
 #include <climits>
+#include <cstdlib>
 
 #include "engine.cuh"
 
@@ -65,9 +66,15 @@ __global__ void k_charge_final(const int* __restrict__ lo, const int* __restrict
 
 std::vector<std::vector<int>> bond_charges(Engine& e, const int* phys_host) {
   const int N = e.N, d = e.d;
-  for (int s = 0; s < d; ++s)
+  long long cmax = 0;
+  for (int s = 0; s < d; ++s) {
     tdvp_require(phys_host[s] > -(1 << 20) && phys_host[s] < (1 << 20), TDVP_ERR_INVALID_ARG,
                  "bond_charges: local charges must lie within +-2^20");
+    cmax = std::max(cmax, (long long)std::abs(phys_host[s]));
+  }
+  // every bond charge is a sum of at most N local charges: keep it inside int
+  tdvp_require((long long)N * cmax < (1LL << 30), TDVP_ERR_INVALID_ARG,
+               "bond_charges: N * max |local charge| must stay below 2^30");
   int mmax = 1;
   for (int m : e.psi.m) mmax = std::max(mmax, m);
   RawBuf phys, q_in, q_out, lo, hi, flags;

@@ -476,8 +476,9 @@ class GseTdvp:
         q, dm, off = (C.c_int * max_sectors)(), (C.c_int * max_sectors)(), (C.c_int * max_sectors)()
         n, cont = C.c_int(), C.c_int()
         self._chk(_lib.tdvp_bond_sectors(self.h, ph, bond, max_sectors, q, dm, off, C.byref(n), C.byref(cont)))
-        k = min(n.value, max_sectors)
-        return [(q[i], dm[i], off[i]) for i in range(k)], bool(cont.value)
+        if n.value > max_sectors:
+            return self.bond_sectors(bond, phys, n.value)
+        return [(q[i], dm[i], off[i]) for i in range(n.value)], bool(cont.value)
 
     def center(self):
         v = C.c_int()
