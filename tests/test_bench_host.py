@@ -49,3 +49,21 @@ def test_fig3_reference_energy_matches_dense_ed(n):
     from exact import ground_energy_sz0
     ref = ground_energy_sz0(n, [(i, i + 1, 1.0) for i in range(n - 1)])
     assert abs(bench._chain_ground_energy(n) - ref) < 1e-12
+
+
+def test_u1_roofline_object_follows_the_block_count():
+    """The roofline object of the line: achieved is the H_eff flops over the nonzero blocks per
+    measured apply, frac = achieved / peak, the dense-operand probe kept beside it; job
+    throughput counts every replica's steps against the slowest rank's time."""
+    dense = {"tensor_flops_per_algorithmic_flop": 10, "peak": 1903.1, "peak_source": "measured",
+             "achieved": 106.0, "frac": 106.0 / 1903.1}
+    u1 = {"tflops_blocks": 15.0, "ml": 1024, "mr": 1020, "w": [14, 14], "flops_blocks": 2.52e10,
+          "ms_per_apply": 1.68, "gemm_chunk_pairs_multiplied": 0.216}
+    r = bench.u1_roofline(dense, u1)
+    for key in ("bound", "achieved", "peak", "unit", "frac", "traffic"):
+        assert key in r
+    assert r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
+    assert r["frac"] == pytest.approx(15.0 / 1903.1)
+    assert r["traffic"] > 0 and r["dense_operand_probe"] is dense
+    assert bench.u1_roofline(dict(dense, tensor_flops_per_algorithmic_flop=6), u1)["traffic"] is None
+    assert bench.job_throughput(4, 20, 10.0) == pytest.approx(8.0)
