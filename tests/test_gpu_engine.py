@@ -54,6 +54,28 @@ def test_create_is_exact_gauge_move(g):
     st.close()
 
 
+def test_sweep_krylov_dimensions_equal_the_oracle(g):
+    """Each local exponential stops by the same test on both sides (R11), so the Krylov
+    dimensions of a sweep, summed, and the number of exponentials equal the oracle's.  Small
+    local problems launch several Lanczos iterations per host check, guided by the previous
+    run's dimension: three sweeps in a row (the later ones with hints) keep the counts."""
+    lat = wl.zigzag_ladder(5, 1.0, 1.0)
+    W = wl.heisenberg_mpo(lat)
+    psi = O.right_canonicalize(wl.random_mps(lat.n, 10, 8))
+    psi[0] /= np.linalg.norm(psi[0])
+    st = g.GseTdvp(psi, W, eps=0.0, chi_max=64)
+    ref = psi
+    for _ in range(3):
+        stats = {}
+        st.sweep(0.1, g.REAL)
+        ref = O.tdvp1_sweep(ref, W, 0.1, "real", 0.0, 64, stats=stats)
+        nfo = st.trunc_stats()
+        assert nfo["lanczos_calls"] == len(stats["lanczos_iters"])
+        assert nfo["lanczos_iters"] == sum(stats["lanczos_iters"])
+    assert abs(abs(O.mps_overlap(st.get_mps(), ref)) - 1) < 1e-10
+    st.close()
+
+
 @pytest.mark.parametrize("kind", ["real", "imag"])
 def test_tdvp1_sweep_matches_oracle(g, kind):
     lat = wl.zigzag_ladder(5, 1.0, 1.0)
