@@ -67,3 +67,19 @@ def test_u1_roofline_object_follows_the_block_count():
     assert r["traffic"] > 0 and r["dense_operand_probe"] is dense
     assert bench.u1_roofline(dict(dense, tensor_flops_per_algorithmic_flop=6), u1)["traffic"] is None
     assert bench.job_throughput(4, 20, 10.0) == pytest.approx(8.0)
+
+
+@pytest.mark.parametrize("prec", ["bf16x10", "bf16x6", "tf32x3", "fp64"])
+def test_roofline_line_assembles_for_every_precision(monkeypatch, prec):
+    """The dense-operand roofline object (the probe's timing replaced by fixed numbers): peaks
+    and traffic sources per precision form, frac = achieved / peak."""
+    monkeypatch.setattr(bench, "heff_roofline", lambda g, torch, chi, W, p: (4.813e11, 4.5, 5.1))
+    g = argparse.Namespace(**{v: i for i, v in enumerate(bench.PRECISIONS.values())})
+    W = wl.heisenberg_mpo(wl.cylinder_snake(16, 4))
+    a = argparse.Namespace(precision=prec, heff_chi=1024)
+    r = bench.roofline_line(a, g, None, W)
+    assert r["achieved"] == pytest.approx(4.813e11 / 4.5e-3 / 1e12)
+    assert r["frac"] == pytest.approx(r["achieved"] / r["peak"])
+    assert r["bound"] == "tensor" and r["unit"] == "TFLOP/s"
+    assert (r["traffic"] is not None) == (prec in ("bf16x10", "bf16x6"))
+    assert r["tensor_flops_per_algorithmic_flop"] == {"bf16x10": 10, "bf16x6": 6, "tf32x3": 3, "fp64": 1}[prec]
