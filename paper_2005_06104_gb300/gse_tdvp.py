@@ -414,15 +414,33 @@ class GseTdvp:
         """One two-site TDVP step (TDVP2), truncating with eps and chi_max in both time kinds."""
         self._chk(_lib.tdvp_sweep2(self.h, dt, kind))
 
+    def _local_vectors(self, n, **ts):
+        """x and y of a local operator: contiguous CUDA complex128 tensors of n entries (n None:
+        the index is out of range, which the library itself refuses)."""
+        for name, t in ts.items():
+            if not (t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.complex128"):
+                raise ValueError(f"{name} must be a contiguous CUDA complex128 tensor")
+            if n is not None and t.numel() != n:
+                raise ValueError(f"{name} has {t.numel()} entries, the local space has {n}")
+
+    def _site_size(self, site):
+        if not 0 <= site < self.n:
+            return None
+        m = self.bond_dims()
+        return m[site] * self.d * m[site + 1]
+
     def heff_apply(self, site, x, y, precision=PREC_FP64):
+        self._local_vectors(self._site_size(site), x=x, y=y)
         self._chk(_lib.tdvp_heff_apply(self.h, site, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
                                        precision))
 
     def keff_apply(self, bond, x, y, precision=PREC_FP64):
+        self._local_vectors(self.bond_dims()[bond] ** 2 if 1 <= bond < self.n else None, x=x, y=y)
         self._chk(_lib.tdvp_keff_apply(self.h, bond, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
                                        precision))
 
     def evolve_site(self, site, x, y, delta, kind=REAL, precision=PREC_FP64):
+        self._local_vectors(self._site_size(site), x=x, y=y)
         it = C.c_int(0)
         self._chk(_lib.tdvp_evolve_site(self.h, site, C.c_void_p(x.data_ptr()), C.c_void_p(y.data_ptr()),
                                         delta, kind, precision, C.byref(it)))

@@ -97,3 +97,22 @@ def test_contract_wrappers_check_operands_before_the_call():
             fn(L, np.zeros((wl_ + 1, d, d, wr), complex), R, x, y)
         with pytest.raises(ValueError, match="expected"):
             fn(L, W, R, torch.zeros((5, d, 7), dtype=torch.complex128), y)
+
+
+def test_binding_refuses_bad_local_vectors_before_the_library():
+    """The handle methods that take caller device vectors check placement, dtype, layout and
+    the local-space size before any pointer reaches the library (a host tensor, a wrong dtype
+    or a wrong size is refused here)."""
+    torch = pytest.importorskip("torch")
+    from paper_2005_06104_gb300 import gse_tdvp as g
+    h = g.GseTdvp.__new__(g.GseTdvp)
+    h.n, h.d = 3, 2
+    h.bond_dims = lambda: [1, 2, 3, 1]
+    assert h._site_size(0) == 4 and h._site_size(1) == 12 and h._site_size(2) == 6
+    assert h._site_size(3) is None and h._site_size(-1) is None
+    with pytest.raises(ValueError, match="CUDA complex128"):
+        h.heff_apply(1, torch.zeros(12, dtype=torch.complex128), torch.zeros(12, dtype=torch.complex128))
+    with pytest.raises(ValueError, match="CUDA complex128"):
+        h.keff_apply(1, torch.zeros(4, dtype=torch.float64), torch.zeros(4, dtype=torch.float64))
+    with pytest.raises(ValueError, match="CUDA complex128"):
+        h.evolve_site(0, torch.zeros(4, dtype=torch.complex64), torch.zeros(4, dtype=torch.complex64), 0.1)
