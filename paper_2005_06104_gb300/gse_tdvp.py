@@ -188,25 +188,44 @@ def heff_contract(L, W, R, x, y, precision=PREC_FP64, stream=None, env_tag=None)
                                                 int(env_tag), _stream(stream)))
 
 
+def _check_dev(**ts):
+    """name=(tensor, expected shape): contiguous CUDA complex128 tensors of those shapes."""
+    for name, (t, shape) in ts.items():
+        if tuple(t.shape) != tuple(shape):
+            raise ValueError(f"{name} has shape {tuple(t.shape)}, expected {tuple(shape)}")
+        if not (t.is_cuda and t.is_contiguous() and str(t.dtype) == "torch.complex128"):
+            raise ValueError(f"{name} must be a contiguous CUDA complex128 tensor")
+
+
 def keff_contract(L, R, x, y, stream=None):
+    """y[a, c] = sum L[a, w, a'] x[a', b'] R[c, w, b'] on caller tensors: L [ml, w, ml],
+    R [mr, w, mr], x and y [ml, mr] (CUDA complex128)."""
     ml, w, _ = L.shape
     mr = R.shape[0]
+    _check_dev(L=(L, (ml, w, ml)), R=(R, (mr, w, mr)), x=(x, (ml, mr)), y=(y, (ml, mr)))
     _raw_chk(_lib.tdvp_keff_contract(ml, mr, w, _ptr(L), _ptr(R), _ptr(x), _ptr(y), _stream(stream)))
 
 
 def env_contract(side, E, W, A, out, stream=None):
-    """side 0: left environment update through site A; side 1: right environment update."""
+    """side 0: left environment update through site A (E = L [ml, wl, ml] -> out [mr, wr, mr]);
+    side 1: right environment update (E = R [mr, wr, mr] -> out [ml, wl, ml]).  A [ml, d, mr],
+    W host [wl, d, d, wr]."""
     ml, d, mr = A.shape
     wl, wr = W.shape[0], W.shape[3]
+    if W.shape != (wl, d, d, wr):
+        raise ValueError(f"env_contract: W {W.shape} does not fit A {tuple(A.shape)}")
+    if side in (0, 1):
+        e_shape, o_shape = ((ml, wl, ml), (mr, wr, mr)) if side == 0 else ((mr, wr, mr), (ml, wl, ml))
+        _check_dev(E=(E, e_shape), A=(A, (ml, d, mr)), out=(out, o_shape))
     Wc, wp = _host(W)
     _raw_chk(_lib.tdvp_env_contract(C.byref(SiteDims(ml, mr, wl, wr, d)), side, _ptr(E), wp, _ptr(A), _ptr(out),
                                     _stream(stream)))
 
 
 def expm_contract(L, W, R, x, y, delta, kind=REAL, precision=PREC_FP64, tol=1e-12, nmax=40, stream=None):
-    ml, wl, _ = L.shape
-    mr, wr, _ = R.shape
-    d = W.shape[1]
+    """y = exp(-i delta H_eff) x (REAL) or exp(-delta H_eff) x (IMAG) on caller tensors, shapes as
+    heff_contract; returns the Krylov dimension used."""
+    ml, mr, wl, wr, d = _check_site_args(L, W, R, x, y)
     Wc, wp = _host(W)
     it = C.c_int(0)
     _raw_chk(_lib.tdvp_expm_contract(C.byref(SiteDims(ml, mr, wl, wr, d)), _ptr(L), wp, _ptr(R), _ptr(x), _ptr(y),
