@@ -5,7 +5,9 @@ paper's statements.  This checks that the pins can see the mistakes they are the
   * the Krylov operator of Eq. 10 built with the wrong sign of tau;
   * the backward bond step of the TDVP1 sweep (Sec. I.C step 3) with the wrong sign;
   * the full time step on each half-sweep instead of half of it (reading R4);
-  * the weights of Eq. 5 ignored in the state-averaged density matrix.
+  * the weights of Eq. 5 ignored in the state-averaged density matrix;
+  * the last Krylov vector left out of Eq. 5's sum;
+  * the Lanczos stopping tolerance (R11) not honoured.
 """
 import pytest
 
@@ -48,3 +50,18 @@ def test_weights_of_eq5_ignored(monkeypatch):
     monkeypatch.setattr(oracle, "basis_extension",
                         lambda psi, phis, weights=None, *a, **k: orig(psi, phis, None, *a, **k))
     _fails(M.test_extension_weights, 1e-3)
+
+
+def test_last_krylov_vector_left_out_of_the_extension(monkeypatch):
+    """An off-by-one over l = 1..k-1 in Eq. 5 (the last vector dropped from rho~)."""
+    orig = G.basis_extension
+    monkeypatch.setattr(oracle, "basis_extension", lambda psi, phis, *a, **k: orig(psi, phis[:-1], *a, **k))
+    _fails(M.test_extension_spans_krylov_vectors)
+
+
+def test_lanczos_stopping_tolerance_not_honoured(monkeypatch):
+    import test_oracle_pins as P
+    orig = G.lanczos_expm
+    monkeypatch.setattr(oracle, "lanczos_expm",
+                        lambda f, x, delta, kind, tol=1e-12, nmax=40: orig(f, x, delta, kind, 1e-5, nmax))
+    _fails(P.test_lanczos_matches_expm, "real")
